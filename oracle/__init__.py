@@ -1,0 +1,253 @@
+"""CPU FP64 oracle for the H-MLE log-likelihood -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The GPU product path
+(``paper_2104_07146_gb300``) never imports it and shares no code with it.
+
+What it computes (the exact, dense definitions the H-matrix method
+approximates):
+
+* ``matern_matrix`` -- C(theta) of Eq. 2 (Sec. 1): C_ij = sigma^2 M_nu(h/ell)
+  + tau^2 [i == j], M_nu(x) = x^nu K_nu(x) / (2^(nu-1) Gamma(nu)).
+* ``loglik_dense`` -- Eq. 1 (Sec. 1):
+  L = -n/2 log(2 pi) - 1/2 log|C| - 1/2 Z^T C^{-1} Z, with log|C| =
+  2 sum log L_ii (Sec. 2, "Storage and complexity") and
+  Z^T C^{-1} Z = |L^{-1} Z|^2.
+* ``transform`` / ``untransform`` -- the positivity transform of Sec. 5
+  (Test 1a): sigma = 2 / 1.1^s0, ell = 1 / 1.5^l0, nu = 1 / 1.2^n0,
+  tau = 1 / 2^t0.
+* ``nelder_mead`` -- the MLE driver (Sec. 2, "Maximization of the
+  log-likelihood"; threshold 1e-4 and at most 400 iterations).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hmle_oracle.c")
+_LIB = os.path.join(_HERE, "libhmle_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C part of the oracle (gcc, -O2, OpenMP) in-tree."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(
+            ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        d, i64, i32, p = ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+        lib.oracle_besselk_scaled.argtypes = [d, d]
+        lib.oracle_besselk_scaled.restype = d
+        lib.oracle_matern_unit.argtypes = [d, d]
+        lib.oracle_matern_unit.restype = d
+        lib.oracle_matern_matrix.argtypes = [i64, i32, p, d, d, d, d, p]
+        lib.oracle_matern_matrix.restype = i32
+        lib.oracle_matern_cross.argtypes = [i64, i64, i32, p, p, d, d, d, p]
+        lib.oracle_matern_cross.restype = i32
+        lib.oracle_forward_solve.argtypes = [i64, p, p, p]
+        lib.oracle_forward_solve.restype = i32
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def besselk(nu: float, x: float) -> float:
+    """K_nu(x) for x > 0 (integral representation, trapezoid rule)."""
+    return _load().oracle_besselk_scaled(float(nu), float(x)) * math.exp(-float(x))
+
+
+def besselk_scaled(nu: float, x: float) -> float:
+    """e^x K_nu(x) for x > 0."""
+    return _load().oracle_besselk_scaled(float(nu), float(x))
+
+
+def matern_unit(nu: float, x: float) -> float:
+    """M_nu(x) = x^nu K_nu(x) / (2^(nu-1) Gamma(nu)), M_nu(0) = 1."""
+    return _load().oracle_matern_unit(float(nu), float(x))
+
+
+def matern_matrix(locs: np.ndarray, theta) -> np.ndarray:
+    """Dense C(theta) of Eq. 2; theta = (ell, nu, sigma2, tau2)."""
+    locs = np.ascontiguousarray(locs, dtype=np.float64)
+    n, d = locs.shape
+    ell, nu, s2, t2 = (float(v) for v in theta)
+    C = np.empty((n, n), dtype=np.float64)
+    rc = _load().oracle_matern_matrix(n, d, _ptr(locs), ell, nu, s2, t2, _ptr(C))
+    if rc != 0:
+        raise ValueError("oracle_matern_matrix: invalid arguments")
+    return C
+
+
+def matern_cross(A: np.ndarray, B: np.ndarray, theta) -> np.ndarray:
+    """Cross-covariance sigma^2 M_nu(|a_i - b_j| / ell), no nugget."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    ell, nu, s2, _ = (float(v) for v in theta)
+    out = np.empty((A.shape[0], B.shape[0]), dtype=np.float64)
+    rc = _load().oracle_matern_cross(A.shape[0], B.shape[0], A.shape[1], _ptr(A),
+                                     _ptr(B), ell, nu, s2, _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_matern_cross: invalid arguments")
+    return out
+
+
+def forward_solve(L: np.ndarray, z: np.ndarray) -> np.ndarray:
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    w = np.empty_like(z)
+    if _load().oracle_forward_solve(L.shape[0], _ptr(L), _ptr(z), _ptr(w)) != 0:
+        raise np.linalg.LinAlgError("non-positive pivot in forward solve")
+    return w
+
+
+def cholesky(C: np.ndarray) -> np.ndarray:
+    """Dense Cholesky factor (LAPACK dpotrf through numpy); raises
+    numpy.linalg.LinAlgError when C is not positive definite."""
+    return np.linalg.cholesky(C)
+
+
+def loglik_from_matrix(C: np.ndarray, Z: np.ndarray):
+    """(L, log|C|, Z^T C^{-1} Z) of Eq. 1 for a given dense SPD C."""
+    n = C.shape[0]
+    L = cholesky(C)
+    logdet = 0.0
+    for v in np.diag(L):           # sequential sum in index order
+        logdet += 2.0 * math.log(v)
+    w = forward_solve(L, np.asarray(Z, dtype=np.float64))
+    q = 0.0
+    for v in w:
+        q += v * v
+    ll = -0.5 * n * math.log(2.0 * math.pi) - 0.5 * logdet - 0.5 * q
+    return ll, logdet, q
+
+
+def loglik_dense(locs: np.ndarray, Z: np.ndarray, theta):
+    """Exact Eq. 1 with C from Eq. 2.  Returns (L, log|C|, q)."""
+    return loglik_from_matrix(matern_matrix(locs, theta), Z)
+
+
+def simulate(locs: np.ndarray, theta, xi: np.ndarray) -> np.ndarray:
+    """Z = L xi with L the dense Cholesky factor of C(theta)."""
+    return cholesky(matern_matrix(locs, theta)) @ np.asarray(xi, dtype=np.float64)
+
+
+# --- positivity transform of Sec. 5 (Test 1a) ---------------------------------
+
+def transform(x):
+    """Transformed coordinates (s0, l0, n0, t0) -> theta (ell, nu, sigma2, tau2).
+
+    sigma = 2 / 1.1^s0, ell = 1 / 1.5^l0, nu = 1 / 1.2^n0, tau = 1 / 2^t0.
+    """
+    s0, l0, n0, t0 = (float(v) for v in x)
+    sigma = 2.0 / 1.1 ** s0
+    ell = 1.0 / 1.5 ** l0
+    nu = 1.0 / 1.2 ** n0
+    tau = 1.0 / 2.0 ** t0
+    return (ell, nu, sigma * sigma, tau * tau)
+
+
+def untransform(theta):
+    """theta (ell, nu, sigma2, tau2) -> (s0, l0, n0, t0), the exact inverse."""
+    ell, nu, s2, t2 = (float(v) for v in theta)
+    s0 = -math.log(math.sqrt(s2) / 2.0) / math.log(1.1)
+    l0 = -math.log(ell) / math.log(1.5)
+    n0 = -math.log(nu) / math.log(1.2)
+    t0 = -math.log(math.sqrt(t2)) / math.log(2.0)
+    return (s0, l0, n0, t0)
+
+
+# --- Nelder-Mead ---------------------------------------------------------------
+
+def nelder_mead(f, x0, step=1.0, ftol=1e-4, xtol=1e-4, max_iter=400):
+    """Minimise f by the Nelder-Mead simplex method (reflection 1, expansion 2,
+    contraction 1/2, shrink 1/2; Lagarias et al. 1998 ordering rules).
+
+    The initial simplex is x0 plus ``step`` (scalar or per-coordinate) along
+    each axis.  Stops when max_i |f_i - f_best| <= ftol and
+    max_i |x_i - x_best|_inf <= xtol, or after ``max_iter`` iterations.
+    Equal f values keep their previous order (stable sort), so the run is
+    deterministic.  Returns (x_best, f_best, iterations, evaluations).
+    """
+    x0 = np.asarray(x0, dtype=np.float64)
+    m = x0.size
+    steps = np.broadcast_to(np.asarray(step, dtype=np.float64), (m,))
+    simplex = [x0.copy()]
+    for i in range(m):
+        v = x0.copy()
+        v[i] += steps[i]
+        simplex.append(v)
+    fvals = [f(v) for v in simplex]
+    nev = m + 1
+    it = 0
+    while True:
+        order = sorted(range(m + 1), key=lambda i: fvals[i])
+        simplex = [simplex[i] for i in order]
+        fvals = [fvals[i] for i in order]
+        fspread = max(abs(fv - fvals[0]) for fv in fvals[1:])
+        xspread = max(float(np.max(np.abs(v - simplex[0]))) for v in simplex[1:])
+        if (fspread <= ftol and xspread <= xtol) or it >= max_iter:
+            break
+        it += 1
+        centroid = sum(simplex[:-1]) / m
+        worst = simplex[-1]
+        xr = centroid + (centroid - worst)
+        fr = f(xr); nev += 1
+        if fvals[0] <= fr < fvals[-2]:
+            simplex[-1], fvals[-1] = xr, fr
+            continue
+        if fr < fvals[0]:
+            xe = centroid + 2.0 * (centroid - worst)
+            fe = f(xe); nev += 1
+            if fe < fr:
+                simplex[-1], fvals[-1] = xe, fe
+            else:
+                simplex[-1], fvals[-1] = xr, fr
+            continue
+        if fr < fvals[-1]:          # outside contraction
+            xc = centroid + 0.5 * (xr - centroid)
+            fc = f(xc); nev += 1
+            if fc <= fr:
+                simplex[-1], fvals[-1] = xc, fc
+                continue
+        else:                       # inside contraction
+            xc = centroid + 0.5 * (worst - centroid)
+            fc = f(xc); nev += 1
+            if fc < fvals[-1]:
+                simplex[-1], fvals[-1] = xc, fc
+                continue
+        best = simplex[0]           # shrink towards the best vertex
+        for i in range(1, m + 1):
+            simplex[i] = best + 0.5 * (simplex[i] - best)
+            fvals[i] = f(simplex[i]); nev += 1
+    return simplex[0], fvals[0], it, nev
+
+
+def fit(locs, Z, theta0, step=1.0, ftol=1e-4, xtol=1e-4, max_iter=400):
+    """MLE: maximise Eq. 1 over theta by Nelder-Mead in the transformed
+    coordinates of Sec. 5.  Non-SPD trial points score -inf.
+    Returns (theta_hat, L_hat, iterations, evaluations)."""
+
+    def negll(x):
+        try:
+            return -loglik_dense(locs, Z, transform(x))[0]
+        except np.linalg.LinAlgError:
+            return math.inf
+
+    xb, fb, it, nev = nelder_mead(negll, untransform(theta0), step, ftol, xtol, max_iter)
+    return transform(xb), -fb, it, nev

@@ -1,0 +1,278 @@
+"""Pins of the CPU oracle against facts fixed by mathematics and the paper.
+
+None of these re-derive the oracle's own formula: closed forms of
+half-integer Bessel functions, the recurrence and Wronskian of K_nu, brute
+force determinants, the exact O(n) likelihood of the exponential kernel on a
+line (Kalman filter), invariances of Eq. 1, and Nelder-Mead on functions
+with known minima.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_07146_gb300 import synth
+
+XS = np.logspace(-6, 2.5, 41)
+HALF_PI = math.pi / 2.0
+
+
+# --- K_nu and the Matern function (Eq. 2) ------------------------------------
+
+@pytest.mark.parametrize("nu,poly", [
+    (0.5, lambda x: 1.0),
+    (1.5, lambda x: 1.0 + 1.0 / x),
+    (2.5, lambda x: 1.0 + 3.0 / x + 3.0 / (x * x)),
+])
+def test_besselk_half_integer_closed_forms(nu, poly):
+    # K_{n+1/2}(x) = sqrt(pi/(2x)) e^{-x} * (finite polynomial in 1/x)
+    for x in XS:
+        ref = math.sqrt(HALF_PI / x) * poly(x)          # e^x K_nu(x)
+        got = oracle.besselk_scaled(nu, x)
+        assert abs(got - ref) <= 1e-13 * ref, (nu, x, got, ref)
+
+
+@pytest.mark.parametrize("nu,f", [
+    (0.5, lambda x: math.exp(-x)),
+    (1.5, lambda x: (1.0 + x) * math.exp(-x)),
+    (2.5, lambda x: (1.0 + x + x * x / 3.0) * math.exp(-x)),
+])
+def test_matern_half_integer_closed_forms(nu, f):
+    for x in np.concatenate([XS, [0.0]]):
+        ref = f(x)
+        got = oracle.matern_unit(nu, x)
+        assert abs(got - ref) <= 1e-13 * max(ref, 1e-300) + 1e-300, (nu, x, got, ref)
+
+
+@pytest.mark.parametrize("nu", [0.3, 0.8, 1.3, 2.2])
+def test_besselk_recurrence(nu):
+    # K_{nu+1}(x) = K_{nu-1}(x) + (2 nu / x) K_nu(x), with K_{-mu} = K_mu
+    for x in np.logspace(-3, 2, 21):
+        lhs = oracle.besselk_scaled(nu + 1, x)
+        rhs = oracle.besselk_scaled(abs(nu - 1), x) + 2 * nu / x * oracle.besselk_scaled(nu, x)
+        assert abs(lhs - rhs) <= 1e-13 * lhs, (nu, x)
+
+
+def _besseli(nu, x, terms=200):
+    s, k = 0.0, 0
+    while k < terms:
+        s += math.exp((2 * k + nu) * math.log(x / 2) - math.lgamma(k + 1) - math.lgamma(k + nu + 1))
+        k += 1
+    return s
+
+
+@pytest.mark.parametrize("nu", [0.3, 0.75, 1.6, 2.4])
+def test_besselk_wronskian(nu):
+    # I_nu K_{nu+1} + I_{nu+1} K_nu = 1/x  (power series for I in the test)
+    for x in [0.05, 0.3, 1.0, 3.0, 8.0, 15.0]:
+        k0 = oracle.besselk(nu, x)
+        k1 = oracle.besselk(nu + 1, x)
+        w = _besseli(nu, x) * k1 + _besseli(nu + 1, x) * k0
+        assert abs(w * x - 1.0) <= 1e-12, (nu, x, w * x)
+
+
+@pytest.mark.parametrize("nu", [0.3, 0.5, 1.0, 2.5])
+def test_matern_origin_limit(nu):
+    # x^nu K_nu(x) -> 2^(nu-1) Gamma(nu): M_nu(x) -> 1 continuously at 0
+    assert oracle.matern_unit(nu, 0.0) == 1.0
+    assert abs(oracle.matern_unit(nu, 1e-14) - 1.0) < 1e-6
+    vals = [oracle.matern_unit(nu, x) for x in np.logspace(-4, 1.5, 30)]
+    assert all(a > b for a, b in zip(vals, vals[1:]))          # strictly decreasing
+
+
+def test_besselk_against_library():
+    special = pytest.importorskip("scipy.special")
+    rng = np.random.default_rng(7)
+    for _ in range(60):
+        nu = rng.uniform(0.3, 2.5)
+        x = 10 ** rng.uniform(-4, 2)
+        ref = special.kve(nu, x)
+        assert abs(oracle.besselk_scaled(nu, x) - ref) <= 1e-12 * ref
+
+
+# --- dense log-likelihood (Eq. 1) -------------------------------------------
+
+LOG2PI = math.log(2.0 * math.pi)
+
+
+def test_loglik_nugget_only_closed_form():
+    # sigma^2 = 0: C = tau^2 I, L = -n/2 log 2pi - n/2 log tau^2 - Z.Z/(2 tau^2)
+    n = 60
+    locs = synth.locations_uniform(n, 2, seed=3)
+    Z = synth.normal(4, n)
+    t2 = 0.37
+    ll, logdet, q = oracle.loglik_dense(locs, Z, (0.1, 0.7, 0.0, t2))
+    ref = -0.5 * n * LOG2PI - 0.5 * n * math.log(t2) - float(Z @ Z) / (2 * t2)
+    assert abs(ll - ref) <= 1e-12 * abs(ref)
+    assert abs(logdet - n * math.log(t2)) <= 1e-12 * n
+
+
+def _leibniz_det(A):
+    n = A.shape[0]
+    tot = 0.0
+    for p in itertools.permutations(range(n)):
+        inv = sum(1 for i in range(n) for j in range(i + 1, n) if p[i] > p[j])
+        prod = 1.0
+        for i in range(n):
+            prod *= A[i, p[i]]
+        tot += -prod if inv % 2 else prod
+    return tot
+
+
+@pytest.mark.parametrize("n,theta", [(3, (0.3, 0.9, 1.2, 0.05)), (8, (0.2, 1.7, 0.8, 0.01))])
+def test_loglik_brute_force(n, theta):
+    locs = synth.locations_uniform(n, 2, seed=10 + n)
+    Z = synth.normal(20 + n, n)
+    C = oracle.matern_matrix(locs, theta)
+    det = _leibniz_det(C)
+    # Cramer's rule: x_i = det(C with column i replaced by Z) / det(C)
+    x = np.empty(n)
+    for i in range(n):
+        Ci = C.copy()
+        Ci[:, i] = Z
+        x[i] = _leibniz_det(Ci) / det
+    ref = -0.5 * n * LOG2PI - 0.5 * math.log(det) - 0.5 * float(Z @ x)
+    ll, logdet, q = oracle.loglik_dense(locs, Z, theta)
+    assert abs(logdet - math.log(det)) <= 1e-10 * max(1.0, abs(logdet))
+    assert abs(q - float(Z @ x)) <= 1e-9 * abs(q)
+    assert abs(ll - ref) <= 1e-10 * abs(ref)
+
+
+def test_loglik_scaling_invariant():
+    # C(c sigma2, c tau2) = c C  =>  logdet += n log c, q /= c
+    n = 300
+    locs = synth.locations_uniform(n, 2, seed=5)
+    Z = synth.normal(6, n)
+    th = (0.15, 1.2, 1.3, 0.02)
+    c = 3.7
+    ll, ld, q = oracle.loglik_dense(locs, Z, th)
+    ll2, ld2, q2 = oracle.loglik_dense(locs, Z, (th[0], th[1], c * th[2], c * th[3]))
+    assert abs(ld2 - (ld + n * math.log(c))) <= 1e-11 * n
+    assert abs(q2 - q / c) <= 1e-11 * q
+    assert abs(ll2 - (ll - 0.5 * n * math.log(c) - 0.5 * q * (1 / c - 1))) <= 1e-10 * abs(ll)
+
+
+def test_loglik_permutation_invariant():
+    n = 400
+    locs = synth.locations_uniform(n, 2, seed=8)
+    Z = synth.normal(9, n)
+    th = (0.1, 0.8, 1.0, 0.01)
+    p = np.argsort(synth.uniform(11, n))
+    a = oracle.loglik_dense(locs, Z, th)
+    b = oracle.loglik_dense(locs[p], Z[p], th)
+    for u, v in zip(a, b):
+        assert abs(u - v) <= 1e-10 * max(1.0, abs(u))
+
+
+def _kalman_ou_loglik(x, z, ell, s2, t2):
+    """Exact L for C_ij = s2 exp(-|x_i - x_j|/ell) + t2 [i==j] on sorted x:
+    the exponential kernel is an Ornstein-Uhlenbeck process, so the
+    prediction-error decomposition of a scalar Kalman filter gives Eq. 1."""
+    m, P = 0.0, s2                       # prior of the latent state at x_0
+    ll = 0.0
+    for i in range(len(x)):
+        if i > 0:
+            rho = math.exp(-(x[i] - x[i - 1]) / ell)
+            m, P = rho * m, rho * rho * P + s2 * (1 - rho * rho)
+        S = P + t2
+        e = z[i] - m
+        ll += -0.5 * (LOG2PI + math.log(S) + e * e / S)
+        K = P / S
+        m, P = m + K * e, (1 - K) * P
+    return ll
+
+
+@pytest.mark.parametrize("t2", [0.0, 1e-3, 0.05])
+def test_loglik_exponential_on_a_line_matches_kalman(t2):
+    n = 700
+    locs = synth.locations_collinear(n, seed=12)
+    Z = synth.normal(13, n)
+    ell, s2 = 0.07, 1.4
+    ll, _, _ = oracle.loglik_dense(locs, Z, (ell, 0.5, s2, t2))
+    ref = _kalman_ou_loglik(locs[:, 0], Z, ell, s2, t2)
+    assert abs(ll - ref) <= 1e-9 * abs(ref), (ll, ref)
+
+
+def test_loglik_tiny_range_is_white_noise():
+    # ell -> 0 with distinct points: C -> (sigma2 + tau2) I
+    n = 200
+    locs = synth.locations_uniform(n, 2, seed=14)
+    Z = synth.normal(15, n)
+    s2, t2 = 0.8, 0.2
+    ll, _, _ = oracle.loglik_dense(locs, Z, (1e-9, 1.0, s2, t2))
+    v = s2 + t2
+    ref = -0.5 * n * LOG2PI - 0.5 * n * math.log(v) - float(Z @ Z) / (2 * v)
+    assert abs(ll - ref) <= 1e-12 * abs(ref)
+
+
+def test_loglik_rejects_non_spd():
+    # two coincident points with tau2 = 0 make C singular
+    locs = np.array([[0.2, 0.3], [0.2, 0.3], [0.7, 0.1]])
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.loglik_dense(locs, np.ones(3), (0.3, 0.5, 1.0, 0.0))
+
+
+def test_simulated_field_quadratic_form_is_chi2():
+    # Z = L xi  =>  Z^T C^{-1} Z = |xi|^2 ~ chi^2_n
+    n = 1500
+    locs = synth.locations_uniform(n, 2, seed=16)
+    th = (0.1, 0.5, 1.0, 0.01)
+    xi = synth.normal(17, n)
+    Z = oracle.simulate(locs, th, xi)
+    _, _, q = oracle.loglik_dense(locs, Z, th)
+    assert abs(q - float(xi @ xi)) <= 1e-8 * q
+    assert abs(q / n - 1.0) <= 5 * math.sqrt(2.0 / n)
+
+
+# --- transform and Nelder-Mead ----------------------------------------------
+
+def test_transform_golden_start_point():
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "transform_start.json")))
+    ell, nu, s2, t2 = oracle.transform(g["x0"])
+    assert abs(math.sqrt(s2) - g["sigma"]) <= 1e-15
+    assert abs(ell - g["ell"]) <= 1e-15
+    assert abs(nu - g["nu"]) <= 1e-15
+    assert abs(math.sqrt(t2) - g["tau"]) <= 1e-20
+
+
+def test_transform_roundtrip():
+    for th in [(0.2, 1.0, 0.5, 0.05), (0.01, 2.4, 3.0, 1e-9), (0.5, 0.31, 0.1, 0.3)]:
+        back = oracle.transform(oracle.untransform(th))
+        for a, b in zip(th, back):
+            assert abs(a - b) <= 1e-13 * a
+
+
+def test_nelder_mead_quadratic():
+    c = np.array([1.0, -2.0, 0.5, 3.0])
+    w = np.array([1.0, 4.0, 0.5, 2.0])
+    f = lambda x: float(np.sum(w * (x - c) ** 2))
+    x, fx, it, nev = oracle.nelder_mead(f, np.zeros(4), 1.0, 1e-14, 1e-8, 5000)
+    assert np.max(np.abs(x - c)) < 1e-6 and fx < 1e-12
+
+
+def test_nelder_mead_rosenbrock():
+    f = lambda x: 100.0 * (x[1] - x[0] ** 2) ** 2 + (1 - x[0]) ** 2
+    x, fx, it, nev = oracle.nelder_mead(f, np.array([-1.2, 1.0]), 0.5, 1e-14, 1e-10, 5000)
+    assert np.max(np.abs(x - 1.0)) < 1e-5
+
+
+def test_nelder_mead_iteration_cap():
+    f = lambda x: float(np.sum(x ** 2))
+    _, _, it, _ = oracle.nelder_mead(f, np.full(3, 50.0), 1.0, 0.0, 0.0, 17)
+    assert it == 17
+
+
+@pytest.mark.slow
+def test_fit_recovers_simulated_theta():
+    n = 500
+    locs = synth.locations_uniform(n, 2, seed=18)
+    th = (0.1, 0.5, 1.0, 0.01)
+    Z = oracle.simulate(locs, th, synth.normal(19, n))
+    th_hat, ll_hat, it, nev = oracle.fit(locs, Z, (0.2, 1.0, 0.5, 0.05), max_iter=400)
+    ll_true = oracle.loglik_dense(locs, Z, th)[0]
+    assert ll_hat >= ll_true - 1e-3          # the MLE is at least as likely as the truth
+    assert 0.03 < th_hat[0] < 0.3 and 0.2 < th_hat[1] < 1.2 and 0.3 < th_hat[2] < 3.0
