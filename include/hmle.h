@@ -1,0 +1,221 @@
+/*
+ * hmle.h -- C ABI of the GB300-native H-MLE library (libhmle.so).
+ *
+ * The library evaluates the Gaussian log-likelihood of Eq. 1 (Sec. 1),
+ *
+ *     L(theta) = -n/2 log(2 pi) - 1/2 log|C(theta)| - 1/2 Z^T C(theta)^{-1} Z,
+ *
+ * for the Matern covariance of Eq. 2 (Sec. 1),
+ *
+ *     C(h; theta) = sigma^2 / (2^(nu-1) Gamma(nu)) (h/ell)^nu K_nu(h/ell) + tau^2 I,
+ *
+ * with C(theta) held as a hierarchical matrix (Sec. 2): a cluster tree and a
+ * block tree partition C into admissible blocks, approximated by low-rank
+ * factors built on the fly, and inadmissible leaf blocks kept dense.  The
+ * H-Cholesky factor C ~= L L^T gives log|C| = 2 sum log L_ii and
+ * Z^T C^{-1} Z = |L^{-1} Z|^2 (Sec. 2, "Storage and complexity").  The
+ * maximum-likelihood estimate maximises L over theta (Sec. 2,
+ * "Maximization of the log-likelihood"; positivity transform of Sec. 5).
+ *
+ * Every numerical step runs in CUDA kernels on the current device; the host
+ * only plans (θ-independent schedules), launches and runs the optimiser's
+ * 4-dimensional simplex bookkeeping.
+ *
+ * Conventions
+ *  - All functions return an hmle_status and never abort.  On failure the
+ *    context keeps a message, readable with hmle_last_error().
+ *  - Pointers to caller data may be host or CUDA device memory; the kind is
+ *    detected with cudaPointerGetAttributes.  The caller keeps ownership of
+ *    every array it passes; the library copies what it keeps.
+ *  - Handles (hmle_ctx, hmle_tree, hmle_hmatrix, hmle_hfactor) are owned by
+ *    the library and released with the matching *_destroy call.  A handle
+ *    must not be used concurrently from two host threads.
+ *  - theta is passed by name, in the order (ell, nu, sigma2, tau2).
+ *  - Z is always given in the caller's point order; the internal cluster
+ *    permutation never leaks out.
+ */
+#ifndef HMLE_H
+#define HMLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HMLE_OK = 0,
+  HMLE_ERR_INVALID_ARG = 1,    /* bad size, NULL, non-finite or out-of-range value */
+  HMLE_ERR_NOT_SPD = 2,        /* a non-positive pivot in a diagonal leaf factorisation */
+  HMLE_ERR_OOM = 3,            /* device or host allocation failed */
+  HMLE_ERR_CUDA = 4,           /* a CUDA runtime call failed (message has the detail) */
+  HMLE_ERR_RANK_OVERFLOW = 5,  /* a low-rank block needed more than max_rank terms */
+  HMLE_ERR_TIMEOUT = 6,        /* a bounded device wait ran out */
+  HMLE_ERR_NOT_CONVERGED = 7,  /* hmle_fit hit max_iter before its tolerance */
+  HMLE_ERR_NOT_IMPLEMENTED = 8
+} hmle_status;
+
+typedef enum { HMLE_FP64 = 0 } hmle_precision;
+
+/* Matern parameters of Eq. 2: range ell > 0, smoothness nu > 0,
+ * variance sigma2 >= 0, nugget tau2 >= 0. */
+typedef struct {
+  double ell, nu, sigma2, tau2;
+} hmle_theta;
+
+/* H-matrix options (the paper leaves the H-matrix construction to the
+ * library it used; these are the knobs of this implementation).
+ *  leaf_size  b: clusters with at most b points are leaves (8..128).
+ *  eta        admissibility: block (t, s) is low-rank when
+ *             min(diam t, diam s) <= eta * dist(t, s) (bounding boxes).
+ *  aca_eps    relative accuracy of every low-rank block: ACA of C stops at
+ *             |u_k||v_k| <= eps |S_k|_F; truncation of the Schur-complement
+ *             blocks keeps singular values above eps * |block|_F.
+ *  max_rank   capacity (columns) of every low-rank block, 8..96.
+ *  oversample extra random samples beyond max_rank for the compression of
+ *             updated low-rank blocks (>= 4).
+ *  seed       seed of the counter-based random signs used by that
+ *             compression (the result is deterministic for a given seed). */
+typedef struct {
+  int32_t leaf_size;
+  double eta;
+  double aca_eps;
+  int32_t max_rank;
+  int32_t oversample;
+  int32_t precision; /* hmle_precision */
+  uint64_t seed;
+} hmle_opts;
+
+/* Nelder-Mead options of hmle_fit (Sec. 2: threshold 1e-4, <= 400 iterations). */
+typedef struct {
+  double ftol;      /* stop when max |f_i - f_best| over the simplex <= ftol ... */
+  double xtol;      /* ... and max |x_i - x_best|_inf (transformed coords) <= xtol */
+  int32_t max_iter; /* iteration cap */
+  double step[4];   /* initial simplex steps in transformed coordinates
+                       (sigma0, ell0, nu0, tau0); all 0 means 1.0 each */
+} hmle_fit_opts;
+
+typedef struct {
+  int64_t n;            /* number of points */
+  int32_t d;            /* dimension (2 or 3) */
+  int32_t depth;        /* leaves are at this level; root is level 0 */
+  int32_t n_leaves;     /* 2^depth */
+  int32_t n_dense;      /* dense leaf blocks in the lower triangle (incl. diagonal) */
+  int32_t n_lowrank;    /* admissible blocks in the lower triangle */
+  int64_t dense_words;  /* doubles held by dense blocks */
+  int64_t lowrank_words;/* doubles reserved for low-rank factors (C and L) */
+  int64_t device_bytes; /* device memory held by the tree and its plan */
+} hmle_tree_info;
+
+typedef struct {
+  double logdet;        /* log|C~| */
+  double quad;          /* Z^T C~^{-1} Z */
+  double loglik;        /* Eq. 1 */
+  int32_t max_rank_c;   /* largest ACA rank among blocks of C~ */
+  int32_t max_rank_l;   /* largest rank among low-rank blocks of L~ */
+  double mean_rank_l;   /* mean rank of low-rank blocks of L~ */
+  int32_t status;       /* hmle_status of the evaluation */
+} hmle_eval_info;
+
+typedef struct hmle_ctx hmle_ctx;
+typedef struct hmle_tree hmle_tree;
+typedef struct hmle_hmatrix hmle_hmatrix;
+typedef struct hmle_hfactor hmle_hfactor;
+
+/* Fill *opts with defaults: leaf 64, eta 2, aca_eps 1e-8, max_rank 32,
+ * oversample 8, FP64, seed 0x5eed.  Always HMLE_OK for non-NULL opts. */
+hmle_status hmle_opts_default(hmle_opts *opts);
+
+/* Fill *opts with the paper's optimiser settings: ftol = xtol = 1e-4,
+ * max_iter = 400, unit steps. */
+hmle_status hmle_fit_opts_default(hmle_fit_opts *opts);
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t to
+ * launch on, or NULL for a stream owned by the context.  One context per
+ * stream; a context must not be shared between host threads. */
+hmle_status hmle_ctx_create(hmle_ctx **ctx, void *stream);
+void hmle_ctx_destroy(hmle_ctx *ctx);
+
+/* Message of the last failure on this context ("" when none).  The string
+ * stays valid until the next call on the context. */
+const char *hmle_last_error(const hmle_ctx *ctx);
+
+/* a1-a2 (Sec. 2, recursive block partition): build the geometric cluster
+ * tree (bounding boxes, median split along the longest axis, stable point
+ * permutation) and the block tree (admissibility by eta) on the device, then
+ * the θ-independent factorisation schedule.
+ *  locs  n x d doubles, row-major (point i at locs[i*d .. i*d+d-1]), host or
+ *        device memory; copied.
+ *  n     >= 2 points;  d in {2, 3};  opts may be NULL for defaults.
+ * Errors: INVALID_ARG (sizes, non-finite coordinates, bad options), OOM, CUDA. */
+hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n,
+                            int32_t d, const hmle_opts *opts, hmle_tree **out);
+void hmle_tree_destroy(hmle_tree *tree);
+hmle_status hmle_tree_get_info(const hmle_tree *tree, hmle_tree_info *info);
+/* perm[k] = caller index of the point at cluster position k (host array of n). */
+hmle_status hmle_tree_permutation(const hmle_tree *tree, int32_t *perm);
+
+/* a3-a4 (Eq. 2; Sec. 2, low-rank approximation on the fly): assemble
+ * C~(theta) on the device -- Matern entries of the dense leaf blocks and
+ * adaptive-cross-approximation factors U V^T of the admissible blocks,
+ * built from rows and columns of the kernel without forming the block.
+ * Errors: INVALID_ARG (theta out of range), RANK_OVERFLOW, OOM, CUDA. */
+hmle_status hmle_assemble(hmle_ctx *ctx, const hmle_tree *tree,
+                          const hmle_theta *theta, hmle_hmatrix **out);
+void hmle_hmatrix_destroy(hmle_hmatrix *h);
+
+/* y = C~ x for one vector (caller order, host or device, n doubles each);
+ * a check of the assembled H-matrix. */
+hmle_status hmle_hmatrix_matvec(hmle_ctx *ctx, const hmle_hmatrix *h,
+                                const double *x, double *y);
+
+/* a6-a10 (Sec. 2, H-Cholesky and solve): factor C~ = L~ L~^T by a
+ * left-looking sweep over the leaf clusters (dense diagonal and near-field
+ * leaves; low-rank blocks recompressed after their Schur-complement updates
+ * by randomised sampling + eigen-based truncation), and, when Z is not NULL,
+ * run the forward solve w = L~^{-1} P Z inside the same sweep.
+ *  h  the assembled matrix; it is not modified and may be reused.
+ *  Z  n doubles in caller order (host or device) or NULL.
+ * Errors: NOT_SPD, RANK_OVERFLOW, OOM, CUDA. */
+hmle_status hmle_factor(hmle_ctx *ctx, const hmle_hmatrix *h, const double *Z,
+                        hmle_hfactor **out);
+void hmle_factor_destroy(hmle_hfactor *f);
+
+/* a9-a12 (Eq. 1): log-likelihood from a factor.  If the factor was built
+ * with the same Z pointer contents the fused solve is reused, otherwise a
+ * forward-solve sweep runs.  loglik must not be NULL; logdet and quad may be.
+ * Errors: INVALID_ARG, CUDA. */
+hmle_status hmle_loglik(hmle_ctx *ctx, const hmle_hfactor *f, const double *Z,
+                        double *loglik, double *logdet, double *quad);
+
+/* One full evaluation L(theta): assemble + factor with the fused solve +
+ * combine, on a tree.  info may be NULL.  This is the unit of work of the
+ * MLE (Sec. 2: one H-Cholesky, one solve and one scalar product per
+ * iteration).  Errors: as hmle_assemble and hmle_factor. */
+hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tree,
+                             const hmle_theta *theta, const double *Z,
+                             double *loglik, hmle_eval_info *info);
+
+/* a13 (Sec. 2 and Sec. 5): maximise L over theta by Nelder-Mead in the
+ * transformed coordinates sigma = 2/1.1^s0, ell = 1/1.5^l0, nu = 1/1.2^n0,
+ * tau = 1/2^t0.  Trial points whose factorisation is not SPD score -inf.
+ *  theta0     start point; fopts may be NULL for hmle_fit_opts_default.
+ *  theta_hat  best point found; loglik_hat its L; n_iter / n_evals may be NULL.
+ * Returns HMLE_OK on convergence, HMLE_ERR_NOT_CONVERGED when max_iter was
+ * reached (theta_hat is still the best point seen), or the first hard error. */
+hmle_status hmle_fit(hmle_ctx *ctx, const hmle_tree *tree, const double *Z,
+                     const hmle_theta *theta0, const hmle_fit_opts *fopts,
+                     hmle_theta *theta_hat, double *loglik_hat,
+                     int32_t *n_iter, int32_t *n_evals);
+
+/* Matern correlation M_nu(x) = x^nu K_nu(x) / (2^(nu-1) Gamma(nu)) of Eq. 2
+ * as the device evaluates it (Chebyshev tables built per nu from the
+ * integral representation of K_nu), for x >= 0; out[i] for x[i], host or
+ * device arrays of m doubles.  A check of the device Bessel kernel. */
+hmle_status hmle_matern_eval(hmle_ctx *ctx, double nu, const double *x,
+                             int64_t m, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMLE_H */

@@ -1,0 +1,388 @@
+// Host planner: the θ-independent schedule of the left-looking leaf sweep.
+//
+// The H-Cholesky factor L~ of C~ (Sec. 2) has the block structure of C~:
+// dense leaf blocks near the diagonal, and admissible blocks (rho, sigma)
+// held as U W^T.  With S_{rho,sigma} = C_{rho,sigma} - L_{rho,<s} L_{sigma,<s}^T
+// (s = first column of sigma) the factor block is
+//     L_{rho,sigma} = S_{rho,sigma} L_{sigma,sigma}^{-T},
+// so the sweep over leaves K = 0..N-1 does, at step K:
+//   1. compress S of every low-rank block whose column cluster starts at K
+//      (all its updates come from columns < s, finished earlier) into
+//      U W0^T and start W = W0;
+//   2. form the dense blocks of column K (S = C - updates), POTRF the
+//      diagonal leaf, TRSM the others;
+//   3. forward-solve the rows of leaf K of every open W-panel
+//      (W <- L_{sigma,sigma}^{-1} W0 advances one leaf; the right-hand side
+//      Z is the panel of the root cluster, which gives w = L^{-1} Z);
+//   4. push the contribution of every block whose columns end at K into the
+//      rows below it of every open W-panel containing it.
+// Every update L_{X,<s} L_{Y,<s}^T is a sum over pairs of blocks (A, B)
+// covering rows X and Y and overlapping columns: U_A G_AB U_B^T with
+// G_AB = W_A[ov]^T W_B[ov] (a dense leaf block acts as U = D, W = I).
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <unordered_map>
+
+#include "hmle_internal.h"
+
+namespace hmle {
+
+namespace {
+
+inline int cid(int l, int i) { return (1 << l) - 1 + i; }
+
+struct Builder {
+  Plan &P;
+  std::vector<std::vector<int32_t>> rowlist;  // blocks whose rows contain leaf I
+  std::vector<int32_t> stampA, stampB;
+  int32_t stamp = 0;
+  explicit Builder(Plan &p) : P(p) {}
+
+  int span(const BlockDesc &B) const { return 1 << (P.depth - B.level); }
+  bool overlap(const BlockDesc &A, const BlockDesc &B) const {
+    return std::max(A.cbeg, B.cbeg) < std::min(A.cend, B.cend);
+  }
+  int64_t kof(const BlockDesc &B) const { return B.kind == kLowRank ? P.kcap : P.b; }
+
+  // blocks covering leaves [l0, l1) with columns ending at or before s
+  void collect(int l0, int l1, int32_t s, std::vector<int32_t> &out,
+               std::vector<int32_t> &stampv) {
+    ++stamp;
+    out.clear();
+    for (int I = l0; I < l1; ++I)
+      for (int32_t x : rowlist[I]) {
+        const BlockDesc &X = P.blocks[x];
+        if (X.cend <= s && stampv[x] != stamp) {
+          stampv[x] = stamp;
+          out.push_back(x);
+        }
+      }
+    std::sort(out.begin(), out.end());
+  }
+};
+
+}  // namespace
+
+std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
+                       const std::vector<int32_t> &cl_beg,
+                       const std::vector<int32_t> &cl_end,
+                       const std::vector<int4> &blk, int32_t kcap, int32_t kc,
+                       int32_t r, int32_t nrhs) {
+  P.n = n; P.d = d; P.b = b; P.depth = depth; P.nleaf = 1 << depth;
+  P.kcap = kcap; P.kc = kc; P.r = r;
+  P.cl_beg = cl_beg; P.cl_end = cl_end;
+  const int N = P.nleaf;
+
+  // --- blocks, in a fixed order: by column leaf, then dense before
+  // low-rank, then row leaf (the device block tree is already deterministic;
+  // this order only fixes storage offsets).
+  std::vector<int4> order(blk);
+  auto key = [&](const int4 &q) {
+    int sh = depth - q.x;
+    return std::make_tuple(q.z << sh, q.w, q.y << sh, q.x);
+  };
+  std::sort(order.begin(), order.end(),
+            [&](const int4 &a, const int4 &c) { return key(a) < key(c); });
+  P.blocks.clear();
+  P.diag_of_leaf.assign(N, -1);
+  int64_t dw = 0, ucw = 0, uw = 0;
+  P.n_lr_blocks = P.n_dense_blocks = 0;
+  for (const int4 &q : order) {
+    BlockDesc B{};
+    B.level = q.x;
+    B.kind = q.w;
+    int hr = cid(q.x, q.y), hc = cid(q.x, q.z);
+    B.rbeg = cl_beg[hr]; B.rend = cl_end[hr];
+    B.cbeg = cl_beg[hc]; B.cend = cl_end[hc];
+    B.rleaf = q.y << (depth - q.x);
+    B.cleaf = q.z << (depth - q.x);
+    B.panel = -1; B.slot = 0;
+    B.off_d = B.off_uc = B.off_vc = B.off_u = -1;
+    if (B.kind == kDense) {
+      if (q.x != depth) return "dense block above the leaf level";
+      B.off_d = dw; dw += (int64_t)b * b;
+      if (q.y == q.z) P.diag_of_leaf[q.y] = (int32_t)P.blocks.size();
+      ++P.n_dense_blocks;
+    } else {
+      if (q.y <= q.z) return "admissible block on or above the diagonal";
+      int64_t m = B.rend - B.rbeg, p = B.cend - B.cbeg;
+      B.off_uc = ucw; ucw += m * kc;
+      B.off_vc = ucw; ucw += p * kc;
+      B.off_u = uw; uw += m * kcap;
+      ++P.n_lr_blocks;
+    }
+    P.blocks.push_back(B);
+  }
+  for (int K = 0; K < N; ++K)
+    if (P.diag_of_leaf[K] < 0) return "missing diagonal block";
+  P.dense_words = dw; P.uc_words = ucw; P.u_words = uw;
+
+  // --- W-panels: one per column cluster holding low-rank blocks
+  std::vector<int32_t> panel_of(2 * N, -1);
+  P.panels.clear();
+  int64_t ww = 0;
+  for (size_t x = 0; x < P.blocks.size(); ++x) {
+    BlockDesc &B = P.blocks[x];
+    if (B.kind != kLowRank) continue;
+    int hc = cid(B.level, B.cleaf >> (depth - B.level));
+    if (panel_of[hc] < 0) {
+      PanelDesc pd{};
+      pd.rbeg = B.cbeg; pd.rend = B.cend; pd.width = 0;
+      pd.leaf0 = B.cleaf; pd.off = 0;
+      panel_of[hc] = (int32_t)P.panels.size();
+      P.panels.push_back(pd);
+    }
+    PanelDesc &pd = P.panels[panel_of[hc]];
+    B.panel = panel_of[hc];
+    B.slot = pd.width;
+    pd.width += kcap;
+  }
+  // right-hand side panel: the root cluster
+  {
+    PanelDesc pd{};
+    pd.rbeg = 0; pd.rend = n; pd.width = std::max(nrhs, 1); pd.leaf0 = 0;
+    P.rhs_panel = (int32_t)P.panels.size();
+    panel_of[0] = panel_of[0] < 0 ? P.rhs_panel : panel_of[0];
+    P.panels.push_back(pd);
+  }
+  for (PanelDesc &pd : P.panels) {
+    pd.off = ww;
+    ww += (int64_t)(pd.rend - pd.rbeg) * pd.width;
+  }
+  P.w_words = ww;
+  // panel span in leaves, by cluster heap id (without the rhs panel)
+  std::vector<int32_t> panel_level(P.panels.size(), 0);
+  std::vector<int32_t> panel_cid(P.panels.size(), 0);
+  for (int h = 0; h < 2 * N - 1; ++h)
+    if (panel_of[h] >= 0 && panel_of[h] != P.rhs_panel) {
+      int l = 0;
+      while ((1 << (l + 1)) - 1 <= h) ++l;
+      panel_level[panel_of[h]] = l;
+      panel_cid[panel_of[h]] = h;
+    }
+
+  Builder Bd(P);
+  Bd.rowlist.assign(N, {});
+  for (size_t x = 0; x < P.blocks.size(); ++x) {
+    const BlockDesc &B = P.blocks[x];
+    if (B.kind == kDense && B.rleaf == B.cleaf) continue;  // diagonal
+    for (int I = B.rleaf; I < B.rleaf + Bd.span(B); ++I) Bd.rowlist[I].push_back((int32_t)x);
+  }
+  Bd.stampA.assign(P.blocks.size(), 0);
+  Bd.stampB.assign(P.blocks.size(), 0);
+
+  // blocks grouped by first column leaf / by last column leaf
+  std::vector<std::vector<int32_t>> starts(N), ends(N);
+  for (size_t x = 0; x < P.blocks.size(); ++x) {
+    const BlockDesc &B = P.blocks[x];
+    starts[B.cleaf].push_back((int32_t)x);
+    if (!(B.kind == kDense && B.rleaf == B.cleaf))
+      ends[B.cleaf + Bd.span(B) - 1].push_back((int32_t)x);
+  }
+
+  P.grams.clear(); P.lrt.clear(); P.aent.clear(); P.bent.clear();
+  P.apair.clear(); P.bpair.clear(); P.lrpairs.clear();
+  P.arow.clear(); P.brow.clear(); P.arow_ent.clear(); P.brow_ent.clear();
+  P.dns.clear(); P.dpairs.clear(); P.wpan.clear(); P.hts.clear();
+  P.urows.clear(); P.uents.clear(); P.steps.clear();
+  P.ws_max = 0;
+
+  std::vector<int32_t> Aset, Bset;
+  std::unordered_map<int64_t, int64_t> gram_of;  // (a, b) -> offset, per step
+  const int64_t kk = (int64_t)kcap * kcap;
+
+  for (int K = 0; K < N; ++K) {
+    StepRange st{};
+    int64_t ws = 0;
+    gram_of.clear();
+    st.gram0 = (int32_t)P.grams.size();
+    auto gram = [&](int32_t a, int32_t c) -> int64_t {
+      const BlockDesc &A = P.blocks[a], &C = P.blocks[c];
+      if (A.kind != kLowRank || C.kind != kLowRank) return -1;
+      int64_t key = (int64_t)a * (int64_t)P.blocks.size() + c;
+      auto it = gram_of.find(key);
+      if (it != gram_of.end()) return it->second;
+      GramTask g{};
+      g.a = a; g.b = c;
+      g.ovb = std::max(A.cbeg, C.cbeg); g.ove = std::min(A.cend, C.cend);
+      g.goff = ws; ws += kk;
+      P.grams.push_back(g);
+      gram_of[key] = g.goff;
+      return g.goff;
+    };
+
+    // 1. low-rank targets whose column cluster starts at leaf K
+    st.lrt0 = (int32_t)P.lrt.size();
+    st.aent0 = (int32_t)P.aent.size();
+    st.bent0 = (int32_t)P.bent.size();
+    st.arow0 = (int32_t)P.arow.size();
+    st.brow0 = (int32_t)P.brow.size();
+    for (int32_t t : starts[K]) {
+      const BlockDesc &T = P.blocks[t];
+      if (T.kind != kLowRank) continue;
+      LrTarget L{};
+      L.blk = t;
+      L.m = T.rend - T.rbeg; L.p = T.cend - T.cbeg;
+      const int sp = Bd.span(T);
+      Bd.collect(T.rleaf, T.rleaf + sp, T.cbeg, Aset, Bd.stampA);
+      Bd.collect(T.cleaf, T.cleaf + sp, T.cbeg, Bset, Bd.stampB);
+      int32_t ti = (int32_t)P.lrt.size();
+      L.a0 = (int32_t)P.aent.size();
+      std::unordered_map<int32_t, int32_t> aidx, bidx;
+      for (int32_t a : Aset) {
+        SideEntry e{};
+        e.target = ti; e.blk = a;
+        e.toff = ws; ws += Bd.kof(P.blocks[a]) * r;
+        e.soff = ws; ws += Bd.kof(P.blocks[a]) * r;
+        aidx[a] = (int32_t)P.aent.size();
+        P.aent.push_back(e);
+      }
+      L.a1 = (int32_t)P.aent.size();
+      L.b0 = (int32_t)P.bent.size();
+      for (int32_t c : Bset) {
+        SideEntry e{};
+        e.target = ti; e.blk = c;
+        e.toff = ws; ws += Bd.kof(P.blocks[c]) * r;
+        e.soff = ws; ws += Bd.kof(P.blocks[c]) * r;
+        bidx[c] = (int32_t)P.bent.size();
+        P.bent.push_back(e);
+      }
+      L.b1 = (int32_t)P.bent.size();
+      // pairs, grouped per A-entry and per B-entry
+      std::vector<std::vector<int32_t>> pa(Aset.size()), pb(Bset.size());
+      for (size_t ia = 0; ia < Aset.size(); ++ia)
+        for (size_t ib = 0; ib < Bset.size(); ++ib) {
+          const BlockDesc &A = P.blocks[Aset[ia]], &C = P.blocks[Bset[ib]];
+          if (!Bd.overlap(A, C)) continue;
+          LrPair pr{};
+          pr.ae = L.a0 + (int32_t)ia; pr.be = L.b0 + (int32_t)ib;
+          pr.goff = gram(Aset[ia], Bset[ib]);
+          int32_t pi = (int32_t)P.lrpairs.size();
+          P.lrpairs.push_back(pr);
+          pa[ia].push_back(pi);
+          pb[ib].push_back(pi);
+        }
+      for (size_t ia = 0; ia < Aset.size(); ++ia) {
+        SideEntry &e = P.aent[L.a0 + ia];
+        e.p0 = (int32_t)P.apair.size();
+        P.apair.insert(P.apair.end(), pa[ia].begin(), pa[ia].end());
+        e.p1 = (int32_t)P.apair.size();
+      }
+      for (size_t ib = 0; ib < Bset.size(); ++ib) {
+        SideEntry &e = P.bent[L.b0 + ib];
+        e.p0 = (int32_t)P.bpair.size();
+        P.bpair.insert(P.bpair.end(), pb[ib].begin(), pb[ib].end());
+        e.p1 = (int32_t)P.bpair.size();
+      }
+      // row tasks
+      for (int I = T.rleaf; I < T.rleaf + sp; ++I) {
+        RowTask rt{};
+        rt.target = ti; rt.leaf = I;
+        rt.e0 = (int32_t)P.arow_ent.size();
+        for (int32_t x : Bd.rowlist[I]) {
+          auto it = aidx.find(x);
+          if (it != aidx.end()) P.arow_ent.push_back(it->second);
+        }
+        rt.e1 = (int32_t)P.arow_ent.size();
+        P.arow.push_back(rt);
+      }
+      for (int J = T.cleaf; J < T.cleaf + sp; ++J) {
+        RowTask rt{};
+        rt.target = ti; rt.leaf = J;
+        rt.e0 = (int32_t)P.brow_ent.size();
+        for (int32_t x : Bd.rowlist[J]) {
+          auto it = bidx.find(x);
+          if (it != bidx.end()) P.brow_ent.push_back(it->second);
+        }
+        rt.e1 = (int32_t)P.brow_ent.size();
+        P.brow.push_back(rt);
+      }
+      L.yoff = ws; ws += (int64_t)L.m * r;
+      L.zoff = ws; ws += (int64_t)L.p * r;
+      L.soff = ws; ws += 4LL * r * r;
+      L.tcoff = ws; ws += (int64_t)std::max(kc, r) * r;
+      P.lrt.push_back(L);
+    }
+    st.lrt1 = (int32_t)P.lrt.size();
+    st.aent1 = (int32_t)P.aent.size();
+    st.bent1 = (int32_t)P.bent.size();
+    st.arow1 = (int32_t)P.arow.size();
+    st.brow1 = (int32_t)P.brow.size();
+
+    // 2. dense targets of column K, the diagonal first
+    st.dns0 = (int32_t)P.dns.size();
+    std::vector<int32_t> dlist;
+    dlist.push_back(P.diag_of_leaf[K]);
+    for (int32_t t : starts[K])
+      if (P.blocks[t].kind == kDense && t != P.diag_of_leaf[K]) dlist.push_back(t);
+    for (int32_t t : dlist) {
+      const BlockDesc &T = P.blocks[t];
+      DenseTarget dt{};
+      dt.blk = t;
+      dt.p0 = (int32_t)P.dpairs.size();
+      Bd.collect(T.rleaf, T.rleaf + 1, T.cbeg, Aset, Bd.stampA);
+      Bd.collect(T.cleaf, T.cleaf + 1, T.cbeg, Bset, Bd.stampB);
+      for (int32_t a : Aset)
+        for (int32_t c : Bset) {
+          if (!Bd.overlap(P.blocks[a], P.blocks[c])) continue;
+          DPair pr{};
+          pr.a = a; pr.b = c; pr.goff = gram(a, c);
+          P.dpairs.push_back(pr);
+        }
+      dt.p1 = (int32_t)P.dpairs.size();
+      P.dns.push_back(dt);
+    }
+    st.dns1 = (int32_t)P.dns.size();
+    st.gram1 = (int32_t)P.grams.size();
+
+    // 3. panels advanced by the forward solve of leaf K
+    st.wpan0 = (int32_t)P.wpan.size();
+    for (size_t pi = 0; pi < P.panels.size(); ++pi) {
+      const PanelDesc &pd = P.panels[pi];
+      int sp = ((int)pi == P.rhs_panel) ? N : (1 << (depth - panel_level[pi]));
+      if (pd.leaf0 <= K && K < pd.leaf0 + sp) P.wpan.push_back((int32_t)pi);
+    }
+    st.wpan1 = (int32_t)P.wpan.size();
+
+    // 4. deferred updates by blocks whose columns end at leaf K
+    st.ht0 = (int32_t)P.hts.size();
+    st.ur0 = (int32_t)P.urows.size();
+    std::map<std::pair<int32_t, int32_t>, std::vector<UpdEntry>> rows;  // (panel, leaf)
+    for (int32_t a : ends[K]) {
+      const BlockDesc &A = P.blocks[a];
+      for (size_t pi = 0; pi < P.panels.size(); ++pi) {
+        const PanelDesc &pd = P.panels[pi];
+        if (!(pd.rbeg <= A.cbeg && A.rend <= pd.rend)) continue;
+        UpdEntry ue{};
+        ue.a = a; ue.hoff = -1;
+        if (A.kind == kLowRank) {
+          HTask h{};
+          h.a = a; h.panel = (int32_t)pi;
+          h.hoff = ws; ws += (int64_t)kcap * pd.width;
+          P.hts.push_back(h);
+          ue.hoff = h.hoff;
+        }
+        for (int I = A.rleaf; I < A.rleaf + Bd.span(A); ++I)
+          rows[{(int32_t)pi, I}].push_back(ue);
+      }
+    }
+    st.ht1 = (int32_t)P.hts.size();
+    for (auto &kv : rows) {
+      UpdRow ur{};
+      ur.panel = kv.first.first; ur.leaf = kv.first.second;
+      ur.e0 = (int32_t)P.uents.size();
+      P.uents.insert(P.uents.end(), kv.second.begin(), kv.second.end());
+      ur.e1 = (int32_t)P.uents.size();
+      P.urows.push_back(ur);
+    }
+    st.ur1 = (int32_t)P.urows.size();
+    st.ws_words = ws;
+    P.ws_max = std::max(P.ws_max, ws);
+    P.steps.push_back(st);
+  }
+  return "";
+}
+
+}  // namespace hmle
