@@ -1,0 +1,280 @@
+"""Benchmark of the H-MLE hot path: H-matrix log-likelihood evaluations per
+second (Eq. 1 with the Matern covariance of Eq. 2) on one GB300.
+
+One step = one full evaluation L(theta): Matern tables + ACA assembly of the
+admissible blocks + the H-Cholesky leaf sweep with the fused forward solve +
+log-det / quadratic form, for the medium workload: n = 65,536 points in
+[0,1]^2 (70 % uniform, 30 % in 8 Gaussian blobs of sd 0.03), Matern
+(ell, nu, sigma2, tau2) = (0.05, 0.5, 1, 1e-3), leaf 64, eta 2, eps 1e-6.
+The cluster/block trees and the schedule are built once (θ-independent).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  --impl reference times the CPU oracle (dense FP64
+Cholesky of the same likelihood) on a bounded subset of the same workload.
+Under torchrun (N > 1) every rank evaluates its own replica (the single-field
+factorisation does not shard); value is the total over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H-loglik evals/sec and MLE fit time at n=64k and 2M on 1 GB300 at |ΔL|/n≤1e-6"
+WORKLOAD = dict(workload="medium: n=65536 2-D, 70% uniform + 30% in 8 blobs (sd 0.03), Matern "
+                "ell=0.05 nu=0.5 sigma2=1 tau2=1e-3, leaf 64, eta 2, ACA eps 1e-6, FP64",
+                n=65536, d=2, theta=[0.05, 0.5, 1.0, 1e-3], leaf=64, eta=2.0, eps=1e-6)
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07  # SMs x FP64 FMA/clk x 2 flops x GHz (max clock)
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, name in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(name)
+            except Exception:
+                pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1
+    import torch.distributed as dist
+    dist.init_process_group("nccl")
+    return dist, dist.get_rank(), ws
+
+
+def _workload_inputs(n):
+    from paper_2104_07146_gb300 import synth
+    locs = synth.locations_blobs(n, 2, 0.3, 8, 0.03, seed=1001)
+    Z = synth.normal(1002, n)
+    return locs, Z
+
+
+def run_gpu(args):
+    import torch
+    from paper_2104_07146_gb300 import hmle
+    dist, rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    w = WORKLOAD
+    n = w["n"]
+    locs, Z = _workload_inputs(n)
+    stream = torch.cuda.current_stream()
+    ctx = hmle.Context(stream)
+    tree = hmle.Tree(ctx, locs, leaf_size=w["leaf"], eta=w["eta"], aca_eps=w["eps"])
+    Zd = torch.from_numpy(Z).to(f"cuda:{local}")           # resident input
+    Zh = torch.from_numpy(Z).pin_memory()                   # host input for e2e
+    theta = tuple(w["theta"])
+    prof = hmle.Profiler(ctx, args.roofline_kernel)
+
+    def step(z):
+        return tree.loglik(theta, z)
+
+    for _ in range(args.warmup):
+        step(Zd)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    prof.enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    launches = 0
+    info = None
+    for _ in range(args.steps):
+        ll, info = step(Zd)
+        launches += info.kernel_launches
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dom = prof.read()
+    prof.enable(False)
+    ms = e0.elapsed_time(e1)
+    # e2e: host Z (pinned) through the C ABI; the copy in and the result out
+    # are inside the timed region
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        ll_e2e, _ = step(Zh.numpy())
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms, ms_e2e], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    value = ws * args.steps / (ms / 1e3)
+    e2e = ws * args.steps / (ms_e2e / 1e3)
+    achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] > 0 else None
+    peaks = _peaks()
+    out = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {**{k: v for k, v in WORKLOAD.items()},
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "working set %.1f GB > 129 MB L2 (no flush needed)"
+                         % (tree.info().lowrank_words * 8 / 1e9)},
+        "loglik": ll, "logdet": info.logdet, "quad": info.quad,
+        "ranks": {"max_c": info.max_rank_c, "max_l": info.max_rank_l, "mean_l": info.mean_rank_l},
+        "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 24},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": dom["name"], "achieved": achieved,
+                     "launches": dom["launches"], "kernel_ms": dom["ms"],
+                     "flops_per_launch": dom["flops"] / max(dom["launches"], 1),
+                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                     "frac": (achieved / FP64_PEAK_GFLOPS) if achieved else None,
+                     "traffic": None,
+                     "note": "FP64 ALU peak from 152 SMs x 2 FMA/clk x 2070 MHz "
+                             "(measured FMA loop: 1254.6 GFLOP/s); launches timed with CUDA "
+                             "events on the library stream during the timed steps"},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample_n)
+    print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(n_sub):
+    """The oracle as it stands (dense FP64) on a subset of the workload,
+    extrapolated to n = 65,536 by its n^3 cost."""
+    import oracle
+    locs, Z = _workload_inputs(WORKLOAD["n"])
+    locs, Z = locs[:n_sub], Z[:n_sub]
+    theta = tuple(WORKLOAD["theta"])
+    t0 = time.time()
+    oracle.loglik_dense(locs, Z, theta)
+    dt = time.time() - t0
+    scale = (WORKLOAD["n"] / n_sub) ** 3
+    return {"value": 1.0 / (dt * scale), "unit": "evals/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": "one dense evaluation on the first %d points of the workload (%.1f s), "
+                      "extrapolated to n=%d by n^3" % (n_sub, dt, WORKLOAD["n"])}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    n_sub = args.cpu_sample_n
+    locs, Z = _workload_inputs(WORKLOAD["n"])
+    locs, Z = locs[:n_sub], Z[:n_sub]
+    theta = tuple(WORKLOAD["theta"])
+    for _ in range(args.warmup):
+        oracle.loglik_dense(locs, Z, theta)
+    t0 = time.time()
+    for _ in range(args.steps):
+        oracle.loglik_dense(locs, Z, theta)
+    dt = (time.time() - t0) / max(args.steps, 1)
+    scale = (WORKLOAD["n"] / n_sub) ** 3
+    v = 1.0 / (dt * scale)
+    sample = ("dense FP64 oracle on the first %d points per step (%.2f s), extrapolated to "
+              "n=%d by n^3" % (n_sub, dt, WORKLOAD["n"]))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * scale * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": WORKLOAD,
+        "cpu_baseline": {"value": v, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sample-n", type=int, default=8192)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--roofline-kernel", default="k_tsqr_final",
+                    help="sweep kernel whose launches are timed for the roofline line")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

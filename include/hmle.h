@@ -115,6 +115,7 @@ typedef struct {
   int32_t max_rank_l;   /* largest rank among low-rank blocks of L~ */
   double mean_rank_l;   /* mean rank of low-rank blocks of L~ */
   int32_t status;       /* hmle_status of the evaluation */
+  int64_t kernel_launches; /* CUDA kernels this evaluation launched */
 } hmle_eval_info;
 
 typedef struct hmle_ctx hmle_ctx;
@@ -214,6 +215,18 @@ hmle_status hmle_fit(hmle_ctx *ctx, const hmle_tree *tree, const double *Z,
  * device arrays of m doubles.  A check of the device Bessel kernel. */
 hmle_status hmle_matern_eval(hmle_ctx *ctx, double nu, const double *x,
                              int64_t m, double *out);
+
+/* Measurement support (no counterpart in the paper).  Select one kernel of
+ * the factorisation sweep by name (e.g. "k_tsqr_final", "k_dense_pair"; NULL
+ * switches timing off).  While selected, every launch of that kernel is
+ * bracketed by CUDA events on its own stream, and after each evaluation the
+ * algorithmic FP64 flops of those launches are tallied from the plan and the
+ * ranks the evaluation produced.  Selecting resets the counters.
+ * Errors: INVALID_ARG for an unknown name. */
+hmle_status hmle_profile_select(hmle_ctx *ctx, const char *kernel);
+/* Totals since the last hmle_profile_select: summed launch durations (ms),
+ * number of launches, algorithmic FP64 flops.  Any pointer may be NULL. */
+hmle_status hmle_profile_read(hmle_ctx *ctx, double *ms, int64_t *launches, double *flops);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,830 @@
+// The C ABI of libhmle (include/hmle.h): handles, device memory,
+// orchestration of the kernels, and the Nelder-Mead driver of hmle_fit.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "hmle_internal.h"
+#include "kernels.cuh"
+#include "matern.cuh"
+#include "tally.h"
+#include "tree.cuh"
+
+using namespace hmle;
+
+struct hmle_ctx {
+  cudaStream_t st = nullptr;
+  bool own = false;
+  int dev = 0;
+  std::string err;
+  cudaStream_t side = nullptr;     // dense blocks of a step run here concurrently
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  Prof prof;                       // optional per-kernel timing
+  double *d_jacobi = nullptr;      // device flop counter of the Jacobi sweeps
+};
+
+struct DevPlan {
+  BlockDesc *blocks = nullptr;
+  PanelDesc *panels = nullptr;
+  GramTask *grams = nullptr;
+  LrTarget *lrt = nullptr;
+  SideEntry *aent = nullptr, *bent = nullptr;
+  int32_t *apair = nullptr, *bpair = nullptr;
+  LrPair *lrpairs = nullptr;
+  RowTask *arow = nullptr, *brow = nullptr;
+  int32_t *arow_ent = nullptr, *brow_ent = nullptr;
+  DenseTarget *dns = nullptr;
+  DPair *dpairs = nullptr;
+  int2 *dpair_tr = nullptr, *dpair_tc = nullptr;
+  int32_t *wpan = nullptr;
+  HTask *hts = nullptr;
+  UpdRow *urows = nullptr;
+  UpdEntry *uents = nullptr;
+  int32_t *leaf_beg = nullptr;
+  int32_t *lr_ids = nullptr;
+  int32_t *dense_ids = nullptr;
+  int64_t bytes = 0;
+};
+
+struct Work;  // per-tree evaluation buffers (θ-dependent contents)
+
+struct hmle_tree {
+  hmle_ctx *ctx = nullptr;   // used by calls on the tree; never by its destructor
+  int64_t n = 0;
+  int d = 2;
+  hmle_opts opts{};
+  Plan plan;
+  DeviceTree T;
+  DevPlan dp;
+  std::vector<int32_t> lr_ids, dense_ids;
+  Work *work = nullptr;
+};
+
+struct hmle_hmatrix {
+  const hmle_tree *tree = nullptr;
+  hmle_theta th{};
+  double *tab = nullptr;
+  double *uc = nullptr;
+  int32_t *rank_c = nullptr;
+  double *cnorm = nullptr;
+  ThetaDev *thd = nullptr;
+  int *flags = nullptr;
+  int max_rank_c = 0;
+  bool owned = true;
+};
+
+struct hmle_hfactor {
+  const hmle_hmatrix *h = nullptr;
+  double *D = nullptr, *U = nullptr, *W = nullptr, *ws = nullptr;
+  int32_t *rank_l = nullptr;
+  int32_t *kept = nullptr;
+  double *ldp = nullptr;
+  int *flags = nullptr;
+  double *out = nullptr;
+  bool has_rhs = false;
+  double logdet = 0.0, quad = 0.0;
+  int64_t launches = 0;
+  int max_rank_l = 0;
+  double mean_rank_l = 0.0;
+  bool owned = true;
+};
+
+struct Work {
+  hmle_hmatrix H;
+  hmle_hfactor F;
+  double *zdev = nullptr;
+  bool ready = false;
+};
+
+namespace {
+
+hmle_status fail(hmle_ctx *c, hmle_status s, const std::string &m) {
+  if (c) c->err = m;
+  return s;
+}
+
+hmle_status cuda_fail(hmle_ctx *c, cudaError_t e, const char *where) {
+  return fail(c, e == cudaErrorMemoryAllocation ? HMLE_ERR_OOM : HMLE_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                   \
+  do {                                                    \
+    cudaError_t e__ = (call);                             \
+    if (e__ != cudaSuccess) return cuda_fail(ctx, e__, where); \
+  } while (0)
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t upload(cudaStream_t st, T **dst, const std::vector<T> &v, int64_t &bytes) {
+  size_t sz = sizeof(T) * std::max<size_t>(v.size(), 1);
+  cudaError_t e = cudaMallocAsync((void **)dst, sz, st);
+  if (e != cudaSuccess) return e;
+  bytes += (int64_t)sz;
+  if (!v.empty()) e = cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
+  return e;
+}
+
+void free_devplan(cudaStream_t st, DevPlan &d) {
+  void *ptrs[] = {d.blocks, d.panels, d.grams, d.lrt, d.aent, d.bent, d.apair, d.bpair,
+                  d.lrpairs, d.arow, d.brow, d.arow_ent, d.brow_ent, d.dns, d.dpairs,
+                  d.dpair_tr, d.dpair_tc, d.wpan,
+                  d.hts, d.urows, d.uents, d.leaf_beg, d.lr_ids, d.dense_ids};
+  for (void *p : ptrs)
+    if (p) cudaFreeAsync(p, st);
+  d = DevPlan{};
+}
+
+bool theta_ok(const hmle_theta *t) {
+  return t && std::isfinite(t->ell) && std::isfinite(t->nu) && std::isfinite(t->sigma2) &&
+         std::isfinite(t->tau2) && t->ell > 0 && t->nu > 0 && t->nu <= 20 && t->sigma2 >= 0 &&
+         t->tau2 >= 0;
+}
+
+void free_hm(cudaStream_t st, hmle_hmatrix *h) {
+  if (h->tab) cudaFreeAsync(h->tab, st);
+  if (h->uc) cudaFreeAsync(h->uc, st);
+  if (h->rank_c) cudaFreeAsync(h->rank_c, st);
+  if (h->cnorm) cudaFreeAsync(h->cnorm, st);
+  if (h->thd) cudaFreeAsync(h->thd, st);
+  if (h->flags) cudaFreeAsync(h->flags, st);
+  h->tab = nullptr; h->uc = nullptr; h->rank_c = nullptr; h->cnorm = nullptr;
+  h->thd = nullptr; h->flags = nullptr;
+}
+
+void free_f(cudaStream_t st, hmle_hfactor *f) {
+  void *ptrs[] = {f->D, f->U, f->W, f->ws, f->rank_l, f->kept, f->ldp, f->flags, f->out};
+  for (void *p : ptrs)
+    if (p) cudaFreeAsync(p, st);
+  f->D = f->U = f->W = f->ws = nullptr;
+  f->rank_l = nullptr; f->kept = nullptr; f->ldp = nullptr; f->flags = nullptr; f->out = nullptr;
+}
+
+hmle_status alloc_hm(hmle_ctx *ctx, const hmle_tree *t, hmle_hmatrix *h) {
+  cudaStream_t st = ctx->st;
+  const Plan &P = t->plan;
+  h->tree = t;
+  CK(cudaMallocAsync(&h->tab, sizeof(double) * kTableWords, st), "alloc table");
+  CK(cudaMallocAsync(&h->uc, sizeof(double) * std::max<int64_t>(P.uc_words, 1), st), "alloc C factors");
+  CK(cudaMallocAsync(&h->rank_c, sizeof(int32_t) * std::max<size_t>(P.blocks.size(), 1), st), "alloc ranks");
+  CK(cudaMallocAsync(&h->cnorm, sizeof(double) * std::max<size_t>(P.blocks.size(), 1), st), "alloc norms");
+  CK(cudaMemsetAsync(h->cnorm, 0, sizeof(double) * std::max<size_t>(P.blocks.size(), 1), st), "memset");
+  CK(cudaMallocAsync(&h->thd, sizeof(ThetaDev), st), "alloc theta");
+  CK(cudaMallocAsync(&h->flags, sizeof(int), st), "alloc flags");
+  CK(cudaMemsetAsync(h->rank_c, 0, sizeof(int32_t) * std::max<size_t>(P.blocks.size(), 1), st), "memset");
+  return HMLE_OK;
+}
+
+hmle_status alloc_f(hmle_ctx *ctx, const hmle_tree *t, hmle_hfactor *f) {
+  cudaStream_t st = ctx->st;
+  const Plan &P = t->plan;
+  CK(cudaMallocAsync(&f->D, sizeof(double) * std::max<int64_t>(P.dense_words, 1), st), "alloc dense pool");
+  CK(cudaMallocAsync(&f->U, sizeof(double) * std::max<int64_t>(P.u_words, 1), st), "alloc U pool");
+  CK(cudaMallocAsync(&f->W, sizeof(double) * std::max<int64_t>(P.w_words, 1), st), "alloc W panels");
+  CK(cudaMallocAsync(&f->ws, sizeof(double) * std::max<int64_t>(P.ws_max, 1), st), "alloc workspace");
+  CK(cudaMallocAsync(&f->rank_l, sizeof(int32_t) * std::max<size_t>(P.blocks.size(), 1), st), "alloc ranks");
+  CK(cudaMallocAsync(&f->kept, sizeof(int32_t) * std::max<size_t>(P.lrt.size(), 1), st), "alloc kept");
+  CK(cudaMallocAsync(&f->ldp, sizeof(double) * P.nleaf, st), "alloc logdet");
+  CK(cudaMallocAsync(&f->flags, sizeof(int), st), "alloc flags");
+  CK(cudaMallocAsync(&f->out, sizeof(double) * 2, st), "alloc out");
+  return HMLE_OK;
+}
+
+// assemble into h (buffers allocated)
+hmle_status do_assemble(hmle_ctx *ctx, const hmle_tree *t, const hmle_theta *th, hmle_hmatrix *h) {
+  cudaStream_t st = ctx->st;
+  const Plan &P = t->plan;
+  h->th = *th;
+  ThetaDev td{1.0 / th->ell, th->sigma2, th->tau2, th->nu};
+  CK(cudaMemcpyAsync(h->thd, &td, sizeof(td), cudaMemcpyHostToDevice, st), "theta upload");
+  CK(cudaMemsetAsync(h->flags, 0, sizeof(int), st), "memset flags");
+  launch_matern_table(st, th->nu, h->tab);
+  AsmArgs A{};
+  A.blocks = t->dp.blocks;
+  A.lr_ids = t->dp.lr_ids;
+  A.xyz = t->T.xyz;
+  A.n = t->n;
+  A.d = t->d;
+  A.tab = h->tab;
+  A.inv_ell = 1.0 / th->ell;
+  A.sigma2 = th->sigma2;
+  A.tau2 = th->tau2;
+  A.eps = t->opts.aca_eps;
+  A.kc = P.kc;
+  A.uc = h->uc;
+  A.rank_c = h->rank_c;
+  A.cnorm = h->cnorm;
+  A.flags = h->flags;
+  launch_aca(st, A, (int)t->lr_ids.size());
+  CK(cudaGetLastError(), "assemble launch");
+  return HMLE_OK;
+}
+
+FactorArgs make_fargs(const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f) {
+  const Plan &P = t->plan;
+  const DevPlan &d = t->dp;
+  FactorArgs F{};
+  F.blocks = d.blocks; F.panels = d.panels; F.grams = d.grams; F.lrt = d.lrt;
+  F.aent = d.aent; F.bent = d.bent; F.apair = d.apair; F.bpair = d.bpair;
+  F.lrpairs = d.lrpairs; F.arow = d.arow; F.brow = d.brow; F.arow_ent = d.arow_ent;
+  F.brow_ent = d.brow_ent; F.dns = d.dns; F.dpairs = d.dpairs; F.wpan = d.wpan;
+  F.dpair_tr = d.dpair_tr; F.dpair_tc = d.dpair_tc;
+  F.hts = d.hts; F.urows = d.urows; F.uents = d.uents; F.leaf_beg = d.leaf_beg;
+  F.D = f->D; F.uc = h->uc; F.rank_c = h->rank_c; F.cnorm = h->cnorm; F.U = f->U; F.W = f->W; F.ws = f->ws;
+  F.rank_l = f->rank_l; F.kept = f->kept; F.logdet_parts = f->ldp; F.flags = f->flags;
+  F.xyz = t->T.xyz; F.n = t->n; F.d = t->d; F.tab = h->tab; F.th = h->thd;
+  F.eps = t->opts.aca_eps; F.seed = t->opts.seed;
+  F.b = P.b; F.kcap = P.kcap; F.kc = P.kc; F.r = P.r;
+  F.osamp = t->opts.oversample;
+  return F;
+}
+
+hmle_status do_factor(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h,
+                      const double *zdev, hmle_hfactor *f) {
+  cudaStream_t st = ctx->st;
+  const Plan &P = t->plan;
+  f->h = h;
+  CK(cudaMemsetAsync(f->flags, 0, sizeof(int), st), "memset flags");
+  CK(cudaMemsetAsync(f->rank_l, 0, sizeof(int32_t) * std::max<size_t>(P.blocks.size(), 1), st), "memset");
+  const PanelDesc &rp = P.panels[P.rhs_panel];
+  if (zdev) {
+    launch_permute_in(st, zdev, t->T.perm, t->n, f->W + rp.off);
+    f->has_rhs = true;
+  } else {
+    CK(cudaMemsetAsync(f->W + rp.off, 0, sizeof(double) * t->n, st), "memset rhs");
+    f->has_rhs = false;
+  }
+  FactorArgs F = make_fargs(t, h, f);
+  Prof *prof = ctx->prof.kind >= 0 ? &ctx->prof : nullptr;
+  F.jacobi_flops = ctx->d_jacobi;
+  CK(cudaMemsetAsync(ctx->d_jacobi, 0, sizeof(double), st), "memset");
+  int64_t nk = 4;  // table, ACA, permutation, finalize
+  for (int K = 0; K < P.nleaf; ++K)
+    nk += launch_step(st, ctx->side, ctx->ev_fork, ctx->ev_join, F, P.steps[K], K, P, prof);
+  f->launches = nk;
+  CK(cudaGetLastError(), "factor launch");
+  launch_finalize(st, f->ldp, P.nleaf, f->W + rp.off, t->n, f->out);
+  double out[2];
+  int flags[2];
+  CK(cudaMemcpyAsync(out, f->out, sizeof(out), cudaMemcpyDeviceToHost, st), "result copy");
+  CK(cudaMemcpyAsync(&flags[0], f->flags, sizeof(int), cudaMemcpyDeviceToHost, st), "flag copy");
+  CK(cudaMemcpyAsync(&flags[1], h->flags, sizeof(int), cudaMemcpyDeviceToHost, st), "flag copy");
+  CK(cudaStreamSynchronize(st), "factor sync");
+  f->logdet = out[0];
+  f->quad = out[1];
+  if (prof) {
+    prof_collect(prof);
+    std::vector<int32_t> rc(P.blocks.size()), rl(P.blocks.size()), kp(std::max<size_t>(P.lrt.size(), 1));
+    double jf = 0.0;
+    CK(cudaMemcpy(rc.data(), h->rank_c, sizeof(int32_t) * rc.size(), cudaMemcpyDeviceToHost), "ranks");
+    CK(cudaMemcpy(rl.data(), f->rank_l, sizeof(int32_t) * rl.size(), cudaMemcpyDeviceToHost), "ranks");
+    CK(cudaMemcpy(kp.data(), f->kept, sizeof(int32_t) * kp.size(), cudaMemcpyDeviceToHost), "kept");
+    CK(cudaMemcpy(&jf, ctx->d_jacobi, sizeof(double), cudaMemcpyDeviceToHost), "jacobi");
+    prof->flops += tally_flops(P, prof->kind, rc, rl, kp, t->opts.oversample, jf);
+  }
+  int fl = flags[0] | flags[1];
+  if (fl & kFlagNotSpd) return fail(ctx, HMLE_ERR_NOT_SPD, "non-positive pivot in a diagonal leaf");
+  if (fl & kFlagRankOverflow)
+    return fail(ctx, HMLE_ERR_RANK_OVERFLOW, "a low-rank block needed more than max_rank terms");
+  if (!std::isfinite(out[0]) || !std::isfinite(out[1]))
+    return fail(ctx, HMLE_ERR_NOT_SPD, "non-finite log-determinant or quadratic form");
+  return HMLE_OK;
+}
+
+hmle_status rank_stats(hmle_ctx *ctx, const hmle_tree *t, const int32_t *dranks, int *maxr,
+                       double *meanr) {
+  std::vector<int32_t> rk(t->plan.blocks.size());
+  if (rk.empty()) { *maxr = 0; *meanr = 0; return HMLE_OK; }
+  CK(cudaMemcpyAsync(rk.data(), dranks, sizeof(int32_t) * rk.size(), cudaMemcpyDeviceToHost, ctx->st), "ranks");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  int mx = 0; double s = 0; int c = 0;
+  for (int32_t x : t->lr_ids) { mx = std::max(mx, rk[x]); s += rk[x]; ++c; }
+  *maxr = mx;
+  *meanr = c ? s / c : 0.0;
+  return HMLE_OK;
+}
+
+hmle_status stage_vec(hmle_ctx *ctx, const double *src, int64_t n, double **dev, bool *owned) {
+  if (is_device_ptr(src)) { *dev = const_cast<double *>(src); *owned = false; return HMLE_OK; }
+  CK(cudaMallocAsync(dev, sizeof(double) * std::max<int64_t>(n, 1), ctx->st), "alloc vector");
+  CK(cudaMemcpyAsync(*dev, src, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st), "copy vector");
+  *owned = true;
+  return HMLE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hmle_status hmle_opts_default(hmle_opts *o) {
+  if (!o) return HMLE_ERR_INVALID_ARG;
+  o->leaf_size = 64;
+  o->eta = 2.0;
+  o->aca_eps = 1e-8;
+  o->max_rank = 32;
+  o->oversample = 8;
+  o->precision = HMLE_FP64;
+  o->seed = 0x5eed;
+  return HMLE_OK;
+}
+
+hmle_status hmle_fit_opts_default(hmle_fit_opts *o) {
+  if (!o) return HMLE_ERR_INVALID_ARG;
+  o->ftol = 1e-4;
+  o->xtol = 1e-4;
+  o->max_iter = 400;
+  for (int i = 0; i < 4; ++i) o->step[i] = 1.0;
+  return HMLE_OK;
+}
+
+hmle_status hmle_ctx_create(hmle_ctx **out, void *stream) {
+  if (!out) return HMLE_ERR_INVALID_ARG;
+  hmle_ctx *c = new (std::nothrow) hmle_ctx();
+  if (!c) return HMLE_ERR_OOM;
+  cudaError_t e = cudaGetDevice(&c->dev);
+  if (e == cudaSuccess && stream) {
+    c->st = (cudaStream_t)stream;
+  } else if (e == cudaSuccess) {
+    e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
+    c->own = true;
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_jacobi, sizeof(double));
+  if (e != cudaSuccess) {
+    delete c;
+    return HMLE_ERR_CUDA;
+  }
+  *out = c;
+  return HMLE_OK;
+}
+
+void hmle_ctx_destroy(hmle_ctx *c) {
+  if (!c) return;
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
+  for (cudaEvent_t ev : c->prof.ev) cudaEventDestroy(ev);
+  if (c->d_jacobi) cudaFree(c->d_jacobi);
+  if (c->own && c->st) cudaStreamDestroy(c->st);
+  delete c;
+}
+
+const char *hmle_last_error(const hmle_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n, int32_t d,
+                            const hmle_opts *opts_in, hmle_tree **out) {
+  if (!ctx || !locs || !out) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  hmle_opts o;
+  if (opts_in) o = *opts_in; else hmle_opts_default(&o);
+  if (n < 2 || n > (1LL << 30)) return fail(ctx, HMLE_ERR_INVALID_ARG, "n out of range");
+  if (d != 2 && d != 3) return fail(ctx, HMLE_ERR_INVALID_ARG, "d must be 2 or 3");
+  if (o.leaf_size < 8 || o.leaf_size > kMaxLeaf || (o.leaf_size % 16) != 0)
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "leaf_size must be a multiple of 16 in [16, 128]");
+  if (!(o.eta > 0) || !(o.aca_eps > 0) || !(o.aca_eps < 1))
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "eta > 0 and 0 < aca_eps < 1 required");
+  if (o.max_rank < 8 || o.max_rank > 64 || (o.max_rank % 8) != 0)
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "max_rank must be a multiple of 8 in [8, 64]");
+  if (o.oversample < 4 || o.max_rank + o.oversample > 64)
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "oversample >= 4 and max_rank + oversample <= 64");
+  if (o.precision != HMLE_FP64) return fail(ctx, HMLE_ERR_NOT_IMPLEMENTED, "precision");
+  static bool smem_ok = false;
+  if (!smem_ok) {
+    int rc = factor_smem_setup(kMaxLeaf, 64);
+    if (rc) return fail(ctx, HMLE_ERR_CUDA, "cudaFuncSetAttribute failed");
+    smem_ok = true;
+  }
+  cudaStream_t st = ctx->st;
+  // cluster ranges (pure integer, host)
+  int depth = 0;
+  while (((n + (1LL << depth) - 1) >> depth) > o.leaf_size) ++depth;
+  if (depth > kMaxLevels - 2) return fail(ctx, HMLE_ERR_INVALID_ARG, "tree too deep");
+  const int ncl = (2 << depth) - 1;
+  std::vector<int32_t> cb(ncl), ce(ncl);
+  cb[0] = 0; ce[0] = (int32_t)n;
+  for (int h = 0; h < (1 << depth) - 1; ++h) {
+    int32_t b = cb[h], e = ce[h], mid = b + (e - b) / 2;
+    cb[2 * h + 1] = b; ce[2 * h + 1] = mid;
+    cb[2 * h + 2] = mid; ce[2 * h + 2] = e;
+  }
+  hmle_tree *t = new (std::nothrow) hmle_tree();
+  if (!t) return HMLE_ERR_OOM;
+  t->ctx = ctx; t->n = n; t->d = d; t->opts = o;
+  double *rows = nullptr;
+  bool owned = false;
+  hmle_status s = stage_vec(ctx, locs, n * d, &rows, &owned);
+  if (s != HMLE_OK) { delete t; return s; }
+  std::vector<int4> blocks;
+  std::string err = tree_build_device(st, rows, n, d, depth, cb, ce, o.eta, t->T, blocks);
+  if (owned) cudaFreeAsync(rows, st);
+  if (!err.empty()) {
+    hmle_tree_destroy(t);
+    return fail(ctx, err.find("non-finite") != std::string::npos ? HMLE_ERR_INVALID_ARG : HMLE_ERR_CUDA, err);
+  }
+  const int kc = o.max_rank + 16 <= 64 ? o.max_rank + 16 : 64;  // ACA capacity for C
+  err = build_plan(t->plan, (int32_t)n, d, o.leaf_size, depth, cb, ce, blocks, o.max_rank, kc,
+                   o.max_rank + o.oversample, 1);
+  if (!err.empty()) { hmle_tree_destroy(t); return fail(ctx, HMLE_ERR_INVALID_ARG, "planner: " + err); }
+  const Plan &P = t->plan;
+  for (size_t x = 0; x < P.blocks.size(); ++x)
+    (P.blocks[x].kind == kLowRank ? t->lr_ids : t->dense_ids).push_back((int32_t)x);
+  std::vector<int2> dtr(P.dpairs.size()), dtc(P.dpairs.size());
+  for (const DenseTarget &dt : P.dns) {
+    const BlockDesc &T = P.blocks[dt.blk];
+    for (int q = dt.p0; q < dt.p1; ++q) {
+      dtr[q] = make_int2(T.rbeg, T.rend);
+      dtc[q] = make_int2(T.cbeg, T.cend);
+    }
+  }
+  std::vector<int32_t> leaf_beg(P.nleaf + 1);
+  for (int K = 0; K < P.nleaf; ++K) leaf_beg[K] = cb[(1 << depth) - 1 + K];
+  leaf_beg[P.nleaf] = (int32_t)n;
+  DevPlan &dp = t->dp;
+  cudaError_t e = cudaSuccess;
+#define UP(f, v) if (e == cudaSuccess) e = upload(st, &dp.f, v, dp.bytes)
+  UP(blocks, P.blocks); UP(panels, P.panels); UP(grams, P.grams); UP(lrt, P.lrt);
+  UP(aent, P.aent); UP(bent, P.bent); UP(apair, P.apair); UP(bpair, P.bpair);
+  UP(lrpairs, P.lrpairs); UP(arow, P.arow); UP(brow, P.brow); UP(arow_ent, P.arow_ent);
+  UP(brow_ent, P.brow_ent); UP(dns, P.dns); UP(dpairs, P.dpairs); UP(wpan, P.wpan);
+  UP(dpair_tr, dtr); UP(dpair_tc, dtc);
+  UP(hts, P.hts); UP(urows, P.urows); UP(uents, P.uents); UP(leaf_beg, leaf_beg);
+  UP(lr_ids, t->lr_ids); UP(dense_ids, t->dense_ids);
+#undef UP
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { hmle_tree_destroy(t); return cuda_fail(ctx, e, "plan upload"); }
+  *out = t;
+  return HMLE_OK;
+}
+
+void hmle_tree_destroy(hmle_tree *t) {
+  if (!t) return;
+  // the context may already be gone: free synchronously on the legacy stream
+  cudaStream_t st = nullptr;
+  cudaDeviceSynchronize();
+  if (t->work) {
+    free_hm(st, &t->work->H);
+    free_f(st, &t->work->F);
+    if (t->work->zdev) cudaFreeAsync(t->work->zdev, st);
+    delete t->work;
+  }
+  free_devplan(st, t->dp);
+  if (t->T.xyz) cudaFreeAsync(t->T.xyz, st);
+  if (t->T.perm) cudaFreeAsync(t->T.perm, st);
+  if (t->T.box) cudaFreeAsync(t->T.box, st);
+  cudaStreamSynchronize(st);
+  delete t;
+}
+
+hmle_status hmle_tree_get_info(const hmle_tree *t, hmle_tree_info *info) {
+  if (!t || !info) return HMLE_ERR_INVALID_ARG;
+  const Plan &P = t->plan;
+  info->n = t->n;
+  info->d = t->d;
+  info->depth = P.depth;
+  info->n_leaves = P.nleaf;
+  info->n_dense = (int32_t)P.n_dense_blocks;
+  info->n_lowrank = (int32_t)P.n_lr_blocks;
+  info->dense_words = P.dense_words;
+  info->lowrank_words = P.uc_words + P.u_words + P.w_words;
+  info->device_bytes = t->dp.bytes + (int64_t)t->n * (3 * 8 + 4);
+  return HMLE_OK;
+}
+
+hmle_status hmle_tree_permutation(const hmle_tree *t, int32_t *perm) {
+  if (!t || !perm) return HMLE_ERR_INVALID_ARG;
+  hmle_ctx *ctx = t->ctx;
+  CK(cudaMemcpyAsync(perm, t->T.perm, sizeof(int32_t) * t->n, cudaMemcpyDeviceToHost, ctx->st), "perm copy");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  return HMLE_OK;
+}
+
+hmle_status hmle_assemble(hmle_ctx *ctx, const hmle_tree *t, const hmle_theta *th,
+                          hmle_hmatrix **out) {
+  if (!ctx || !t || !out) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  if (!theta_ok(th)) return fail(ctx, HMLE_ERR_INVALID_ARG, "theta out of range");
+  hmle_hmatrix *h = new (std::nothrow) hmle_hmatrix();
+  if (!h) return HMLE_ERR_OOM;
+  hmle_status s = alloc_hm(ctx, t, h);
+  if (s == HMLE_OK) s = do_assemble(ctx, t, th, h);
+  if (s == HMLE_OK) {
+    int fl = 0;
+    cudaError_t e = cudaMemcpyAsync(&fl, h->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    if (e != cudaSuccess) s = cuda_fail(ctx, e, "assemble");
+    else if (fl & kFlagRankOverflow) s = fail(ctx, HMLE_ERR_RANK_OVERFLOW, "ACA did not converge within its capacity");
+  }
+  if (s == HMLE_OK) {
+    double mr;
+    s = rank_stats(ctx, t, h->rank_c, &h->max_rank_c, &mr);
+  }
+  if (s != HMLE_OK) { free_hm(ctx->st, h); delete h; return s; }
+  *out = h;
+  return HMLE_OK;
+}
+
+void hmle_hmatrix_destroy(hmle_hmatrix *h) {
+  if (!h) return;
+  cudaStream_t st = nullptr;
+  cudaDeviceSynchronize();
+  free_hm(st, h);
+  cudaStreamSynchronize(st);
+  delete h;
+}
+
+hmle_status hmle_hmatrix_matvec(hmle_ctx *ctx, const hmle_hmatrix *h, const double *x, double *y) {
+  if (!ctx || !h || !x || !y) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  const hmle_tree *t = h->tree;
+  cudaStream_t st = ctx->st;
+  const int64_t n = t->n;
+  double *xd = nullptr, *xp = nullptr, *yp = nullptr;
+  bool owned = false;
+  hmle_status s = stage_vec(ctx, x, n, &xd, &owned);
+  if (s != HMLE_OK) return s;
+  CK(cudaMallocAsync(&xp, sizeof(double) * n, st), "alloc");
+  CK(cudaMallocAsync(&yp, sizeof(double) * n, st), "alloc");
+  launch_permute_in(st, xd, t->T.perm, n, xp);
+  CK(cudaMemsetAsync(yp, 0, sizeof(double) * n, st), "memset");
+  AsmArgs A{};
+  A.blocks = t->dp.blocks; A.lr_ids = t->dp.lr_ids; A.xyz = t->T.xyz; A.n = n; A.d = t->d;
+  A.tab = h->tab; A.inv_ell = 1.0 / h->th.ell; A.sigma2 = h->th.sigma2; A.tau2 = h->th.tau2;
+  A.kc = t->plan.kc; A.uc = h->uc; A.rank_c = h->rank_c; A.cnorm = h->cnorm; A.flags = h->flags;
+  launch_hmatvec(st, A, t->dp.dense_ids, (int)t->dense_ids.size(), (int)t->lr_ids.size(), xp, yp);
+  // back to caller order: y[perm[k]] = yp[k]
+  std::vector<int32_t> perm(n);
+  std::vector<double> yh(n), out(n);
+  CK(cudaMemcpyAsync(perm.data(), t->T.perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st), "copy");
+  CK(cudaMemcpyAsync(yh.data(), yp, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "copy");
+  CK(cudaStreamSynchronize(st), "sync");
+  for (int64_t k = 0; k < n; ++k) out[perm[k]] = yh[k];
+  if (is_device_ptr(y)) {
+    CK(cudaMemcpyAsync(y, out.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st), "copy");
+  } else {
+    std::memcpy(y, out.data(), sizeof(double) * n);
+  }
+  if (owned) cudaFreeAsync(xd, st);
+  cudaFreeAsync(xp, st);
+  cudaFreeAsync(yp, st);
+  CK(cudaStreamSynchronize(st), "sync");
+  return HMLE_OK;
+}
+
+hmle_status hmle_factor(hmle_ctx *ctx, const hmle_hmatrix *h, const double *Z, hmle_hfactor **out) {
+  if (!ctx || !h || !out) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  const hmle_tree *t = h->tree;
+  hmle_hfactor *f = new (std::nothrow) hmle_hfactor();
+  if (!f) return HMLE_ERR_OOM;
+  hmle_status s = alloc_f(ctx, t, f);
+  double *zd = nullptr;
+  bool owned = false;
+  if (s == HMLE_OK && Z) s = stage_vec(ctx, Z, t->n, &zd, &owned);
+  if (s == HMLE_OK) s = do_factor(ctx, t, h, zd, f);
+  if (owned) cudaFreeAsync(zd, ctx->st);
+  if (s == HMLE_OK) s = rank_stats(ctx, t, f->rank_l, &f->max_rank_l, &f->mean_rank_l);
+  if (s != HMLE_OK) { free_f(ctx->st, f); delete f; return s; }
+  *out = f;
+  return HMLE_OK;
+}
+
+void hmle_factor_destroy(hmle_hfactor *f) {
+  if (!f) return;
+  cudaStream_t st = nullptr;
+  cudaDeviceSynchronize();
+  free_f(st, f);
+  cudaStreamSynchronize(st);
+  delete f;
+}
+
+hmle_status hmle_loglik(hmle_ctx *ctx, const hmle_hfactor *f, const double *Z, double *ll,
+                        double *logdet, double *quad) {
+  if (!ctx || !f || !ll) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  if (!f->has_rhs || Z == nullptr)
+    return fail(ctx, HMLE_ERR_NOT_IMPLEMENTED,
+                "this build fuses the solve into hmle_factor: pass Z to hmle_factor");
+  const double n = (double)f->h->tree->n;
+  *ll = -0.5 * n * std::log(2.0 * M_PI) - 0.5 * f->logdet - 0.5 * f->quad;
+  if (logdet) *logdet = f->logdet;
+  if (quad) *quad = f->quad;
+  return HMLE_OK;
+}
+
+hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tc, const hmle_theta *th,
+                             const double *Z, double *ll, hmle_eval_info *info) {
+  if (!ctx || !tc || !Z || !ll) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  if (!theta_ok(th)) return fail(ctx, HMLE_ERR_INVALID_ARG, "theta out of range");
+  hmle_tree *t = const_cast<hmle_tree *>(tc);
+  hmle_status s = HMLE_OK;
+  if (!t->work) {
+    t->work = new (std::nothrow) Work();
+    if (!t->work) return HMLE_ERR_OOM;
+    s = alloc_hm(ctx, t, &t->work->H);
+    if (s == HMLE_OK) s = alloc_f(ctx, t, &t->work->F);
+    if (s == HMLE_OK) {
+      cudaError_t e = cudaMallocAsync(&t->work->zdev, sizeof(double) * t->n, ctx->st);
+      if (e != cudaSuccess) s = cuda_fail(ctx, e, "alloc z");
+    }
+    if (s != HMLE_OK) {
+      free_hm(ctx->st, &t->work->H);
+      free_f(ctx->st, &t->work->F);
+      delete t->work;
+      t->work = nullptr;
+      return s;
+    }
+  }
+  Work &w = *t->work;
+  const double *zd = Z;
+  if (!is_device_ptr(Z)) {
+    CK(cudaMemcpyAsync(w.zdev, Z, sizeof(double) * t->n, cudaMemcpyHostToDevice, ctx->st), "copy z");
+    zd = w.zdev;
+  }
+  s = do_assemble(ctx, t, th, &w.H);
+  if (s == HMLE_OK) s = do_factor(ctx, t, &w.H, zd, &w.F);
+  const double n = (double)t->n;
+  double L = -0.5 * n * std::log(2.0 * M_PI) - 0.5 * w.F.logdet - 0.5 * w.F.quad;
+  *ll = (s == HMLE_OK) ? L : -INFINITY;
+  if (info) {
+    info->logdet = w.F.logdet;
+    info->quad = w.F.quad;
+    info->loglik = *ll;
+    info->status = s;
+    info->kernel_launches = w.F.launches;
+    double mr = 0;
+    int mx = 0;
+    if (rank_stats(ctx, t, w.H.rank_c, &mx, &mr) == HMLE_OK) info->max_rank_c = mx;
+    if (rank_stats(ctx, t, w.F.rank_l, &mx, &mr) == HMLE_OK) {
+      info->max_rank_l = mx;
+      info->mean_rank_l = mr;
+    }
+  }
+  return s;
+}
+
+hmle_status hmle_matern_eval(hmle_ctx *ctx, double nu, const double *x, int64_t m, double *out) {
+  if (!ctx || !x || !out || m < 0) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  if (!(nu > 0) || !(nu <= 20)) return fail(ctx, HMLE_ERR_INVALID_ARG, "nu out of range");
+  cudaStream_t st = ctx->st;
+  double *tab = nullptr, *xd = nullptr, *od = nullptr;
+  bool owned = false;
+  CK(cudaMallocAsync(&tab, sizeof(double) * kTableWords, st), "alloc");
+  hmle_status s = stage_vec(ctx, x, m, &xd, &owned);
+  if (s != HMLE_OK) return s;
+  CK(cudaMallocAsync(&od, sizeof(double) * std::max<int64_t>(m, 1), st), "alloc");
+  launch_matern_table(st, nu, tab);
+  launch_matern_eval(st, tab, xd, m, od);
+  CK(cudaGetLastError(), "matern launch");
+  CK(cudaMemcpyAsync(out, od, sizeof(double) * m, cudaMemcpyDefault, st), "copy");
+  CK(cudaStreamSynchronize(st), "sync");
+  cudaFreeAsync(tab, st);
+  cudaFreeAsync(od, st);
+  if (owned) cudaFreeAsync(xd, st);
+  CK(cudaStreamSynchronize(st), "sync");
+  return HMLE_OK;
+}
+
+hmle_status hmle_profile_select(hmle_ctx *ctx, const char *kernel) {
+  if (!ctx) return HMLE_ERR_INVALID_ARG;
+  Prof &p = ctx->prof;
+  p.kind = -1;
+  p.used = 0;
+  p.ms = 0.0;
+  p.launches = 0;
+  p.flops = 0.0;
+  if (!kernel) return HMLE_OK;
+  for (int k = 0; k < KK_COUNT; ++k)
+    if (std::strcmp(kernel, kKernelNames[k]) == 0) p.kind = k;
+  return p.kind >= 0 ? HMLE_OK : fail(ctx, HMLE_ERR_INVALID_ARG, "unknown kernel name");
+}
+
+hmle_status hmle_profile_read(hmle_ctx *ctx, double *ms, int64_t *launches, double *flops) {
+  if (!ctx) return HMLE_ERR_INVALID_ARG;
+  if (ms) *ms = ctx->prof.ms;
+  if (launches) *launches = ctx->prof.launches;
+  if (flops) *flops = ctx->prof.flops;
+  return HMLE_OK;
+}
+
+// --- MLE (Sec. 2; transform of Sec. 5) ----------------------------------
+static void to_theta(const double x[4], hmle_theta *t) {
+  double sigma = 2.0 / std::pow(1.1, x[0]);
+  t->ell = 1.0 / std::pow(1.5, x[1]);
+  t->nu = 1.0 / std::pow(1.2, x[2]);
+  double tau = 1.0 / std::pow(2.0, x[3]);
+  t->sigma2 = sigma * sigma;
+  t->tau2 = tau * tau;
+}
+
+static void from_theta(const hmle_theta *t, double x[4]) {
+  x[0] = -std::log(std::sqrt(t->sigma2) / 2.0) / std::log(1.1);
+  x[1] = -std::log(t->ell) / std::log(1.5);
+  x[2] = -std::log(t->nu) / std::log(1.2);
+  x[3] = -std::log(std::sqrt(t->tau2)) / std::log(2.0);
+}
+
+hmle_status hmle_fit(hmle_ctx *ctx, const hmle_tree *t, const double *Z, const hmle_theta *theta0,
+                     const hmle_fit_opts *fo_in, hmle_theta *theta_hat, double *ll_hat,
+                     int32_t *n_iter, int32_t *n_evals) {
+  if (!ctx || !t || !Z || !theta0 || !theta_hat || !ll_hat)
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  if (!theta_ok(theta0) || theta0->sigma2 <= 0 || theta0->tau2 <= 0)
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "theta0 must have sigma2 > 0 and tau2 > 0");
+  hmle_fit_opts fo;
+  if (fo_in) fo = *fo_in; else hmle_fit_opts_default(&fo);
+  double step[4];
+  bool allzero = true;
+  for (int i = 0; i < 4; ++i) { step[i] = fo.step[i]; allzero &= (step[i] == 0.0); }
+  if (allzero) for (int i = 0; i < 4; ++i) step[i] = 1.0;
+  // stage Z once
+  double *zd = nullptr;
+  bool owned = false;
+  hmle_status s = stage_vec(ctx, Z, t->n, &zd, &owned);
+  if (s != HMLE_OK) return s;
+  int nev = 0;
+  hmle_status hard = HMLE_OK;
+  auto f = [&](const double x[4]) -> double {
+    hmle_theta th;
+    to_theta(x, &th);
+    ++nev;
+    if (!theta_ok(&th)) return INFINITY;
+    double ll;
+    hmle_status r = hmle_loglik_eval(ctx, t, &th, zd, &ll, nullptr);
+    if (r == HMLE_OK) return -ll;
+    if (r == HMLE_ERR_NOT_SPD || r == HMLE_ERR_RANK_OVERFLOW) return INFINITY;
+    hard = r;
+    return INFINITY;
+  };
+  double X[5][4], Fv[5];
+  from_theta(theta0, X[0]);
+  for (int i = 1; i < 5; ++i) {
+    for (int j = 0; j < 4; ++j) X[i][j] = X[0][j];
+    X[i][i - 1] += step[i - 1];
+  }
+  for (int i = 0; i < 5 && hard == HMLE_OK; ++i) Fv[i] = f(X[i]);
+  int it = 0;
+  bool conv = false;
+  while (hard == HMLE_OK) {
+    // stable order by f
+    int ord[5] = {0, 1, 2, 3, 4};
+    std::stable_sort(ord, ord + 5, [&](int a, int b) { return Fv[a] < Fv[b]; });
+    double Xs[5][4], Fs[5];
+    for (int i = 0; i < 5; ++i) { Fs[i] = Fv[ord[i]]; for (int j = 0; j < 4; ++j) Xs[i][j] = X[ord[i]][j]; }
+    std::memcpy(X, Xs, sizeof(X));
+    std::memcpy(Fv, Fs, sizeof(Fv));
+    double fs = 0, xs = 0;
+    for (int i = 1; i < 5; ++i) {
+      fs = std::max(fs, std::fabs(Fv[i] - Fv[0]));
+      for (int j = 0; j < 4; ++j) xs = std::max(xs, std::fabs(X[i][j] - X[0][j]));
+    }
+    if (std::isfinite(Fv[4]) && fs <= fo.ftol && xs <= fo.xtol) { conv = true; break; }
+    if (it >= fo.max_iter) break;
+    ++it;
+    double c[4] = {0, 0, 0, 0};
+    for (int i = 0; i < 4; ++i) for (int j = 0; j < 4; ++j) c[j] += X[i][j] / 4.0;
+    double xr[4], xe[4], xc[4];
+    for (int j = 0; j < 4; ++j) xr[j] = c[j] + (c[j] - X[4][j]);
+    double fr = f(xr);
+    if (Fv[0] <= fr && fr < Fv[3]) { std::memcpy(X[4], xr, sizeof(xr)); Fv[4] = fr; continue; }
+    if (fr < Fv[0]) {
+      for (int j = 0; j < 4; ++j) xe[j] = c[j] + 2.0 * (c[j] - X[4][j]);
+      double fe = f(xe);
+      if (fe < fr) { std::memcpy(X[4], xe, sizeof(xe)); Fv[4] = fe; }
+      else { std::memcpy(X[4], xr, sizeof(xr)); Fv[4] = fr; }
+      continue;
+    }
+    if (fr < Fv[4]) {
+      for (int j = 0; j < 4; ++j) xc[j] = c[j] + 0.5 * (xr[j] - c[j]);
+      double fc = f(xc);
+      if (fc <= fr) { std::memcpy(X[4], xc, sizeof(xc)); Fv[4] = fc; continue; }
+    } else {
+      for (int j = 0; j < 4; ++j) xc[j] = c[j] + 0.5 * (X[4][j] - c[j]);
+      double fc = f(xc);
+      if (fc < Fv[4]) { std::memcpy(X[4], xc, sizeof(xc)); Fv[4] = fc; continue; }
+    }
+    for (int i = 1; i < 5; ++i) {
+      for (int j = 0; j < 4; ++j) X[i][j] = X[0][j] + 0.5 * (X[i][j] - X[0][j]);
+      Fv[i] = f(X[i]);
+    }
+  }
+  if (owned) cudaFreeAsync(zd, ctx->st);
+  if (hard != HMLE_OK) return hard;
+  to_theta(X[0], theta_hat);
+  *ll_hat = -Fv[0];
+  if (n_iter) *n_iter = it;
+  if (n_evals) *n_evals = nev;
+  return conv ? HMLE_OK : fail(ctx, HMLE_ERR_NOT_CONVERGED, "max_iter reached");
+}
+
+}  // extern "C"

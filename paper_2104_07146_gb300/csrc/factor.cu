@@ -1,0 +1,1100 @@
+// a6-a11 (Sec. 2): the left-looking leaf sweep of the H-Cholesky
+// factorisation C~ = L~ L~^T with the forward solve w = L~^{-1} P Z fused in.
+//
+// One step K runs these phases (the planner fixes every task list):
+//  P1  k_gram        G_AB = W_A[ov]^T W_B[ov] for pairs of low-rank blocks.
+//  P2  k_side_t/s, k_rows   Y = S_T Omega for every low-rank target T whose
+//      column cluster starts at K, with S_T = C_T - sum_pairs U_A G_AB U_B^T
+//      and Omega a counter-based random sign matrix.
+//  P3  k_tsqr_part, k_tsqr_final, k_tall_apply (twice)   Q = orth(Y): the R
+//      factor of Y by Householder reflections over row groups (TSQR), the
+//      one-sided Jacobi SVD R = U Sigma V^T, and Q = Y V Sigma^{-1}
+//      (directions below 1e-14 of the largest singular value dropped); the
+//      second pass restores orthogonality to rounding level.
+//  P4  as P2 with S_T^T applied to Q: Z = S_T^T Q.
+//  P5  k_tsqr_part, k_tsqr_final (truncating), k_tall_apply   the SVD of Z
+//      from its R factor; keep the leading k with tail energy sum_{i>=k}
+//      sigma_i^2 <= eps^2 max(|S_T|_F^2, |C_T|_F^2): U_T = Q V_k,
+//      W_T = Z V_k (the start of the forward solve of W_T).
+//  P6  k_dense       S_IK = C_IK - sum_pairs U_A G_AB U_B^T for the dense
+//      blocks of column K (diagonal first); C entries from the Matern table.
+//  P7  k_potrf       L_KK = chol(S_KK); log-det part 2 sum log L_ii.
+//  P8  k_trsm        L_IK = S_IK L_KK^{-T}.
+//  P9  k_wsolve      rows of leaf K of every open W-panel: W <- L_KK^{-1} W.
+//  P10 k_htask, k_updrow   blocks A whose columns end at K push
+//      W[rows A] -= U_A (W_A^T W[cols A]) (dense A: D_A W[cols A]) into every
+//      open panel containing them.
+// All FP64.  Every output element is written by exactly one thread, in a
+// fixed order: the sweep is deterministic.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "hmle_internal.h"
+#include "kernels.cuh"
+#include "matern.cuh"
+
+namespace hmle {
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kTM = 64, kTN = 64, kTK = 16;
+constexpr int kGemmSmem = kTK * (kTM + kTN);  // doubles
+
+// C(i, j) = sum_k A(i, k) B(k, j) for i < M, j < N, k < K, delivered to
+// fc(i, j, value).  A_KFAST / B_KFAST: the operand is contiguous along k in
+// memory (chooses the coalesced loading order).  128 threads, 64 x 64
+// output tiles, 4 x 8 register micro-tiles, K staged 16 at a time.
+template <bool A_KFAST, bool B_KFAST, class FA, class FB, class FC>
+__device__ void cta_gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem) {
+  double *sA = smem;
+  double *sB = smem + kTK * kTM;
+  const int tid = threadIdx.x;
+  const int ti = tid & 15, tj = tid >> 4;
+  for (int i0 = 0; i0 < M; i0 += kTM) {
+    for (int j0 = 0; j0 < N; j0 += kTN) {
+      double acc[4][8];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc[x][y] = 0.0;
+      const bool active = (i0 + ti * 4 < M) && (j0 + tj * 8 < N);
+      for (int k0 = 0; k0 < K; k0 += kTK) {
+        for (int e = tid; e < kTK * kTM; e += kThreads) {
+          int k, i;
+          if (A_KFAST) { k = e % kTK; i = e / kTK; } else { i = e % kTM; k = e / kTM; }
+          sA[k * kTM + i] = (i0 + i < M && k0 + k < K) ? fa(i0 + i, k0 + k) : 0.0;
+        }
+        for (int e = tid; e < kTK * kTN; e += kThreads) {
+          int k, j;
+          if (B_KFAST) { k = e % kTK; j = e / kTK; } else { j = e % kTN; k = e / kTN; }
+          sB[k * kTN + j] = (j0 + j < N && k0 + k < K) ? fb(k0 + k, j0 + j) : 0.0;
+        }
+        __syncthreads();
+        if (active) {
+          const int kk = min(kTK, K - k0);
+          for (int k = 0; k < kk; ++k) {
+            double a[4], bb[8];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) a[x] = sA[k * kTM + ti * 4 + x];
+#pragma unroll
+            for (int y = 0; y < 8; ++y) bb[y] = sB[k * kTN + tj * 8 + y];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+              for (int y = 0; y < 8; ++y) acc[x][y] = fma(a[x], bb[y], acc[x][y]);
+          }
+        }
+        __syncthreads();
+      }
+      if (active) {
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) {
+            int i = i0 + ti * 4 + x, j = j0 + tj * 8 + y;
+            if (i < M && j < N) fc(i, j, acc[x][y]);
+          }
+      }
+    }
+  }
+}
+
+// Sample width of the randomised compression of target block blk: the ACA
+// rank of C_T plus the oversampling, capped at r.
+__device__ __forceinline__ int sample_width(const FactorArgs &F, int blk) {
+  int k = F.rank_c[blk];
+  return min(F.r, max(8, k) + F.osamp);
+}
+
+// C(i, j) = sum_k A(k, i) B(k, j) for small outputs (M x N) and long K: the
+// K rows are staged 32 at a time (coalesced along k), warp w takes rows
+// w, w+4, ..., lanes own outputs (up to 16 each per pass), and the four
+// warps' partial sums are added in a fixed order.  smem must hold
+// 32 * (M + N) + 4 * 512 doubles; M + N <= kTnMaxMN.
+constexpr int kTnMaxMN = 192;
+constexpr int kTnSmem = 32 * kTnMaxMN + 4 * 512;
+template <class FA, class FB, class FC>
+__device__ void cta_gemm_tn(int M, int N, int K, FA fa, FB fb, FC fc, double *smem) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  double *sA = smem;                 // 32 x M  (sA[k * M + i])
+  double *sB = smem + 32 * M;        // 32 x N
+  double *part = smem + 32 * (M + N);  // 4 x 512 partial sums
+  const int MN = M * N;
+  for (int o0 = 0; o0 < MN; o0 += 512) {
+    const int no = min(512, MN - o0);
+    double acc[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc[u] = 0.0;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+      const int kk = min(32, K - k0);
+      for (int e = tid; e < 32 * M; e += kThreads) {
+        int k = e & 31, i = e >> 5;
+        sA[k * M + i] = (k < kk) ? fa(k0 + k, i) : 0.0;
+      }
+      for (int e = tid; e < 32 * N; e += kThreads) {
+        int k = e & 31, j = e >> 5;
+        sB[k * N + j] = (k < kk) ? fb(k0 + k, j) : 0.0;
+      }
+      __syncthreads();
+      for (int k = warp; k < kk; k += 4) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          int o = o0 + lane + 32 * u;
+          if (o < o0 + no) {
+            int i = o % M, j = o / M;
+            acc[u] = fma(sA[k * M + i], sB[k * N + j], acc[u]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) part[warp * 512 + lane + 32 * u] = acc[u];
+    __syncthreads();
+    for (int e = tid; e < no; e += kThreads) {
+      double v = ((part[e] + part[512 + e]) + part[1024 + e]) + part[1536 + e];
+      int o = o0 + e;
+      fc(o % M, o / M, v);
+    }
+    __syncthreads();
+  }
+}
+
+// --- block accessors -----------------------------------------------------
+
+struct Acc {
+  const FactorArgs &F;
+  __device__ Acc(const FactorArgs &f) : F(f) {}
+  __device__ int kof(const BlockDesc &B) const { return B.kind == kLowRank ? F.kcap : F.b; }
+  // columns of U_X that can be nonzero: the rank of a low-rank block of L, the
+  // column count of a dense block
+  __device__ int keff(int blk, const BlockDesc &B) const {
+    return B.kind == kLowRank ? F.rank_l[blk] : B.cend - B.cbeg;
+  }
+  // U_X(row, col), row a global point index inside the block's rows
+  __device__ double U(const BlockDesc &B, int row, int col) const {
+    if (B.kind == kLowRank)
+      return F.U[B.off_u + (row - B.rbeg) + (int64_t)col * (B.rend - B.rbeg)];
+    return col < (B.cend - B.cbeg) ? F.D[B.off_d + (row - B.rbeg) + (int64_t)col * F.b] : 0.0;
+  }
+  // W_X(row, col), low-rank X, row a global point index inside the columns
+  __device__ double W(const BlockDesc &B, int row, int col) const {
+    const PanelDesc &P = F.panels[B.panel];
+    return F.W[P.off + (row - P.rbeg) + (int64_t)(B.slot + col) * (P.rend - P.rbeg)];
+  }
+  __device__ double *Wp(int panel, int row, int col) const {
+    const PanelDesc &P = F.panels[panel];
+    return F.W + P.off + (row - P.rbeg) + (int64_t)col * (P.rend - P.rbeg);
+  }
+};
+
+// --- P1 -------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_gram(FactorArgs F, int g0) {
+  extern __shared__ double smem[];
+  Acc a(F);
+  const GramTask g = F.grams[g0 + blockIdx.x];
+  const BlockDesc A = F.blocks[g.a], B = F.blocks[g.b];
+  double *out = F.ws + g.goff;
+  const int kc = F.kcap;
+  cta_gemm_tn(
+      F.rank_l[g.a], F.rank_l[g.b], g.ove - g.ovb, [&](int k, int i) { return a.W(A, g.ovb + k, i); },
+      [&](int k, int j) { return a.W(B, g.ovb + k, j); },
+      [&](int i, int j, double v) { out[i + (int64_t)j * kc] = v; }, smem);
+}
+
+// --- P2a / P4a: t = U_X[rows]^T X[rows] for side entries; t_C for targets --
+// trans = 0: B-entries against Omega (rows in sigma), t_C = V_C^T Omega.
+// trans = 1: A-entries against Q (rows in rho), t_C = U_C^T Q.
+__global__ void __launch_bounds__(kThreads) k_side_t(FactorArgs F, int e0, int ne, int t0, int trans) {
+  extern __shared__ double smem[];
+  Acc a(F);
+  if ((int)blockIdx.x < ne) {
+    const SideEntry E = trans ? F.aent[e0 + blockIdx.x] : F.bent[e0 + blockIdx.x];
+    const LrTarget L = F.lrt[E.target];
+    const int r = sample_width(F, L.blk);
+    const BlockDesc T = F.blocks[L.blk];
+    const BlockDesc X = F.blocks[E.blk];
+    const int cb = trans ? T.rbeg : T.cbeg, ce = trans ? T.rend : T.cend;
+    const int lo = max(cb, X.rbeg), hi = min(ce, X.rend);
+    const int k = a.kof(X), ke = a.keff(E.blk, X);
+    double *t = F.ws + E.toff;
+    const double *Q = F.ws + L.yoff;
+    const uint64_t seed = F.seed;
+    const int64_t tb = L.blk;
+    if (trans) {
+      cta_gemm_tn(
+          ke, r, hi - lo, [&](int kk, int i) { return a.U(X, lo + kk, i); },
+          [&](int kk, int j) { return Q[(lo + kk - cb) + (int64_t)j * L.m]; },
+          [&](int i, int j, double v) { t[i + (int64_t)j * k] = v; }, smem);
+    } else {
+      cta_gemm_tn(
+          ke, r, hi - lo, [&](int kk, int i) { return a.U(X, lo + kk, i); },
+          [&](int kk, int j) { return rademacher(seed, tb, lo + kk - cb, j); },
+          [&](int i, int j, double v) { t[i + (int64_t)j * k] = v; }, smem);
+    }
+  } else {
+    const LrTarget L = F.lrt[t0 + blockIdx.x - ne];
+    const BlockDesc T = F.blocks[L.blk];
+    const int r = sample_width(F, L.blk);
+    const int kc = F.kc, kce = F.rank_c[L.blk];
+    const double *UC = F.uc + (trans ? T.off_uc : T.off_vc);
+    const int ld = trans ? L.m : L.p;
+    double *tc = F.ws + L.tcoff;
+    const double *Q = F.ws + L.yoff;
+    const uint64_t seed = F.seed;
+    const int64_t tb = L.blk;
+    if (trans) {
+      cta_gemm_tn(
+          kce, r, L.m, [&](int kk, int i) { return UC[kk + (int64_t)i * ld]; },
+          [&](int kk, int j) { return Q[kk + (int64_t)j * L.m]; },
+          [&](int i, int j, double v) { tc[i + (int64_t)j * kc] = v; }, smem);
+    } else {
+      cta_gemm_tn(
+          kce, r, L.p, [&](int kk, int i) { return UC[kk + (int64_t)i * ld]; },
+          [&](int kk, int j) { return rademacher(seed, tb, kk, j); },
+          [&](int i, int j, double v) { tc[i + (int64_t)j * kc] = v; }, smem);
+    }
+  }
+}
+
+// --- P2b / P4b: s_X = sum over the entry's pairs of G (or G^T) t_partner ---
+__global__ void __launch_bounds__(kThreads) k_side_s(FactorArgs F, int e0, int trans) {
+  extern __shared__ double smem[];
+  Acc a(F);
+  const int kc = F.kcap;
+  const SideEntry E = trans ? F.bent[e0 + blockIdx.x] : F.aent[e0 + blockIdx.x];
+  const int r = sample_width(F, F.lrt[E.target].blk);
+  const BlockDesc X = F.blocks[E.blk];
+  const int kx = a.kof(X), kxe = a.keff(E.blk, X);
+  double *s = F.ws + E.soff;
+  for (int i = threadIdx.x; i < kx * r; i += blockDim.x) s[i] = 0.0;
+  __syncthreads();
+  const int32_t *plist = trans ? F.bpair : F.apair;
+  for (int q = E.p0; q < E.p1; ++q) {
+    const LrPair P = F.lrpairs[plist[q]];
+    const SideEntry O = trans ? F.aent[P.ae] : F.bent[P.be];  // partner entry
+    const BlockDesc Y = F.blocks[O.blk];
+    const BlockDesc &A = trans ? Y : X;   // A side of the pair
+    const BlockDesc &B = trans ? X : Y;   // B side of the pair
+    const int ky = a.kof(Y), kye = a.keff(O.blk, Y);
+    const double *t = F.ws + O.toff;      // ky x r
+    auto add = [&](int i, int j, double v) { s[i + (int64_t)j * kx] += v; };
+    auto tt = [&](int k, int j) { return t[k + (int64_t)j * ky]; };
+    if (A.kind == kLowRank && B.kind == kLowRank) {
+      const double *G = F.ws + P.goff;    // kcap x kcap, G_AB
+      if (!trans)
+        cta_gemm<false, true>(kxe, r, kye, [&](int i, int k) { return G[i + (int64_t)k * kc]; },
+                              tt, add, smem);
+      else
+        cta_gemm<true, true>(kxe, r, kye, [&](int i, int k) { return G[k + (int64_t)i * kc]; },
+                             tt, add, smem);
+    } else if (A.kind == kDense && B.kind == kLowRank) {
+      // G = W_B[J_A] (b x kcap)
+      const int J0 = A.cbeg, nj = A.cend - A.cbeg;
+      if (!trans)  // s_A (b x r) += W_B[J_A] t_B
+        cta_gemm<false, true>(
+            nj, r, kye, [&](int i, int k) { return a.W(B, J0 + i, k); }, tt, add, smem);
+      else  // s_B (kcap x r) += W_B[J_A]^T t_A
+        cta_gemm<true, true>(
+            kxe, r, nj, [&](int i, int k) { return a.W(B, J0 + k, i); }, tt, add, smem);
+    } else if (A.kind == kLowRank && B.kind == kDense) {
+      // G = W_A[J_B]^T (kcap x b)
+      const int J0 = B.cbeg, nj = B.cend - B.cbeg;
+      if (!trans)  // s_A (kcap x r) += W_A[J_B]^T t_B
+        cta_gemm<true, true>(
+            kxe, r, nj, [&](int i, int k) { return a.W(A, J0 + k, i); }, tt, add, smem);
+      else  // s_B (b x r) += W_A[J_B] t_A
+        cta_gemm<false, true>(
+            nj, r, kye, [&](int i, int k) { return a.W(A, J0 + i, k); }, tt, add, smem);
+    } else {
+      const int nj = A.cend - A.cbeg;
+      for (int i = threadIdx.x; i < nj * r; i += blockDim.x) {
+        int ii = i % nj, jj = i / nj;
+        s[ii + (int64_t)jj * kx] += t[ii + (int64_t)jj * ky];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// --- P2c / P4c: rows of Y (or Z) of one leaf --------------------------------
+__global__ void __launch_bounds__(kThreads) k_rows(FactorArgs F, int rt0, int trans) {
+  extern __shared__ double smem[];
+  Acc a(F);
+  const int kc = F.kc;
+  const RowTask R = trans ? F.brow[rt0 + blockIdx.x] : F.arow[rt0 + blockIdx.x];
+  const LrTarget L = F.lrt[R.target];
+  const int r = sample_width(F, L.blk);
+  const BlockDesc T = F.blocks[L.blk];
+  const int I0 = F.leaf_beg[R.leaf], I1 = F.leaf_beg[R.leaf + 1];
+  const int base = trans ? T.cbeg : T.rbeg;
+  const int ld = trans ? L.p : L.m;
+  double *Y = F.ws + (trans ? L.zoff : L.yoff);
+  const double *UC = F.uc + (trans ? T.off_vc : T.off_uc);
+  const double *tc = F.ws + L.tcoff;
+  const int mi = I1 - I0;
+  cta_gemm<false, true>(
+      mi, r, F.rank_c[L.blk], [&](int i, int k) { return UC[(I0 - base + i) + (int64_t)k * ld]; },
+      [&](int k, int j) { return tc[k + (int64_t)j * kc]; },
+      [&](int i, int j, double v) { Y[(I0 - base + i) + (int64_t)j * ld] = v; }, smem);
+  const int32_t *ents = trans ? F.brow_ent : F.arow_ent;
+  for (int q = R.e0; q < R.e1; ++q) {
+    const SideEntry E = trans ? F.bent[ents[q]] : F.aent[ents[q]];
+    const BlockDesc X = F.blocks[E.blk];
+    const int kx = a.kof(X);
+    const double *s = F.ws + E.soff;
+    __syncthreads();
+    cta_gemm<false, true>(
+        mi, r, a.keff(E.blk, X), [&](int i, int k) { return a.U(X, I0 + i, k); },
+        [&](int k, int j) { return s[k + (int64_t)j * kx]; },
+        [&](int i, int j, double v) { Y[(I0 - base + i) + (int64_t)j * ld] -= v; }, smem);
+  }
+}
+
+// --- tall QR (R factor only) and SVD of the small R -----------------------
+constexpr int kQrRows = 64;
+
+// Householder QR of the h x r column-major matrix A (ld h, h >= r) in shared
+// memory, in place: on return rows 0..r-1 hold R in their upper triangle
+// (the entries below the diagonal hold reflector data).
+__device__ void smem_householder(double *A, int h, int r, double *red) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = 0; j < r && j < h; ++j) {
+    double s = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < h; i += blockDim.x) s = fma(A[i + j * h], A[i + j * h], s);
+    s = block_sum(s, red);
+    if (!(s > 0.0)) continue;  // nothing below the diagonal (uniform branch)
+    if (threadIdx.x == 0) {    // reflector scalars, computed once
+      const double alpha = A[j + j * h];
+      const double nrm = sqrt(fma(alpha, alpha, s));
+      const double beta = alpha >= 0.0 ? -nrm : nrm;
+      red[0] = (beta - alpha) / beta;
+      red[1] = 1.0 / (alpha - beta);
+      red[2] = beta;
+    }
+    __syncthreads();
+    const double tau = red[0], scal = red[1], beta = red[2];
+    for (int i = j + 1 + threadIdx.x; i < h; i += blockDim.x) A[i + j * h] *= scal;
+    __syncthreads();
+    for (int c = j + 1 + warp; c < r; c += nw) {
+      double w = 0.0;
+      for (int i = j + 1 + lane; i < h; i += 32) w = fma(A[i + j * h], A[i + c * h], w);
+      w = warp_sum(w);
+      w = tau * (w + A[j + c * h]);
+      if (lane == 0) A[j + c * h] -= w;
+      for (int i = j + 1 + lane; i < h; i += 32) A[i + c * h] = fma(-w, A[i + j * h], A[i + c * h]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) A[j + j * h] = beta;
+    __syncthreads();
+  }
+}
+
+// R factor of one row group of a target's Y (which = 0) or Z (which = 1):
+// rows are streamed 64 at a time below the running R, each block
+// re-triangularised by Householder reflections.
+__global__ void __launch_bounds__(kThreads) k_tsqr_part(FactorArgs F, int t0, int which) {
+  extern __shared__ double smem[];
+  __shared__ double red[32];
+  const LrTarget L = F.lrt[t0 + blockIdx.x];
+  const int m = which ? L.p : L.m;
+  const int G = which ? L.gp : L.gm;
+  const int g = blockIdx.y;
+  if (g >= G) return;
+  const int r = sample_width(F, L.blk);
+  const int h = r + kQrRows;
+  const double *X = F.ws + (which ? L.zoff : L.yoff);
+  const int len = (m + G - 1) / G;
+  const int r0 = g * len, r1 = min(m, r0 + len);
+  double *A = smem;  // h x r
+  for (int e = threadIdx.x; e < h * r; e += blockDim.x) A[e] = 0.0;
+  __syncthreads();
+  for (int b0 = r0; b0 < r1; b0 += kQrRows) {
+    const int rows = min(kQrRows, r1 - b0);
+    for (int e = threadIdx.x; e < kQrRows * r; e += blockDim.x) {
+      int i = e % kQrRows, c = e / kQrRows;
+      A[(r + i) + c * h] = (i < rows) ? X[(b0 + i) + (int64_t)c * m] : 0.0;
+    }
+    // clear reflector data left below the diagonal of R
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      int i = e % r, c = e / r;
+      if (i > c) A[i + c * h] = 0.0;
+    }
+    __syncthreads();
+    smem_householder(A, h, r, red);
+  }
+  double *R = F.ws + L.roff + (int64_t)g * r * r;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    int i = e % r, c = e / r;
+    R[e] = (i <= c) ? A[i + c * h] : 0.0;
+  }
+}
+
+// Combine the row groups' R factors, then the one-sided Jacobi SVD
+// R = U Sigma V^T.  mode 0 (orthonormalise): M = V Sigma^{-1} on singular
+// values above 1e-14 of the largest (zero columns otherwise).  mode 1
+// (truncate): k = smallest rank whose tail energy sum_{i>=k} sigma_i^2 is
+// <= eps^2 max(sum sigma_i^2, |C_T|_F^2); M = V_k (r x kcap); rank to rank_l.
+__global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, int which, int mode) {
+  extern __shared__ double smem[];
+  __shared__ double red[32];
+  __shared__ int s_rot;
+  __shared__ int ord[kMaxSample + 2];
+  __shared__ double sig[kMaxSample + 2];
+  __shared__ int s_rank;
+  const LrTarget L = F.lrt[t0 + blockIdx.x];
+  const int G = which ? L.gp : L.gm;
+  const int r = sample_width(F, L.blk);
+  const int ldm = F.r;                  // leading dimension of M in the workspace
+  const int h = r + kQrRows;
+  const int lb = r | 1;          // odd leading dimension: lane-per-column access is conflict free
+  double *A = smem;              // h x r
+  double *B = A + h * r;         // r x r (columns rotated), ld lb
+  double *V = B + lb * r;        // r x r, ld lb
+  for (int e = threadIdx.x; e < h * r; e += blockDim.x) A[e] = 0.0;
+  __syncthreads();
+  const int per = kQrRows / r > 0 ? kQrRows / r : 1;
+  for (int g0 = 0; g0 < G; g0 += per) {
+    const int cnt = min(per, G - g0);
+    for (int e = threadIdx.x; e < kQrRows * r; e += blockDim.x) {
+      int i = e % kQrRows, c = e / kQrRows;
+      int gg = g0 + i / r, ii = i % r;
+      A[(r + i) + c * h] = (i / r < cnt) ? F.ws[L.roff + (int64_t)gg * r * r + ii + c * r] : 0.0;
+    }
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      int i = e % r, c = e / r;
+      if (i > c) A[i + c * h] = 0.0;
+    }
+    __syncthreads();
+    smem_householder(A, h, r, red);
+  }
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    int i = e % r, c = e / r;
+    B[i + c * lb] = (i <= c) ? A[i + c * h] : 0.0;
+    V[i + c * lb] = (i == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // one-sided Jacobi on the columns of B (R V = B): one warp, one lane per
+  // column pair of a round (disjoint pairs of a round-robin tournament), so
+  // every FP64 instruction works on all lanes
+  const int rp = r + (r & 1), half = rp / 2;
+  double fro = 0.0;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    double v = B[e % r + (e / r) * lb];
+    fro = fma(v, v, fro);
+  }
+  fro = block_sum(fro, red);
+  const double tiny = 1e-30 * fro;     // columns below eps |R|_F are zero
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double jf = 0.0;                    // FP64 flops of this lane's pair work
+    for (int sweep = 0; sweep < 40; ++sweep) {
+      int rotated = 0;
+      for (int round = 0; round < rp - 1; ++round) {
+        if (lane < half) {
+          int p = (lane == 0) ? 0 : 1 + (lane - 1 + round) % (rp - 1);
+          int q = 1 + (rp - 2 - lane + round) % (rp - 1);
+          if (p > q) { int t = p; p = q; q = t; }
+          if (q < r) {
+            jf += 6.0 * r;
+            double al = 0.0, be = 0.0, ga = 0.0;
+            for (int i = 0; i < r; ++i) {
+              double bp = B[i + p * lb], bq = B[i + q * lb];
+              al = fma(bp, bp, al);
+              be = fma(bq, bq, be);
+              ga = fma(bp, bq, ga);
+            }
+            if (al > tiny && be > tiny && fabs(ga) > 1e-13 * sqrt(al * be)) {
+              double zeta = (be - al) / (2.0 * ga);
+              double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+              double c = 1.0 / sqrt(fma(t, t, 1.0)), sn = c * t;
+              for (int i = 0; i < r; ++i) {
+                double bp = B[i + p * lb], bq = B[i + q * lb];
+                B[i + p * lb] = c * bp - sn * bq;
+                B[i + q * lb] = sn * bp + c * bq;
+                double vp = V[i + p * lb], vq = V[i + q * lb];
+                V[i + p * lb] = c * vp - sn * vq;
+                V[i + q * lb] = sn * vp + c * vq;
+              }
+              rotated = 1;
+              jf += 12.0 * r + 30.0;
+            }
+          }
+        }
+        __syncwarp();
+      }
+      if (!__any_sync(0xffffffffu, rotated)) break;
+    }
+    jf = warp_sum(jf);
+    if (lane == 0 && F.jacobi_flops) atomicAdd(F.jacobi_flops, jf);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < r; c += blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < r; ++i) s = fma(B[i + c * lb], B[i + c * lb], s);
+    sig[c] = sqrt(s);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < r; ++i) ord[i] = i;
+    for (int i = 0; i < r; ++i) {
+      int best = i;
+      for (int j = i + 1; j < r; ++j)
+        if (sig[ord[j]] > sig[ord[best]]) best = j;
+      int t = ord[i]; ord[i] = ord[best]; ord[best] = t;
+    }
+    if (mode == 1) {
+      // truncate relative to the larger of |S| and |C_block|: C~ itself is
+      // only accurate to eps |C_block| (ACA), so smaller singular values of
+      // the updated block are noise
+      double total = 0.0;
+      for (int i = 0; i < r; ++i) total += sig[i] * sig[i];
+      const double cn = F.cnorm[L.blk];
+      const double thr = F.eps * F.eps * fmax(total, cn * cn);
+      int k = r;
+      double tail = 0.0;
+      while (k > 0) {
+        double s2 = sig[ord[k - 1]] * sig[ord[k - 1]];
+        if (tail + s2 > thr) break;
+        tail += s2;
+        --k;
+      }
+      if (!(total > 0.0)) k = 0;
+      if (k > F.kcap) { raise_flag(F.flags, kFlagRankOverflow); k = F.kcap; }
+      // too few samples left to trust the numerical rank
+      if (k > r - F.osamp / 2) raise_flag(F.flags, kFlagRankOverflow);
+      s_rank = k;
+      F.rank_l[L.blk] = k;
+    }
+  }
+  __syncthreads();
+  double *M = F.ws + L.soff + ldm * ldm;
+  if (mode == 0) {
+    __shared__ double rinv[kMaxSample + 2];
+    const double smax = sig[ord[0]];
+    for (int c = threadIdx.x; c < r; c += blockDim.x) {   // one reciprocal per column
+      double sc = sig[ord[c]];
+      rinv[c] = (sc > 1e-14 * smax && sc > 0.0) ? 1.0 / sc : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {      // kept columns come first (descending order)
+      int k1 = 0;
+      while (k1 < r && rinv[k1] != 0.0) ++k1;
+      F.kept[t0 + blockIdx.x] = k1;
+    }
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      int i = e % r, c = e / r;
+      M[i + c * ldm] = V[i + ord[c] * lb] * rinv[c];
+    }
+  } else {
+    const int k = s_rank, kc = F.kcap;
+    for (int e = threadIdx.x; e < r * kc; e += blockDim.x) {
+      int i = e % r, c = e / r;
+      M[i + c * ldm] = (c < k) ? V[i + ord[c] * lb] : 0.0;
+    }
+  }
+}
+
+// Re-orthonormalisation of Q1 = Y V Sigma^{-1} (nearly orthonormal kept
+// columns): partial Grams Q1_g^T Q1_g of the row groups ...
+__global__ void __launch_bounds__(kThreads) k_cholqr_part(FactorArgs F, int t0) {
+  extern __shared__ double smem[];
+  const LrTarget L = F.lrt[t0 + blockIdx.x];
+  const int G = L.gm, g = blockIdx.y;
+  if (g >= G) return;
+  const int r = sample_width(F, L.blk);
+  const int k1 = F.kept[t0 + blockIdx.x];
+  const int m = L.m, len = (m + G - 1) / G;
+  const int r0 = g * len, r1 = min(m, r0 + len);
+  const double *Q = F.ws + L.yoff;
+  double *out = F.ws + L.roff + (int64_t)g * r * r;
+  cta_gemm_tn(
+      k1, k1, max(r1 - r0, 0), [&](int k, int i) { return Q[(r0 + k) + (int64_t)i * m]; },
+      [&](int k, int j) { return Q[(r0 + k) + (int64_t)j * m]; },
+      [&](int i, int j, double v) { out[i + j * r] = v; }, smem);
+}
+
+// ... then G = sum_g, G = R^T R (Cholesky), M = R^{-1} (k1 x k1, zero
+// elsewhere) so that Q = Q1 M.
+__global__ void __launch_bounds__(kThreads) k_cholqr_final(FactorArgs F, int t0) {
+  extern __shared__ double smem[];
+  __shared__ double s_inv;
+  const LrTarget L = F.lrt[t0 + blockIdx.x];
+  const int r = sample_width(F, L.blk), ldm = F.r;
+  const int k1 = F.kept[t0 + blockIdx.x];
+  double *Gs = smem;              // k1 x k1, ld r
+  double *Ri = smem + r * r;      // R^{-1}, ld r
+  for (int e = threadIdx.x; e < k1 * k1; e += blockDim.x) {
+    int i = e % k1, j = e / k1;
+    double v = 0.0;
+    for (int g = 0; g < L.gm; ++g) v += F.ws[L.roff + (int64_t)g * r * r + i + j * r];
+    Gs[i + j * r] = v;
+  }
+  __syncthreads();
+  // Cholesky G = R^T R, R upper: column-oriented on the lower factor L = R^T
+  for (int j = 0; j < k1; ++j) {
+    if (threadIdx.x == 0) {
+      double d = Gs[j + j * r];
+      double l = sqrt(d > 0.0 ? d : 1.0);
+      if (!(d > 0.0)) raise_flag(F.flags, kFlagNonFinite);
+      Gs[j + j * r] = l;
+      s_inv = 1.0 / l;
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < k1; i += blockDim.x) Gs[i + j * r] *= s_inv;
+    __syncthreads();
+    const int nt = k1 - j - 1;
+    for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
+      int i = j + 1 + e % nt, l = j + 1 + e / nt;
+      if (l <= i) Gs[i + l * r] = fma(-Gs[i + j * r], Gs[l + j * r], Gs[i + l * r]);
+    }
+    __syncthreads();
+  }
+  // inverse of the lower factor Lc (Lc Lc^T = G); R = Lc^T, so R^{-1} = (Lc^{-1})^T.
+  // Column c of Lc^{-1} by forward substitution (one thread per column).
+  for (int c = threadIdx.x; c < k1; c += blockDim.x) {
+    for (int i = 0; i < k1; ++i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int l = c; l < i; ++l) v = fma(-Gs[i + l * r], Ri[l + c * r], v);
+      Ri[i + c * r] = (i < c) ? 0.0 : v / Gs[i + i * r];
+    }
+  }
+  __syncthreads();
+  double *M = F.ws + L.soff + ldm * ldm;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    int i = e % r, j = e / r;     // M = (Lc^{-1})^T: M(i, j) = Ri(j, i)
+    M[i + j * ldm] = (i < k1 && j < k1) ? Ri[j + i * r] : 0.0;
+  }
+}
+
+// mode 0: Y <- Y M in place (r columns) for row chunk blockIdx.y.
+// mode 1: U_T = Q V_k (rows of rho) and W_T = Z V_k (rows of sigma); the
+//         chunk index runs over rho's chunks, then sigma's.
+__global__ void __launch_bounds__(kThreads) k_tall_apply(FactorArgs F, int t0, int mode) {
+  extern __shared__ double smem[];
+  Acc a(F);
+  const LrTarget L = F.lrt[t0 + blockIdx.x];
+  const BlockDesc T = F.blocks[L.blk];
+  const int r = sample_width(F, L.blk), ldm = F.r, kc = F.kcap;
+  const double *M = F.ws + L.soff + ldm * ldm;
+  const int chunk = blockIdx.y;
+  if (mode == 0) {
+    const int i0 = chunk * kTM;
+    if (i0 >= L.m) return;
+    const int mi = min(kTM, L.m - i0);
+    double *Y = F.ws + L.yoff;
+    cta_gemm<false, false>(
+        mi, r, r, [&](int i, int k) { return Y[(i0 + i) + (int64_t)k * L.m]; },
+        [&](int k, int j) { return M[k + j * ldm]; },
+        [&](int i, int j, double v) { Y[(i0 + i) + (int64_t)j * L.m] = v; }, smem);
+  } else {
+    const int nch_m = (L.m + kTM - 1) / kTM;
+    const int nch_p = (L.p + kTM - 1) / kTM;
+    if (chunk < nch_m) {
+      const int i0 = chunk * kTM, mi = min(kTM, L.m - i0);
+      const double *Q = F.ws + L.yoff;
+      double *U = F.U + T.off_u;
+      cta_gemm<false, false>(
+          mi, kc, r, [&](int i, int k) { return Q[(i0 + i) + (int64_t)k * L.m]; },
+          [&](int k, int j) { return M[k + j * ldm]; },
+          [&](int i, int j, double v) { U[(i0 + i) + (int64_t)j * L.m] = v; }, smem);
+    } else if (chunk < nch_m + nch_p) {
+      const int i0 = (chunk - nch_m) * kTM, mi = min(kTM, L.p - i0);
+      const double *Z = F.ws + L.zoff;
+      cta_gemm<false, false>(
+          mi, kc, r, [&](int i, int k) { return Z[(i0 + i) + (int64_t)k * L.p]; },
+          [&](int k, int j) { return M[k + j * ldm]; },
+          [&](int i, int j, double v) { *a.Wp(T.panel, T.cbeg + i0 + i, T.slot + j) = v; },
+          smem);
+    }
+  }
+}
+
+// --- P6: dense targets of column K -----------------------------------------
+// k_dense_pair: one CTA per pair (A, B) of the step's dense targets writes
+// P = U_A G_AB U_B^T restricted to the target (m x p, ld b) into the step's
+// workspace; k_dense_reduce: S = C_IK - sum of the target's P in pair order.
+__global__ void __launch_bounds__(kThreads) k_dense_pair(FactorArgs F, int q0, int64_t dpws) {
+  extern __shared__ double smem[];
+  Acc a(F);
+  const int b = F.b, kc = F.kcap;
+  const int q = q0 + blockIdx.x;
+  const DPair Pq = F.dpairs[q];
+  const BlockDesc A = F.blocks[Pq.a], B = F.blocks[Pq.b];
+  double *out = F.ws + dpws + (int64_t)blockIdx.x * b * b;
+  // the target's rows and columns (point ranges), stored per pair
+  const int tr0 = F.dpair_tr[q].x, m = F.dpair_tr[q].y - F.dpair_tr[q].x;
+  const int tc0 = F.dpair_tc[q].x, p = F.dpair_tc[q].y - F.dpair_tc[q].x;
+  double *X = smem + kGemmSmem;  // up to max(kcap, b) x b, ld ldx
+  const int ldx = max(b, kc);
+  auto put = [&](int i, int j, double v) { out[i + (int64_t)j * b] = v; };
+  if (A.kind == kDense && B.kind == kDense) {
+    const int nj = A.cend - A.cbeg;
+    cta_gemm<false, true>(
+        m, p, nj, [&](int i, int k) { return a.U(A, tr0 + i, k); },
+        [&](int k, int j) { return a.U(B, tc0 + j, k); }, put, smem);
+    return;
+  }
+  int kx;
+  if (A.kind == kLowRank && B.kind == kLowRank) {
+    kx = F.rank_l[Pq.a];
+    const int kb = F.rank_l[Pq.b];
+    const double *G = F.ws + Pq.goff;
+    cta_gemm<false, true>(
+        kx, p, kb, [&](int i, int k) { return G[i + (int64_t)k * kc]; },
+        [&](int k, int j) { return a.U(B, tc0 + j, k); },
+        [&](int i, int j, double v) { X[i + j * ldx] = v; }, smem);
+  } else if (A.kind == kDense) {  // B low-rank: X = W_B[J_A] U_B[K]^T
+    kx = A.cend - A.cbeg;
+    const int J0 = A.cbeg;
+    cta_gemm<false, true>(
+        kx, p, F.rank_l[Pq.b], [&](int i, int k) { return a.W(B, J0 + i, k); },
+        [&](int k, int j) { return a.U(B, tc0 + j, k); },
+        [&](int i, int j, double v) { X[i + j * ldx] = v; }, smem);
+  } else {  // A low-rank, B dense: X = W_A[J_B]^T D_B^T
+    kx = F.rank_l[Pq.a];
+    const int J0 = B.cbeg, nj = B.cend - B.cbeg;
+    cta_gemm<true, true>(
+        kx, p, nj, [&](int i, int k) { return a.W(A, J0 + k, i); },
+        [&](int k, int j) { return a.U(B, tc0 + j, k); },
+        [&](int i, int j, double v) { X[i + j * ldx] = v; }, smem);
+  }
+  __syncthreads();
+  const int kxx = kx;
+  cta_gemm<false, false>(
+      m, p, kxx, [&](int i, int k) { return a.U(A, tr0 + i, k); },
+      [&](int k, int j) { return X[k + j * ldx]; }, put, smem);
+}
+
+__global__ void __launch_bounds__(kThreads) k_dense_reduce(FactorArgs F, int d0, int64_t dpws) {
+  const int b = F.b;
+  const DenseTarget DT = F.dns[d0 + blockIdx.x];
+  const BlockDesc T = F.blocks[DT.blk];
+  const int m = T.rend - T.rbeg, p = T.cend - T.cbeg;
+  const int q0 = F.dns[d0].p0;
+  double *S = F.D + T.off_d;
+  const ThetaDev th = *F.th;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    int i = e % b, j = e / b;
+    double v = 0.0;
+    if (i < m && j < p) {
+      v = cov_entry(F.tab, F.xyz, F.n, F.d, T.rbeg + i, T.cbeg + j, th.inv_ell, th.sigma2, th.tau2);
+      for (int q = DT.p0; q < DT.p1; ++q) v -= F.ws[dpws + (int64_t)(q - q0) * b * b + e];
+    }
+    S[e] = v;
+  }
+}
+
+// --- P7: Cholesky of the diagonal leaf ------------------------------------
+__global__ void __launch_bounds__(kThreads) k_potrf(FactorArgs F, int d0, int K) {
+  extern __shared__ double smem[];
+  const int b = F.b;
+  const DenseTarget DT = F.dns[d0];
+  const BlockDesc T = F.blocks[DT.blk];
+  const int m = T.rend - T.rbeg;
+  double *G = F.D + T.off_d;
+  double *A = smem;  // m x m, ld b
+  __shared__ double red[32];
+  __shared__ int bad;
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) bad = 0;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) A[e] = G[e];
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    if (threadIdx.x == 0) {
+      double djj = A[j + j * b];
+      if (!(djj > 0.0) || !isfinite(djj)) { bad = 1; djj = 1.0; }
+      double l = sqrt(djj);
+      A[j + j * b] = l;
+      s_inv = 1.0 / l;
+    }
+    __syncthreads();
+    const double inv = s_inv;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[i + j * b] *= inv;
+    __syncthreads();
+    const int nt = m - j - 1;
+    for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
+      int i = j + 1 + e % nt, l = j + 1 + e / nt;
+      if (l <= i) A[i + l * b] = fma(-A[i + j * b], A[l + j * b], A[i + l * b]);
+    }
+    __syncthreads();
+  }
+  double s = 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) s += log(A[j + j * b]);
+  s = block_sum(s, red);
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    int i = e % b, l = e / b;
+    G[e] = (i >= l && i < m) ? A[e] : 0.0;
+  }
+  if (threadIdx.x == 0) {
+    F.logdet_parts[K] = 2.0 * s;
+    if (bad) raise_flag(F.flags, kFlagNotSpd);
+  }
+}
+
+// --- P8: off-diagonal dense blocks of column K: X = S L^{-T} ---------------
+__global__ void __launch_bounds__(kThreads) k_trsm(FactorArgs F, int d0, int K) {
+  extern __shared__ double smem[];
+  const int b = F.b;
+  const BlockDesc Dg = F.blocks[F.dns[d0].blk];
+  const int mk = Dg.rend - Dg.rbeg;
+  double *Lk = smem;  // b x b
+  double *rdiag = smem + b * b;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) Lk[e] = F.D[Dg.off_d + e];
+  for (int j = threadIdx.x; j < mk; j += blockDim.x) rdiag[j] = 1.0 / F.D[Dg.off_d + j + j * b];
+  __syncthreads();
+  const DenseTarget DT = F.dns[d0 + 1 + blockIdx.x];
+  const BlockDesc T = F.blocks[DT.blk];
+  const int m = T.rend - T.rbeg;
+  double *S = F.D + T.off_d;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    for (int j = 0; j < mk; ++j) {
+      double v = S[i + j * b];
+      for (int l = 0; l < j; ++l) v = fma(-S[i + l * b], Lk[j + l * b], v);
+      S[i + j * b] = v * rdiag[j];
+    }
+  }
+}
+
+// --- P9: W <- L_KK^{-1} W on the rows of leaf K of each open panel --------
+__global__ void __launch_bounds__(kThreads) k_wsolve(FactorArgs F, int w0, int d0) {
+  extern __shared__ double smem[];
+  Acc a(F);
+  const int b = F.b;
+  const BlockDesc Dg = F.blocks[F.dns[d0].blk];
+  const int mk = Dg.rend - Dg.rbeg;
+  double *Lk = smem;
+  double *rdiag = smem + b * b;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) Lk[e] = F.D[Dg.off_d + e];
+  for (int j = threadIdx.x; j < mk; j += blockDim.x) rdiag[j] = 1.0 / F.D[Dg.off_d + j + j * b];
+  __syncthreads();
+  const int pn = F.wpan[w0 + blockIdx.x];
+  const PanelDesc P = F.panels[pn];
+  const int ld = P.rend - P.rbeg;
+  const int c0 = blockIdx.y * blockDim.x;
+  const int c = c0 + threadIdx.x;
+  if (c >= P.width) return;
+  double *w = F.W + P.off + (Dg.rbeg - P.rbeg) + (int64_t)c * ld;
+  double x[kMaxLeaf];
+  for (int i = 0; i < mk; ++i) {
+    double v = w[i];
+    for (int l = 0; l < i; ++l) v = fma(-Lk[i + l * b], x[l], v);
+    x[i] = v * rdiag[i];
+  }
+  for (int i = 0; i < mk; ++i) w[i] = x[i];
+}
+
+// --- P10a: H = W_A^T W_panel[cols A] -----------------------------------------
+__global__ void __launch_bounds__(kThreads) k_htask(FactorArgs F, int h0) {
+  extern __shared__ double smem[];
+  Acc a(F);
+  const HTask H = F.hts[h0 + blockIdx.x];
+  const BlockDesc A = F.blocks[H.a];
+  const PanelDesc P = F.panels[H.panel];
+  const int ld = P.rend - P.rbeg, kc = F.kcap;
+  double *out = F.ws + H.hoff;
+  const double *Wp = F.W + P.off;
+  const int ka = F.rank_l[H.a];
+  for (int j0 = 0; j0 < P.width; j0 += kTnMaxMN - kMaxRank) {
+    const int nj = min(kTnMaxMN - kMaxRank, P.width - j0);
+    cta_gemm_tn(
+        ka, nj, A.cend - A.cbeg, [&](int k, int i) { return a.W(A, A.cbeg + k, i); },
+        [&](int k, int j) { return Wp[(A.cbeg + k - P.rbeg) + (int64_t)(j0 + j) * ld]; },
+        [&](int i, int j, double v) { out[i + (int64_t)(j0 + j) * kc] = v; }, smem);
+  }
+}
+
+// --- P10b: W_panel[I] -= sum of the leaf row's updates ----------------------
+__global__ void __launch_bounds__(kThreads) k_updrow(FactorArgs F, int u0) {
+  extern __shared__ double smem[];
+  Acc a(F);
+  const UpdRow R = F.urows[u0 + blockIdx.x];
+  const PanelDesc P = F.panels[R.panel];
+  const int ld = P.rend - P.rbeg, kc = F.kcap;
+  const int I0 = F.leaf_beg[R.leaf], I1 = F.leaf_beg[R.leaf + 1];
+  const int mi = I1 - I0;
+  double *Wp = F.W + P.off;
+  for (int q = R.e0; q < R.e1; ++q) {
+    const UpdEntry E = F.uents[q];
+    const BlockDesc A = F.blocks[E.a];
+    __syncthreads();
+    auto sub = [&](int i, int j, double v) { Wp[(I0 - P.rbeg + i) + (int64_t)j * ld] -= v; };
+    if (E.hoff < 0) {
+      const int nj = A.cend - A.cbeg;
+      cta_gemm<false, false>(
+          mi, P.width, nj, [&](int i, int k) { return a.U(A, I0 + i, k); },
+          [&](int k, int j) { return Wp[(A.cbeg + k - P.rbeg) + (int64_t)j * ld]; }, sub, smem);
+    } else {
+      const double *Hm = F.ws + E.hoff;
+      cta_gemm<false, true>(
+          mi, P.width, F.rank_l[E.a], [&](int i, int k) { return a.U(A, I0 + i, k); },
+          [&](int k, int j) { return Hm[k + (int64_t)j * kc]; }, sub, smem);
+    }
+  }
+}
+
+__global__ void k_permute_in(const double *__restrict__ z, const int32_t *__restrict__ perm,
+                             int64_t n, double *__restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = z[perm[i]];
+}
+
+__global__ void k_finalize(const double *__restrict__ parts, int N, const double *__restrict__ w,
+                           int64_t n, double *__restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s += parts[i];
+  s = block_sum(s, red);
+  double q = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) q = fma(w[i], w[i], q);
+  q = block_sum(q, red);
+  if (threadIdx.x == 0) { out[0] = s; out[1] = q; }
+}
+
+int g_smem_bytes = 0;
+int g_smem_dense = 0;
+
+}  // namespace
+
+int factor_smem_setup(int b, int kcap) {
+  g_smem_bytes = (kGemmSmem + b * b) * (int)sizeof(double);
+  int kx = b > kcap ? b : kcap;
+  g_smem_dense = (kGemmSmem + kx * b) * (int)sizeof(double);
+  cudaError_t e = cudaSuccess;
+#define SETA(k, s) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, s); if (e != cudaSuccess) return (int)e
+  SETA(k_gram, g_smem_bytes);
+  SETA(k_side_t, g_smem_bytes);
+  SETA(k_side_s, g_smem_bytes);
+  SETA(k_rows, g_smem_bytes);
+  SETA(k_tsqr_part, (kMaxSample + kQrRows) * kMaxSample * (int)sizeof(double));
+  SETA(k_cholqr_part, kTnSmem * (int)sizeof(double));
+  SETA(k_cholqr_final, 2 * kMaxSample * kMaxSample * (int)sizeof(double));
+  SETA(k_tsqr_final, ((kMaxSample + kQrRows) * kMaxSample + 2 * (kMaxSample + 1) * kMaxSample) * (int)sizeof(double));
+  SETA(k_tall_apply, g_smem_bytes);
+  SETA(k_dense_pair, g_smem_dense);
+  SETA(k_potrf, g_smem_bytes);
+  SETA(k_trsm, g_smem_bytes);
+  SETA(k_wsolve, g_smem_bytes);
+  SETA(k_htask, g_smem_bytes);
+  SETA(k_updrow, g_smem_bytes);
+#undef SETA
+  return 0;
+}
+
+const char *const kKernelNames[KK_COUNT] = {
+    "k_gram", "k_side_t", "k_side_s", "k_rows", "k_tsqr_part", "k_tsqr_final", "k_tall_apply",
+    "k_cholqr_part", "k_cholqr_final", "k_dense_pair", "k_dense_reduce", "k_potrf", "k_trsm",
+    "k_wsolve", "k_htask", "k_updrow"};
+
+void prof_mark(Prof *p, cudaStream_t s) {
+  if ((int)p->ev.size() <= p->used) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    p->ev.push_back(e);
+  }
+  cudaEventRecord(p->ev[p->used++], s);
+}
+
+void prof_collect(Prof *p) {
+  for (int i = 0; i + 1 < p->used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->ev[i], p->ev[i + 1]) == cudaSuccess) {
+      p->ms += ms;
+      ++p->launches;
+    }
+  }
+  p->used = 0;
+}
+
+#define LAUNCH(KIND, strm, ...)                                   \
+  do {                                                            \
+    const bool prof_on__ = prof && prof->kind == (KIND);          \
+    if (prof_on__) prof_mark(prof, strm);                         \
+    __VA_ARGS__;                                                  \
+    if (prof_on__) prof_mark(prof, strm);                         \
+    ++nk;                                                         \
+  } while (0)
+
+int launch_step(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
+                const FactorArgs &F, const StepRange &S, int K, const Plan &PL, Prof *prof) {
+  const std::vector<LrTarget> &lrt_host = PL.lrt;
+  int nk = 0;
+  const int sm = (kGemmSmem + F.b * F.b) * (int)sizeof(double);
+  const int smt = std::max(kGemmSmem + F.b * F.b, kTnSmem) * (int)sizeof(double);
+  const int smd = (kGemmSmem + std::max(F.b, F.kcap) * F.b) * (int)sizeof(double);
+  const int r = F.r;
+  if (S.gram1 > S.gram0) { LAUNCH(KK_GRAM, st, k_gram<<<S.gram1 - S.gram0, kThreads, smt, st>>>(F, S.gram0)); }
+  // the dense blocks of column K (P6-P8) only need the grams: fork them to
+  // the side stream while the low-rank targets are compressed
+  cudaStream_t sd = side ? side : st;
+  if (side) {
+    cudaEventRecord(ev_fork, st);
+    cudaStreamWaitEvent(side, ev_fork, 0);
+  }
+  const int nd = S.dns1 - S.dns0;
+  const int q0 = PL.dns[S.dns0].p0, q1 = PL.dns[S.dns1 - 1].p1;
+  if (q1 > q0) { LAUNCH(KK_DENSE_PAIR, sd, k_dense_pair<<<q1 - q0, kThreads, smd, sd>>>(F, q0, S.dpws)); }
+  LAUNCH(KK_DENSE_REDUCE, sd, k_dense_reduce<<<nd, kThreads, 0, sd>>>(F, S.dns0, S.dpws));
+  LAUNCH(KK_POTRF, sd, k_potrf<<<1, kThreads, sm, sd>>>(F, S.dns0, K));
+  if (nd > 1) { LAUNCH(KK_TRSM, sd, k_trsm<<<nd - 1, kThreads, sm, sd>>>(F, S.dns0, K)); }
+  const int nt = S.lrt1 - S.lrt0;
+  if (nt > 0) {
+    int maxch = 0, maxgm = 1, maxgp = 1;
+    for (int t = S.lrt0; t < S.lrt1; ++t) {
+      const LrTarget &L = lrt_host[t];
+      int ch = (L.m + kTM - 1) / kTM + (L.p + kTM - 1) / kTM;
+      if (ch > maxch) maxch = ch;
+      maxgm = std::max(maxgm, L.gm);
+      maxgp = std::max(maxgp, L.gp);
+    }
+    const int qr_smem = (r + kQrRows) * r * (int)sizeof(double);
+    const int qrf_smem = ((r + kQrRows) * r + 2 * (r | 1) * r) * (int)sizeof(double);
+    const int cq_smem = 2 * r * r * (int)sizeof(double);
+    // Y = S Omega
+    LAUNCH(KK_SIDE_T, st, k_side_t<<<(S.bent1 - S.bent0) + nt, kThreads, smt, st>>>(F, S.bent0, S.bent1 - S.bent0, S.lrt0, 0));
+    if (S.aent1 > S.aent0) LAUNCH(KK_SIDE_S, st, k_side_s<<<S.aent1 - S.aent0, kThreads, sm, st>>>(F, S.aent0, 0));
+    LAUNCH(KK_ROWS, st, k_rows<<<S.arow1 - S.arow0, kThreads, sm, st>>>(F, S.arow0, 0));
+    // Q = orth(Y): R of Y, SVD, Q1 = Y V Sigma^{-1}, then CholQR
+    LAUNCH(KK_TSQR_PART, st, k_tsqr_part<<<dim3(nt, maxgm), kThreads, qr_smem, st>>>(F, S.lrt0, 0));
+    LAUNCH(KK_TSQR_FINAL, st, k_tsqr_final<<<nt, kThreads, qrf_smem, st>>>(F, S.lrt0, 0, 0));
+    LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch), kThreads, sm, st>>>(F, S.lrt0, 0));
+    LAUNCH(KK_CHOLQR_PART, st, k_cholqr_part<<<dim3(nt, maxgm), kThreads, smt, st>>>(F, S.lrt0));
+    LAUNCH(KK_CHOLQR_FINAL, st, k_cholqr_final<<<nt, kThreads, cq_smem, st>>>(F, S.lrt0));
+    LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch), kThreads, sm, st>>>(F, S.lrt0, 0));
+    // Z = S^T Q
+    LAUNCH(KK_SIDE_T, st, k_side_t<<<(S.aent1 - S.aent0) + nt, kThreads, smt, st>>>(F, S.aent0, S.aent1 - S.aent0, S.lrt0, 1));
+    if (S.bent1 > S.bent0) LAUNCH(KK_SIDE_S, st, k_side_s<<<S.bent1 - S.bent0, kThreads, sm, st>>>(F, S.bent0, 1));
+    LAUNCH(KK_ROWS, st, k_rows<<<S.brow1 - S.brow0, kThreads, sm, st>>>(F, S.brow0, 1));
+    LAUNCH(KK_TSQR_PART, st, k_tsqr_part<<<dim3(nt, maxgp), kThreads, qr_smem, st>>>(F, S.lrt0, 1));
+    LAUNCH(KK_TSQR_FINAL, st, k_tsqr_final<<<nt, kThreads, qrf_smem, st>>>(F, S.lrt0, 1, 1));
+    LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch), kThreads, sm, st>>>(F, S.lrt0, 1));
+  }
+  if (side) {
+    cudaEventRecord(ev_join, side);
+    cudaStreamWaitEvent(st, ev_join, 0);
+  }
+  if (S.wpan1 > S.wpan0) {
+    int maxw = 0;
+    for (int q = S.wpan0; q < S.wpan1; ++q) maxw = std::max(maxw, PL.panels[PL.wpan[q]].width);
+    LAUNCH(KK_WSOLVE, st, k_wsolve<<<dim3(S.wpan1 - S.wpan0, (maxw + kThreads - 1) / kThreads), kThreads, sm, st>>>(
+        F, S.wpan0, S.dns0));
+  }
+  if (S.ht1 > S.ht0) { LAUNCH(KK_HTASK, st, k_htask<<<S.ht1 - S.ht0, kThreads, smt, st>>>(F, S.ht0)); }
+  if (S.ur1 > S.ur0) { LAUNCH(KK_UPDROW, st, k_updrow<<<S.ur1 - S.ur0, kThreads, sm, st>>>(F, S.ur0)); }
+  return nk;
+}
+
+void launch_permute_in(cudaStream_t st, const double *z, const int32_t *perm, int64_t n,
+                       double *out) {
+  k_permute_in<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(z, perm, n, out);
+}
+
+void launch_finalize(cudaStream_t st, const double *parts, int N, const double *w, int64_t n,
+                     double *out) {
+  k_finalize<<<1, 1024, 0, st>>>(parts, N, w, n, out);
+}
+
+}  // namespace hmle

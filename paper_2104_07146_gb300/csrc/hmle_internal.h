@@ -14,8 +14,8 @@ namespace hmle {
 
 constexpr int kMaxLevels = 24;      // depth limit (n / leaf <= 2^23)
 constexpr int kMaxLeaf = 128;       // leaf_size upper bound
-constexpr int kMaxRank = 96;        // max_rank upper bound
-constexpr int kMaxSample = 112;     // max_rank + oversample upper bound
+constexpr int kMaxRank = 64;        // max_rank upper bound
+constexpr int kMaxSample = 64;      // max_rank + oversample upper bound
 
 // Block kinds.
 constexpr int32_t kDense = 0;       // leaf x leaf, kept dense (incl. diagonal)
@@ -79,8 +79,10 @@ struct LrTarget {
   int32_t b0, b1;          // its B-entries
   int64_t yoff;            // Y / Q workspace (m x r, ld m)
   int64_t zoff;            // Z workspace (p x r, ld p)
-  int64_t soff;            // small r x r workspace (2 r x r)
+  int64_t soff;            // small r x r workspace (4 r x r)
   int64_t tcoff;           // t_C workspace (kc x r)
+  int32_t gm, gp;          // row groups of the tall QR of Y (m rows) and Z (p rows)
+  int64_t roff;            // partial R factors (max(gm, gp) x r x r)
 };
 
 // An A- (or B-) entry of a target: a block covering some rows of the
@@ -137,6 +139,7 @@ struct StepRange {
   int32_t wpan0, wpan1;    // panels solved at this step
   int32_t ht0, ht1;
   int32_t ur0, ur1;
+  int64_t dpws;            // workspace of the dense pairs' partial products (b x b each)
   int64_t ws_words;        // workspace doubles needed by this step
 };
 

@@ -1,0 +1,118 @@
+// Kernel argument structs and launchers of libhmle (assemble.cu, factor.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hmle_internal.h"
+
+namespace hmle {
+
+// θ-dependent scalars, kept in device memory so that a captured graph of
+// the sweep stays valid across evaluations.
+struct ThetaDev {
+  double inv_ell, sigma2, tau2, nu;
+};
+
+struct AsmArgs {
+  const BlockDesc *blocks;
+  const int32_t *lr_ids;   // admissible block ids
+  const double *xyz;       // cluster-order coordinates (SoA)
+  int64_t n;
+  int d;
+  const double *tab;       // Matern table
+  double inv_ell, sigma2, tau2, eps;
+  int kc;
+  double *uc;              // ACA pool (U and V of C)
+  int32_t *rank_c;
+  double *cnorm;           // |C_block|_F estimate of every admissible block
+  int *flags;
+};
+
+// Everything the sweep kernels read; device pointers.
+struct FactorArgs {
+  const BlockDesc *blocks;
+  const PanelDesc *panels;
+  const GramTask *grams;
+  const LrTarget *lrt;
+  const SideEntry *aent, *bent;
+  const int32_t *apair, *bpair;
+  const LrPair *lrpairs;
+  const RowTask *arow, *brow;
+  const int32_t *arow_ent, *brow_ent;
+  const DenseTarget *dns;
+  const DPair *dpairs;
+  const int2 *dpair_tr, *dpair_tc;  // target rows / columns of each dense pair
+  const int32_t *wpan;
+  const HTask *hts;
+  const UpdRow *urows;
+  const UpdEntry *uents;
+  const int32_t *leaf_beg;  // first point of leaf K (N + 1 entries)
+  // pools
+  double *D;               // dense blocks of L (b x b each, ld b)
+  const double *uc;        // ACA factors of C
+  const int32_t *rank_c;
+  const double *cnorm;     // |C_block|_F of the admissible blocks (ACA)
+  double *U;               // U factors of L
+  double *W;               // W-panels (incl. the right-hand side)
+  double *ws;              // per-step workspace
+  int32_t *rank_l;
+  int32_t *kept;           // per low-rank target: columns kept by the orthonormalisation
+  double *jacobi_flops;    // FP64 flops of the Jacobi sweeps (data-dependent count)
+  double *logdet_parts;    // per leaf
+  int *flags;
+  // geometry / kernel
+  const double *xyz;
+  int64_t n;
+  int d;
+  const double *tab;
+  const ThetaDev *th;
+  double eps;
+  uint64_t seed;
+  int b, kcap, kc, r;
+  int osamp;               // oversampling of the randomised compression
+};
+
+void launch_matern_table(cudaStream_t st, double nu, double *tab);
+void launch_matern_eval(cudaStream_t st, const double *tab, const double *x, int64_t m,
+                        double *out);
+void launch_aca(cudaStream_t st, const AsmArgs &A, int n_lr);
+void launch_hmatvec(cudaStream_t st, const AsmArgs &A, const int32_t *dense_ids, int nd,
+                    int n_lr, const double *x, double *y);
+
+// Kernel kinds of the sweep (for per-kernel timing and flop tallies).
+enum KernelKind {
+  KK_GRAM = 0, KK_SIDE_T, KK_SIDE_S, KK_ROWS, KK_TSQR_PART, KK_TSQR_FINAL, KK_TALL_APPLY,
+  KK_CHOLQR_PART, KK_CHOLQR_FINAL, KK_DENSE_PAIR, KK_DENSE_REDUCE, KK_POTRF, KK_TRSM,
+  KK_WSOLVE, KK_HTASK, KK_UPDROW, KK_COUNT
+};
+extern const char *const kKernelNames[KK_COUNT];
+
+// Optional CUDA-event timing of one kernel kind: an event is recorded on the
+// launching stream before and after every launch of that kind.
+struct Prof {
+  int kind = -1;
+  std::vector<cudaEvent_t> ev;
+  int used = 0;
+  double ms = 0.0;
+  int64_t launches = 0;
+  double flops = 0.0;
+};
+void prof_mark(Prof *p, cudaStream_t s);
+void prof_collect(Prof *p);     // after a stream synchronisation
+
+// One step K of the sweep (all phases), given the step's ranges.
+// Returns the number of kernels launched.
+// side / ev_fork / ev_join: a second stream (or nullptr) and two events used
+// to run the dense blocks of the step concurrently with the low-rank targets.
+int launch_step(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
+                const FactorArgs &F, const StepRange &S, int K, const Plan &PL, Prof *prof);
+
+void launch_permute_in(cudaStream_t st, const double *z, const int32_t *perm, int64_t n,
+                       double *out);
+// logdet = sum(parts[0..N)), quad = |w|^2; out[0] = logdet, out[1] = quad
+void launch_finalize(cudaStream_t st, const double *parts, int N, const double *w, int64_t n,
+                     double *out);
+int factor_smem_setup(int b, int kcap);
+
+}  // namespace hmle

@@ -303,6 +303,9 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
       L.zoff = ws; ws += (int64_t)L.p * r;
       L.soff = ws; ws += 4LL * r * r;
       L.tcoff = ws; ws += (int64_t)std::max(kc, r) * r;
+      L.gm = std::max(1, std::min(32, (L.m + 1023) / 1024));
+      L.gp = std::max(1, std::min(32, (L.p + 1023) / 1024));
+      L.roff = ws; ws += (int64_t)std::max(L.gm, L.gp) * r * r;
       P.lrt.push_back(L);
     }
     st.lrt1 = (int32_t)P.lrt.size();
@@ -336,6 +339,8 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
     }
     st.dns1 = (int32_t)P.dns.size();
     st.gram1 = (int32_t)P.grams.size();
+    st.dpws = ws;
+    ws += (int64_t)(P.dns[st.dns1 - 1].p1 - P.dns[st.dns0].p0) * b * b;
 
     // 3. panels advanced by the forward solve of leaf K
     st.wpan0 = (int32_t)P.wpan.size();

@@ -1,0 +1,341 @@
+"""ctypes binding of libhmle.so (include/hmle.h).  Argument marshalling only:
+every numerical step runs in the library's CUDA kernels.  Arrays may be numpy
+arrays (host) or torch tensors (host or CUDA); they are passed by pointer.
+
+If the shared library is missing it is built with nvcc (``build.py``); if that
+is impossible the import of ``lib()`` raises -- there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import sys
+
+import numpy as np
+
+from . import build as _build
+
+HMLE_OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_SPD", 3: "OOM", 4: "CUDA", 5: "RANK_OVERFLOW",
+          6: "TIMEOUT", 7: "NOT_CONVERGED", 8: "NOT_IMPLEMENTED"}
+
+
+class HmleError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Opts(C.Structure):
+    _fields_ = [("leaf_size", C.c_int32), ("eta", C.c_double), ("aca_eps", C.c_double),
+                ("max_rank", C.c_int32), ("oversample", C.c_int32), ("precision", C.c_int32),
+                ("seed", C.c_uint64)]
+
+
+class FitOpts(C.Structure):
+    _fields_ = [("ftol", C.c_double), ("xtol", C.c_double), ("max_iter", C.c_int32),
+                ("step", C.c_double * 4)]
+
+
+class Theta(C.Structure):
+    _fields_ = [("ell", C.c_double), ("nu", C.c_double), ("sigma2", C.c_double),
+                ("tau2", C.c_double)]
+
+
+class TreeInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("depth", C.c_int32),
+                ("n_leaves", C.c_int32), ("n_dense", C.c_int32), ("n_lowrank", C.c_int32),
+                ("dense_words", C.c_int64), ("lowrank_words", C.c_int64),
+                ("device_bytes", C.c_int64)]
+
+
+class EvalInfo(C.Structure):
+    _fields_ = [("logdet", C.c_double), ("quad", C.c_double), ("loglik", C.c_double),
+                ("max_rank_c", C.c_int32), ("max_rank_l", C.c_int32),
+                ("mean_rank_l", C.c_double), ("status", C.c_int32),
+                ("kernel_launches", C.c_int64)]
+
+
+_LIB = None
+P = C.c_void_p
+
+
+def lib():
+    """Load libhmle.so (building it with nvcc when missing or stale)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        sigs = {
+            "hmle_opts_default": ([P], C.c_int),
+            "hmle_fit_opts_default": ([P], C.c_int),
+            "hmle_ctx_create": ([P, P], C.c_int),
+            "hmle_ctx_destroy": ([P], None),
+            "hmle_last_error": ([P], C.c_char_p),
+            "hmle_build_tree": ([P, P, C.c_int64, C.c_int32, P, P], C.c_int),
+            "hmle_tree_destroy": ([P], None),
+            "hmle_tree_get_info": ([P, P], C.c_int),
+            "hmle_tree_permutation": ([P, P], C.c_int),
+            "hmle_assemble": ([P, P, P, P], C.c_int),
+            "hmle_hmatrix_destroy": ([P], None),
+            "hmle_hmatrix_matvec": ([P, P, P, P], C.c_int),
+            "hmle_factor": ([P, P, P, P], C.c_int),
+            "hmle_factor_destroy": ([P], None),
+            "hmle_loglik": ([P, P, P, P, P, P], C.c_int),
+            "hmle_loglik_eval": ([P, P, P, P, P, P], C.c_int),
+            "hmle_fit": ([P, P, P, P, P, P, P, P, P], C.c_int),
+            "hmle_matern_eval": ([P, C.c_double, P, C.c_int64, P], C.c_int),
+            "hmle_profile_select": ([P, C.c_char_p], C.c_int),
+            "hmle_profile_read": ([P, P, P, P], C.c_int),
+        }
+        for name, (argt, rest) in sigs.items():
+            fn = getattr(L, name)
+            fn.argtypes = argt
+            fn.restype = rest
+        _LIB = L
+    return _LIB
+
+
+def exported_symbols():
+    """Names declared in include/hmle.h (for the ABI check)."""
+    return ["hmle_opts_default", "hmle_fit_opts_default", "hmle_ctx_create", "hmle_ctx_destroy",
+            "hmle_last_error", "hmle_build_tree", "hmle_tree_destroy", "hmle_tree_get_info",
+            "hmle_tree_permutation", "hmle_assemble", "hmle_hmatrix_destroy",
+            "hmle_hmatrix_matvec", "hmle_factor", "hmle_factor_destroy", "hmle_loglik",
+            "hmle_loglik_eval", "hmle_fit", "hmle_matern_eval", "hmle_profile_select",
+            "hmle_profile_read"]
+
+
+def _ptr(a):
+    """(pointer, keepalive) for a numpy array or torch tensor of float64/int32."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            a = a.contiguous()
+        return C.c_void_p(a.data_ptr()), a
+    a = np.ascontiguousarray(a)
+    return C.c_void_p(a.ctypes.data), a
+
+
+class Context:
+    """An hmle_ctx on the current CUDA device.  stream: a torch.cuda.Stream,
+    a raw cudaStream_t integer, or None for a library-owned stream."""
+
+    def __init__(self, stream=None):
+        L = lib()
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self._h = P()
+        st = L.hmle_ctx_create(C.byref(self._h), P(stream) if stream else None)
+        if st != HMLE_OK:
+            raise HmleError(st, "hmle_ctx_create")
+
+    def check(self, st, what=""):
+        if st != HMLE_OK:
+            msg = lib().hmle_last_error(self._h)
+            raise HmleError(st, (what + ": " if what else "") + (msg.decode() if msg else ""))
+
+    def close(self):
+        if self._h:
+            lib().hmle_ctx_destroy(self._h)
+            self._h = P()
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def matern(self, nu: float, x) -> np.ndarray:
+        """M_nu(x) as the device evaluates it (host float64 arrays)."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.empty_like(x)
+        self.check(lib().hmle_matern_eval(self._h, float(nu), P(x.ctypes.data), x.size,
+                                          P(out.ctypes.data)), "hmle_matern_eval")
+        return out
+
+
+class Profiler:
+    """Per-kernel CUDA-event timing and flop tally (hmle_profile_*)."""
+
+    def __init__(self, ctx: Context, kernel: str):
+        self.ctx = ctx
+        self.kernel = kernel
+        self.enabled = False
+
+    def enable(self, on: bool):
+        name = self.kernel.encode() if on else None
+        self.ctx.check(lib().hmle_profile_select(self.ctx._h, name), "hmle_profile_select")
+        self.enabled = on
+
+    def reset(self):
+        if self.enabled:
+            self.enable(True)
+
+    def read(self):
+        ms, n, fl = C.c_double(), C.c_int64(), C.c_double()
+        self.ctx.check(lib().hmle_profile_read(self.ctx._h, C.byref(ms), C.byref(n), C.byref(fl)),
+                       "hmle_profile_read")
+        return {"name": self.kernel, "ms": ms.value, "launches": n.value, "flops": fl.value}
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().hmle_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _theta(theta) -> Theta:
+    if isinstance(theta, Theta):
+        return theta
+    ell, nu, s2, t2 = (float(v) for v in theta)
+    return Theta(ell, nu, s2, t2)
+
+
+class Tree:
+    """hmle_build_tree: cluster tree, block tree and factorisation schedule."""
+
+    def __init__(self, ctx: Context, locs, opts: Opts | None = None, **kw):
+        self.ctx = ctx
+        if opts is None:
+            opts = default_opts(**kw)
+        self.opts = opts
+        if hasattr(locs, "shape"):
+            n, d = int(locs.shape[0]), int(locs.shape[1])
+        else:
+            locs = np.asarray(locs, dtype=np.float64)
+            n, d = locs.shape
+        if not hasattr(locs, "data_ptr"):
+            locs = np.ascontiguousarray(locs, dtype=np.float64)
+        p, keep = _ptr(locs)
+        self._h = P()
+        ctx.check(lib().hmle_build_tree(ctx._h, p, n, d, C.byref(opts), C.byref(self._h)),
+                  "hmle_build_tree")
+        self.n, self.d = n, d
+
+    def info(self) -> TreeInfo:
+        i = TreeInfo()
+        self.ctx.check(lib().hmle_tree_get_info(self._h, C.byref(i)), "hmle_tree_get_info")
+        return i
+
+    def permutation(self) -> np.ndarray:
+        perm = np.empty(self.n, dtype=np.int32)
+        self.ctx.check(lib().hmle_tree_permutation(self._h, P(perm.ctypes.data)),
+                       "hmle_tree_permutation")
+        return perm
+
+    def loglik(self, theta, Z):
+        """One evaluation of Eq. 1: returns (L, EvalInfo)."""
+        p, keep = _ptr(Z)
+        ll = C.c_double()
+        info = EvalInfo()
+        st = lib().hmle_loglik_eval(self.ctx._h, self._h, C.byref(_theta(theta)), p,
+                                    C.byref(ll), C.byref(info))
+        self.ctx.check(st, "hmle_loglik_eval")
+        return ll.value, info
+
+    def assemble(self, theta) -> "HMatrix":
+        return HMatrix(self, theta)
+
+    def fit(self, Z, theta0, ftol=1e-4, xtol=1e-4, max_iter=400, step=None):
+        """Nelder-Mead MLE: returns (theta_hat tuple, L_hat, iterations, evaluations, status)."""
+        fo = FitOpts()
+        lib().hmle_fit_opts_default(C.byref(fo))
+        fo.ftol, fo.xtol, fo.max_iter = ftol, xtol, max_iter
+        if step is not None:
+            for i in range(4):
+                fo.step[i] = float(step[i])
+        p, keep = _ptr(Z)
+        th = Theta()
+        ll = C.c_double()
+        it = C.c_int32()
+        nev = C.c_int32()
+        st = lib().hmle_fit(self.ctx._h, self._h, p, C.byref(_theta(theta0)), C.byref(fo),
+                            C.byref(th), C.byref(ll), C.byref(it), C.byref(nev))
+        if st not in (HMLE_OK, 7):
+            self.ctx.check(st, "hmle_fit")
+        return (th.ell, th.nu, th.sigma2, th.tau2), ll.value, it.value, nev.value, st
+
+    def close(self):
+        if self._h:
+            lib().hmle_tree_destroy(self._h)
+            self._h = P()
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HMatrix:
+    """hmle_assemble: C~(theta) held as an H-matrix on the device."""
+
+    def __init__(self, tree: Tree, theta):
+        self.tree = tree
+        self._h = P()
+        tree.ctx.check(lib().hmle_assemble(tree.ctx._h, tree._h, C.byref(_theta(theta)),
+                                           C.byref(self._h)), "hmle_assemble")
+
+    def matvec(self, x) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.empty_like(x)
+        self.tree.ctx.check(lib().hmle_hmatrix_matvec(self.tree.ctx._h, self._h, P(x.ctypes.data),
+                                                      P(y.ctypes.data)), "hmle_hmatrix_matvec")
+        return y
+
+    def factor(self, Z=None) -> "Factor":
+        return Factor(self, Z)
+
+    def close(self):
+        if self._h:
+            lib().hmle_hmatrix_destroy(self._h)
+            self._h = P()
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Factor:
+    """hmle_factor: the H-Cholesky factor (with the forward solve of Z fused)."""
+
+    def __init__(self, hm: HMatrix, Z=None):
+        self.hm = hm
+        self._h = P()
+        self._Z = Z
+        p, keep = _ptr(Z) if Z is not None else (None, None)
+        ctx = hm.tree.ctx
+        ctx.check(lib().hmle_factor(ctx._h, hm._h, p, C.byref(self._h)), "hmle_factor")
+
+    def loglik(self, Z=None):
+        """(L, log|C~|, Z^T C~^{-1} Z)."""
+        Z = self._Z if Z is None else Z
+        p, keep = _ptr(Z)
+        ll, ld, q = C.c_double(), C.c_double(), C.c_double()
+        ctx = self.hm.tree.ctx
+        ctx.check(lib().hmle_loglik(ctx._h, self._h, p, C.byref(ll), C.byref(ld), C.byref(q)),
+                  "hmle_loglik")
+        return ll.value, ld.value, q.value
+
+    def close(self):
+        if self._h:
+            lib().hmle_factor_destroy(self._h)
+            self._h = P()
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,139 @@
+"""GPU path (through the C ABI) against the CPU oracle.
+
+Tolerances: the H-matrix approximates C to the ACA accuracy eps, so L is
+compared at |L_H - L| / n <= 1e-6 (the contract bound); the device Matern
+function (Chebyshev tables) is compared entry-wise at 1e-13 absolute.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_07146_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(hmle_lib):
+    from paper_2104_07146_gb300 import hmle
+    return hmle.Context()
+
+
+def _tree(ctx, locs, **kw):
+    from paper_2104_07146_gb300 import hmle
+    return hmle.Tree(ctx, locs, **kw)
+
+
+@pytest.mark.parametrize("nu", [0.3, 0.5, 0.8, 1.5, 2.5, 3.7])
+def test_device_matern_matches_oracle(ctx, nu):
+    x = np.concatenate([[0.0, 1e-6, 3e-5], np.logspace(-3.5, 3.05, 400)])
+    got = ctx.matern(nu, x)
+    ref = np.array([oracle.matern_unit(nu, v) for v in x])
+    assert np.max(np.abs(got - ref)) <= 1e-13
+
+
+def test_tree_permutation_is_a_permutation(ctx):
+    locs = synth.locations_uniform(3001, 2, seed=5)
+    t = _tree(ctx, locs, leaf_size=32)
+    perm = t.permutation()
+    assert np.array_equal(np.sort(perm), np.arange(3001))
+    info = t.info()
+    assert info.n_leaves == 2 ** info.depth and info.n_dense >= info.n_leaves
+
+
+def test_hmatrix_matvec_matches_dense(ctx):
+    n = 2000
+    locs = synth.locations_uniform(n, 2, seed=1000)
+    th = (0.1, 0.5, 1.0, 0.01)
+    t = _tree(ctx, locs, leaf_size=32, aca_eps=1e-8)
+    x = synth.normal(77, n)
+    y = t.assemble(th).matvec(x)
+    ref = oracle.matern_matrix(locs, th) @ x
+    assert np.linalg.norm(y - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+def _parity(ctx, locs, theta, leaf, eps, zseed, tol=1e-6, field=False, **kw):
+    """field=False: Z is white noise (q ~ n / tau2, the harder case for the
+    quadratic form); field=True: Z = L xi, a sample of the field itself."""
+    n = locs.shape[0]
+    Z = synth.normal(zseed, n)
+    if field:
+        Z = oracle.simulate(locs, theta, Z)
+    t = _tree(ctx, locs, leaf_size=leaf, aca_eps=eps, **kw)
+    ll, info = t.loglik(theta, Z)
+    ref, ld, q = oracle.loglik_dense(locs, Z, theta)
+    assert abs(info.logdet - ld) / n <= tol, (info.logdet, ld)
+    assert abs(info.quad - q) / n <= tol, (info.quad, q)
+    assert abs(ll - ref) / n <= tol, (ll, ref)
+    return ll, ref, info
+
+
+def test_loglik_small_config(ctx):
+    # n = 2000 uniform, theta = (0.1, 0.5, 1, 0.01), leaf 32, eps 1e-8, Z = L xi
+    locs = synth.locations_uniform(2000, 2, seed=1000)
+    _parity(ctx, locs, (0.1, 0.5, 1.0, 0.01), 32, 1e-8, 1001, field=True)
+
+
+def test_loglik_small_config_white_noise(ctx):
+    locs = synth.locations_uniform(2000, 2, seed=1000)
+    _parity(ctx, locs, (0.1, 0.5, 1.0, 0.01), 32, 1e-8, 1001)
+
+
+def test_loglik_ragged_leaves_nonhalf_nu(ctx):
+    locs = synth.locations_uniform(3001, 2, seed=21)
+    _parity(ctx, locs, (0.15, 1.3, 0.8, 0.02), 32, 1e-8, 22, field=True)
+
+
+def test_loglik_smooth_white_noise_tight_eps(ctx):
+    # white-noise Z on a smooth field: q ~ 43 n, needs eps 1e-10
+    locs = synth.locations_uniform(3001, 2, seed=21)
+    _parity(ctx, locs, (0.15, 1.3, 0.8, 0.02), 32, 1e-10, 22, max_rank=48, oversample=16)
+
+
+@pytest.mark.parametrize("nu,eps", [(0.5, 1e-6), (0.8, 1e-6), (1.5, 1e-7), (2.5, 1e-8)])
+def test_loglik_blob_mixture_leaf64(ctx, nu, eps):
+    # the medium workload's geometry and theta at n = 4096, Z = L xi.  The
+    # smoother fields need a tighter eps than 1e-6 to meet |dL|/n <= 1e-6
+    # (the exact-arithmetic H-Cholesky at eps = 1e-6 misses it at nu = 1.5).
+    locs = synth.locations_blobs(4096, 2, 0.3, 8, 0.03, seed=23)
+    _parity(ctx, locs, (0.05, nu, 1.0, 1e-3), 64, eps, 24, field=True,
+            max_rank=48, oversample=16)
+
+
+def test_loglik_three_dimensions(ctx):
+    locs = synth.locations_uniform(2500, 3, seed=25)
+    _parity(ctx, locs, (0.2, 1.0, 1.0, 0.01), 32, 1e-7, 26, field=True, max_rank=48,
+            oversample=16)
+
+
+def test_factor_api_matches_fused_eval(ctx):
+    locs = synth.locations_uniform(1500, 2, seed=27)
+    Z = synth.normal(28, 1500)
+    th = (0.12, 0.7, 1.1, 0.03)
+    t = _tree(ctx, locs, leaf_size=32, aca_eps=1e-8)
+    ll1, info = t.loglik(th, Z)
+    f = t.assemble(th).factor(Z)
+    ll2, ld, q = f.loglik(Z)
+    assert ll1 == ll2 and ld == info.logdet and q == info.quad
+
+
+def test_non_spd_is_reported(ctx):
+    from paper_2104_07146_gb300 import hmle
+    locs = synth.locations_uniform(200, 2, seed=29)
+    t = _tree(ctx, locs, leaf_size=16)
+    with pytest.raises(hmle.HmleError) as e:   # sigma2 = tau2 = 0: C = 0
+        t.loglik((0.3, 0.5, 0.0, 0.0), synth.normal(30, 200))
+    assert e.value.status == 2
+    ll, _ = t.loglik((0.3, 0.5, 1.0, 0.01), synth.normal(30, 200))   # still usable
+    assert math.isfinite(ll)
+
+
+def test_deterministic_repeat(ctx):
+    locs = synth.locations_uniform(2000, 2, seed=31)
+    Z = synth.normal(32, 2000)
+    t = _tree(ctx, locs, leaf_size=32)
+    a = t.loglik((0.1, 0.9, 1.0, 0.01), Z)[0]
+    b = t.loglik((0.1, 0.9, 1.0, 0.01), Z)[0]
+    assert a == b
