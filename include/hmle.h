@@ -75,7 +75,10 @@ typedef struct {
  *  oversample extra random samples beyond max_rank for the compression of
  *             updated low-rank blocks (>= 4).
  *  seed       seed of the counter-based random signs used by that
- *             compression (the result is deterministic for a given seed). */
+ *             compression (the result is deterministic for a given seed).
+ *  leaf_lowrank  0 (default): admissible blocks between two leaf clusters
+ *             (at most leaf_size^2 entries) are kept dense and exact; 1: they
+ *             are held low-rank like the coarser admissible blocks. */
 typedef struct {
   int32_t leaf_size;
   double eta;
@@ -84,6 +87,7 @@ typedef struct {
   int32_t oversample;
   int32_t precision; /* hmle_precision */
   uint64_t seed;
+  int32_t leaf_lowrank;
 } hmle_opts;
 
 /* Nelder-Mead options of hmle_fit (Sec. 2: threshold 1e-4, <= 400 iterations). */
@@ -124,7 +128,8 @@ typedef struct hmle_hmatrix hmle_hmatrix;
 typedef struct hmle_hfactor hmle_hfactor;
 
 /* Fill *opts with defaults: leaf 64, eta 2, aca_eps 1e-8, max_rank 32,
- * oversample 8, FP64, seed 0x5eed.  Always HMLE_OK for non-NULL opts. */
+ * oversample 8, FP64, seed 0x5eed, leaf_lowrank 0.  Always HMLE_OK for
+ * non-NULL opts. */
 hmle_status hmle_opts_default(hmle_opts *opts);
 
 /* Fill *opts with the paper's optimiser settings: ftol = xtol = 1e-4,

@@ -339,6 +339,7 @@ hmle_status hmle_opts_default(hmle_opts *o) {
   o->oversample = 8;
   o->precision = HMLE_FP64;
   o->seed = 0x5eed;
+  o->leaf_lowrank = 0;
   return HMLE_OK;
 }
 
@@ -437,6 +438,9 @@ hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n, int32_
     return fail(ctx, err.find("non-finite") != std::string::npos ? HMLE_ERR_INVALID_ARG : HMLE_ERR_CUDA, err);
   }
   const int kc = o.max_rank + 16 <= 64 ? o.max_rank + 16 : 64;  // ACA capacity for C
+  if (!o.leaf_lowrank)  // leaf x leaf admissible blocks are kept dense (exact)
+    for (int4 &q : blocks)
+      if (q.w == kLowRank && q.x == depth) q.w = kDense;
   err = build_plan(t->plan, (int32_t)n, d, o.leaf_size, depth, cb, ce, blocks, o.max_rank, kc,
                    o.max_rank + o.oversample, 1);
   if (!err.empty()) { hmle_tree_destroy(t); return fail(ctx, HMLE_ERR_INVALID_ARG, "planner: " + err); }

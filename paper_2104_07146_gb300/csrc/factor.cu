@@ -40,6 +40,7 @@ namespace hmle {
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kMaxEntries = 512;     // side entries covering one leaf row of a target
 constexpr int kTM = 64, kTN = 64, kTK = 16;
 constexpr int kGemmSmem = kTK * (kTM + kTN);  // doubles
 
@@ -262,7 +263,6 @@ __global__ void __launch_bounds__(kThreads) k_side_t(FactorArgs F, int e0, int n
 
 // --- P2b / P4b: s_X = sum over the entry's pairs of G (or G^T) t_partner ---
 __global__ void __launch_bounds__(kThreads) k_side_s(FactorArgs F, int e0, int trans) {
-  extern __shared__ double smem[];
   Acc a(F);
   const int kc = F.kcap;
   const SideEntry E = trans ? F.bent[e0 + blockIdx.x] : F.aent[e0 + blockIdx.x];
@@ -270,59 +270,50 @@ __global__ void __launch_bounds__(kThreads) k_side_s(FactorArgs F, int e0, int t
   const BlockDesc X = F.blocks[E.blk];
   const int kx = a.kof(X), kxe = a.keff(E.blk, X);
   double *s = F.ws + E.soff;
-  for (int i = threadIdx.x; i < kx * r; i += blockDim.x) s[i] = 0.0;
-  __syncthreads();
   const int32_t *plist = trans ? F.bpair : F.apair;
-  for (int q = E.p0; q < E.p1; ++q) {
-    const LrPair P = F.lrpairs[plist[q]];
-    const SideEntry O = trans ? F.aent[P.ae] : F.bent[P.be];  // partner entry
-    const BlockDesc Y = F.blocks[O.blk];
-    const BlockDesc &A = trans ? Y : X;   // A side of the pair
-    const BlockDesc &B = trans ? X : Y;   // B side of the pair
-    const int ky = a.kof(Y), kye = a.keff(O.blk, Y);
-    const double *t = F.ws + O.toff;      // ky x r
-    auto add = [&](int i, int j, double v) { s[i + (int64_t)j * kx] += v; };
-    auto tt = [&](int k, int j) { return t[k + (int64_t)j * ky]; };
-    if (A.kind == kLowRank && B.kind == kLowRank) {
-      const double *G = F.ws + P.goff;    // kcap x kcap, G_AB
-      if (!trans)
-        cta_gemm<false, true>(kxe, r, kye, [&](int i, int k) { return G[i + (int64_t)k * kc]; },
-                              tt, add, smem);
-      else
-        cta_gemm<true, true>(kxe, r, kye, [&](int i, int k) { return G[k + (int64_t)i * kc]; },
-                             tt, add, smem);
-    } else if (A.kind == kDense && B.kind == kLowRank) {
-      // G = W_B[J_A] (b x kcap)
-      const int J0 = A.cbeg, nj = A.cend - A.cbeg;
-      if (!trans)  // s_A (b x r) += W_B[J_A] t_B
-        cta_gemm<false, true>(
-            nj, r, kye, [&](int i, int k) { return a.W(B, J0 + i, k); }, tt, add, smem);
-      else  // s_B (kcap x r) += W_B[J_A]^T t_A
-        cta_gemm<true, true>(
-            kxe, r, nj, [&](int i, int k) { return a.W(B, J0 + k, i); }, tt, add, smem);
-    } else if (A.kind == kLowRank && B.kind == kDense) {
-      // G = W_A[J_B]^T (kcap x b)
-      const int J0 = B.cbeg, nj = B.cend - B.cbeg;
-      if (!trans)  // s_A (kcap x r) += W_A[J_B]^T t_B
-        cta_gemm<true, true>(
-            kxe, r, nj, [&](int i, int k) { return a.W(A, J0 + k, i); }, tt, add, smem);
-      else  // s_B (b x r) += W_A[J_B] t_A
-        cta_gemm<false, true>(
-            nj, r, kye, [&](int i, int k) { return a.W(A, J0 + i, k); }, tt, add, smem);
-    } else {
-      const int nj = A.cend - A.cbeg;
-      for (int i = threadIdx.x; i < nj * r; i += blockDim.x) {
-        int ii = i % nj, jj = i / nj;
-        s[ii + (int64_t)jj * kx] += t[ii + (int64_t)jj * ky];
+  // each thread owns outputs (i, j) of s (kx x r, only the first kxe rows
+  // can be nonzero) and accumulates all the entry's pairs in order
+  for (int o = threadIdx.x; o < kx * r; o += blockDim.x) {
+    const int i = o % kx, j = o / kx;
+    double acc = 0.0;
+    if (i < kxe || X.kind == kDense) {
+      for (int q = E.p0; q < E.p1; ++q) {
+        const LrPair P = F.lrpairs[plist[q]];
+        const int oe = trans ? P.ae : P.be;
+        const SideEntry O = trans ? F.aent[oe] : F.bent[oe];
+        const BlockDesc Y = F.blocks[O.blk];
+        const BlockDesc &A = trans ? Y : X;
+        const BlockDesc &B = trans ? X : Y;
+        const int ky = a.kof(Y), kye = a.keff(O.blk, Y);
+        const double *t = F.ws + O.toff + (int64_t)j * ky;   // column j of the partner's t
+        if (A.kind == kLowRank && B.kind == kLowRank) {
+          const double *G = F.ws + P.goff;
+          if (!trans) { for (int k = 0; k < kye; ++k) acc = fma(G[i + k * kc], t[k], acc); }
+          else { for (int k = 0; k < kye; ++k) acc = fma(G[k + i * kc], t[k], acc); }
+        } else if (A.kind == kDense && B.kind == kLowRank) {
+          const int J0 = A.cbeg, nj = A.cend - A.cbeg;
+          if (!trans) { if (i < nj) for (int k = 0; k < kye; ++k) acc = fma(a.W(B, J0 + i, k), t[k], acc); }
+          else { for (int k = 0; k < nj; ++k) acc = fma(a.W(B, J0 + k, i), t[k], acc); }
+        } else if (A.kind == kLowRank && B.kind == kDense) {
+          const int J0 = B.cbeg, nj = B.cend - B.cbeg;
+          if (!trans) { for (int k = 0; k < nj; ++k) acc = fma(a.W(A, J0 + k, i), t[k], acc); }
+          else { if (i < nj) for (int k = 0; k < kye; ++k) acc = fma(a.W(A, J0 + i, k), t[k], acc); }
+        } else {
+          if (i < A.cend - A.cbeg) acc += t[i];
+        }
       }
     }
-    __syncthreads();
+    s[i + (int64_t)j * kx] = acc;
   }
 }
 
 // --- P2c / P4c: rows of Y (or Z) of one leaf --------------------------------
 __global__ void __launch_bounds__(kThreads) k_rows(FactorArgs F, int rt0, int trans) {
   extern __shared__ double smem[];
+  __shared__ int kbeg[kMaxEntries + 2];
+  __shared__ int eblk[kMaxEntries + 2];
+  __shared__ int64_t esoff[kMaxEntries + 2];
+  __shared__ int ekx[kMaxEntries + 2];
   Acc a(F);
   const int kc = F.kc;
   const RowTask R = trans ? F.brow[rt0 + blockIdx.x] : F.arow[rt0 + blockIdx.x];
@@ -336,22 +327,44 @@ __global__ void __launch_bounds__(kThreads) k_rows(FactorArgs F, int rt0, int tr
   const double *UC = F.uc + (trans ? T.off_vc : T.off_uc);
   const double *tc = F.ws + L.tcoff;
   const int mi = I1 - I0;
-  cta_gemm<false, true>(
-      mi, r, F.rank_c[L.blk], [&](int i, int k) { return UC[(I0 - base + i) + (int64_t)k * ld]; },
-      [&](int k, int j) { return tc[k + (int64_t)j * kc]; },
-      [&](int i, int j, double v) { Y[(I0 - base + i) + (int64_t)j * ld] = v; }, smem);
   const int32_t *ents = trans ? F.brow_ent : F.arow_ent;
-  for (int q = R.e0; q < R.e1; ++q) {
-    const SideEntry E = trans ? F.bent[ents[q]] : F.aent[ents[q]];
-    const BlockDesc X = F.blocks[E.blk];
-    const int kx = a.kof(X);
-    const double *s = F.ws + E.soff;
-    __syncthreads();
-    cta_gemm<false, true>(
-        mi, r, a.keff(E.blk, X), [&](int i, int k) { return a.U(X, I0 + i, k); },
-        [&](int k, int j) { return s[k + (int64_t)j * kx]; },
-        [&](int i, int j, double v) { Y[(I0 - base + i) + (int64_t)j * ld] -= v; }, smem);
+  const int ne = R.e1 - R.e0;
+  // K = [rank_c | k_e1 | k_e2 | ...]: Y[I] = [U_C[I], -U_e1[I], ...] [t_C; s_e1; ...]
+  if (threadIdx.x == 0) {
+    int k = F.rank_c[L.blk];
+    kbeg[0] = 0;
+    for (int q = 0; q < ne; ++q) {
+      const SideEntry E = trans ? F.bent[ents[R.e0 + q]] : F.aent[ents[R.e0 + q]];
+      const BlockDesc X = F.blocks[E.blk];
+      kbeg[q + 1] = k;
+      eblk[q] = E.blk;
+      esoff[q] = E.soff;
+      ekx[q] = a.kof(X);
+      k += a.keff(E.blk, X);
+    }
+    kbeg[ne + 1] = k;
   }
+  __syncthreads();
+  const int K = kbeg[ne + 1];
+  auto seg = [&](int k) {       // entry index of column k (0 = U_C)
+    int q = 0;
+    while (q < ne && kbeg[q + 1] <= k) ++q;
+    return q;
+  };
+  cta_gemm<false, true>(
+      mi, r, K,
+      [&](int i, int k) {
+        int q = seg(k);
+        if (q == 0) return UC[(I0 - base + i) + (int64_t)k * ld];
+        const BlockDesc X = F.blocks[eblk[q - 1]];
+        return -a.U(X, I0 + i, k - kbeg[q]);
+      },
+      [&](int k, int j) {
+        int q = seg(k);
+        if (q == 0) return tc[k + (int64_t)j * kc];
+        return F.ws[esoff[q - 1] + (k - kbeg[q]) + (int64_t)j * ekx[q - 1]];
+      },
+      [&](int i, int j, double v) { Y[(I0 - base + i) + (int64_t)j * ld] = v; }, smem);
 }
 
 // --- tall QR (R factor only) and SVD of the small R -----------------------
@@ -477,9 +490,11 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, i
     V[i + c * lb] = (i == c) ? 1.0 : 0.0;
   }
   __syncthreads();
-  // one-sided Jacobi on the columns of B (R V = B): one warp, one lane per
-  // column pair of a round (disjoint pairs of a round-robin tournament), so
-  // every FP64 instruction works on all lanes
+  // one-sided Jacobi on the columns of B (R V = B).  A round rotates the
+  // disjoint column pairs of a round-robin tournament; each pair is handled
+  // by a group of g lanes (all four warps busy, so all four FP64 pipes of the
+  // SM), the group's lanes split the rows, and the rotation parameters are
+  // computed once per group and broadcast.
   const int rp = r + (r & 1), half = rp / 2;
   double fro = 0.0;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
@@ -488,50 +503,74 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, i
   }
   fro = block_sum(fro, red);
   const double tiny = 1e-30 * fro;     // columns below eps |R|_F are zero
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    double jf = 0.0;                    // FP64 flops of this lane's pair work
-    for (int sweep = 0; sweep < 40; ++sweep) {
-      int rotated = 0;
-      for (int round = 0; round < rp - 1; ++round) {
-        if (lane < half) {
-          int p = (lane == 0) ? 0 : 1 + (lane - 1 + round) % (rp - 1);
-          int q = 1 + (rp - 2 - lane + round) % (rp - 1);
-          if (p > q) { int t = p; p = q; q = t; }
-          if (q < r) {
-            jf += 6.0 * r;
-            double al = 0.0, be = 0.0, ga = 0.0;
-            for (int i = 0; i < r; ++i) {
-              double bp = B[i + p * lb], bq = B[i + q * lb];
-              al = fma(bp, bp, al);
-              be = fma(bq, bq, be);
-              ga = fma(bp, bq, ga);
-            }
-            if (al > tiny && be > tiny && fabs(ga) > 1e-13 * sqrt(al * be)) {
-              double zeta = (be - al) / (2.0 * ga);
-              double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-              double c = 1.0 / sqrt(fma(t, t, 1.0)), sn = c * t;
-              for (int i = 0; i < r; ++i) {
-                double bp = B[i + p * lb], bq = B[i + q * lb];
-                B[i + p * lb] = c * bp - sn * bq;
-                B[i + q * lb] = sn * bp + c * bq;
-                double vp = V[i + p * lb], vq = V[i + q * lb];
-                V[i + p * lb] = c * vp - sn * vq;
-                V[i + q * lb] = sn * vp + c * vq;
-              }
-              rotated = 1;
-              jf += 12.0 * r + 30.0;
-            }
-          }
-        }
-        __syncwarp();
+  int g = 1;                            // lanes per pair: largest power of 2 with half * g <= 128
+  while (g < 32 && half * g * 2 <= kThreads) g *= 2;
+  const int grp = threadIdx.x / g, gl = threadIdx.x % g;
+  const unsigned gmask = (g == 32) ? 0xffffffffu : (((1u << g) - 1u) << ((threadIdx.x & 31) / g * g));
+  double jf = 0.0;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    __syncthreads();                    // every thread has read the previous flag
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < rp - 1; ++round) {
+      bool active = grp < half;
+      int p = 0, q = 0;
+      if (active) {
+        p = (grp == 0) ? 0 : 1 + (grp - 1 + round) % (rp - 1);
+        q = 1 + (rp - 2 - grp + round) % (rp - 1);
+        if (p > q) { int t = p; p = q; q = t; }
+        active = q < r;
       }
-      if (!__any_sync(0xffffffffu, rotated)) break;
+      double al = 0.0, be = 0.0, ga = 0.0;
+      if (active) {
+        for (int i = gl; i < r; i += g) {
+          double bp = B[i + p * lb], bq = B[i + q * lb];
+          al = fma(bp, bp, al);
+          be = fma(bq, bq, be);
+          ga = fma(bp, bq, ga);
+        }
+      }
+      for (int o = g / 2; o > 0; o >>= 1) {
+        al += __shfl_xor_sync(0xffffffffu, al, o);
+        be += __shfl_xor_sync(0xffffffffu, be, o);
+        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+      }
+      double c = 1.0, sn = 0.0;
+      int rot = 0;
+      if (active && gl == 0 && al > tiny && be > tiny && fabs(ga) > 1e-13 * sqrt(al * be)) {
+        double zeta = (be - al) / (2.0 * ga);
+        double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+        c = 1.0 / sqrt(fma(t, t, 1.0));
+        sn = c * t;
+        rot = 1;
+        jf += 30.0;
+      }
+      const int src = (threadIdx.x & 31) / g * g;
+      rot = __shfl_sync(0xffffffffu, rot, src);
+      c = __shfl_sync(0xffffffffu, c, src);
+      sn = __shfl_sync(0xffffffffu, sn, src);
+      if (active && gl == 0) jf += 6.0 * r;
+      if (active && rot) {
+        for (int i = gl; i < r; i += g) {
+          double bp = B[i + p * lb], bq = B[i + q * lb];
+          B[i + p * lb] = c * bp - sn * bq;
+          B[i + q * lb] = sn * bp + c * bq;
+          double vp = V[i + p * lb], vq = V[i + q * lb];
+          V[i + p * lb] = c * vp - sn * vq;
+          V[i + q * lb] = sn * vp + c * vq;
+        }
+        if (gl == 0) {
+          s_rot = 1;
+          jf += 12.0 * r;
+        }
+      }
+      __syncthreads();
     }
-    jf = warp_sum(jf);
-    if (lane == 0 && F.jacobi_flops) atomicAdd(F.jacobi_flops, jf);
+    if (s_rot == 0) break;
   }
-  __syncthreads();
+  (void)gmask;
+  jf = block_sum(jf, red);
+  if (threadIdx.x == 0 && F.jacobi_flops) atomicAdd(F.jacobi_flops, jf);
   for (int c = threadIdx.x; c < r; c += blockDim.x) {
     double s = 0.0;
     for (int i = 0; i < r; ++i) s = fma(B[i + c * lb], B[i + c * lb], s);

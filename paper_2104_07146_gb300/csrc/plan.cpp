@@ -102,6 +102,7 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
     B.off_d = B.off_uc = B.off_vc = B.off_u = -1;
     if (B.kind == kDense) {
       if (q.x != depth) return "dense block above the leaf level";
+      if (q.y < q.z) return "dense block above the diagonal";
       B.off_d = dw; dw += (int64_t)b * b;
       if (q.y == q.z) P.diag_of_leaf[q.y] = (int32_t)P.blocks.size();
       ++P.n_dense_blocks;
@@ -286,6 +287,7 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
           if (it != aidx.end()) P.arow_ent.push_back(it->second);
         }
         rt.e1 = (int32_t)P.arow_ent.size();
+        if (rt.e1 - rt.e0 > 512) return "more than 512 blocks cover one leaf row of a target";
         P.arow.push_back(rt);
       }
       for (int J = T.cleaf; J < T.cleaf + sp; ++J) {
@@ -297,6 +299,7 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
           if (it != bidx.end()) P.brow_ent.push_back(it->second);
         }
         rt.e1 = (int32_t)P.brow_ent.size();
+        if (rt.e1 - rt.e0 > 512) return "more than 512 blocks cover one leaf row of a target";
         P.brow.push_back(rt);
       }
       L.yoff = ws; ws += (int64_t)L.m * r;

@@ -29,7 +29,7 @@ class HmleError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("leaf_size", C.c_int32), ("eta", C.c_double), ("aca_eps", C.c_double),
                 ("max_rank", C.c_int32), ("oversample", C.c_int32), ("precision", C.c_int32),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("leaf_lowrank", C.c_int32)]
 
 
 class FitOpts(C.Structure):
