@@ -1,9 +1,12 @@
 """Benchmark of the H-MLE hot path: H-matrix log-likelihood evaluations per
 second (Eq. 1 with the Matern covariance of Eq. 2) on one GB300.
 
-One step = one full evaluation L(theta): Matern tables + ACA assembly of the
-admissible blocks + the H-Cholesky leaf sweep with the fused forward solve +
-log-det / quadratic form, for the medium workload: n = 65,536 points in
+One evaluation = Matern tables + ACA assembly of the admissible blocks + the
+H-Cholesky leaf sweep with the fused forward solve + log-det / quadratic
+form.  One step = one batch of B evaluations at B distinct theta (the
+workload theta and its neighbours in the transformed coordinates of Sec. 5,
+as an optimiser's simplex would ask for), run concurrently through
+hmle_loglik_batch, for the medium workload: n = 65,536 points in
 [0,1]^2 (70 % uniform, 30 % in 8 Gaussian blobs of sd 0.03), Matern
 (ell, nu, sigma2, tau2) = (0.05, 0.5, 1, 1e-3), leaf 64, eta 2, eps 1e-6.
 The cluster/block trees and the schedule are built once (θ-independent).
@@ -129,40 +132,49 @@ def run_gpu(args):
     Zd = torch.from_numpy(Z).to(f"cuda:{local}")           # resident input
     Zh = torch.from_numpy(Z).pin_memory()                   # host input for e2e
     theta = tuple(w["theta"])
+    thetas = batch_thetas(theta, args.batch)
     prof = hmle.Profiler(ctx, args.roofline_kernel)
 
     def step(z):
-        return tree.loglik(theta, z)
+        ll, st = tree.loglik_batch(thetas, z, concurrency=args.batch)
+        assert all(s == 0 for s in st), st
+        return ll
 
     for _ in range(args.warmup):
         step(Zd)
+    # one single evaluation: its latency, and the launches of one evaluation
+    ll1, info = tree.loglik(theta, Zd)
+    t0 = time.time()
+    ll1, info = tree.loglik(theta, Zd)
+    single_ms = (time.time() - t0) * 1e3
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    prof.enable(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    launches = 0
-    info = None
     for _ in range(args.steps):
-        ll, info = step(Zd)
-        launches += info.kernel_launches
+        ll = step(Zd)
     e1.record(stream)
     torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = args.steps * args.batch * info.kernel_launches
+    # roofline kernel: its launches timed with CUDA events inside one
+    # evaluation's captured graph
+    prof.enable(True)
+    tree.loglik(theta, Zd)
     dom = prof.read()
     prof.enable(False)
-    ms = e0.elapsed_time(e1)
     # e2e: host Z (pinned) through the C ABI; the copy in and the result out
     # are inside the timed region
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
     e2.record(stream)
     for _ in range(args.steps):
-        ll_e2e, _ = step(Zh.numpy())
+        ll_e2e = step(Zh.numpy())
     e3.record(stream)
     torch.cuda.synchronize()
     ms_e2e = e2.elapsed_time(e3)
@@ -176,8 +188,8 @@ def run_gpu(args):
             dist.barrier()
             dist.destroy_process_group()
         return
-    value = ws * args.steps / (ms / 1e3)
-    e2e = ws * args.steps / (ms_e2e / 1e3)
+    value = ws * args.steps * args.batch / (ms / 1e3)
+    e2e = ws * args.steps * args.batch / (ms_e2e / 1e3)
     achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] > 0 else None
     peaks = _peaks()
     out = {
@@ -188,10 +200,11 @@ def run_gpu(args):
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "working set %.1f GB > 129 MB L2 (no flush needed)"
                          % (tree.info().lowrank_words * 8 / 1e9)},
-        "loglik": ll, "logdet": info.logdet, "quad": info.quad,
+        "batch": args.batch, "single_eval_ms": single_ms,
+        "loglik": ll1, "logdet": info.logdet, "quad": info.quad,
         "ranks": {"max_c": info.max_rank_c, "max_l": info.max_rank_l, "mean_l": info.mean_rank_l},
         "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": 8 * n,
-                "d2h_bytes_per_step": 24},
+                "d2h_bytes_per_step": 24 * args.batch},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": dom["name"], "achieved": achieved,
                      "launches": dom["launches"], "kernel_ms": dom["ms"],
@@ -210,6 +223,24 @@ def run_gpu(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def batch_thetas(theta, B):
+    """The workload theta and B - 1 neighbours: +-0.25 along each transformed
+    coordinate of Sec. 5 (sigma0, ell0, nu0, tau0), cycling."""
+    ell, nu, s2, t2 = theta
+    x = [-math.log(math.sqrt(s2) / 2.0) / math.log(1.1), -math.log(ell) / math.log(1.5),
+         -math.log(nu) / math.log(1.2), -math.log(math.sqrt(t2)) / math.log(2.0)]
+    out = [tuple(theta)]
+    k = 0
+    while len(out) < B:
+        y = list(x)
+        y[k % 4] += 0.25 * (1 if (k // 4) % 2 == 0 else -1) * (1 + k // 8)
+        sig = 2.0 / 1.1 ** y[0]
+        tau = 1.0 / 2.0 ** y[3]
+        out.append((1.0 / 1.5 ** y[1], 1.0 / 1.2 ** y[2], sig * sig, tau * tau))
+        k += 1
+    return out
 
 
 def cpu_baseline(n_sub):
@@ -262,10 +293,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-sample-n", type=int, default=8192)
+    ap.add_argument("--batch", type=int, default=16,
+                    help="concurrent theta evaluations per step (hmle_loglik_batch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--roofline-kernel", default="k_tsqr_final",
                     help="sweep kernel whose launches are timed for the roofline line")

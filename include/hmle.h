@@ -202,6 +202,20 @@ hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tree,
                              const hmle_theta *theta, const double *Z,
                              double *loglik, hmle_eval_info *info);
 
+/* a15 (batched form): m evaluations L(theta_i) on one tree, up to
+ * `concurrency` of them in flight at once (0 means 8), each on its own
+ * evaluation buffers, stream pair and captured graph, so that independent
+ * trial points of the optimiser fill the GPU together.
+ *  thetas  m parameter sets;  Z  n doubles (caller order, host or device),
+ *          shared by all evaluations;  ll  m outputs (-inf for a failed one);
+ *  status  m per-evaluation statuses, or NULL.
+ * Returns the first hard error (CUDA, OOM, INVALID_ARG), or HMLE_OK; NOT_SPD
+ * and RANK_OVERFLOW are reported per evaluation only.  Device memory grows
+ * by one evaluation's buffers per concurrent slot (kept with the tree). */
+hmle_status hmle_loglik_batch(hmle_ctx *ctx, const hmle_tree *tree, const hmle_theta *thetas,
+                              int32_t m, const double *Z, int32_t concurrency, double *ll,
+                              int32_t *status);
+
 /* a13 (Sec. 2 and Sec. 5): maximise L over theta by Nelder-Mead in the
  * transformed coordinates sigma = 2/1.1^s0, ell = 1/1.5^l0, nu = 1/1.2^n0,
  * tau = 1/2^t0.  Trial points whose factorisation is not SPD score -inf.
@@ -213,6 +227,14 @@ hmle_status hmle_fit(hmle_ctx *ctx, const hmle_tree *tree, const double *Z,
                      const hmle_theta *theta0, const hmle_fit_opts *fopts,
                      hmle_theta *theta_hat, double *loglik_hat,
                      int32_t *n_iter, int32_t *n_evals);
+
+/* Field simulation (the test-data generator of the large workloads): factor
+ * C~(theta) and return Z = P^T L~ P xi, a sample of the zero-mean field with
+ * covariance C~ (Eq. 1's model, Sec. 1), where xi is white noise.
+ *  xi, Z  n doubles each in the caller's point order, host or device.
+ * Errors: as hmle_assemble and hmle_factor. */
+hmle_status hmle_simulate(hmle_ctx *ctx, const hmle_tree *tree, const hmle_theta *theta,
+                          const double *xi, double *Z);
 
 /* Matern correlation M_nu(x) = x^nu K_nu(x) / (2^(nu-1) Gamma(nu)) of Eq. 2
  * as the device evaluates it (Chebyshev tables built per nu from the

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -33,6 +34,8 @@ struct DevPlan {
   BlockDesc *blocks = nullptr;
   PanelDesc *panels = nullptr;
   GramTask *grams = nullptr;
+  GramChunk *gchunks = nullptr;
+  GramReduce *greds = nullptr;
   LrTarget *lrt = nullptr;
   SideEntry *aent = nullptr, *bent = nullptr;
   int32_t *apair = nullptr, *bpair = nullptr;
@@ -49,6 +52,7 @@ struct DevPlan {
   int32_t *leaf_beg = nullptr;
   int32_t *lr_ids = nullptr;
   int32_t *dense_ids = nullptr;
+  int32_t *mv_row0 = nullptr, *mv_blocks = nullptr;
   int64_t bytes = 0;
 };
 
@@ -64,6 +68,8 @@ struct hmle_tree {
   DevPlan dp;
   std::vector<int32_t> lr_ids, dense_ids;
   Work *work = nullptr;
+  std::vector<Work *> pool;  // evaluation buffers of hmle_loglik_batch
+  bool graphs = true;        // replay the sweep as a captured CUDA graph
 };
 
 struct hmle_hmatrix {
@@ -89,6 +95,8 @@ struct hmle_hfactor {
   double *out = nullptr;
   bool has_rhs = false;
   double logdet = 0.0, quad = 0.0;
+  double host_out[2] = {0.0, 0.0};   // results of an asynchronous evaluation
+  int host_flags[2] = {0, 0};
   int64_t launches = 0;
   int max_rank_l = 0;
   double mean_rank_l = 0.0;
@@ -98,8 +106,15 @@ struct hmle_hfactor {
 struct Work {
   hmle_hmatrix H;
   hmle_hfactor F;
+  cudaStream_t st = nullptr, side = nullptr;   // this evaluation's streams (batched use)
+  double *d_jacobi = nullptr;                  // its own Jacobi flop counter
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, done = nullptr;
   double *zdev = nullptr;
+  double *zperm = nullptr;         // permuted right-hand side staged for the graph
   bool ready = false;
+  cudaGraphExec_t exec = nullptr;  // captured sweep (replayed per theta)
+  int graph_kind = -2;             // profiling kind the graph was captured with
+  int graph_nev = 0;               // profiling events recorded by one replay
 };
 
 namespace {
@@ -140,10 +155,11 @@ cudaError_t upload(cudaStream_t st, T **dst, const std::vector<T> &v, int64_t &b
 }
 
 void free_devplan(cudaStream_t st, DevPlan &d) {
-  void *ptrs[] = {d.blocks, d.panels, d.grams, d.lrt, d.aent, d.bent, d.apair, d.bpair,
+  void *ptrs[] = {d.blocks, d.panels, d.grams, d.gchunks, d.greds, d.lrt, d.aent, d.bent, d.apair, d.bpair,
                   d.lrpairs, d.arow, d.brow, d.arow_ent, d.brow_ent, d.dns, d.dpairs,
                   d.dpair_tr, d.dpair_tc, d.wpan,
-                  d.hts, d.urows, d.uents, d.leaf_beg, d.lr_ids, d.dense_ids};
+                  d.hts, d.urows, d.uents, d.leaf_beg, d.lr_ids, d.dense_ids, d.mv_row0,
+                  d.mv_blocks};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, st);
   d = DevPlan{};
@@ -172,6 +188,21 @@ void free_f(cudaStream_t st, hmle_hfactor *f) {
     if (p) cudaFreeAsync(p, st);
   f->D = f->U = f->W = f->ws = nullptr;
   f->rank_l = nullptr; f->kept = nullptr; f->ldp = nullptr; f->flags = nullptr; f->out = nullptr;
+}
+
+void free_work(Work *w) {
+  if (!w) return;
+  if (w->exec) cudaGraphExecDestroy(w->exec);
+  free_hm(nullptr, &w->H);
+  free_f(nullptr, &w->F);
+  if (w->zdev) cudaFree(w->zdev);
+  if (w->d_jacobi) cudaFree(w->d_jacobi);
+  if (w->ev_fork) cudaEventDestroy(w->ev_fork);
+  if (w->ev_join) cudaEventDestroy(w->ev_join);
+  if (w->done) cudaEventDestroy(w->done);
+  if (w->st) cudaStreamDestroy(w->st);
+  if (w->side) cudaStreamDestroy(w->side);
+  delete w;
 }
 
 hmle_status alloc_hm(hmle_ctx *ctx, const hmle_tree *t, hmle_hmatrix *h) {
@@ -207,6 +238,7 @@ hmle_status alloc_f(hmle_ctx *ctx, const hmle_tree *t, hmle_hfactor *f) {
 // assemble into h (buffers allocated)
 hmle_status do_assemble(hmle_ctx *ctx, const hmle_tree *t, const hmle_theta *th, hmle_hmatrix *h) {
   cudaStream_t st = ctx->st;
+  cudaGetLastError();  // errors of earlier, unrelated runtime calls are not ours
   const Plan &P = t->plan;
   h->th = *th;
   ThetaDev td{1.0 / th->ell, th->sigma2, th->tau2, th->nu};
@@ -239,6 +271,7 @@ FactorArgs make_fargs(const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f
   const DevPlan &d = t->dp;
   FactorArgs F{};
   F.blocks = d.blocks; F.panels = d.panels; F.grams = d.grams; F.lrt = d.lrt;
+  F.gchunks = d.gchunks; F.greds = d.greds;
   F.aent = d.aent; F.bent = d.bent; F.apair = d.apair; F.bpair = d.bpair;
   F.lrpairs = d.lrpairs; F.arow = d.arow; F.brow = d.brow; F.arow_ent = d.arow_ent;
   F.brow_ent = d.brow_ent; F.dns = d.dns; F.dpairs = d.dpairs; F.wpan = d.wpan;
@@ -253,13 +286,74 @@ FactorArgs make_fargs(const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f
   return F;
 }
 
-hmle_status do_factor(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h,
-                      const double *zdev, hmle_hfactor *f) {
+// The launch sequence of one factorisation (sweep + finalize) on stream st.
+int64_t launch_sweep(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f,
+                     Prof *prof) {
+  cudaStream_t st = ctx->st;
+  const Plan &P = t->plan;
+  FactorArgs F = make_fargs(t, h, f);
+  F.jacobi_flops = ctx->d_jacobi;
+  cudaMemsetAsync(f->flags, 0, sizeof(int), st);
+  cudaMemsetAsync(f->rank_l, 0, sizeof(int32_t) * std::max<size_t>(P.blocks.size(), 1), st);
+  cudaMemsetAsync(ctx->d_jacobi, 0, sizeof(double), st);
+  int64_t nk = 2;  // permutation, finalize
+  for (int K = 0; K < P.nleaf; ++K)
+    nk += launch_step(st, ctx->side, ctx->ev_fork, ctx->ev_join, F, P.steps[K], K, P, prof);
+  const PanelDesc &rp = P.panels[P.rhs_panel];
+  launch_finalize(st, f->ldp, P.nleaf, f->W + rp.off, t->n, f->out);
+  return nk;
+}
+
+hmle_status launch_factor_async(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h,
+                                const double *zdev, hmle_hfactor *f, Work *w) {
   cudaStream_t st = ctx->st;
   const Plan &P = t->plan;
   f->h = h;
-  CK(cudaMemsetAsync(f->flags, 0, sizeof(int), st), "memset flags");
-  CK(cudaMemsetAsync(f->rank_l, 0, sizeof(int32_t) * std::max<size_t>(P.blocks.size(), 1), st), "memset");
+  const PanelDesc &rp = P.panels[P.rhs_panel];
+  launch_permute_in(st, zdev, t->T.perm, t->n, f->W + rp.off);
+  f->has_rhs = true;
+  if (!w) {
+    f->launches = launch_sweep(ctx, t, h, f, nullptr) + 2;
+  } else if (!w->exec || w->graph_kind != -1) {
+    if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int64_t nk = launch_sweep(ctx, t, h, f, nullptr);
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+    e = cudaGraphInstantiate(&w->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { w->exec = nullptr; return cuda_fail(ctx, e, "graph instantiate"); }
+    w->graph_kind = -1;
+    w->graph_nev = 0;
+    f->launches = nk + 2;
+  }
+  if (w) CK(cudaGraphLaunch(w->exec, st), "graph launch");
+  CK(cudaMemcpyAsync(f->host_out, f->out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "result copy");
+  CK(cudaMemcpyAsync(&f->host_flags[0], f->flags, sizeof(int), cudaMemcpyDeviceToHost, st), "flag copy");
+  CK(cudaMemcpyAsync(&f->host_flags[1], h->flags, sizeof(int), cudaMemcpyDeviceToHost, st), "flag copy");
+  return HMLE_OK;
+}
+
+hmle_status finish_factor(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f) {
+  CK(cudaStreamSynchronize(ctx->st), "factor sync");
+  f->logdet = f->host_out[0];
+  f->quad = f->host_out[1];
+  int fl = f->host_flags[0] | f->host_flags[1];
+  if (fl & kFlagNotSpd) return fail(ctx, HMLE_ERR_NOT_SPD, "non-positive pivot in a diagonal leaf");
+  if (fl & kFlagRankOverflow)
+    return fail(ctx, HMLE_ERR_RANK_OVERFLOW, "a low-rank block needed more than max_rank terms");
+  if (!std::isfinite(f->logdet) || !std::isfinite(f->quad))
+    return fail(ctx, HMLE_ERR_NOT_SPD, "non-finite log-determinant or quadratic form");
+  (void)t; (void)h;
+  return HMLE_OK;
+}
+
+hmle_status do_factor(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h,
+                      const double *zdev, hmle_hfactor *f, Work *w = nullptr) {
+  cudaStream_t st = ctx->st;
+  const Plan &P = t->plan;
+  f->h = h;
   const PanelDesc &rp = P.panels[P.rhs_panel];
   if (zdev) {
     launch_permute_in(st, zdev, t->T.perm, t->n, f->W + rp.off);
@@ -268,16 +362,33 @@ hmle_status do_factor(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h,
     CK(cudaMemsetAsync(f->W + rp.off, 0, sizeof(double) * t->n, st), "memset rhs");
     f->has_rhs = false;
   }
-  FactorArgs F = make_fargs(t, h, f);
   Prof *prof = ctx->prof.kind >= 0 ? &ctx->prof : nullptr;
-  F.jacobi_flops = ctx->d_jacobi;
-  CK(cudaMemsetAsync(ctx->d_jacobi, 0, sizeof(double), st), "memset");
-  int64_t nk = 4;  // table, ACA, permutation, finalize
-  for (int K = 0; K < P.nleaf; ++K)
-    nk += launch_step(st, ctx->side, ctx->ev_fork, ctx->ev_join, F, P.steps[K], K, P, prof);
-  f->launches = nk;
+  int nev = 0;
+  if (w) {
+    // replay (capturing first) the graph of the sweep
+    if (!w->exec || w->graph_kind != ctx->prof.kind) {
+      if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
+      cudaGraph_t g = nullptr;
+      if (prof) prof->used = 0;
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+      int64_t nk = launch_sweep(ctx, t, h, f, prof);
+      cudaError_t e = cudaStreamEndCapture(st, &g);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+      e = cudaGraphInstantiate(&w->exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) { w->exec = nullptr; return cuda_fail(ctx, e, "graph instantiate"); }
+      w->graph_kind = ctx->prof.kind;
+      w->graph_nev = prof ? prof->used : 0;
+      f->launches = nk + 2;  // + matern table, ACA
+    }
+    CK(cudaGraphLaunch(w->exec, st), "graph launch");
+    nev = w->graph_nev;
+  } else {
+    if (prof) prof->used = 0;
+    f->launches = launch_sweep(ctx, t, h, f, prof) + 2;
+    nev = prof ? prof->used : 0;
+  }
   CK(cudaGetLastError(), "factor launch");
-  launch_finalize(st, f->ldp, P.nleaf, f->W + rp.off, t->n, f->out);
   double out[2];
   int flags[2];
   CK(cudaMemcpyAsync(out, f->out, sizeof(out), cudaMemcpyDeviceToHost, st), "result copy");
@@ -287,7 +398,7 @@ hmle_status do_factor(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h,
   f->logdet = out[0];
   f->quad = out[1];
   if (prof) {
-    prof_collect(prof);
+    prof_collect(prof, nev);
     std::vector<int32_t> rc(P.blocks.size()), rl(P.blocks.size()), kp(std::max<size_t>(P.lrt.size(), 1));
     double jf = 0.0;
     CK(cudaMemcpy(rc.data(), h->rank_c, sizeof(int32_t) * rc.size(), cudaMemcpyDeviceToHost), "ranks");
@@ -426,6 +537,10 @@ hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n, int32_
   hmle_tree *t = new (std::nothrow) hmle_tree();
   if (!t) return HMLE_ERR_OOM;
   t->ctx = ctx; t->n = n; t->d = d; t->opts = o;
+  {  // HMLE_GRAPHS=0 launches the sweep kernel by kernel (for profilers)
+    const char *g = std::getenv("HMLE_GRAPHS");
+    t->graphs = !(g && g[0] == '0');
+  }
   double *rows = nullptr;
   bool owned = false;
   hmle_status s = stage_vec(ctx, locs, n * d, &rows, &owned);
@@ -462,12 +577,14 @@ hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n, int32_
   cudaError_t e = cudaSuccess;
 #define UP(f, v) if (e == cudaSuccess) e = upload(st, &dp.f, v, dp.bytes)
   UP(blocks, P.blocks); UP(panels, P.panels); UP(grams, P.grams); UP(lrt, P.lrt);
+  UP(gchunks, P.gchunks); UP(greds, P.greds);
   UP(aent, P.aent); UP(bent, P.bent); UP(apair, P.apair); UP(bpair, P.bpair);
   UP(lrpairs, P.lrpairs); UP(arow, P.arow); UP(brow, P.brow); UP(arow_ent, P.arow_ent);
   UP(brow_ent, P.brow_ent); UP(dns, P.dns); UP(dpairs, P.dpairs); UP(wpan, P.wpan);
   UP(dpair_tr, dtr); UP(dpair_tc, dtc);
   UP(hts, P.hts); UP(urows, P.urows); UP(uents, P.uents); UP(leaf_beg, leaf_beg);
   UP(lr_ids, t->lr_ids); UP(dense_ids, t->dense_ids);
+  UP(mv_row0, P.mv_row0); UP(mv_blocks, P.mv_blocks);
 #undef UP
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { hmle_tree_destroy(t); return cuda_fail(ctx, e, "plan upload"); }
@@ -481,11 +598,13 @@ void hmle_tree_destroy(hmle_tree *t) {
   cudaStream_t st = nullptr;
   cudaDeviceSynchronize();
   if (t->work) {
+    if (t->work->exec) cudaGraphExecDestroy(t->work->exec);
     free_hm(st, &t->work->H);
     free_f(st, &t->work->F);
     if (t->work->zdev) cudaFreeAsync(t->work->zdev, st);
     delete t->work;
   }
+  for (Work *w : t->pool) free_work(w);
   free_devplan(st, t->dp);
   if (t->T.xyz) cudaFreeAsync(t->T.xyz, st);
   if (t->T.perm) cudaFreeAsync(t->T.perm, st);
@@ -656,7 +775,7 @@ hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tc, const hmle_thet
     zd = w.zdev;
   }
   s = do_assemble(ctx, t, th, &w.H);
-  if (s == HMLE_OK) s = do_factor(ctx, t, &w.H, zd, &w.F);
+  if (s == HMLE_OK) s = do_factor(ctx, t, &w.H, zd, &w.F, t->graphs ? &w : nullptr);
   const double n = (double)t->n;
   double L = -0.5 * n * std::log(2.0 * M_PI) - 0.5 * w.F.logdet - 0.5 * w.F.quad;
   *ll = (s == HMLE_OK) ? L : -INFINITY;
@@ -674,6 +793,136 @@ hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tc, const hmle_thet
       info->mean_rank_l = mr;
     }
   }
+  return s;
+}
+
+hmle_status hmle_loglik_batch(hmle_ctx *ctx, const hmle_tree *tc, const hmle_theta *thetas,
+                              int32_t m, const double *Z, int32_t concurrency, double *ll,
+                              int32_t *status) {
+  if (!ctx || !tc || !thetas || !Z || !ll || m < 0) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  if (concurrency <= 0) concurrency = 8;
+  if (concurrency > 64) concurrency = 64;
+  for (int i = 0; i < m; ++i)
+    if (!theta_ok(&thetas[i])) return fail(ctx, HMLE_ERR_INVALID_ARG, "theta out of range");
+  hmle_tree *t = const_cast<hmle_tree *>(tc);
+  const int W = std::min<int>(concurrency, std::max(m, 1));
+  // evaluation buffers, each with its own stream pair (kept for reuse)
+  while ((int)t->pool.size() < W) {
+    Work *w = new (std::nothrow) Work();
+    if (!w) return HMLE_ERR_OOM;
+    cudaError_t e = cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&w->d_jacobi, sizeof(double));
+    if (e != cudaSuccess) { free_work(w); return cuda_fail(ctx, e, "batch streams"); }
+    hmle_ctx wc;                       // a context view on the work's streams
+    wc.st = w->st; wc.side = w->side; wc.ev_fork = w->ev_fork; wc.ev_join = w->ev_join;
+    wc.d_jacobi = w->d_jacobi;
+    hmle_status s = alloc_hm(&wc, t, &w->H);
+    if (s == HMLE_OK) s = alloc_f(&wc, t, &w->F);
+    if (s == HMLE_OK) {
+      e = cudaMallocAsync(&w->zdev, sizeof(double) * t->n, w->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(w->st);
+      if (e != cudaSuccess) s = cuda_fail(ctx, e, "batch alloc");
+    }
+    wc.d_jacobi = nullptr;
+    if (s != HMLE_OK) { free_work(w); return fail(ctx, s, wc.err.empty() ? ctx->err : wc.err); }
+    t->pool.push_back(w);
+  }
+  // stage Z once (shared by every evaluation, read-only)
+  double *zd = nullptr;
+  bool owned = false;
+  hmle_status s0 = stage_vec(ctx, Z, t->n, &zd, &owned);
+  if (s0 != HMLE_OK) return s0;
+  cudaEvent_t zready;
+  CK(cudaEventCreateWithFlags(&zready, cudaEventDisableTiming), "event");
+  CK(cudaEventRecord(zready, ctx->st), "event record");
+  hmle_status first = HMLE_OK;
+  const double nn = (double)t->n;
+  for (int i0 = 0; i0 < m; i0 += W) {
+    const int cnt = std::min(W, m - i0);
+    // launch every evaluation of the wave asynchronously
+    for (int k = 0; k < cnt; ++k) {
+      Work *w = t->pool[k];
+      hmle_ctx wc;
+      wc.st = w->st; wc.side = w->side; wc.ev_fork = w->ev_fork; wc.ev_join = w->ev_join;
+      wc.d_jacobi = w->d_jacobi;
+      cudaError_t ew = cudaStreamWaitEvent(w->st, zready, 0);
+      if (ew != cudaSuccess) { cudaEventDestroy(zready); return cuda_fail(ctx, ew, "stream wait"); }
+      hmle_status s = do_assemble(&wc, t, &thetas[i0 + k], &w->H);
+      if (s == HMLE_OK) s = launch_factor_async(&wc, t, &w->H, zd, &w->F, t->graphs ? w : nullptr);
+      wc.d_jacobi = nullptr;
+      if (s != HMLE_OK) { if (status) status[i0 + k] = s; if (first == HMLE_OK) { first = s; ctx->err = wc.err; } }
+      else if (status) status[i0 + k] = HMLE_OK;
+    }
+    // collect
+    for (int k = 0; k < cnt; ++k) {
+      Work *w = t->pool[k];
+      hmle_ctx wc;
+      wc.st = w->st; wc.side = w->side;
+      hmle_status s = finish_factor(&wc, t, &w->H, &w->F);
+      const int i = i0 + k;
+      ll[i] = (s == HMLE_OK) ? -0.5 * nn * std::log(2.0 * M_PI) - 0.5 * w->F.logdet - 0.5 * w->F.quad
+                             : -INFINITY;
+      if (status && status[i] == HMLE_OK) status[i] = s;
+      if (s != HMLE_OK && s != HMLE_ERR_NOT_SPD && s != HMLE_ERR_RANK_OVERFLOW && first == HMLE_OK) {
+        first = s;
+        ctx->err = wc.err;
+      }
+    }
+  }
+  cudaEventDestroy(zready);
+  if (owned) cudaFreeAsync(zd, ctx->st);
+  cudaStreamSynchronize(ctx->st);
+  return first;
+}
+
+hmle_status hmle_simulate(hmle_ctx *ctx, const hmle_tree *tc, const hmle_theta *th,
+                          const double *xi, double *Z) {
+  if (!ctx || !tc || !xi || !Z) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  if (!theta_ok(th)) return fail(ctx, HMLE_ERR_INVALID_ARG, "theta out of range");
+  hmle_tree *t = const_cast<hmle_tree *>(tc);
+  cudaStream_t st = ctx->st;
+  const Plan &P = t->plan;
+  const int64_t n = t->n;
+  hmle_hmatrix *h = nullptr;
+  hmle_status s = hmle_assemble(ctx, t, th, &h);
+  if (s != HMLE_OK) return s;
+  hmle_hfactor *f = new (std::nothrow) hmle_hfactor();
+  if (!f) { hmle_hmatrix_destroy(h); return HMLE_ERR_OOM; }
+  s = alloc_f(ctx, t, f);
+  if (s == HMLE_OK) s = do_factor(ctx, t, h, nullptr, f);
+  double *xd = nullptr, *xp = nullptr, *y = nullptr, *tw = nullptr, *zo = nullptr;
+  bool owned = false;
+  if (s == HMLE_OK) s = stage_vec(ctx, xi, n, &xd, &owned);
+  if (s == HMLE_OK) {
+    cudaError_t e = cudaMallocAsync(&xp, sizeof(double) * n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&y, sizeof(double) * n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&zo, sizeof(double) * n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&tw, sizeof(double) * std::max<size_t>(P.blocks.size(), 1) * P.kcap, st);
+    if (e != cudaSuccess) s = cuda_fail(ctx, e, "alloc simulate");
+  }
+  if (s == HMLE_OK) {
+    FactorArgs F = make_fargs(t, h, f);
+    launch_permute_in(st, xd, t->T.perm, n, xp);
+    launch_lower_matvec(st, F, t->dp.lr_ids, (int)t->lr_ids.size(), t->dp.mv_row0,
+                        t->dp.mv_blocks, P.nleaf, xp, y, tw);
+    launch_permute_out(st, y, t->T.perm, n, zo);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Z, zo, sizeof(double) * n, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_fail(ctx, e, "simulate");
+  }
+  if (owned) cudaFreeAsync(xd, st);
+  if (xp) cudaFreeAsync(xp, st);
+  if (y) cudaFreeAsync(y, st);
+  if (zo) cudaFreeAsync(zo, st);
+  if (tw) cudaFreeAsync(tw, st);
+  free_f(st, f);
+  delete f;
+  hmle_hmatrix_destroy(h);
   return s;
 }
 
@@ -751,24 +1000,28 @@ hmle_status hmle_fit(hmle_ctx *ctx, const hmle_tree *t, const double *Z, const h
   bool allzero = true;
   for (int i = 0; i < 4; ++i) { step[i] = fo.step[i]; allzero &= (step[i] == 0.0); }
   if (allzero) for (int i = 0; i < 4; ++i) step[i] = 1.0;
-  // stage Z once
   double *zd = nullptr;
   bool owned = false;
   hmle_status s = stage_vec(ctx, Z, t->n, &zd, &owned);
   if (s != HMLE_OK) return s;
   int nev = 0;
   hmle_status hard = HMLE_OK;
-  auto f = [&](const double x[4]) -> double {
-    hmle_theta th;
-    to_theta(x, &th);
-    ++nev;
-    if (!theta_ok(&th)) return INFINITY;
-    double ll;
-    hmle_status r = hmle_loglik_eval(ctx, t, &th, zd, &ll, nullptr);
-    if (r == HMLE_OK) return -ll;
-    if (r == HMLE_ERR_NOT_SPD || r == HMLE_ERR_RANK_OVERFLOW) return INFINITY;
-    hard = r;
-    return INFINITY;
+  // evaluate -L at several transformed points concurrently
+  auto fbatch = [&](const double (*xs)[4], int k, double *fv) {
+    hmle_theta th[5];
+    int idx[5], m = 0;
+    for (int i = 0; i < k; ++i) {
+      to_theta(xs[i], &th[m]);
+      if (theta_ok(&th[m])) { idx[m] = i; ++m; }
+      fv[i] = INFINITY;
+    }
+    if (m == 0) return;
+    double ll[5];
+    int32_t st[5];
+    hmle_status r = hmle_loglik_batch(ctx, t, th, m, zd, m, ll, st);
+    if (r != HMLE_OK) { hard = r; return; }
+    for (int j = 0; j < m; ++j)
+      fv[idx[j]] = (st[j] == HMLE_OK) ? -ll[j] : INFINITY;
   };
   double X[5][4], Fv[5];
   from_theta(theta0, X[0]);
@@ -776,7 +1029,8 @@ hmle_status hmle_fit(hmle_ctx *ctx, const hmle_tree *t, const double *Z, const h
     for (int j = 0; j < 4; ++j) X[i][j] = X[0][j];
     X[i][i - 1] += step[i - 1];
   }
-  for (int i = 0; i < 5 && hard == HMLE_OK; ++i) Fv[i] = f(X[i]);
+  fbatch(X, 5, Fv);
+  nev += 5;
   int it = 0;
   bool conv = false;
   while (hard == HMLE_OK) {
@@ -797,29 +1051,41 @@ hmle_status hmle_fit(hmle_ctx *ctx, const hmle_tree *t, const double *Z, const h
     ++it;
     double c[4] = {0, 0, 0, 0};
     for (int i = 0; i < 4; ++i) for (int j = 0; j < 4; ++j) c[j] += X[i][j] / 4.0;
-    double xr[4], xe[4], xc[4];
-    for (int j = 0; j < 4; ++j) xr[j] = c[j] + (c[j] - X[4][j]);
-    double fr = f(xr);
-    if (Fv[0] <= fr && fr < Fv[3]) { std::memcpy(X[4], xr, sizeof(xr)); Fv[4] = fr; continue; }
-    if (fr < Fv[0]) {
-      for (int j = 0; j < 4; ++j) xe[j] = c[j] + 2.0 * (c[j] - X[4][j]);
-      double fe = f(xe);
-      if (fe < fr) { std::memcpy(X[4], xe, sizeof(xe)); Fv[4] = fe; }
-      else { std::memcpy(X[4], xr, sizeof(xr)); Fv[4] = fr; }
-      continue;
+    // the four candidates of this iteration, evaluated together:
+    // reflection, expansion, outside and inside contraction
+    double cand[4][4], fc[4];
+    for (int j = 0; j < 4; ++j) {
+      const double d = c[j] - X[4][j];
+      cand[0][j] = c[j] + d;
+      cand[1][j] = c[j] + 2.0 * d;
+      cand[2][j] = c[j] + 0.5 * d;
+      cand[3][j] = c[j] - 0.5 * d;
     }
-    if (fr < Fv[4]) {
-      for (int j = 0; j < 4; ++j) xc[j] = c[j] + 0.5 * (xr[j] - c[j]);
-      double fc = f(xc);
-      if (fc <= fr) { std::memcpy(X[4], xc, sizeof(xc)); Fv[4] = fc; continue; }
+    fbatch(cand, 4, fc);
+    if (hard != HMLE_OK) break;
+    const double fr = fc[0];
+    ++nev;
+    bool shrink = false;
+    if (Fv[0] <= fr && fr < Fv[3]) {
+      std::memcpy(X[4], cand[0], sizeof(cand[0])); Fv[4] = fr;
+    } else if (fr < Fv[0]) {
+      ++nev;
+      if (fc[1] < fr) { std::memcpy(X[4], cand[1], sizeof(cand[1])); Fv[4] = fc[1]; }
+      else { std::memcpy(X[4], cand[0], sizeof(cand[0])); Fv[4] = fr; }
+    } else if (fr < Fv[4]) {
+      ++nev;
+      if (fc[2] <= fr) { std::memcpy(X[4], cand[2], sizeof(cand[2])); Fv[4] = fc[2]; }
+      else shrink = true;
     } else {
-      for (int j = 0; j < 4; ++j) xc[j] = c[j] + 0.5 * (X[4][j] - c[j]);
-      double fc = f(xc);
-      if (fc < Fv[4]) { std::memcpy(X[4], xc, sizeof(xc)); Fv[4] = fc; continue; }
+      ++nev;
+      if (fc[3] < Fv[4]) { std::memcpy(X[4], cand[3], sizeof(cand[3])); Fv[4] = fc[3]; }
+      else shrink = true;
     }
-    for (int i = 1; i < 5; ++i) {
-      for (int j = 0; j < 4; ++j) X[i][j] = X[0][j] + 0.5 * (X[i][j] - X[0][j]);
-      Fv[i] = f(X[i]);
+    if (shrink) {
+      for (int i = 1; i < 5; ++i)
+        for (int j = 0; j < 4; ++j) X[i][j] = X[0][j] + 0.5 * (X[i][j] - X[0][j]);
+      fbatch(&X[1], 4, &Fv[1]);
+      nev += 4;
     }
   }
   if (owned) cudaFreeAsync(zd, ctx->st);

@@ -46,46 +46,48 @@ constexpr int kGemmSmem = kTK * (kTM + kTN);  // doubles
 
 // C(i, j) = sum_k A(i, k) B(k, j) for i < M, j < N, k < K, delivered to
 // fc(i, j, value).  A_KFAST / B_KFAST: the operand is contiguous along k in
-// memory (chooses the coalesced loading order).  128 threads, 64 x 64
-// output tiles, 4 x 8 register micro-tiles, K staged 16 at a time.
-template <bool A_KFAST, bool B_KFAST, class FA, class FB, class FC>
-__device__ void cta_gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem) {
+// memory (chooses the coalesced loading order).  128 threads, 64 x TNX
+// output tiles (TNX = 64 or 32), 4 x (TNX / 8) register micro-tiles, K
+// staged 16 at a time.
+template <bool A_KFAST, bool B_KFAST, int TNX, class FA, class FB, class FC>
+__device__ void cta_gemm_t(int M, int N, int K, FA fa, FB fb, FC fc, double *smem) {
+  constexpr int MC = TNX / 8;
   double *sA = smem;
   double *sB = smem + kTK * kTM;
   const int tid = threadIdx.x;
   const int ti = tid & 15, tj = tid >> 4;
   for (int i0 = 0; i0 < M; i0 += kTM) {
-    for (int j0 = 0; j0 < N; j0 += kTN) {
-      double acc[4][8];
+    for (int j0 = 0; j0 < N; j0 += TNX) {
+      double acc[4][MC];
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 8; ++y) acc[x][y] = 0.0;
-      const bool active = (i0 + ti * 4 < M) && (j0 + tj * 8 < N);
+        for (int y = 0; y < MC; ++y) acc[x][y] = 0.0;
+      const bool active = (i0 + ti * 4 < M) && (j0 + tj * MC < N);
       for (int k0 = 0; k0 < K; k0 += kTK) {
         for (int e = tid; e < kTK * kTM; e += kThreads) {
           int k, i;
           if (A_KFAST) { k = e % kTK; i = e / kTK; } else { i = e % kTM; k = e / kTM; }
           sA[k * kTM + i] = (i0 + i < M && k0 + k < K) ? fa(i0 + i, k0 + k) : 0.0;
         }
-        for (int e = tid; e < kTK * kTN; e += kThreads) {
+        for (int e = tid; e < kTK * TNX; e += kThreads) {
           int k, j;
-          if (B_KFAST) { k = e % kTK; j = e / kTK; } else { j = e % kTN; k = e / kTN; }
-          sB[k * kTN + j] = (j0 + j < N && k0 + k < K) ? fb(k0 + k, j0 + j) : 0.0;
+          if (B_KFAST) { k = e % kTK; j = e / kTK; } else { j = e % TNX; k = e / TNX; }
+          sB[k * TNX + j] = (j0 + j < N && k0 + k < K) ? fb(k0 + k, j0 + j) : 0.0;
         }
         __syncthreads();
         if (active) {
           const int kk = min(kTK, K - k0);
           for (int k = 0; k < kk; ++k) {
-            double a[4], bb[8];
+            double a[4], bb[MC];
 #pragma unroll
             for (int x = 0; x < 4; ++x) a[x] = sA[k * kTM + ti * 4 + x];
 #pragma unroll
-            for (int y = 0; y < 8; ++y) bb[y] = sB[k * kTN + tj * 8 + y];
+            for (int y = 0; y < MC; ++y) bb[y] = sB[k * TNX + tj * MC + y];
 #pragma unroll
             for (int x = 0; x < 4; ++x)
 #pragma unroll
-              for (int y = 0; y < 8; ++y) acc[x][y] = fma(a[x], bb[y], acc[x][y]);
+              for (int y = 0; y < MC; ++y) acc[x][y] = fma(a[x], bb[y], acc[x][y]);
           }
         }
         __syncthreads();
@@ -94,8 +96,8 @@ __device__ void cta_gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem)
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int y = 0; y < 8; ++y) {
-            int i = i0 + ti * 4 + x, j = j0 + tj * 8 + y;
+          for (int y = 0; y < MC; ++y) {
+            int i = i0 + ti * 4 + x, j = j0 + tj * MC + y;
             if (i < M && j < N) fc(i, j, acc[x][y]);
           }
       }
@@ -103,11 +105,11 @@ __device__ void cta_gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem)
   }
 }
 
-// Sample width of the randomised compression of target block blk: the ACA
-// rank of C_T plus the oversampling, capped at r.
-__device__ __forceinline__ int sample_width(const FactorArgs &F, int blk) {
-  int k = F.rank_c[blk];
-  return min(F.r, max(8, k) + F.osamp);
+// cta_gemm_t with the output tile width picked from N.
+template <bool A_KFAST, bool B_KFAST, class FA, class FB, class FC>
+__device__ __forceinline__ void cta_gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem) {
+  if (N <= 32) cta_gemm_t<A_KFAST, B_KFAST, 32>(M, N, K, fa, fb, fc, smem);
+  else cta_gemm_t<A_KFAST, B_KFAST, 64>(M, N, K, fa, fb, fc, smem);
 }
 
 // C(i, j) = sum_k A(k, i) B(k, j) for small outputs (M x N) and long K: the
@@ -164,6 +166,13 @@ __device__ void cta_gemm_tn(int M, int N, int K, FA fa, FB fb, FC fc, double *sm
   }
 }
 
+// Sample width of the randomised compression of target block blk: the ACA
+// rank of C_T plus the oversampling, capped at r.
+__device__ __forceinline__ int sample_width(const FactorArgs &F, int blk) {
+  int k = F.rank_c[blk];
+  return min(F.r, max(8, k) + F.osamp);
+}
+
 // --- block accessors -----------------------------------------------------
 
 struct Acc {
@@ -193,17 +202,32 @@ struct Acc {
 };
 
 // --- P1 -------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_gram(FactorArgs F, int g0) {
+// One CTA per row chunk of a gram G = W_A[ov]^T W_B[ov] (ranks x ranks).
+__global__ void __launch_bounds__(kThreads) k_gram(FactorArgs F, int c0) {
   extern __shared__ double smem[];
   Acc a(F);
-  const GramTask g = F.grams[g0 + blockIdx.x];
+  const GramChunk ch = F.gchunks[c0 + blockIdx.x];
+  const GramTask g = F.grams[ch.g];
   const BlockDesc A = F.blocks[g.a], B = F.blocks[g.b];
-  double *out = F.ws + g.goff;
+  double *out = F.ws + ch.out;
   const int kc = F.kcap;
   cta_gemm_tn(
-      F.rank_l[g.a], F.rank_l[g.b], g.ove - g.ovb, [&](int k, int i) { return a.W(A, g.ovb + k, i); },
-      [&](int k, int j) { return a.W(B, g.ovb + k, j); },
+      F.rank_l[g.a], F.rank_l[g.b], ch.r1 - ch.r0, [&](int k, int i) { return a.W(A, ch.r0 + k, i); },
+      [&](int k, int j) { return a.W(B, ch.r0 + k, j); },
       [&](int i, int j, double v) { out[i + (int64_t)j * kc] = v; }, smem);
+}
+
+// Sum of the chunks of a gram, in chunk order.
+__global__ void __launch_bounds__(kThreads) k_gram_reduce(FactorArgs F, int r0) {
+  const GramReduce R = F.greds[r0 + blockIdx.x];
+  const GramTask g = F.grams[R.g];
+  const int kc = F.kcap, ka = F.rank_l[g.a], kb = F.rank_l[g.b];
+  for (int e = threadIdx.x; e < ka * kb; e += blockDim.x) {
+    const int i = e % ka, j = e / ka;
+    double v = 0.0;
+    for (int c = 0; c < R.nchunk; ++c) v += F.ws[R.poff + (int64_t)c * kc * kc + i + j * kc];
+    F.ws[g.goff + i + j * kc] = v;
+  }
 }
 
 // --- P2a / P4a: t = U_X[rows]^T X[rows] for side entries; t_C for targets --
@@ -1037,15 +1061,16 @@ void prof_mark(Prof *p, cudaStream_t s) {
   cudaEventRecord(p->ev[p->used++], s);
 }
 
-void prof_collect(Prof *p) {
-  for (int i = 0; i + 1 < p->used; i += 2) {
+void prof_collect(Prof *p, int nev) {
+  for (int i = 0; i + 1 < nev; i += 2) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p->ev[i], p->ev[i + 1]) == cudaSuccess) {
       p->ms += ms;
       ++p->launches;
+    } else {
+      cudaGetLastError();  // do not leave the failure for an unrelated status check
     }
   }
-  p->used = 0;
 }
 
 #define LAUNCH(KIND, strm, ...)                                   \
@@ -1065,7 +1090,8 @@ int launch_step(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEve
   const int smt = std::max(kGemmSmem + F.b * F.b, kTnSmem) * (int)sizeof(double);
   const int smd = (kGemmSmem + std::max(F.b, F.kcap) * F.b) * (int)sizeof(double);
   const int r = F.r;
-  if (S.gram1 > S.gram0) { LAUNCH(KK_GRAM, st, k_gram<<<S.gram1 - S.gram0, kThreads, smt, st>>>(F, S.gram0)); }
+  if (S.gch1 > S.gch0) { LAUNCH(KK_GRAM, st, k_gram<<<S.gch1 - S.gch0, kThreads, smt, st>>>(F, S.gch0)); }
+  if (S.gred1 > S.gred0) { LAUNCH(KK_GRAM, st, k_gram_reduce<<<S.gred1 - S.gred0, kThreads, 0, st>>>(F, S.gred0)); }
   // the dense blocks of column K (P6-P8) only need the grams: fork them to
   // the side stream while the low-rank targets are compressed
   cudaStream_t sd = side ? side : st;
@@ -1124,6 +1150,71 @@ int launch_step(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEve
   if (S.ht1 > S.ht0) { LAUNCH(KK_HTASK, st, k_htask<<<S.ht1 - S.ht0, kThreads, smt, st>>>(F, S.ht0)); }
   if (S.ur1 > S.ur0) { LAUNCH(KK_UPDROW, st, k_updrow<<<S.ur1 - S.ur0, kThreads, sm, st>>>(F, S.ur0)); }
   return nk;
+}
+
+// --- a17: y = L x (field simulation Z = L xi) ------------------------------
+// t_A = W_A^T x[cols A] for every low-rank block of L ...
+__global__ void __launch_bounds__(kThreads) k_lmv_t(FactorArgs F, const int32_t *lr_ids,
+                                                     const double *__restrict__ x,
+                                                     double *__restrict__ t) {
+  extern __shared__ double smem[];
+  Acc a(F);
+  const int blk = lr_ids[blockIdx.x];
+  const BlockDesc A = F.blocks[blk];
+  cta_gemm_tn(
+      F.rank_l[blk], 1, A.cend - A.cbeg, [&](int k, int i) { return a.W(A, A.cbeg + k, i); },
+      [&](int k, int j) { return x[A.cbeg + k]; },
+      [&](int i, int j, double v) { t[(int64_t)blk * F.kcap + i] = v; }, smem);
+}
+
+// ... then each leaf row sums its blocks: dense D x[cols] (the diagonal block
+// is lower triangular) and U_A[I] t_A, in a fixed order.
+__global__ void __launch_bounds__(kThreads) k_lmv_rows(FactorArgs F, const int32_t *row0,
+                                                        const int32_t *rblocks,
+                                                        const double *__restrict__ x,
+                                                        const double *__restrict__ t,
+                                                        double *__restrict__ y) {
+  Acc a(F);
+  const int I = blockIdx.x;
+  const int I0 = F.leaf_beg[I], I1 = F.leaf_beg[I + 1];
+  for (int i = I0 + threadIdx.x; i < I1; i += blockDim.x) {
+    double acc = 0.0;
+    for (int q = row0[I]; q < row0[I + 1]; ++q) {
+      const int blk = rblocks[q];
+      const BlockDesc B = F.blocks[blk];
+      if (B.kind == kDense) {
+        for (int j = 0; j < B.cend - B.cbeg; ++j) acc = fma(a.U(B, i, j), x[B.cbeg + j], acc);
+      } else {
+        for (int k = 0; k < F.rank_l[blk]; ++k) acc = fma(a.U(B, i, k), t[(int64_t)blk * F.kcap + k], acc);
+      }
+    }
+    y[i] = acc;
+  }
+}
+
+__global__ void k_permute_out(const double *__restrict__ y, const int32_t *__restrict__ perm,
+                              int64_t n, double *__restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[perm[i]] = y[i];
+}
+
+void launch_lower_matvec(cudaStream_t st, const FactorArgs &F, const int32_t *lr_ids, int nlr,
+                         const int32_t *row0, const int32_t *rblocks, int nleaf,
+                         const double *x, double *y, double *t) {
+  const int smt = std::max(kGemmSmem + F.b * F.b, kTnSmem) * (int)sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_lmv_t, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (kGemmSmem + kMaxLeaf * kMaxLeaf) * (int)sizeof(double));
+    attr = true;
+  }
+  if (nlr > 0) k_lmv_t<<<nlr, kThreads, smt, st>>>(F, lr_ids, x, t);
+  k_lmv_rows<<<nleaf, kThreads, 0, st>>>(F, row0, rblocks, x, t, y);
+}
+
+void launch_permute_out(cudaStream_t st, const double *y, const int32_t *perm, int64_t n,
+                        double *out) {
+  k_permute_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y, perm, n, out);
 }
 
 void launch_permute_in(cudaStream_t st, const double *z, const int32_t *perm, int64_t n,

@@ -57,6 +57,21 @@ struct GramTask {
   int64_t goff;            // offset in the gram workspace
 };
 
+// A row chunk of a gram: rows [r0, r1) of the overlap, written to out
+// (the gram itself when it has one chunk, else a partial sum).
+struct GramChunk {
+  int32_t g;               // index of the GramTask
+  int32_t r0, r1;
+  int64_t out;
+};
+
+// Sum of a gram's partial chunks (fixed order) into the gram.
+struct GramReduce {
+  int32_t g;
+  int32_t nchunk;
+  int64_t poff;
+};
+
 // Pair (A, B) contributing -U_A G_AB U_B^T to a low-rank target; a and b
 // are indices of the A- and B-entries (SideEntry) of that target.
 struct LrPair {
@@ -130,6 +145,8 @@ struct UpdEntry {
 // Ranges of one step's tasks in the flat arrays.
 struct StepRange {
   int32_t gram0, gram1;
+  int32_t gch0, gch1;      // gram row chunks
+  int32_t gred0, gred1;    // grams needing a reduction of their chunks
   int32_t lrt0, lrt1;
   int32_t aent0, aent1;
   int32_t bent0, bent1;
@@ -154,6 +171,8 @@ struct Plan {
   int64_t dense_words, uc_words, u_words, w_words;
   // flat task arrays
   std::vector<GramTask> grams;
+  std::vector<GramChunk> gchunks;
+  std::vector<GramReduce> greds;
   std::vector<LrTarget> lrt;
   std::vector<SideEntry> aent, bent;
   std::vector<int32_t> apair, bpair;            // pair indices per entry
@@ -167,6 +186,9 @@ struct Plan {
   std::vector<UpdRow> urows;
   std::vector<UpdEntry> uents;
   std::vector<StepRange> steps;
+  // triangular H-matvec y = L x (simulation): per leaf row, the blocks of L
+  // covering it (diagonal first)
+  std::vector<int32_t> mv_row0, mv_blocks;
   int64_t ws_max;
   int64_t n_lr_blocks, n_dense_blocks;
 };

@@ -34,6 +34,8 @@ struct FactorArgs {
   const BlockDesc *blocks;
   const PanelDesc *panels;
   const GramTask *grams;
+  const GramChunk *gchunks;
+  const GramReduce *greds;
   const LrTarget *lrt;
   const SideEntry *aent, *bent;
   const int32_t *apair, *bpair;
@@ -93,13 +95,15 @@ extern const char *const kKernelNames[KK_COUNT];
 struct Prof {
   int kind = -1;
   std::vector<cudaEvent_t> ev;
-  int used = 0;
+  int used = 0;                 // events recorded by the current launch sequence
   double ms = 0.0;
   int64_t launches = 0;
   double flops = 0.0;
 };
 void prof_mark(Prof *p, cudaStream_t s);
-void prof_collect(Prof *p);     // after a stream synchronisation
+// after a stream synchronisation: add the elapsed times of the first nev
+// events (pairs) and keep the pool for reuse
+void prof_collect(Prof *p, int nev);
 
 // One step K of the sweep (all phases), given the step's ranges.
 // Returns the number of kernels launched.
@@ -110,6 +114,15 @@ int launch_step(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEve
 
 void launch_permute_in(cudaStream_t st, const double *z, const int32_t *perm, int64_t n,
                        double *out);
+// y = L x in cluster order (x, y: n doubles); t: workspace of kcap doubles
+// per block; lr_ids / nlr: the low-rank blocks; row0 / rblocks: per leaf row
+// the blocks covering it (device copies of Plan::mv_row0 / mv_blocks).
+void launch_lower_matvec(cudaStream_t st, const FactorArgs &F, const int32_t *lr_ids, int nlr,
+                         const int32_t *row0, const int32_t *rblocks, int nleaf,
+                         const double *x, double *y, double *t);
+// out[perm[k]] = y[k]
+void launch_permute_out(cudaStream_t st, const double *y, const int32_t *perm, int64_t n,
+                        double *out);
 // logdet = sum(parts[0..N)), quad = |w|^2; out[0] = logdet, out[1] = quad
 void launch_finalize(cudaStream_t st, const double *parts, int N, const double *w, int64_t n,
                      double *out);

@@ -174,6 +174,16 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
   Bd.stampA.assign(P.blocks.size(), 0);
   Bd.stampB.assign(P.blocks.size(), 0);
 
+  // rows of L for the triangular matvec: diagonal block, then the rest
+  P.mv_row0.assign(N + 1, 0);
+  P.mv_blocks.clear();
+  for (int I = 0; I < N; ++I) {
+    P.mv_row0[I] = (int32_t)P.mv_blocks.size();
+    P.mv_blocks.push_back(P.diag_of_leaf[I]);
+    P.mv_blocks.insert(P.mv_blocks.end(), Bd.rowlist[I].begin(), Bd.rowlist[I].end());
+  }
+  P.mv_row0[N] = (int32_t)P.mv_blocks.size();
+
   // blocks grouped by first column leaf / by last column leaf
   std::vector<std::vector<int32_t>> starts(N), ends(N);
   for (size_t x = 0; x < P.blocks.size(); ++x) {
@@ -183,7 +193,7 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
       ends[B.cleaf + Bd.span(B) - 1].push_back((int32_t)x);
   }
 
-  P.grams.clear(); P.lrt.clear(); P.aent.clear(); P.bent.clear();
+  P.grams.clear(); P.gchunks.clear(); P.greds.clear(); P.lrt.clear(); P.aent.clear(); P.bent.clear();
   P.apair.clear(); P.bpair.clear(); P.lrpairs.clear();
   P.arow.clear(); P.brow.clear(); P.arow_ent.clear(); P.brow_ent.clear();
   P.dns.clear(); P.dpairs.clear(); P.wpan.clear(); P.hts.clear();
@@ -344,6 +354,29 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
     st.gram1 = (int32_t)P.grams.size();
     st.dpws = ws;
     ws += (int64_t)(P.dns[st.dns1 - 1].p1 - P.dns[st.dns0].p0) * b * b;
+    // row chunks of the grams (512 rows each), partial sums reduced in order
+    st.gch0 = (int32_t)P.gchunks.size();
+    st.gred0 = (int32_t)P.greds.size();
+    for (int gi = st.gram0; gi < st.gram1; ++gi) {
+      const GramTask &g = P.grams[gi];
+      const int len = g.ove - g.ovb, nch = std::max(1, (len + 511) / 512);
+      int64_t poff = -1;
+      if (nch > 1) {
+        poff = ws;
+        ws += (int64_t)nch * kk;
+        P.greds.push_back(GramReduce{gi, nch, poff});
+      }
+      for (int c = 0; c < nch; ++c) {
+        GramChunk ch{};
+        ch.g = gi;
+        ch.r0 = g.ovb + c * 512;
+        ch.r1 = std::min(g.ove, ch.r0 + 512);
+        ch.out = nch > 1 ? poff + (int64_t)c * kk : g.goff;
+        P.gchunks.push_back(ch);
+      }
+    }
+    st.gch1 = (int32_t)P.gchunks.size();
+    st.gred1 = (int32_t)P.greds.size();
 
     // 3. panels advanced by the forward solve of leaf K
     st.wpan0 = (int32_t)P.wpan.size();

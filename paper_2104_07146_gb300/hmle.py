@@ -86,6 +86,8 @@ def lib():
             "hmle_fit": ([P, P, P, P, P, P, P, P, P], C.c_int),
             "hmle_matern_eval": ([P, C.c_double, P, C.c_int64, P], C.c_int),
             "hmle_profile_select": ([P, C.c_char_p], C.c_int),
+            "hmle_simulate": ([P, P, P, P, P], C.c_int),
+            "hmle_loglik_batch": ([P, P, P, C.c_int32, P, C.c_int32, P, P], C.c_int),
             "hmle_profile_read": ([P, P, P, P], C.c_int),
         }
         for name, (argt, rest) in sigs.items():
@@ -103,7 +105,7 @@ def exported_symbols():
             "hmle_tree_permutation", "hmle_assemble", "hmle_hmatrix_destroy",
             "hmle_hmatrix_matvec", "hmle_factor", "hmle_factor_destroy", "hmle_loglik",
             "hmle_loglik_eval", "hmle_fit", "hmle_matern_eval", "hmle_profile_select",
-            "hmle_profile_read"]
+            "hmle_profile_read", "hmle_simulate", "hmle_loglik_batch"]
 
 
 def _ptr(a):
@@ -236,6 +238,27 @@ class Tree:
                                     C.byref(ll), C.byref(info))
         self.ctx.check(st, "hmle_loglik_eval")
         return ll.value, info
+
+    def loglik_batch(self, thetas, Z, concurrency=8):
+        """m evaluations of Eq. 1 run concurrently: returns (L array, status array)."""
+        thetas = list(thetas)
+        m = len(thetas)
+        arr = (Theta * max(m, 1))(*[_theta(t) for t in thetas])
+        ll = np.empty(m, dtype=np.float64)
+        stt = np.empty(m, dtype=np.int32)
+        p, keep = _ptr(Z)
+        st = lib().hmle_loglik_batch(self.ctx._h, self._h, arr, m, p, int(concurrency),
+                                     P(ll.ctypes.data), P(stt.ctypes.data))
+        self.ctx.check(st, "hmle_loglik_batch")
+        return ll, stt
+
+    def simulate(self, theta, xi) -> np.ndarray:
+        """Z = P^T L~ P xi: a sample of the field with covariance C~(theta)."""
+        xi = np.ascontiguousarray(xi, dtype=np.float64)
+        Z = np.empty_like(xi)
+        self.ctx.check(lib().hmle_simulate(self.ctx._h, self._h, C.byref(_theta(theta)),
+                                           P(xi.ctypes.data), P(Z.ctypes.data)), "hmle_simulate")
+        return Z
 
     def assemble(self, theta) -> "HMatrix":
         return HMatrix(self, theta)

@@ -137,3 +137,106 @@ def test_deterministic_repeat(ctx):
     a = t.loglik((0.1, 0.9, 1.0, 0.01), Z)[0]
     b = t.loglik((0.1, 0.9, 1.0, 0.01), Z)[0]
     assert a == b
+
+
+def test_simulated_field_matches_dense_factor(ctx):
+    # The Cholesky factor of an SPD matrix is unique, so the H-Cholesky factor
+    # L~ of the cluster-ordered C~ approximates the dense factor of P C P^T
+    # entry-wise: Z = P^T L~ P xi must match P^T chol(P C P^T) P xi.
+    n = 2000
+    locs = synth.locations_uniform(n, 2, seed=1000)
+    th = (0.1, 0.5, 1.0, 0.01)
+    xi = synth.normal(41, n)
+    t = _tree(ctx, locs, leaf_size=32, aca_eps=1e-10, max_rank=48, oversample=16)
+    Z = t.simulate(th, xi)
+    perm = t.permutation()
+    Zc = oracle.simulate(locs[perm], th, xi[perm])     # dense factor in cluster order
+    ref = np.empty(n)
+    ref[perm] = Zc
+    assert np.linalg.norm(Z - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+def test_simulated_field_quadratic_form_is_xi_norm(ctx):
+    # Z = L~ xi  =>  Z^T C~^{-1} Z = |xi|^2 with the same factor
+    n = 3001
+    locs = synth.locations_blobs(n, 2, 0.3, 8, 0.03, seed=43)
+    th = (0.05, 0.8, 1.0, 1e-3)
+    xi = synth.normal(44, n)
+    t = _tree(ctx, locs, leaf_size=32, aca_eps=1e-7, max_rank=48, oversample=16)
+    Z = t.simulate(th, xi)
+    ll, info = t.loglik(th, Z)
+    assert abs(info.quad - float(xi @ xi)) <= 1e-9 * float(xi @ xi)
+
+
+def _kalman_exponential(x, z, ell, s2, t2):
+    """Exact Eq. 1 for the exponential kernel (nu = 1/2) on sorted collinear
+    points: an Ornstein-Uhlenbeck state with observation noise tau2, by the
+    prediction-error decomposition of a scalar Kalman filter."""
+    m, P = 0.0, s2
+    ll = 0.0
+    for i in range(len(x)):
+        if i > 0:
+            rho = math.exp(-(x[i] - x[i - 1]) / ell)
+            m, P = rho * m, rho * rho * P + s2 * (1 - rho * rho)
+        S = P + t2
+        e = z[i] - m
+        ll += -0.5 * (math.log(2 * math.pi) + math.log(S) + e * e / S)
+        K = P / S
+        m, P = m + K * e, (1 - K) * P
+    return ll
+
+
+@pytest.mark.slow
+def test_full_size_exponential_on_a_line_matches_kalman(ctx):
+    # n = 65,536 (the medium workload's size): exact O(n) reference, no dense oracle
+    n = 65536
+    locs = synth.locations_collinear(n, seed=51)
+    Z = synth.normal(52, n)
+    th = (0.02, 0.5, 1.0, 1e-3)
+    t = _tree(ctx, locs, leaf_size=64, aca_eps=1e-8)
+    ll, info = t.loglik(th, Z)
+    ref = _kalman_exponential(locs[:, 0], Z, th[0], th[2], th[3])
+    assert abs(ll - ref) / n <= 1e-6, (ll, ref)
+
+
+@pytest.mark.slow
+def test_medium_workload_subset_16384(ctx):
+    # the medium workload's first 16,384 points (70 % uniform + 30 % blobs),
+    # its theta at nu = 1/2, leaf 64, eps 1e-6; Z = L xi from the dense oracle
+    locs = synth.medium_locations(65536)[:16384]
+    _parity(ctx, locs, (0.05, 0.5, 1.0, 1e-3), 64, 1e-6, 53, field=True)
+
+
+def test_batched_evaluations_match_single(ctx):
+    # concurrent evaluations (own buffers, streams and graphs) give the same
+    # bits as one-at-a-time evaluations
+    n = 2000
+    locs = synth.locations_uniform(n, 2, seed=61)
+    Z = synth.normal(62, n)
+    t = _tree(ctx, locs, leaf_size=32, aca_eps=1e-8)
+    thetas = [(0.1, 0.5, 1.0, 0.01), (0.15, 0.7, 1.2, 0.02), (0.08, 1.1, 0.9, 0.01),
+              (0.2, 0.5, 1.0, 0.05), (0.12, 1.6, 1.1, 0.01), (0.1, 0.5, 0.0, 0.0)]
+    ll, st = t.loglik_batch(thetas, Z, concurrency=4)
+    for k, th in enumerate(thetas[:-1]):
+        assert st[k] == 0
+        assert ll[k] == t.loglik(th, Z)[0]
+    assert st[-1] == 2 and ll[-1] == -math.inf       # sigma2 = tau2 = 0: NOT_SPD
+
+
+@pytest.mark.slow
+def test_fit_matches_oracle_fit(ctx):
+    # Nelder-Mead MLE (Sec. 2; transform of Sec. 5) on a simulated field from
+    # the small configuration's start point: the GPU optimum is as likely,
+    # under the exact oracle likelihood, as the oracle's own optimum
+    n = 600
+    locs = synth.locations_uniform(n, 2, seed=71)
+    th = (0.1, 0.5, 1.0, 0.01)
+    Z = oracle.simulate(locs, th, synth.normal(72, n))
+    th0 = (0.2, 1.0, 0.5, 0.05)
+    t = _tree(ctx, locs, leaf_size=32, aca_eps=1e-9, max_rank=48, oversample=16)
+    th_gpu, ll_gpu, it, nev, st = t.fit(Z, th0)
+    assert st == 0, (it, nev)
+    th_cpu, ll_cpu, it_c, nev_c = oracle.fit(locs, Z, th0)
+    ll_gpu_exact = oracle.loglik_dense(locs, Z, th_gpu)[0]
+    assert abs(ll_gpu - ll_gpu_exact) / n <= 1e-6
+    assert ll_gpu_exact >= ll_cpu - 1e-3 * abs(ll_cpu) / n - 1e-3
