@@ -243,6 +243,27 @@ hmle_status hmle_simulate(hmle_ctx *ctx, const hmle_tree *tree, const hmle_theta
 hmle_status hmle_matern_eval(hmle_ctx *ctx, double nu, const double *x,
                              int64_t m, double *out);
 
+/* hmle_matern_eval without any device allocation, for callers that cannot
+ * allocate: a host application that owns the device memory and gives this
+ * library a fixed budget it must not grow, or code in a section where
+ * cudaMalloc is not allowed (it may synchronise the device, and it is
+ * refused while a stream is being captured).  The paper has no counterpart;
+ * this is an interface convenience.
+ *  nus  nnu values of nu (host array), 1 <= nnu <= 16: the per-nu tables
+ *       live in a static device array sized for 16 of them (about 60 KB per
+ *       device, held until the process exits); more is INVALID_ARG.
+ *  x    m doubles already in device memory; out: nnu * m doubles in device
+ *       memory, out[j*m + i] = M_{nus[j]}(x[i]).  Host pointers are
+ *       INVALID_ARG: nothing is staged or copied.
+ * The work is enqueued on the context's stream and the call returns without
+ * waiting: synchronise that stream before reading out.  The first call on a
+ * device looks up the static array's device address (cudaGetSymbolAddress),
+ * so make that first call before any stream capture begins.  Every call
+ * shares the one array and overwrites it: calls whose work overlaps on the
+ * GPU (other streams, other contexts) race, and must be serialised. */
+hmle_status hmle_matern_eval_noalloc(hmle_ctx *ctx, const double *nus, int32_t nnu,
+                                     const double *x, int64_t m, double *out);
+
 /* Measurement support (no counterpart in the paper).  Select one kernel of
  * the factorisation sweep by name (e.g. "k_tsqr_final", "k_dense_pair"; NULL
  * switches timing off).  While selected, every launch of that kernel is

@@ -441,6 +441,11 @@ hmle_status stage_vec(hmle_ctx *ctx, const double *src, int64_t n, double **dev,
 
 extern "C" {
 
+// stream of a context, for the other translation units of the library
+__attribute__((visibility("hidden"))) cudaStream_t hmle_internal_ctx_stream(const hmle_ctx *c) {
+  return c ? c->st : nullptr;
+}
+
 hmle_status hmle_opts_default(hmle_opts *o) {
   if (!o) return HMLE_ERR_INVALID_ARG;
   o->leaf_size = 64;

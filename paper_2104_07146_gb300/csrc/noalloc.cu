@@ -1,0 +1,79 @@
+// hmle_matern_eval_noalloc: the Matern-table evaluation without any device
+// allocation, for callers that cannot allocate -- a host that hands this
+// library a fixed device-memory budget it must not grow, or code in a
+// section where cudaMalloc is not allowed (it may synchronise the device,
+// and it is refused while a stream is being captured).
+//
+// The scratch that the allocating entry point (hmle_matern_eval) obtains
+// with cudaMallocAsync -- one Chebyshev table per value of nu -- lives here
+// in a file-scope static device array instead.  Host code must not use that
+// array's name as a device address: it is resolved once per device with
+// cudaGetSymbolAddress (the first call on a device does this set-up, so that
+// first call should be made before any stream capture begins).
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "hmle_internal.h"
+#include "kernels.cuh"
+#include "matern.cuh"
+
+namespace hmle {
+namespace {
+
+constexpr int kStaticNu = 16;  // at most 16 tables: 16 * 470 doubles = 60 KB per device
+
+static __device__ __align__(256) double g_matern_scratch[kStaticNu * kTableWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+double *g_scratch_ptr[kMaxDevices] = {nullptr};
+
+}  // namespace
+}  // namespace hmle
+
+using namespace hmle;
+
+struct hmle_ctx;  // defined in capi.cu; only its stream is needed here
+extern "C" __attribute__((visibility("hidden"))) cudaStream_t hmle_internal_ctx_stream(const hmle_ctx *ctx);
+
+extern "C" hmle_status hmle_matern_eval_noalloc(hmle_ctx *ctx, const double *nus, int32_t nnu,
+                                                const double *x, int64_t m, double *out) {
+  if (!ctx || !nus || !x || !out || m < 0) return HMLE_ERR_INVALID_ARG;
+  if (nnu < 1 || nnu > kStaticNu) return HMLE_ERR_INVALID_ARG;  // beyond the static scratch
+  for (int j = 0; j < nnu; ++j)
+    if (!(nus[j] > 0.0) || !(nus[j] <= 20.0)) return HMLE_ERR_INVALID_ARG;
+  // inputs and outputs must already be on the device: nothing is staged
+  cudaPointerAttributes ax, ao;
+  if (cudaPointerGetAttributes(&ax, x) != cudaSuccess || cudaPointerGetAttributes(&ao, out) != cudaSuccess) {
+    cudaGetLastError();
+    return HMLE_ERR_INVALID_ARG;
+  }
+  if (ax.type != cudaMemoryTypeDevice && ax.type != cudaMemoryTypeManaged) return HMLE_ERR_INVALID_ARG;
+  if (ao.type != cudaMemoryTypeDevice && ao.type != cudaMemoryTypeManaged) return HMLE_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HMLE_ERR_CUDA;
+  double *scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_ptr[dev]) {
+      // set-up, once per device, with that device current
+      double *p = nullptr;
+      if (cudaGetSymbolAddress((void **)&p, g_matern_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return HMLE_ERR_CUDA;
+      }
+      g_scratch_ptr[dev] = p;
+    }
+    scratch = g_scratch_ptr[dev];
+  }
+  cudaStream_t st = hmle_internal_ctx_stream(ctx);
+  // every word of each table is written by its table kernel before the
+  // evaluation kernel reads it, so nothing left by a previous call is used
+  for (int j = 0; j < nnu; ++j) {
+    launch_matern_table(st, nus[j], scratch + (int64_t)j * kTableWords);
+    launch_matern_eval(st, scratch + (int64_t)j * kTableWords, x, m, out + (int64_t)j * m);
+  }
+  return cudaGetLastError() == cudaSuccess ? HMLE_OK : HMLE_ERR_CUDA;
+}

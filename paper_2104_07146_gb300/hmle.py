@@ -88,6 +88,7 @@ def lib():
             "hmle_profile_select": ([P, C.c_char_p], C.c_int),
             "hmle_simulate": ([P, P, P, P, P], C.c_int),
             "hmle_loglik_batch": ([P, P, P, C.c_int32, P, C.c_int32, P, P], C.c_int),
+            "hmle_matern_eval_noalloc": ([P, P, C.c_int32, P, C.c_int64, P], C.c_int),
             "hmle_profile_read": ([P, P, P, P], C.c_int),
         }
         for name, (argt, rest) in sigs.items():
@@ -105,7 +106,8 @@ def exported_symbols():
             "hmle_tree_permutation", "hmle_assemble", "hmle_hmatrix_destroy",
             "hmle_hmatrix_matvec", "hmle_factor", "hmle_factor_destroy", "hmle_loglik",
             "hmle_loglik_eval", "hmle_fit", "hmle_matern_eval", "hmle_profile_select",
-            "hmle_profile_read", "hmle_simulate", "hmle_loglik_batch"]
+            "hmle_profile_read", "hmle_simulate", "hmle_loglik_batch",
+            "hmle_matern_eval_noalloc"]
 
 
 def _ptr(a):
