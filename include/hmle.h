@@ -55,7 +55,19 @@ typedef enum {
   HMLE_ERR_NOT_IMPLEMENTED = 8
 } hmle_status;
 
-typedef enum { HMLE_FP64 = 0 } hmle_precision;
+/* Arithmetic of the factorisation.
+ *  HMLE_FP64        every step in FP64.
+ *  HMLE_MIXED_FP32  the mixed form: the products of the Schur-complement
+ *                   updates and of the W-panel solves run in FP32 with FP32
+ *                   accumulation; the QR / SVD recompression, the diagonal
+ *                   POTRF, the TRSM, the log-determinant and the solves used
+ *                   as a preconditioner stay FP64.  log|C~| comes from the
+ *                   mixed factor; Z^T C~^{-1} Z is won back by preconditioned
+ *                   conjugate gradients on the FP64 H-matrix of C with the
+ *                   mixed factor as preconditioner (pcg_tol, pcg_max_iter).
+ *                   The mixed factor is truncated at max(aca_eps, 1e-7): the
+ *                   FP32 products leave noise near 1e-7 of a block's norm. */
+typedef enum { HMLE_FP64 = 0, HMLE_MIXED_FP32 = 1 } hmle_precision;
 
 /* Matern parameters of Eq. 2: range ell > 0, smoothness nu > 0,
  * variance sigma2 >= 0, nugget tau2 >= 0. */
@@ -78,7 +90,10 @@ typedef struct {
  *             compression (the result is deterministic for a given seed).
  *  leaf_lowrank  0 (default): admissible blocks between two leaf clusters
  *             (at most leaf_size^2 entries) are kept dense and exact; 1: they
- *             are held low-rank like the coarser admissible blocks. */
+ *             are held low-rank like the coarser admissible blocks.
+ *  pcg_tol, pcg_max_iter  mixed form only: PCG stops when |r| <= pcg_tol |Z|
+ *             (default 1e-10) or fails with HMLE_ERR_NOT_CONVERGED after
+ *             pcg_max_iter iterations (default 50). */
 typedef struct {
   int32_t leaf_size;
   double eta;
@@ -88,6 +103,8 @@ typedef struct {
   int32_t precision; /* hmle_precision */
   uint64_t seed;
   int32_t leaf_lowrank;
+  double pcg_tol;
+  int32_t pcg_max_iter;
 } hmle_opts;
 
 /* Nelder-Mead options of hmle_fit (Sec. 2: threshold 1e-4, <= 400 iterations). */
@@ -120,6 +137,8 @@ typedef struct {
   double mean_rank_l;   /* mean rank of low-rank blocks of L~ */
   int32_t status;       /* hmle_status of the evaluation */
   int64_t kernel_launches; /* CUDA kernels this evaluation launched */
+  int32_t pcg_iters;    /* mixed form: PCG iterations (0 in FP64) */
+  double pcg_relres;    /* mixed form: final |r| / |Z| */
 } hmle_eval_info;
 
 typedef struct hmle_ctx hmle_ctx;
@@ -187,12 +206,21 @@ hmle_status hmle_factor(hmle_ctx *ctx, const hmle_hmatrix *h, const double *Z,
                         hmle_hfactor **out);
 void hmle_factor_destroy(hmle_hfactor *f);
 
-/* a9-a12 (Eq. 1): log-likelihood from a factor.  If the factor was built
- * with the same Z pointer contents the fused solve is reused, otherwise a
- * forward-solve sweep runs.  loglik must not be NULL; logdet and quad may be.
- * Errors: INVALID_ARG, CUDA. */
+/* a9-a12 (Eq. 1): log-likelihood from a factor.  With Z (n doubles, caller
+ * order, host or device) the forward solve w = L~^{-1} P Z runs as a sweep
+ * through the stored factor and q = |w|^2; with Z = NULL the solve fused
+ * into hmle_factor is used (INVALID_ARG if the factor was built without Z).
+ * loglik must not be NULL; logdet and quad may be.  Errors: INVALID_ARG, CUDA. */
 hmle_status hmle_loglik(hmle_ctx *ctx, const hmle_hfactor *f, const double *Z,
                         double *loglik, double *logdet, double *quad);
+
+/* a10-a11 (Sec. 2: "solve the linear system"; Eq. 4's C11^{-1} Z1): X =
+ * C~^{-1} Z = P^T L~^{-T} L~^{-1} P Z, by the forward sweep and the reverse
+ * (backward) sweep through the factor.  Z, X: n doubles in caller order,
+ * host or device (they may not alias).  Afterwards hmle_loglik(f, NULL)
+ * returns L for this Z.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+hmle_status hmle_solve(hmle_ctx *ctx, const hmle_hfactor *f, const double *Z, double *X);
 
 /* One full evaluation L(theta): assemble + factor with the fused solve +
  * combine, on a tree.  info may be NULL.  This is the unit of work of the
@@ -215,6 +243,46 @@ hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tree,
 hmle_status hmle_loglik_batch(hmle_ctx *ctx, const hmle_tree *tree, const hmle_theta *thetas,
                               int32_t m, const double *Z, int32_t concurrency, double *ll,
                               int32_t *status);
+
+/* a15 (batched form over instances): one task = one field on one tree at
+ * one theta.  Tasks may mix trees of different sizes n (instances of uneven
+ * n) and repeat a tree with many thetas (simplex vertices, line-search
+ * trials); they run in waves of up to `concurrency` (0 means 8), each on a
+ * buffer of its own tree, streams and captured graph as in
+ * hmle_loglik_batch.  Z of a task: n_tree doubles in caller order, host or
+ * device; tasks that pass the same Z pointer share one staged copy.
+ * Outputs and errors as hmle_loglik_batch. */
+typedef struct {
+  const hmle_tree *tree;
+  hmle_theta theta;
+  const double *Z;
+} hmle_task;
+hmle_status hmle_loglik_multi(hmle_ctx *ctx, const hmle_task *tasks, int32_t ntask,
+                              int32_t concurrency, double *ll, int32_t *status);
+
+/* a15: autotuner of the batched form (project-written; the paper has no
+ * counterpart).  For this point set (locs n x d, row-major, host or device)
+ * and theta it builds trees with leaf sizes 32, 64 and 128 (the tile of the
+ * leaf sweep; other options from base) and times hmle_loglik_batch at
+ * concurrency 1, 2, 4, ... up to max_concurrency (0 means 16), stopping a
+ * leaf size once doubling the concurrency gains less than 5 %.  Each trial is
+ * one warm-up batch (buffers, graph capture) and one timed batch.
+ *  best    the fastest (leaf_size, concurrency, evals_per_s); best->trials =
+ *          number of trials run.
+ *  trials  if not NULL, up to max_trials trial results in run order;
+ *          *ntrials (may be NULL) receives the number run.
+ * The trees are destroyed before returning.  Errors: INVALID_ARG, OOM,
+ * CUDA, or the first evaluation error if no trial succeeded. */
+typedef struct {
+  int32_t leaf_size;
+  int32_t concurrency;
+  double evals_per_s;
+  int32_t trials;
+} hmle_tune_result;
+hmle_status hmle_autotune(hmle_ctx *ctx, const double *locs, int64_t n, int32_t d,
+                          const hmle_opts *base, const hmle_theta *theta, const double *Z,
+                          int32_t max_concurrency, hmle_tune_result *best,
+                          hmle_tune_result *trials, int32_t max_trials, int32_t *ntrials);
 
 /* a13 (Sec. 2 and Sec. 5): maximise L over theta by Nelder-Mead in the
  * transformed coordinates sigma = 2/1.1^s0, ell = 1/1.5^l0, nu = 1/1.2^n0,
@@ -263,6 +331,68 @@ hmle_status hmle_matern_eval(hmle_ctx *ctx, double nu, const double *x,
  * GPU (other streams, other contexts) race, and must be serialised. */
 hmle_status hmle_matern_eval_noalloc(hmle_ctx *ctx, const double *nus, int32_t nnu,
                                      const double *x, int64_t m, double *out);
+
+/* The positivity transform of Sec. 5 (the coordinates hmle_fit searches):
+ * sigma = 2 / 1.1^x0, ell = 1 / 1.5^x1, nu = 1 / 1.2^x2, tau = 1 / 2^x3, with
+ * sigma2 = sigma^2, tau2 = tau^2.  hmle_theta_to_x needs sigma2, tau2 > 0;
+ * hmle_x_to_theta rejects non-finite x or a theta out of range.
+ * Errors: INVALID_ARG. */
+hmle_status hmle_theta_to_x(const hmle_theta *theta, double x[4]);
+hmle_status hmle_x_to_theta(const double x[4], hmle_theta *theta);
+
+/* a16 (learned start; Sec. 7 suggests precomputing the initial guess of the
+ * optimiser).  A 35-64-64-8 perceptron (tanh, FP32) maps field statistics to
+ * an initial theta (4 transformed coordinates of Sec. 5) and log initial
+ * simplex steps (4), trained on the GPU with hand-written kernels on fields
+ * simulated by hmle_simulate.
+ *
+ * hmle_features: the 35 inputs for one field.  locs n x d row-major and Z
+ * (n, caller order), host or device.  On m = min(n, 4096) points at caller
+ * indices floor(i n / m): the empirical semivariogram in 32 bins of squared
+ * distance h^2 (bin k: S 2^(k-32) <= h^2 < S 2^(k-31); below bin 1 -> bin 0;
+ * h^2 = S -> bin 31; S = squared bounding-box diagonal of the sample):
+ * feat[k] = log of the bin's mean of (Z_i - Z_j)^2 / 2 (an empty bin copies
+ * the nearest non-empty bin above it, else below); feat[32] = log n,
+ * feat[33] = d, feat[34] = log sqrt(S).  feat: 35 floats, host.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+hmle_status hmle_features(hmle_ctx *ctx, const double *locs, int64_t n, int32_t d, const double *Z,
+                          float *feat);
+
+/* The perceptron.  Parameters: one flat FP32 array of hmle_mlp_nparams()
+ * values: W1 (64 x 35, row-major), b1 (64), W2 (64 x 64), b2 (64), W3 (8 x 64),
+ * b3 (8); inputs are standardised with per-feature mu / sd (35 each) before
+ * the first layer.  Outputs per field (8): mu_1..4 (transformed theta) and
+ * s_1..4 (log steps).  Training minimises the batch mean of the Gaussian
+ * negative log-likelihood sum_c [exp(-2 s_c) (t_c - mu_c)^2 / 2 + s_c] by Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8).  Every reduction is in a fixed order.
+ *  create   weights uniform in +-1/sqrt(fan_in) from a counter-based
+ *           generator seeded by `seed`, zero biases, mu = 0, sd = 1.
+ *  set/get  parameters (host or device, may be NULL), mu, sd (host, may be
+ *           NULL); set resets the Adam state.
+ *  forward  m fields: feats m x 35 (host or device) -> out m x 8.
+ *  grad     gradient of the batch loss at feats / targets (m x 4) -> grad
+ *           (nparams), *loss = batch mean loss (either may be NULL).
+ *  adam_step  one Adam update with a given gradient (host or device).
+ *  train    sets mu / sd from feats, then `epochs` passes over the data in
+ *           minibatches of `batch` (a seeded deterministic shuffle per
+ *           epoch, remainder dropped) with learning rate lr; *loss_first /
+ *           *loss_last = mean loss of the first / last epoch (may be NULL).
+ * Errors: INVALID_ARG, OOM, CUDA. */
+typedef struct hmle_mlp hmle_mlp;
+int32_t hmle_mlp_nparams(void);
+hmle_status hmle_mlp_create(hmle_ctx *ctx, uint64_t seed, hmle_mlp **out);
+void hmle_mlp_destroy(hmle_mlp *mlp);
+hmle_status hmle_mlp_set(hmle_ctx *ctx, hmle_mlp *mlp, const float *params, const float *mu,
+                         const float *sd);
+hmle_status hmle_mlp_get(hmle_ctx *ctx, const hmle_mlp *mlp, float *params, float *mu, float *sd);
+hmle_status hmle_mlp_forward(hmle_ctx *ctx, const hmle_mlp *mlp, const float *feats, int32_t m,
+                             float *out);
+hmle_status hmle_mlp_grad(hmle_ctx *ctx, const hmle_mlp *mlp, const float *feats,
+                          const float *targets, int32_t m, float *grad, float *loss);
+hmle_status hmle_mlp_adam_step(hmle_ctx *ctx, hmle_mlp *mlp, const float *grad, float lr);
+hmle_status hmle_mlp_train(hmle_ctx *ctx, hmle_mlp *mlp, const float *feats, const float *targets,
+                           int32_t m, int32_t epochs, int32_t batch, float lr, uint64_t seed,
+                           float *loss_first, float *loss_last);
 
 /* Measurement support (no counterpart in the paper).  Select one kernel of
  * the factorisation sweep by name (e.g. "k_tsqr_final", "k_dense_pair"; NULL

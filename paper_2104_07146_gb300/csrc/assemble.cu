@@ -8,7 +8,6 @@
 //    |u_k| |v_k| <= eps |S_k|_F, with |S_k|_F^2 updated from the new cross
 //    and its inner products with the previous ones.  Dense leaf blocks are
 //    not stored: the factorisation generates their entries on the fly.
-//  * k_hmatvec_*: y = C~ x, a check of the assembled matrix.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -183,65 +182,6 @@ __global__ void __launch_bounds__(256) k_aca(AsmArgs A) {
   }
 }
 
-// y (cluster order) = C~ x: dense leaf blocks (both triangles) ...
-__global__ void k_hmatvec_dense(AsmArgs A, const int32_t *__restrict__ dense_ids, int nd,
-                                const double *__restrict__ x, double *__restrict__ y) {
-  // one block per dense block; accumulate rows with atomics (check path only)
-  const int blk = dense_ids[blockIdx.x];
-  const BlockDesc B = A.blocks[blk];
-  const int m = B.rend - B.rbeg, p = B.cend - B.cbeg;
-  const bool diag = (B.rbeg == B.cbeg);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < p; ++j)
-      s = fma(cov_entry(A.tab, A.xyz, A.n, A.d, B.rbeg + i, B.cbeg + j, A.inv_ell, A.sigma2,
-                        A.tau2),
-              x[B.cbeg + j], s);
-    atomicAdd(&y[B.rbeg + i], s);
-  }
-  if (!diag) {
-    for (int j = threadIdx.x; j < p; j += blockDim.x) {
-      double s = 0.0;
-      for (int i = 0; i < m; ++i)
-        s = fma(cov_entry(A.tab, A.xyz, A.n, A.d, B.rbeg + i, B.cbeg + j, A.inv_ell, A.sigma2,
-                          A.tau2),
-                x[B.rbeg + i], s);
-      atomicAdd(&y[B.cbeg + j], s);
-    }
-  }
-}
-
-// ... and low-rank blocks U V^T and their transposes.
-__global__ void k_hmatvec_lr(AsmArgs A, const double *__restrict__ x, double *__restrict__ y) {
-  __shared__ double red[32];
-  __shared__ double t1[kMaxRank + 8], t2[kMaxRank + 8];
-  const int blk = A.lr_ids[blockIdx.x];
-  const BlockDesc B = A.blocks[blk];
-  const int m = B.rend - B.rbeg, p = B.cend - B.cbeg, kc = A.kc;
-  const int k = A.rank_c[blk];
-  const double *U = A.uc + B.off_uc, *V = A.uc + B.off_vc;
-  for (int l = 0; l < k; ++l) {
-    double a = 0.0, c = 0.0;
-    for (int j = threadIdx.x; j < p; j += blockDim.x) a = fma(V[(int64_t)l * p + j], x[B.cbeg + j], a);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) c = fma(U[(int64_t)l * m + i], x[B.rbeg + i], c);
-    a = block_sum(a, red);
-    c = block_sum(c, red);
-    if (threadIdx.x == 0) { t1[l] = a; t2[l] = c; }
-  }
-  __syncthreads();
-  (void)kc;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    double s = 0.0;
-    for (int l = 0; l < k; ++l) s = fma(U[(int64_t)l * m + i], t1[l], s);
-    atomicAdd(&y[B.rbeg + i], s);
-  }
-  for (int j = threadIdx.x; j < p; j += blockDim.x) {
-    double s = 0.0;
-    for (int l = 0; l < k; ++l) s = fma(V[(int64_t)l * p + j], t2[l], s);
-    atomicAdd(&y[B.cbeg + j], s);
-  }
-}
-
 void launch_matern_table(cudaStream_t st, double nu, double *tab) {
   k_matern_table<<<kNint, 32, 0, st>>>(nu, tab);
 }
@@ -251,11 +191,6 @@ void launch_matern_eval(cudaStream_t st, const double *tab, const double *x, int
 }
 void launch_aca(cudaStream_t st, const AsmArgs &A, int n_lr) {
   if (n_lr > 0) k_aca<<<n_lr, 256, 0, st>>>(A);
-}
-void launch_hmatvec(cudaStream_t st, const AsmArgs &A, const int32_t *dense_ids, int nd,
-                    int n_lr, const double *x, double *y) {
-  if (nd > 0) k_hmatvec_dense<<<nd, 128, 0, st>>>(A, dense_ids, nd, x, y);
-  if (n_lr > 0) k_hmatvec_lr<<<n_lr, 128, 0, st>>>(A, x, y);
 }
 
 }  // namespace hmle

@@ -53,6 +53,14 @@ struct DevPlan {
   int32_t *lr_ids = nullptr;
   int32_t *dense_ids = nullptr;
   int32_t *mv_row0 = nullptr, *mv_blocks = nullptr;
+  HTask *hts_rhs = nullptr;
+  UpdRow *urows_rhs = nullptr;
+  UpdEntry *uents_rhs = nullptr;
+  int32_t *wpan_rhs = nullptr;
+  int32_t *bh_blocks = nullptr;
+  UpdRow *bupd = nullptr;
+  UpdEntry *bents = nullptr;
+  int32_t *mvt_row0 = nullptr, *mvt_blocks = nullptr, *lr_slot = nullptr;
   int64_t bytes = 0;
 };
 
@@ -101,6 +109,10 @@ struct hmle_hfactor {
   int max_rank_l = 0;
   double mean_rank_l = 0.0;
   bool owned = true;
+  double *pcg = nullptr;      // mixed form: right-hand side + PCG workspace
+  cudaGraphExec_t pcg_init = nullptr, pcg_iter = nullptr;   // its captured sequences
+  int pcg_iters = 0;
+  double pcg_relres = 0.0;
 };
 
 struct Work {
@@ -159,7 +171,8 @@ void free_devplan(cudaStream_t st, DevPlan &d) {
                   d.lrpairs, d.arow, d.brow, d.arow_ent, d.brow_ent, d.dns, d.dpairs,
                   d.dpair_tr, d.dpair_tc, d.wpan,
                   d.hts, d.urows, d.uents, d.leaf_beg, d.lr_ids, d.dense_ids, d.mv_row0,
-                  d.mv_blocks};
+                  d.mv_blocks, d.hts_rhs, d.urows_rhs, d.uents_rhs, d.wpan_rhs, d.bh_blocks,
+                  d.bupd, d.bents, d.mvt_row0, d.mvt_blocks, d.lr_slot};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, st);
   d = DevPlan{};
@@ -183,10 +196,13 @@ void free_hm(cudaStream_t st, hmle_hmatrix *h) {
 }
 
 void free_f(cudaStream_t st, hmle_hfactor *f) {
-  void *ptrs[] = {f->D, f->U, f->W, f->ws, f->rank_l, f->kept, f->ldp, f->flags, f->out};
+  void *ptrs[] = {f->D, f->U, f->W, f->ws, f->rank_l, f->kept, f->ldp, f->flags, f->out, f->pcg};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, st);
-  f->D = f->U = f->W = f->ws = nullptr;
+  f->D = f->U = f->W = f->ws = f->pcg = nullptr;
+  if (f->pcg_init) cudaGraphExecDestroy(f->pcg_init);
+  if (f->pcg_iter) cudaGraphExecDestroy(f->pcg_iter);
+  f->pcg_init = f->pcg_iter = nullptr;
   f->rank_l = nullptr; f->kept = nullptr; f->ldp = nullptr; f->flags = nullptr; f->out = nullptr;
 }
 
@@ -266,6 +282,8 @@ hmle_status do_assemble(hmle_ctx *ctx, const hmle_tree *t, const hmle_theta *th,
   return HMLE_OK;
 }
 
+constexpr double kMixedTruncEps = 1e-7;  // truncation floor of the mixed factor
+
 FactorArgs make_fargs(const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f) {
   const Plan &P = t->plan;
   const DevPlan &d = t->dp;
@@ -283,7 +301,59 @@ FactorArgs make_fargs(const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f
   F.eps = t->opts.aca_eps; F.seed = t->opts.seed;
   F.b = P.b; F.kcap = P.kcap; F.kc = P.kc; F.r = P.r;
   F.osamp = t->opts.oversample;
+  F.mixed = t->opts.precision == HMLE_MIXED_FP32 ? 1 : 0;
+  // The FP32 products leave noise of about 1e-7 of |C_T| in a Schur
+  // complement; truncating below that would keep noise as rank.  The mixed
+  // factor is truncated at max(eps, 1e-7); the accuracy of the quadratic
+  // form comes from the FP64 operator of the PCG (ACA at eps).
+  if (F.mixed) F.eps = std::max(F.eps, kMixedTruncEps);
   return F;
+}
+
+// a14: in the mixed form the quadratic form of the fused forward solve carries
+// the FP32 rounding of the factor; it is replaced by b^T x with C x = b solved
+// by PCG (FP64 operator, the mixed factor as preconditioner).  zdev: Z in the
+// caller's order, on the device.
+hmle_status mixed_quad(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f,
+                       const double *zdev) {
+  cudaStream_t st = ctx->st;
+  const Plan &P = t->plan;
+  const int nlr = (int)t->lr_ids.size();
+  int hmax = 1;
+  for (int K = 0; K < P.nleaf; ++K) hmax = std::max(hmax, P.bh0[K + 1] - P.bh0[K]);
+  if (!f->pcg) {
+    const int64_t words = t->n + pcg_words(t->n, nlr, P.kc, hmax * P.kcap);
+    cudaError_t e = cudaMallocAsync(&f->pcg, sizeof(double) * words, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pcg workspace");
+  }
+  double *b = f->pcg;
+  launch_permute_in(st, zdev, t->T.perm, t->n, b);
+  AsmArgs A{};
+  A.blocks = t->dp.blocks; A.lr_ids = t->dp.lr_ids; A.xyz = t->T.xyz; A.n = t->n; A.d = t->d;
+  A.tab = h->tab; A.inv_ell = 1.0 / h->th.ell; A.sigma2 = h->th.sigma2; A.tau2 = h->th.tau2;
+  A.kc = P.kc; A.uc = h->uc; A.rank_c = h->rank_c; A.cnorm = h->cnorm; A.flags = h->flags;
+  A.thd = h->thd;
+  CmvLists L{P.nleaf, t->dp.leaf_beg, t->dp.mv_row0, t->dp.mv_blocks, t->dp.mvt_row0,
+             t->dp.mvt_blocks, t->dp.lr_slot};
+  FactorArgs Fs = make_fargs(t, h, f);
+  Fs.hts = t->dp.hts_rhs;
+  Fs.urows = t->dp.urows_rhs;
+  Fs.uents = t->dp.uents_rhs;
+  double q = 0.0, rel = 0.0;
+  int it = 0;
+  const PanelDesc &rp = P.panels[P.rhs_panel];
+  cudaError_t e = pcg_quad(st, A, nlr, L, Fs, P, t->dp.wpan_rhs, t->dp.bh_blocks, t->dp.bupd,
+                           t->dp.bents, f->W + rp.off, b, t->n, t->opts.pcg_tol,
+                           t->opts.pcg_max_iter, f->pcg + t->n, &q, &it, &rel,
+                           t->graphs ? &f->pcg_init : nullptr, t->graphs ? &f->pcg_iter : nullptr);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "pcg");
+  f->quad = q;
+  f->pcg_iters = it;
+  f->pcg_relres = rel;
+  f->has_rhs = true;
+  if (!(rel <= t->opts.pcg_tol) || !std::isfinite(q))
+    return fail(ctx, HMLE_ERR_NOT_CONVERGED, "PCG: relative residual above pcg_tol after pcg_max_iter");
+  return HMLE_OK;
 }
 
 // The launch sequence of one factorisation (sweep + finalize) on stream st.
@@ -329,14 +399,19 @@ hmle_status launch_factor_async(hmle_ctx *ctx, const hmle_tree *t, const hmle_hm
     f->launches = nk + 2;
   }
   if (w) CK(cudaGraphLaunch(w->exec, st), "graph launch");
-  CK(cudaMemcpyAsync(f->host_out, f->out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "result copy");
-  CK(cudaMemcpyAsync(&f->host_flags[0], f->flags, sizeof(int), cudaMemcpyDeviceToHost, st), "flag copy");
-  CK(cudaMemcpyAsync(&f->host_flags[1], h->flags, sizeof(int), cudaMemcpyDeviceToHost, st), "flag copy");
+  // no copy to host here: host_out is pageable, and a device-to-pageable copy
+  // returns only when it has completed, which would make the caller wait for
+  // this evaluation before it can launch the next one
   return HMLE_OK;
 }
 
 hmle_status finish_factor(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f) {
-  CK(cudaStreamSynchronize(ctx->st), "factor sync");
+  cudaStream_t st = ctx->st;
+  CK(cudaStreamSynchronize(st), "factor sync");
+  CK(cudaMemcpyAsync(f->host_out, f->out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "result copy");
+  CK(cudaMemcpyAsync(&f->host_flags[0], f->flags, sizeof(int), cudaMemcpyDeviceToHost, st), "flag copy");
+  CK(cudaMemcpyAsync(&f->host_flags[1], h->flags, sizeof(int), cudaMemcpyDeviceToHost, st), "flag copy");
+  CK(cudaStreamSynchronize(st), "result sync");
   f->logdet = f->host_out[0];
   f->quad = f->host_out[1];
   int fl = f->host_flags[0] | f->host_flags[1];
@@ -399,6 +474,10 @@ hmle_status do_factor(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h,
   f->quad = out[1];
   if (prof) {
     prof_collect(prof, nev);
+    if (prof->failed)
+      ctx->err = "profiler: " + std::to_string(prof->failed) + " event pairs unreadable (" +
+                 cudaGetErrorString((cudaError_t)prof->first_err) + "), " + std::to_string(nev) +
+                 " events recorded";
     std::vector<int32_t> rc(P.blocks.size()), rl(P.blocks.size()), kp(std::max<size_t>(P.lrt.size(), 1));
     double jf = 0.0;
     CK(cudaMemcpy(rc.data(), h->rank_c, sizeof(int32_t) * rc.size(), cudaMemcpyDeviceToHost), "ranks");
@@ -454,6 +533,8 @@ hmle_status hmle_opts_default(hmle_opts *o) {
   o->max_rank = 32;
   o->oversample = 8;
   o->precision = HMLE_FP64;
+  o->pcg_tol = 1e-10;
+  o->pcg_max_iter = 50;
   o->seed = 0x5eed;
   o->leaf_lowrank = 0;
   return HMLE_OK;
@@ -519,7 +600,10 @@ hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n, int32_
     return fail(ctx, HMLE_ERR_INVALID_ARG, "max_rank must be a multiple of 8 in [8, 64]");
   if (o.oversample < 4 || o.max_rank + o.oversample > 64)
     return fail(ctx, HMLE_ERR_INVALID_ARG, "oversample >= 4 and max_rank + oversample <= 64");
-  if (o.precision != HMLE_FP64) return fail(ctx, HMLE_ERR_NOT_IMPLEMENTED, "precision");
+  if (o.precision != HMLE_FP64 && o.precision != HMLE_MIXED_FP32)
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "precision");
+  if (o.precision == HMLE_MIXED_FP32 && !(o.pcg_tol > 0.0 && o.pcg_max_iter >= 1))
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "pcg_tol / pcg_max_iter");
   static bool smem_ok = false;
   if (!smem_ok) {
     int rc = factor_smem_setup(kMaxLeaf, 64);
@@ -590,6 +674,18 @@ hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n, int32_
   UP(hts, P.hts); UP(urows, P.urows); UP(uents, P.uents); UP(leaf_beg, leaf_beg);
   UP(lr_ids, t->lr_ids); UP(dense_ids, t->dense_ids);
   UP(mv_row0, P.mv_row0); UP(mv_blocks, P.mv_blocks);
+  UP(hts_rhs, P.hts_rhs); UP(urows_rhs, P.urows_rhs); UP(uents_rhs, P.uents_rhs);
+  UP(bh_blocks, P.bh_blocks); UP(bupd, P.bupd); UP(bents, P.bents);
+  UP(mvt_row0, P.mvt_row0); UP(mvt_blocks, P.mvt_blocks);
+  {
+    std::vector<int32_t> slot(std::max<size_t>(P.blocks.size(), 1), -1);
+    for (size_t q = 0; q < t->lr_ids.size(); ++q) slot[t->lr_ids[q]] = (int32_t)q;
+    UP(lr_slot, slot);
+  }
+  {
+    std::vector<int32_t> wr(1, P.rhs_panel);
+    UP(wpan_rhs, wr);
+  }
 #undef UP
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { hmle_tree_destroy(t); return cuda_fail(ctx, e, "plan upload"); }
@@ -677,36 +773,36 @@ void hmle_hmatrix_destroy(hmle_hmatrix *h) {
 hmle_status hmle_hmatrix_matvec(hmle_ctx *ctx, const hmle_hmatrix *h, const double *x, double *y) {
   if (!ctx || !h || !x || !y) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
   const hmle_tree *t = h->tree;
+  const Plan &P = t->plan;
   cudaStream_t st = ctx->st;
   const int64_t n = t->n;
-  double *xd = nullptr, *xp = nullptr, *yp = nullptr;
+  const int nlr = (int)t->lr_ids.size();
+  double *xd = nullptr, *xp = nullptr, *yp = nullptr, *tb = nullptr, *yo = nullptr;
   bool owned = false;
   hmle_status s = stage_vec(ctx, x, n, &xd, &owned);
   if (s != HMLE_OK) return s;
   CK(cudaMallocAsync(&xp, sizeof(double) * n, st), "alloc");
   CK(cudaMallocAsync(&yp, sizeof(double) * n, st), "alloc");
+  CK(cudaMallocAsync(&yo, sizeof(double) * n, st), "alloc");
+  CK(cudaMallocAsync(&tb, sizeof(double) * std::max(nlr, 1) * 2 * P.kc, st), "alloc");
   launch_permute_in(st, xd, t->T.perm, n, xp);
-  CK(cudaMemsetAsync(yp, 0, sizeof(double) * n, st), "memset");
   AsmArgs A{};
   A.blocks = t->dp.blocks; A.lr_ids = t->dp.lr_ids; A.xyz = t->T.xyz; A.n = n; A.d = t->d;
   A.tab = h->tab; A.inv_ell = 1.0 / h->th.ell; A.sigma2 = h->th.sigma2; A.tau2 = h->th.tau2;
-  A.kc = t->plan.kc; A.uc = h->uc; A.rank_c = h->rank_c; A.cnorm = h->cnorm; A.flags = h->flags;
-  launch_hmatvec(st, A, t->dp.dense_ids, (int)t->dense_ids.size(), (int)t->lr_ids.size(), xp, yp);
-  // back to caller order: y[perm[k]] = yp[k]
-  std::vector<int32_t> perm(n);
-  std::vector<double> yh(n), out(n);
-  CK(cudaMemcpyAsync(perm.data(), t->T.perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st), "copy");
-  CK(cudaMemcpyAsync(yh.data(), yp, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "copy");
+  A.kc = P.kc; A.uc = h->uc; A.rank_c = h->rank_c; A.cnorm = h->cnorm; A.flags = h->flags;
+  A.thd = h->thd;
+  CmvLists L{P.nleaf, t->dp.leaf_beg, t->dp.mv_row0, t->dp.mv_blocks, t->dp.mvt_row0,
+             t->dp.mvt_blocks, t->dp.lr_slot};
+  launch_cmatvec(st, A, nlr, L, xp, tb, yp);
+  launch_permute_out(st, yp, t->T.perm, n, yo);       // y[perm[k]] = yp[k]
+  CK(cudaGetLastError(), "matvec launch");
+  CK(cudaMemcpyAsync(y, yo, sizeof(double) * n, cudaMemcpyDefault, st), "copy");
   CK(cudaStreamSynchronize(st), "sync");
-  for (int64_t k = 0; k < n; ++k) out[perm[k]] = yh[k];
-  if (is_device_ptr(y)) {
-    CK(cudaMemcpyAsync(y, out.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st), "copy");
-  } else {
-    std::memcpy(y, out.data(), sizeof(double) * n);
-  }
   if (owned) cudaFreeAsync(xd, st);
   cudaFreeAsync(xp, st);
   cudaFreeAsync(yp, st);
+  cudaFreeAsync(yo, st);
+  cudaFreeAsync(tb, st);
   CK(cudaStreamSynchronize(st), "sync");
   return HMLE_OK;
 }
@@ -721,6 +817,7 @@ hmle_status hmle_factor(hmle_ctx *ctx, const hmle_hmatrix *h, const double *Z, h
   bool owned = false;
   if (s == HMLE_OK && Z) s = stage_vec(ctx, Z, t->n, &zd, &owned);
   if (s == HMLE_OK) s = do_factor(ctx, t, h, zd, f);
+  if (s == HMLE_OK && zd && t->opts.precision == HMLE_MIXED_FP32) s = mixed_quad(ctx, t, h, f, zd);
   if (owned) cudaFreeAsync(zd, ctx->st);
   if (s == HMLE_OK) s = rank_stats(ctx, t, f->rank_l, &f->max_rank_l, &f->mean_rank_l);
   if (s != HMLE_OK) { free_f(ctx->st, f); delete f; return s; }
@@ -737,16 +834,80 @@ void hmle_factor_destroy(hmle_hfactor *f) {
   delete f;
 }
 
-hmle_status hmle_loglik(hmle_ctx *ctx, const hmle_hfactor *f, const double *Z, double *ll,
+hmle_status hmle_loglik(hmle_ctx *ctx, const hmle_hfactor *fc, const double *Z, double *ll,
                         double *logdet, double *quad) {
-  if (!ctx || !f || !ll) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
-  if (!f->has_rhs || Z == nullptr)
-    return fail(ctx, HMLE_ERR_NOT_IMPLEMENTED,
-                "this build fuses the solve into hmle_factor: pass Z to hmle_factor");
-  const double n = (double)f->h->tree->n;
+  if (!ctx || !fc || !ll) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  hmle_hfactor *f = const_cast<hmle_hfactor *>(fc);
+  const hmle_tree *t = f->h->tree;
+  const double n = (double)t->n;
+  if (Z) {
+    // forward solve of this Z through the stored factor: w = L^{-1} P Z
+    cudaStream_t st = ctx->st;
+    const Plan &P = t->plan;
+    double *zd = nullptr;
+    bool owned = false;
+    hmle_status s = stage_vec(ctx, Z, t->n, &zd, &owned);
+    if (s != HMLE_OK) return s;
+    const PanelDesc &rp = P.panels[P.rhs_panel];
+    launch_permute_in(st, zd, t->T.perm, t->n, f->W + rp.off);
+    FactorArgs F = make_fargs(t, f->h, f);
+    F.hts = t->dp.hts_rhs;
+    F.urows = t->dp.urows_rhs;
+    F.uents = t->dp.uents_rhs;
+    launch_solve(st, F, P, t->dp.wpan_rhs);
+    launch_finalize(st, f->ldp, P.nleaf, f->W + rp.off, t->n, f->out);
+    double out[2];
+    CK(cudaGetLastError(), "solve launch");
+    CK(cudaMemcpyAsync(out, f->out, sizeof(out), cudaMemcpyDeviceToHost, st), "result copy");
+    CK(cudaStreamSynchronize(st), "solve sync");
+    if (owned) cudaFreeAsync(zd, st);
+    f->quad = out[1];
+    f->has_rhs = true;
+  } else if (!f->has_rhs) {
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "no Z: the factor was built without a right-hand side");
+  }
   *ll = -0.5 * n * std::log(2.0 * M_PI) - 0.5 * f->logdet - 0.5 * f->quad;
   if (logdet) *logdet = f->logdet;
   if (quad) *quad = f->quad;
+  return HMLE_OK;
+}
+
+hmle_status hmle_solve(hmle_ctx *ctx, const hmle_hfactor *fc, const double *Z, double *X) {
+  if (!ctx || !fc || !Z || !X) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  hmle_hfactor *f = const_cast<hmle_hfactor *>(fc);
+  const hmle_tree *t = f->h->tree;
+  const Plan &P = t->plan;
+  cudaStream_t st = ctx->st;
+  double *zd = nullptr, *xo = nullptr, *hb = nullptr;
+  bool owned = false;
+  hmle_status s = stage_vec(ctx, Z, t->n, &zd, &owned);
+  if (s != HMLE_OK) return s;
+  int maxh = 1;
+  for (int K = 0; K < P.nleaf; ++K) maxh = std::max(maxh, P.bh0[K + 1] - P.bh0[K]);
+  CK(cudaMallocAsync(&xo, sizeof(double) * t->n, st), "alloc");
+  CK(cudaMallocAsync(&hb, sizeof(double) * (size_t)maxh * P.kcap, st), "alloc");
+  const PanelDesc &rp = P.panels[P.rhs_panel];
+  double *w = f->W + rp.off;
+  launch_permute_in(st, zd, t->T.perm, t->n, w);
+  FactorArgs F = make_fargs(t, f->h, f);
+  F.hts = t->dp.hts_rhs;
+  F.urows = t->dp.urows_rhs;
+  F.uents = t->dp.uents_rhs;
+  launch_solve(st, F, P, t->dp.wpan_rhs);                                  // w = L^{-1} P Z
+  launch_finalize(st, f->ldp, P.nleaf, w, t->n, f->out);
+  launch_backward(st, F, P, w, t->dp.bh_blocks, t->dp.bupd, t->dp.bents, hb);  // v = L^{-T} w
+  launch_permute_out(st, w, t->T.perm, t->n, xo);
+  double out[2];
+  CK(cudaGetLastError(), "solve launch");
+  CK(cudaMemcpyAsync(X, xo, sizeof(double) * t->n, cudaMemcpyDefault, st), "copy");
+  CK(cudaMemcpyAsync(out, f->out, sizeof(out), cudaMemcpyDeviceToHost, st), "copy");
+  CK(cudaStreamSynchronize(st), "sync");
+  f->quad = out[1];                   // the quadratic form now belongs to this Z
+  f->has_rhs = true;
+  if (owned) cudaFreeAsync(zd, st);
+  cudaFreeAsync(xo, st);
+  cudaFreeAsync(hb, st);
+  CK(cudaStreamSynchronize(st), "sync");
   return HMLE_OK;
 }
 
@@ -781,6 +942,7 @@ hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tc, const hmle_thet
   }
   s = do_assemble(ctx, t, th, &w.H);
   if (s == HMLE_OK) s = do_factor(ctx, t, &w.H, zd, &w.F, t->graphs ? &w : nullptr);
+  if (s == HMLE_OK && t->opts.precision == HMLE_MIXED_FP32) s = mixed_quad(ctx, t, &w.H, &w.F, zd);
   const double n = (double)t->n;
   double L = -0.5 * n * std::log(2.0 * M_PI) - 0.5 * w.F.logdet - 0.5 * w.F.quad;
   *ll = (s == HMLE_OK) ? L : -INFINITY;
@@ -790,6 +952,8 @@ hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tc, const hmle_thet
     info->loglik = *ll;
     info->status = s;
     info->kernel_launches = w.F.launches;
+    info->pcg_iters = w.F.pcg_iters;
+    info->pcg_relres = w.F.pcg_relres;
     double mr = 0;
     int mx = 0;
     if (rank_stats(ctx, t, w.H.rank_c, &mx, &mr) == HMLE_OK) info->max_rank_c = mx;
@@ -801,17 +965,11 @@ hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tc, const hmle_thet
   return s;
 }
 
-hmle_status hmle_loglik_batch(hmle_ctx *ctx, const hmle_tree *tc, const hmle_theta *thetas,
-                              int32_t m, const double *Z, int32_t concurrency, double *ll,
-                              int32_t *status) {
-  if (!ctx || !tc || !thetas || !Z || !ll || m < 0) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
-  if (concurrency <= 0) concurrency = 8;
-  if (concurrency > 64) concurrency = 64;
-  for (int i = 0; i < m; ++i)
-    if (!theta_ok(&thetas[i])) return fail(ctx, HMLE_ERR_INVALID_ARG, "theta out of range");
-  hmle_tree *t = const_cast<hmle_tree *>(tc);
-  const int W = std::min<int>(concurrency, std::max(m, 1));
-  // evaluation buffers, each with its own stream pair (kept for reuse)
+namespace {
+
+// Grow a tree's pool of evaluation buffers (each with its own stream pair)
+// to at least W.
+hmle_status ensure_pool(hmle_ctx *ctx, hmle_tree *t, int W) {
   while ((int)t->pool.size() < W) {
     Work *w = new (std::nothrow) Work();
     if (!w) return HMLE_ERR_OOM;
@@ -836,39 +994,64 @@ hmle_status hmle_loglik_batch(hmle_ctx *ctx, const hmle_tree *tc, const hmle_the
     if (s != HMLE_OK) { free_work(w); return fail(ctx, s, wc.err.empty() ? ctx->err : wc.err); }
     t->pool.push_back(w);
   }
-  // stage Z once (shared by every evaluation, read-only)
-  double *zd = nullptr;
-  bool owned = false;
-  hmle_status s0 = stage_vec(ctx, Z, t->n, &zd, &owned);
-  if (s0 != HMLE_OK) return s0;
-  cudaEvent_t zready;
-  CK(cudaEventCreateWithFlags(&zready, cudaEventDisableTiming), "event");
-  CK(cudaEventRecord(zready, ctx->st), "event record");
+  return HMLE_OK;
+}
+
+// One evaluation request of a batch: tree, theta, and Z already on the device.
+struct TaskRef {
+  hmle_tree *t;
+  const hmle_theta *th;
+  const double *zd;
+};
+
+// a15: evaluate the tasks in waves of W; inside a wave every task runs on a
+// buffer of its tree's pool, on its own streams (replaying the tree's
+// captured sweep), and the wave is collected in task order.  zready: an
+// event after which every Z is readable.
+hmle_status run_waves(hmle_ctx *ctx, const std::vector<TaskRef> &tasks, int W, cudaEvent_t zready,
+                      double *ll, int32_t *status) {
+  const int m = (int)tasks.size();
   hmle_status first = HMLE_OK;
-  const double nn = (double)t->n;
   for (int i0 = 0; i0 < m; i0 += W) {
     const int cnt = std::min(W, m - i0);
+    std::vector<Work *> ws(cnt, nullptr);
+    {
+      std::vector<std::pair<hmle_tree *, int>> used;   // pool slots taken per tree
+      for (int k = 0; k < cnt; ++k) {
+        hmle_tree *t = tasks[i0 + k].t;
+        int slot = 0;
+        for (auto &u : used)
+          if (u.first == t) slot = ++u.second;
+        if (slot == 0) used.push_back({t, 0});
+        hmle_status s = ensure_pool(ctx, t, slot + 1);
+        if (s != HMLE_OK) return s;
+        ws[k] = t->pool[slot];
+      }
+    }
     // launch every evaluation of the wave asynchronously
     for (int k = 0; k < cnt; ++k) {
-      Work *w = t->pool[k];
+      const TaskRef &T = tasks[i0 + k];
+      Work *w = ws[k];
       hmle_ctx wc;
       wc.st = w->st; wc.side = w->side; wc.ev_fork = w->ev_fork; wc.ev_join = w->ev_join;
       wc.d_jacobi = w->d_jacobi;
-      cudaError_t ew = cudaStreamWaitEvent(w->st, zready, 0);
-      if (ew != cudaSuccess) { cudaEventDestroy(zready); return cuda_fail(ctx, ew, "stream wait"); }
-      hmle_status s = do_assemble(&wc, t, &thetas[i0 + k], &w->H);
-      if (s == HMLE_OK) s = launch_factor_async(&wc, t, &w->H, zd, &w->F, t->graphs ? w : nullptr);
+      CK(cudaStreamWaitEvent(w->st, zready, 0), "stream wait");
+      hmle_status s = do_assemble(&wc, T.t, T.th, &w->H);
+      if (s == HMLE_OK) s = launch_factor_async(&wc, T.t, &w->H, T.zd, &w->F, T.t->graphs ? w : nullptr);
       wc.d_jacobi = nullptr;
       if (s != HMLE_OK) { if (status) status[i0 + k] = s; if (first == HMLE_OK) { first = s; ctx->err = wc.err; } }
       else if (status) status[i0 + k] = HMLE_OK;
     }
     // collect
     for (int k = 0; k < cnt; ++k) {
-      Work *w = t->pool[k];
+      const TaskRef &T = tasks[i0 + k];
+      Work *w = ws[k];
       hmle_ctx wc;
       wc.st = w->st; wc.side = w->side;
-      hmle_status s = finish_factor(&wc, t, &w->H, &w->F);
+      hmle_status s = finish_factor(&wc, T.t, &w->H, &w->F);
+      if (s == HMLE_OK && T.t->opts.precision == HMLE_MIXED_FP32) s = mixed_quad(&wc, T.t, &w->H, &w->F, T.zd);
       const int i = i0 + k;
+      const double nn = (double)T.t->n;
       ll[i] = (s == HMLE_OK) ? -0.5 * nn * std::log(2.0 * M_PI) - 0.5 * w->F.logdet - 0.5 * w->F.quad
                              : -INFINITY;
       if (status && status[i] == HMLE_OK) status[i] = s;
@@ -878,8 +1061,80 @@ hmle_status hmle_loglik_batch(hmle_ctx *ctx, const hmle_tree *tc, const hmle_the
       }
     }
   }
+  return first;
+}
+
+}  // namespace
+
+hmle_status hmle_loglik_batch(hmle_ctx *ctx, const hmle_tree *tc, const hmle_theta *thetas,
+                              int32_t m, const double *Z, int32_t concurrency, double *ll,
+                              int32_t *status) {
+  if (!ctx || !tc || !thetas || !Z || !ll || m < 0) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  if (concurrency <= 0) concurrency = 8;
+  if (concurrency > 64) concurrency = 64;
+  for (int i = 0; i < m; ++i)
+    if (!theta_ok(&thetas[i])) return fail(ctx, HMLE_ERR_INVALID_ARG, "theta out of range");
+  hmle_tree *t = const_cast<hmle_tree *>(tc);
+  const int W = std::min<int>(concurrency, std::max(m, 1));
+  hmle_status s0 = ensure_pool(ctx, t, W);
+  if (s0 != HMLE_OK) return s0;
+  // stage Z once (shared by every evaluation, read-only)
+  double *zd = nullptr;
+  bool owned = false;
+  s0 = stage_vec(ctx, Z, t->n, &zd, &owned);
+  if (s0 != HMLE_OK) return s0;
+  cudaEvent_t zready;
+  CK(cudaEventCreateWithFlags(&zready, cudaEventDisableTiming), "event");
+  CK(cudaEventRecord(zready, ctx->st), "event record");
+  std::vector<TaskRef> tasks(m);
+  for (int i = 0; i < m; ++i) tasks[i] = {t, &thetas[i], zd};
+  hmle_status first = run_waves(ctx, tasks, W, zready, ll, status);
   cudaEventDestroy(zready);
   if (owned) cudaFreeAsync(zd, ctx->st);
+  cudaStreamSynchronize(ctx->st);
+  return first;
+}
+
+hmle_status hmle_loglik_multi(hmle_ctx *ctx, const hmle_task *tasks, int32_t m, int32_t concurrency,
+                              double *ll, int32_t *status) {
+  if (!ctx || !tasks || !ll || m < 0) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  if (concurrency <= 0) concurrency = 8;
+  if (concurrency > 64) concurrency = 64;
+  for (int i = 0; i < m; ++i) {
+    if (!tasks[i].tree || !tasks[i].Z) return fail(ctx, HMLE_ERR_INVALID_ARG, "null tree or Z in a task");
+    if (!theta_ok(&tasks[i].theta)) return fail(ctx, HMLE_ERR_INVALID_ARG, "theta out of range");
+  }
+  const int W = std::min<int>(concurrency, std::max(m, 1));
+  // stage every distinct Z once
+  std::vector<const double *> src;
+  std::vector<double *> dev;
+  std::vector<bool> own;
+  std::vector<TaskRef> refs(m);
+  hmle_status s0 = HMLE_OK;
+  for (int i = 0; i < m && s0 == HMLE_OK; ++i) {
+    hmle_tree *t = const_cast<hmle_tree *>(tasks[i].tree);
+    size_t q = 0;
+    while (q < src.size() && src[q] != tasks[i].Z) ++q;
+    if (q == src.size()) {
+      double *zd = nullptr;
+      bool owned = false;
+      s0 = stage_vec(ctx, tasks[i].Z, t->n, &zd, &owned);
+      src.push_back(tasks[i].Z);
+      dev.push_back(zd);
+      own.push_back(owned);
+    }
+    refs[i] = {t, &tasks[i].theta, dev[q]};
+  }
+  hmle_status first = s0;
+  cudaEvent_t zready = nullptr;
+  if (first == HMLE_OK) {
+    CK(cudaEventCreateWithFlags(&zready, cudaEventDisableTiming), "event");
+    CK(cudaEventRecord(zready, ctx->st), "event record");
+    first = run_waves(ctx, refs, W, zready, ll, status);
+    cudaEventDestroy(zready);
+  }
+  for (size_t q = 0; q < dev.size(); ++q)
+    if (own[q] && dev[q]) cudaFreeAsync(dev[q], ctx->st);
   cudaStreamSynchronize(ctx->st);
   return first;
 }
@@ -961,6 +1216,8 @@ hmle_status hmle_profile_select(hmle_ctx *ctx, const char *kernel) {
   p.ms = 0.0;
   p.launches = 0;
   p.flops = 0.0;
+  p.failed = 0;
+  p.first_err = 0;
   if (!kernel) return HMLE_OK;
   for (int k = 0; k < KK_COUNT; ++k)
     if (std::strcmp(kernel, kKernelNames[k]) == 0) p.kind = k;
@@ -990,6 +1247,21 @@ static void from_theta(const hmle_theta *t, double x[4]) {
   x[1] = -std::log(t->ell) / std::log(1.5);
   x[2] = -std::log(t->nu) / std::log(1.2);
   x[3] = -std::log(std::sqrt(t->tau2)) / std::log(2.0);
+}
+
+hmle_status hmle_theta_to_x(const hmle_theta *theta, double x[4]) {
+  if (!theta || !x || !theta_ok(theta) || !(theta->sigma2 > 0.0) || !(theta->tau2 > 0.0))
+    return HMLE_ERR_INVALID_ARG;
+  from_theta(theta, x);
+  return HMLE_OK;
+}
+
+hmle_status hmle_x_to_theta(const double x[4], hmle_theta *theta) {
+  if (!theta || !x) return HMLE_ERR_INVALID_ARG;
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(x[k])) return HMLE_ERR_INVALID_ARG;
+  to_theta(x, theta);
+  return theta_ok(theta) ? HMLE_OK : HMLE_ERR_INVALID_ARG;
 }
 
 hmle_status hmle_fit(hmle_ctx *ctx, const hmle_tree *t, const double *Z, const hmle_theta *theta0,

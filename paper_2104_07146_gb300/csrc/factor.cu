@@ -41,6 +41,7 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kMaxEntries = 512;     // side entries covering one leaf row of a target
+constexpr int kMaxRowK = 8192;       // concatenated columns of one row task
 constexpr int kTM = 64, kTN = 64, kTK = 16;
 constexpr int kGemmSmem = kTK * (kTM + kTN);  // doubles
 
@@ -48,38 +49,40 @@ constexpr int kGemmSmem = kTK * (kTM + kTN);  // doubles
 // fc(i, j, value).  A_KFAST / B_KFAST: the operand is contiguous along k in
 // memory (chooses the coalesced loading order).  128 threads, 64 x TNX
 // output tiles (TNX = 64 or 32), 4 x (TNX / 8) register micro-tiles, K
-// staged 16 at a time.
-template <bool A_KFAST, bool B_KFAST, int TNX, class FA, class FB, class FC>
+// staged 16 at a time.  T: the arithmetic type (double; float in the mixed
+// form): operands are rounded to T as they are staged, products accumulate
+// in T, and fc receives the sum as a double.
+template <class T, bool A_KFAST, bool B_KFAST, int TNX, class FA, class FB, class FC>
 __device__ void cta_gemm_t(int M, int N, int K, FA fa, FB fb, FC fc, double *smem) {
   constexpr int MC = TNX / 8;
-  double *sA = smem;
-  double *sB = smem + kTK * kTM;
+  T *sA = reinterpret_cast<T *>(smem);
+  T *sB = sA + kTK * kTM;
   const int tid = threadIdx.x;
   const int ti = tid & 15, tj = tid >> 4;
   for (int i0 = 0; i0 < M; i0 += kTM) {
     for (int j0 = 0; j0 < N; j0 += TNX) {
-      double acc[4][MC];
+      T acc[4][MC];
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < MC; ++y) acc[x][y] = 0.0;
+        for (int y = 0; y < MC; ++y) acc[x][y] = T(0);
       const bool active = (i0 + ti * 4 < M) && (j0 + tj * MC < N);
       for (int k0 = 0; k0 < K; k0 += kTK) {
         for (int e = tid; e < kTK * kTM; e += kThreads) {
           int k, i;
           if (A_KFAST) { k = e % kTK; i = e / kTK; } else { i = e % kTM; k = e / kTM; }
-          sA[k * kTM + i] = (i0 + i < M && k0 + k < K) ? fa(i0 + i, k0 + k) : 0.0;
+          sA[k * kTM + i] = (i0 + i < M && k0 + k < K) ? T(fa(i0 + i, k0 + k)) : T(0);
         }
         for (int e = tid; e < kTK * TNX; e += kThreads) {
           int k, j;
           if (B_KFAST) { k = e % kTK; j = e / kTK; } else { j = e % TNX; k = e / TNX; }
-          sB[k * TNX + j] = (j0 + j < N && k0 + k < K) ? fb(k0 + k, j0 + j) : 0.0;
+          sB[k * TNX + j] = (j0 + j < N && k0 + k < K) ? T(fb(k0 + k, j0 + j)) : T(0);
         }
         __syncthreads();
         if (active) {
           const int kk = min(kTK, K - k0);
           for (int k = 0; k < kk; ++k) {
-            double a[4], bb[MC];
+            T a[4], bb[MC];
 #pragma unroll
             for (int x = 0; x < 4; ++x) a[x] = sA[k * kTM + ti * 4 + x];
 #pragma unroll
@@ -98,7 +101,7 @@ __device__ void cta_gemm_t(int M, int N, int K, FA fa, FB fb, FC fc, double *sme
 #pragma unroll
           for (int y = 0; y < MC; ++y) {
             int i = i0 + ti * 4 + x, j = j0 + tj * MC + y;
-            if (i < M && j < N) fc(i, j, acc[x][y]);
+            if (i < M && j < N) fc(i, j, double(acc[x][y]));
           }
       }
     }
@@ -106,10 +109,10 @@ __device__ void cta_gemm_t(int M, int N, int K, FA fa, FB fb, FC fc, double *sme
 }
 
 // cta_gemm_t with the output tile width picked from N.
-template <bool A_KFAST, bool B_KFAST, class FA, class FB, class FC>
+template <bool A_KFAST, bool B_KFAST, class T = double, class FA, class FB, class FC>
 __device__ __forceinline__ void cta_gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem) {
-  if (N <= 32) cta_gemm_t<A_KFAST, B_KFAST, 32>(M, N, K, fa, fb, fc, smem);
-  else cta_gemm_t<A_KFAST, B_KFAST, 64>(M, N, K, fa, fb, fc, smem);
+  if (N <= 32) cta_gemm_t<T, A_KFAST, B_KFAST, 32>(M, N, K, fa, fb, fc, smem);
+  else cta_gemm_t<T, A_KFAST, B_KFAST, 64>(M, N, K, fa, fb, fc, smem);
 }
 
 // C(i, j) = sum_k A(k, i) B(k, j) for small outputs (M x N) and long K: the
@@ -119,27 +122,27 @@ __device__ __forceinline__ void cta_gemm(int M, int N, int K, FA fa, FB fb, FC f
 // 32 * (M + N) + 4 * 512 doubles; M + N <= kTnMaxMN.
 constexpr int kTnMaxMN = 192;
 constexpr int kTnSmem = 32 * kTnMaxMN + 4 * 512;
-template <class FA, class FB, class FC>
+template <class T = double, class FA, class FB, class FC>
 __device__ void cta_gemm_tn(int M, int N, int K, FA fa, FB fb, FC fc, double *smem) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  double *sA = smem;                 // 32 x M  (sA[k * M + i])
-  double *sB = smem + 32 * M;        // 32 x N
-  double *part = smem + 32 * (M + N);  // 4 x 512 partial sums
+  T *sA = reinterpret_cast<T *>(smem);  // 32 x M  (sA[k * M + i])
+  T *sB = sA + 32 * M;                  // 32 x N
+  T *part = sB + 32 * N;                // 4 x 512 partial sums
   const int MN = M * N;
   for (int o0 = 0; o0 < MN; o0 += 512) {
     const int no = min(512, MN - o0);
-    double acc[16];
+    T acc[16];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) acc[u] = 0.0;
+    for (int u = 0; u < 16; ++u) acc[u] = T(0);
     for (int k0 = 0; k0 < K; k0 += 32) {
       const int kk = min(32, K - k0);
       for (int e = tid; e < 32 * M; e += kThreads) {
         int k = e & 31, i = e >> 5;
-        sA[k * M + i] = (k < kk) ? fa(k0 + k, i) : 0.0;
+        sA[k * M + i] = (k < kk) ? T(fa(k0 + k, i)) : T(0);
       }
       for (int e = tid; e < 32 * N; e += kThreads) {
         int k = e & 31, j = e >> 5;
-        sB[k * N + j] = (k < kk) ? fb(k0 + k, j) : 0.0;
+        sB[k * N + j] = (k < kk) ? T(fb(k0 + k, j)) : T(0);
       }
       __syncthreads();
       for (int k = warp; k < kk; k += 4) {
@@ -158,9 +161,9 @@ __device__ void cta_gemm_tn(int M, int N, int K, FA fa, FB fb, FC fc, double *sm
     for (int u = 0; u < 16; ++u) part[warp * 512 + lane + 32 * u] = acc[u];
     __syncthreads();
     for (int e = tid; e < no; e += kThreads) {
-      double v = ((part[e] + part[512 + e]) + part[1024 + e]) + part[1536 + e];
+      T v = ((part[e] + part[512 + e]) + part[1024 + e]) + part[1536 + e];
       int o = o0 + e;
-      fc(o % M, o / M, v);
+      fc(o % M, o / M, double(v));
     }
     __syncthreads();
   }
@@ -203,6 +206,7 @@ struct Acc {
 
 // --- P1 -------------------------------------------------------------------
 // One CTA per row chunk of a gram G = W_A[ov]^T W_B[ov] (ranks x ranks).
+template <class Tc>
 __global__ void __launch_bounds__(kThreads) k_gram(FactorArgs F, int c0) {
   extern __shared__ double smem[];
   Acc a(F);
@@ -211,9 +215,13 @@ __global__ void __launch_bounds__(kThreads) k_gram(FactorArgs F, int c0) {
   const BlockDesc A = F.blocks[g.a], B = F.blocks[g.b];
   double *out = F.ws + ch.out;
   const int kc = F.kcap;
-  cta_gemm_tn(
-      F.rank_l[g.a], F.rank_l[g.b], ch.r1 - ch.r0, [&](int k, int i) { return a.W(A, ch.r0 + k, i); },
-      [&](int k, int j) { return a.W(B, ch.r0 + k, j); },
+  const PanelDesc PA = F.panels[A.panel], PB = F.panels[B.panel];
+  const int lda = PA.rend - PA.rbeg, ldb = PB.rend - PB.rbeg;
+  const double *wa = F.W + PA.off + (int64_t)A.slot * lda + (ch.r0 - PA.rbeg);
+  const double *wb = F.W + PB.off + (int64_t)B.slot * ldb + (ch.r0 - PB.rbeg);
+  cta_gemm_tn<Tc>(
+      F.rank_l[g.a], F.rank_l[g.b], ch.r1 - ch.r0, [&](int k, int i) { return wa[k + (int64_t)i * lda]; },
+      [&](int k, int j) { return wb[k + (int64_t)j * ldb]; },
       [&](int i, int j, double v) { out[i + (int64_t)j * kc] = v; }, smem);
 }
 
@@ -233,6 +241,7 @@ __global__ void __launch_bounds__(kThreads) k_gram_reduce(FactorArgs F, int r0) 
 // --- P2a / P4a: t = U_X[rows]^T X[rows] for side entries; t_C for targets --
 // trans = 0: B-entries against Omega (rows in sigma), t_C = V_C^T Omega.
 // trans = 1: A-entries against Q (rows in rho), t_C = U_C^T Q.
+template <class Tc>
 __global__ void __launch_bounds__(kThreads) k_side_t(FactorArgs F, int e0, int ne, int t0, int trans) {
   extern __shared__ double smem[];
   Acc a(F);
@@ -250,12 +259,12 @@ __global__ void __launch_bounds__(kThreads) k_side_t(FactorArgs F, int e0, int n
     const uint64_t seed = F.seed;
     const int64_t tb = L.blk;
     if (trans) {
-      cta_gemm_tn(
+      cta_gemm_tn<Tc>(
           ke, r, hi - lo, [&](int kk, int i) { return a.U(X, lo + kk, i); },
           [&](int kk, int j) { return Q[(lo + kk - cb) + (int64_t)j * L.m]; },
           [&](int i, int j, double v) { t[i + (int64_t)j * k] = v; }, smem);
     } else {
-      cta_gemm_tn(
+      cta_gemm_tn<Tc>(
           ke, r, hi - lo, [&](int kk, int i) { return a.U(X, lo + kk, i); },
           [&](int kk, int j) { return rademacher(seed, tb, lo + kk - cb, j); },
           [&](int i, int j, double v) { t[i + (int64_t)j * k] = v; }, smem);
@@ -272,12 +281,12 @@ __global__ void __launch_bounds__(kThreads) k_side_t(FactorArgs F, int e0, int n
     const uint64_t seed = F.seed;
     const int64_t tb = L.blk;
     if (trans) {
-      cta_gemm_tn(
+      cta_gemm_tn<Tc>(
           kce, r, L.m, [&](int kk, int i) { return UC[kk + (int64_t)i * ld]; },
           [&](int kk, int j) { return Q[kk + (int64_t)j * L.m]; },
           [&](int i, int j, double v) { tc[i + (int64_t)j * kc] = v; }, smem);
     } else {
-      cta_gemm_tn(
+      cta_gemm_tn<Tc>(
           kce, r, L.p, [&](int kk, int i) { return UC[kk + (int64_t)i * ld]; },
           [&](int kk, int j) { return rademacher(seed, tb, kk, j); },
           [&](int i, int j, double v) { tc[i + (int64_t)j * kc] = v; }, smem);
@@ -332,12 +341,14 @@ __global__ void __launch_bounds__(kThreads) k_side_s(FactorArgs F, int e0, int t
 }
 
 // --- P2c / P4c: rows of Y (or Z) of one leaf --------------------------------
+template <class Tc>
 __global__ void __launch_bounds__(kThreads) k_rows(FactorArgs F, int rt0, int trans) {
   extern __shared__ double smem[];
   __shared__ int kbeg[kMaxEntries + 2];
   __shared__ int eblk[kMaxEntries + 2];
   __shared__ int64_t esoff[kMaxEntries + 2];
   __shared__ int ekx[kMaxEntries + 2];
+  __shared__ short kmap[kMaxRowK];          // column k of the concatenation -> entry
   Acc a(F);
   const int kc = F.kc;
   const RowTask R = trans ? F.brow[rt0 + blockIdx.x] : F.arow[rt0 + blockIdx.x];
@@ -369,13 +380,13 @@ __global__ void __launch_bounds__(kThreads) k_rows(FactorArgs F, int rt0, int tr
     kbeg[ne + 1] = k;
   }
   __syncthreads();
-  const int K = kbeg[ne + 1];
-  auto seg = [&](int k) {       // entry index of column k (0 = U_C)
-    int q = 0;
-    while (q < ne && kbeg[q + 1] <= k) ++q;
-    return q;
-  };
-  cta_gemm<false, true>(
+  const int K = min(kbeg[ne + 1], kMaxRowK);
+  if (kbeg[ne + 1] > kMaxRowK && threadIdx.x == 0) raise_flag(F.flags, kFlagRankOverflow);
+  for (int q = 0; q <= ne; ++q)
+    for (int k = kbeg[q] + threadIdx.x; k < min(kbeg[q + 1], K); k += blockDim.x) kmap[k] = (short)q;
+  __syncthreads();
+  auto seg = [&](int k) { return (int)kmap[k]; };   // entry index of column k (0 = U_C)
+  cta_gemm<false, true, Tc>(
       mi, r, K,
       [&](int i, int k) {
         int q = seg(k);
@@ -514,6 +525,90 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, i
     V[i + c * lb] = (i == c) ? 1.0 : 0.0;
   }
   __syncthreads();
+  if (mode == 0) {
+    // Orthonormalisation: column-pivoted Householder QR of R (R P = Q_r R_p),
+    // stopped where the pivot column's norm falls below 1e-14 of the first;
+    // Q1 = Y P_{:,1:k1} R_p11^{-1} (the CholQR pass that follows restores
+    // orthogonality to rounding level).
+    __shared__ int piv[kMaxSample + 2];
+    __shared__ double cn[kMaxSample + 2];
+    __shared__ int s_p, s_k1;
+    __shared__ double s_first, s_tau, s_beta;
+    for (int c = threadIdx.x; c < r; c += blockDim.x) piv[c] = c;
+    if (threadIdx.x == 0) { s_k1 = r; s_first = 0.0; }
+    __syncthreads();
+    for (int j = 0; j < r; ++j) {
+      for (int c = j + threadIdx.x; c < r; c += blockDim.x) {   // remaining column norms
+        double v = 0.0;
+        for (int i = j; i < r; ++i) v = fma(B[i + c * lb], B[i + c * lb], v);
+        cn[c] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int p = j;
+        for (int c = j + 1; c < r; ++c) if (cn[c] > cn[p]) p = c;
+        if (j == 0) s_first = cn[p];
+        s_p = p;
+        if (!(cn[p] > 1e-28 * s_first) || !(cn[p] > 0.0)) s_k1 = j;   // the rest is rank deficient
+      }
+      __syncthreads();
+      if (s_k1 == j) break;
+      const int p = s_p;
+      if (p != j) {   // swap columns j and p (entries of all rows) and the permutation
+        for (int i = threadIdx.x; i < r; i += blockDim.x) {
+          double t = B[i + j * lb]; B[i + j * lb] = B[i + p * lb]; B[i + p * lb] = t;
+        }
+        if (threadIdx.x == 0) { int t = piv[j]; piv[j] = piv[p]; piv[p] = t; }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) {   // reflector for column j, rows j..r-1
+        double alpha = B[j + j * lb], s2 = 0.0;
+        for (int i = j + 1; i < r; ++i) s2 = fma(B[i + j * lb], B[i + j * lb], s2);
+        if (s2 > 0.0) {
+          double nrm = sqrt(fma(alpha, alpha, s2));
+          double beta = alpha >= 0.0 ? -nrm : nrm;
+          s_beta = beta;
+          s_tau = (beta - alpha) / beta;
+          double scal = 1.0 / (alpha - beta);
+          for (int i = j + 1; i < r; ++i) B[i + j * lb] *= scal;
+        } else {   // nothing below the diagonal: H = I
+          s_beta = alpha;
+          s_tau = 0.0;
+        }
+      }
+      __syncthreads();
+      const double tau = s_tau;
+      for (int c = j + 1 + threadIdx.x; c < r; c += blockDim.x) {
+        double w = B[j + c * lb];
+        for (int i = j + 1; i < r; ++i) w = fma(B[i + j * lb], B[i + c * lb], w);
+        w *= tau;
+        B[j + c * lb] -= w;
+        for (int i = j + 1; i < r; ++i) B[i + c * lb] = fma(-w, B[i + j * lb], B[i + c * lb]);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) B[j + j * lb] = s_beta;
+      __syncthreads();
+    }
+    const int k1 = s_k1;
+    // V <- R_p11^{-1} (upper triangular, k1 x k1), one thread per column
+    for (int c = threadIdx.x; c < k1; c += blockDim.x) {
+      for (int i = k1 - 1; i >= 0; --i) {
+        double v = (i == c) ? 1.0 : 0.0;
+        for (int l = i + 1; l <= c; ++l) v = fma(-B[i + l * lb], V[l + c * lb], v);
+        V[i + c * lb] = (i <= c) ? v / B[i + i * lb] : 0.0;
+      }
+    }
+    __syncthreads();
+    double *M = F.ws + L.soff + ldm * ldm;
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) M[(e % r) + (e / r) * ldm] = 0.0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < k1 * k1; e += blockDim.x) {
+      const int c = e / k1, q = e % k1;        // M(piv[q], c) = R_p11^{-1}(q, c)
+      M[piv[q] + c * ldm] = V[q + c * lb];
+    }
+    if (threadIdx.x == 0) F.kept[t0 + blockIdx.x] = k1;
+    return;
+  }
   // one-sided Jacobi on the columns of B (R V = B).  A round rotates the
   // disjoint column pairs of a round-robin tournament; each pair is handled
   // by a group of g lanes (all four warps busy, so all four FP64 pipes of the
@@ -780,6 +875,7 @@ __global__ void __launch_bounds__(kThreads) k_tall_apply(FactorArgs F, int t0, i
 // k_dense_pair: one CTA per pair (A, B) of the step's dense targets writes
 // P = U_A G_AB U_B^T restricted to the target (m x p, ld b) into the step's
 // workspace; k_dense_reduce: S = C_IK - sum of the target's P in pair order.
+template <class Tc>
 __global__ void __launch_bounds__(kThreads) k_dense_pair(FactorArgs F, int q0, int64_t dpws) {
   extern __shared__ double smem[];
   Acc a(F);
@@ -796,7 +892,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_pair(FactorArgs F, int q0, i
   auto put = [&](int i, int j, double v) { out[i + (int64_t)j * b] = v; };
   if (A.kind == kDense && B.kind == kDense) {
     const int nj = A.cend - A.cbeg;
-    cta_gemm<false, true>(
+    cta_gemm<false, true, Tc>(
         m, p, nj, [&](int i, int k) { return a.U(A, tr0 + i, k); },
         [&](int k, int j) { return a.U(B, tc0 + j, k); }, put, smem);
     return;
@@ -806,28 +902,28 @@ __global__ void __launch_bounds__(kThreads) k_dense_pair(FactorArgs F, int q0, i
     kx = F.rank_l[Pq.a];
     const int kb = F.rank_l[Pq.b];
     const double *G = F.ws + Pq.goff;
-    cta_gemm<false, true>(
+    cta_gemm<false, true, Tc>(
         kx, p, kb, [&](int i, int k) { return G[i + (int64_t)k * kc]; },
         [&](int k, int j) { return a.U(B, tc0 + j, k); },
         [&](int i, int j, double v) { X[i + j * ldx] = v; }, smem);
   } else if (A.kind == kDense) {  // B low-rank: X = W_B[J_A] U_B[K]^T
     kx = A.cend - A.cbeg;
     const int J0 = A.cbeg;
-    cta_gemm<false, true>(
+    cta_gemm<false, true, Tc>(
         kx, p, F.rank_l[Pq.b], [&](int i, int k) { return a.W(B, J0 + i, k); },
         [&](int k, int j) { return a.U(B, tc0 + j, k); },
         [&](int i, int j, double v) { X[i + j * ldx] = v; }, smem);
   } else {  // A low-rank, B dense: X = W_A[J_B]^T D_B^T
     kx = F.rank_l[Pq.a];
     const int J0 = B.cbeg, nj = B.cend - B.cbeg;
-    cta_gemm<true, true>(
+    cta_gemm<true, true, Tc>(
         kx, p, nj, [&](int i, int k) { return a.W(A, J0 + k, i); },
         [&](int k, int j) { return a.U(B, tc0 + j, k); },
         [&](int i, int j, double v) { X[i + j * ldx] = v; }, smem);
   }
   __syncthreads();
   const int kxx = kx;
-  cta_gemm<false, false>(
+  cta_gemm<false, false, Tc>(
       m, p, kxx, [&](int i, int k) { return a.U(A, tr0 + i, k); },
       [&](int k, int j) { return X[k + j * ldx]; }, put, smem);
 }
@@ -951,6 +1047,7 @@ __global__ void __launch_bounds__(kThreads) k_wsolve(FactorArgs F, int w0, int d
 }
 
 // --- P10a: H = W_A^T W_panel[cols A] -----------------------------------------
+template <class Tc>
 __global__ void __launch_bounds__(kThreads) k_htask(FactorArgs F, int h0) {
   extern __shared__ double smem[];
   Acc a(F);
@@ -961,16 +1058,20 @@ __global__ void __launch_bounds__(kThreads) k_htask(FactorArgs F, int h0) {
   double *out = F.ws + H.hoff;
   const double *Wp = F.W + P.off;
   const int ka = F.rank_l[H.a];
+  const PanelDesc PA = F.panels[A.panel];
+  const int lda = PA.rend - PA.rbeg;
+  const double *wa = F.W + PA.off + (int64_t)A.slot * lda + (A.cbeg - PA.rbeg);
   for (int j0 = 0; j0 < P.width; j0 += kTnMaxMN - kMaxRank) {
     const int nj = min(kTnMaxMN - kMaxRank, P.width - j0);
-    cta_gemm_tn(
-        ka, nj, A.cend - A.cbeg, [&](int k, int i) { return a.W(A, A.cbeg + k, i); },
+    cta_gemm_tn<Tc>(
+        ka, nj, A.cend - A.cbeg, [&](int k, int i) { return wa[k + (int64_t)i * lda]; },
         [&](int k, int j) { return Wp[(A.cbeg + k - P.rbeg) + (int64_t)(j0 + j) * ld]; },
         [&](int i, int j, double v) { out[i + (int64_t)(j0 + j) * kc] = v; }, smem);
   }
 }
 
 // --- P10b: W_panel[I] -= sum of the leaf row's updates ----------------------
+template <class Tc>
 __global__ void __launch_bounds__(kThreads) k_updrow(FactorArgs F, int u0) {
   extern __shared__ double smem[];
   Acc a(F);
@@ -987,12 +1088,12 @@ __global__ void __launch_bounds__(kThreads) k_updrow(FactorArgs F, int u0) {
     auto sub = [&](int i, int j, double v) { Wp[(I0 - P.rbeg + i) + (int64_t)j * ld] -= v; };
     if (E.hoff < 0) {
       const int nj = A.cend - A.cbeg;
-      cta_gemm<false, false>(
+      cta_gemm<false, false, Tc>(
           mi, P.width, nj, [&](int i, int k) { return a.U(A, I0 + i, k); },
           [&](int k, int j) { return Wp[(A.cbeg + k - P.rbeg) + (int64_t)j * ld]; }, sub, smem);
     } else {
       const double *Hm = F.ws + E.hoff;
-      cta_gemm<false, true>(
+      cta_gemm<false, true, Tc>(
           mi, P.width, F.rank_l[E.a], [&](int i, int k) { return a.U(A, I0 + i, k); },
           [&](int k, int j) { return Hm[k + (int64_t)j * kc]; }, sub, smem);
     }
@@ -1022,27 +1123,40 @@ int g_smem_dense = 0;
 
 }  // namespace
 
+__global__ void k_bw_h(FactorArgs F, const int32_t *blks, const double *__restrict__ v,
+                       double *__restrict__ h);
+__global__ void k_lmv_t(FactorArgs F, const int32_t *lr_ids, const double *__restrict__ x,
+                        double *__restrict__ t);
+
 int factor_smem_setup(int b, int kcap) {
   g_smem_bytes = (kGemmSmem + b * b) * (int)sizeof(double);
   int kx = b > kcap ? b : kcap;
   g_smem_dense = (kGemmSmem + kx * b) * (int)sizeof(double);
   cudaError_t e = cudaSuccess;
 #define SETA(k, s) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, s); if (e != cudaSuccess) return (int)e
-  SETA(k_gram, g_smem_bytes);
-  SETA(k_side_t, g_smem_bytes);
+  SETA(k_gram<double>, g_smem_bytes);
+  SETA(k_gram<float>, g_smem_bytes);
+  SETA(k_side_t<double>, g_smem_bytes);
+  SETA(k_side_t<float>, g_smem_bytes);
   SETA(k_side_s, g_smem_bytes);
-  SETA(k_rows, g_smem_bytes);
+  SETA(k_rows<double>, g_smem_bytes);
+  SETA(k_rows<float>, g_smem_bytes);
   SETA(k_tsqr_part, (kMaxSample + kQrRows) * kMaxSample * (int)sizeof(double));
   SETA(k_cholqr_part, kTnSmem * (int)sizeof(double));
   SETA(k_cholqr_final, 2 * kMaxSample * kMaxSample * (int)sizeof(double));
   SETA(k_tsqr_final, ((kMaxSample + kQrRows) * kMaxSample + 2 * (kMaxSample + 1) * kMaxSample) * (int)sizeof(double));
   SETA(k_tall_apply, g_smem_bytes);
-  SETA(k_dense_pair, g_smem_dense);
+  SETA(k_dense_pair<double>, g_smem_dense);
+  SETA(k_dense_pair<float>, g_smem_dense);
   SETA(k_potrf, g_smem_bytes);
   SETA(k_trsm, g_smem_bytes);
   SETA(k_wsolve, g_smem_bytes);
-  SETA(k_htask, g_smem_bytes);
-  SETA(k_updrow, g_smem_bytes);
+  SETA(k_htask<double>, g_smem_bytes);
+  SETA(k_htask<float>, g_smem_bytes);
+  SETA(k_updrow<double>, g_smem_bytes);
+  SETA(k_updrow<float>, g_smem_bytes);
+  SETA(k_bw_h, kTnSmem * (int)sizeof(double));
+  SETA(k_lmv_t, kTnSmem * (int)sizeof(double));
 #undef SETA
   return 0;
 }
@@ -1068,7 +1182,8 @@ void prof_collect(Prof *p, int nev) {
       p->ms += ms;
       ++p->launches;
     } else {
-      cudaGetLastError();  // do not leave the failure for an unrelated status check
+      const cudaError_t e = cudaGetLastError();  // do not leave it for an unrelated status check
+      if (!p->failed++) p->first_err = (int)e;
     }
   }
 }
@@ -1082,15 +1197,18 @@ void prof_collect(Prof *p, int nev) {
     ++nk;                                                         \
   } while (0)
 
-int launch_step(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
-                const FactorArgs &F, const StepRange &S, int K, const Plan &PL, Prof *prof) {
+namespace {
+// One step of the sweep with the Schur-update products computed in T.
+template <class Tc>
+int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
+                  const FactorArgs &F, const StepRange &S, int K, const Plan &PL, Prof *prof) {
   const std::vector<LrTarget> &lrt_host = PL.lrt;
   int nk = 0;
   const int sm = (kGemmSmem + F.b * F.b) * (int)sizeof(double);
   const int smt = std::max(kGemmSmem + F.b * F.b, kTnSmem) * (int)sizeof(double);
   const int smd = (kGemmSmem + std::max(F.b, F.kcap) * F.b) * (int)sizeof(double);
   const int r = F.r;
-  if (S.gch1 > S.gch0) { LAUNCH(KK_GRAM, st, k_gram<<<S.gch1 - S.gch0, kThreads, smt, st>>>(F, S.gch0)); }
+  if (S.gch1 > S.gch0) { LAUNCH(KK_GRAM, st, k_gram<Tc><<<S.gch1 - S.gch0, kThreads, smt, st>>>(F, S.gch0)); }
   if (S.gred1 > S.gred0) { LAUNCH(KK_GRAM, st, k_gram_reduce<<<S.gred1 - S.gred0, kThreads, 0, st>>>(F, S.gred0)); }
   // the dense blocks of column K (P6-P8) only need the grams: fork them to
   // the side stream while the low-rank targets are compressed
@@ -1101,7 +1219,7 @@ int launch_step(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEve
   }
   const int nd = S.dns1 - S.dns0;
   const int q0 = PL.dns[S.dns0].p0, q1 = PL.dns[S.dns1 - 1].p1;
-  if (q1 > q0) { LAUNCH(KK_DENSE_PAIR, sd, k_dense_pair<<<q1 - q0, kThreads, smd, sd>>>(F, q0, S.dpws)); }
+  if (q1 > q0) { LAUNCH(KK_DENSE_PAIR, sd, k_dense_pair<Tc><<<q1 - q0, kThreads, smd, sd>>>(F, q0, S.dpws)); }
   LAUNCH(KK_DENSE_REDUCE, sd, k_dense_reduce<<<nd, kThreads, 0, sd>>>(F, S.dns0, S.dpws));
   LAUNCH(KK_POTRF, sd, k_potrf<<<1, kThreads, sm, sd>>>(F, S.dns0, K));
   if (nd > 1) { LAUNCH(KK_TRSM, sd, k_trsm<<<nd - 1, kThreads, sm, sd>>>(F, S.dns0, K)); }
@@ -1119,20 +1237,20 @@ int launch_step(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEve
     const int qrf_smem = ((r + kQrRows) * r + 2 * (r | 1) * r) * (int)sizeof(double);
     const int cq_smem = 2 * r * r * (int)sizeof(double);
     // Y = S Omega
-    LAUNCH(KK_SIDE_T, st, k_side_t<<<(S.bent1 - S.bent0) + nt, kThreads, smt, st>>>(F, S.bent0, S.bent1 - S.bent0, S.lrt0, 0));
+    LAUNCH(KK_SIDE_T, st, k_side_t<Tc><<<(S.bent1 - S.bent0) + nt, kThreads, smt, st>>>(F, S.bent0, S.bent1 - S.bent0, S.lrt0, 0));
     if (S.aent1 > S.aent0) LAUNCH(KK_SIDE_S, st, k_side_s<<<S.aent1 - S.aent0, kThreads, sm, st>>>(F, S.aent0, 0));
-    LAUNCH(KK_ROWS, st, k_rows<<<S.arow1 - S.arow0, kThreads, sm, st>>>(F, S.arow0, 0));
+    LAUNCH(KK_ROWS, st, k_rows<Tc><<<S.arow1 - S.arow0, kThreads, sm, st>>>(F, S.arow0, 0));
     // Q = orth(Y): R of Y, SVD, Q1 = Y V Sigma^{-1}, then CholQR
     LAUNCH(KK_TSQR_PART, st, k_tsqr_part<<<dim3(nt, maxgm), kThreads, qr_smem, st>>>(F, S.lrt0, 0));
     LAUNCH(KK_TSQR_FINAL, st, k_tsqr_final<<<nt, kThreads, qrf_smem, st>>>(F, S.lrt0, 0, 0));
     LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch), kThreads, sm, st>>>(F, S.lrt0, 0));
-    LAUNCH(KK_CHOLQR_PART, st, k_cholqr_part<<<dim3(nt, maxgm), kThreads, smt, st>>>(F, S.lrt0));
+    LAUNCH(KK_CHOLQR_PART, st, k_cholqr_part<<<dim3(nt, maxgm), kThreads, kTnSmem * (int)sizeof(double), st>>>(F, S.lrt0));
     LAUNCH(KK_CHOLQR_FINAL, st, k_cholqr_final<<<nt, kThreads, cq_smem, st>>>(F, S.lrt0));
     LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch), kThreads, sm, st>>>(F, S.lrt0, 0));
     // Z = S^T Q
-    LAUNCH(KK_SIDE_T, st, k_side_t<<<(S.aent1 - S.aent0) + nt, kThreads, smt, st>>>(F, S.aent0, S.aent1 - S.aent0, S.lrt0, 1));
+    LAUNCH(KK_SIDE_T, st, k_side_t<Tc><<<(S.aent1 - S.aent0) + nt, kThreads, smt, st>>>(F, S.aent0, S.aent1 - S.aent0, S.lrt0, 1));
     if (S.bent1 > S.bent0) LAUNCH(KK_SIDE_S, st, k_side_s<<<S.bent1 - S.bent0, kThreads, sm, st>>>(F, S.bent0, 1));
-    LAUNCH(KK_ROWS, st, k_rows<<<S.brow1 - S.brow0, kThreads, sm, st>>>(F, S.brow0, 1));
+    LAUNCH(KK_ROWS, st, k_rows<Tc><<<S.brow1 - S.brow0, kThreads, sm, st>>>(F, S.brow0, 1));
     LAUNCH(KK_TSQR_PART, st, k_tsqr_part<<<dim3(nt, maxgp), kThreads, qr_smem, st>>>(F, S.lrt0, 1));
     LAUNCH(KK_TSQR_FINAL, st, k_tsqr_final<<<nt, kThreads, qrf_smem, st>>>(F, S.lrt0, 1, 1));
     LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch), kThreads, sm, st>>>(F, S.lrt0, 1));
@@ -1147,9 +1265,16 @@ int launch_step(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEve
     LAUNCH(KK_WSOLVE, st, k_wsolve<<<dim3(S.wpan1 - S.wpan0, (maxw + kThreads - 1) / kThreads), kThreads, sm, st>>>(
         F, S.wpan0, S.dns0));
   }
-  if (S.ht1 > S.ht0) { LAUNCH(KK_HTASK, st, k_htask<<<S.ht1 - S.ht0, kThreads, smt, st>>>(F, S.ht0)); }
-  if (S.ur1 > S.ur0) { LAUNCH(KK_UPDROW, st, k_updrow<<<S.ur1 - S.ur0, kThreads, sm, st>>>(F, S.ur0)); }
+  if (S.ht1 > S.ht0) { LAUNCH(KK_HTASK, st, k_htask<Tc><<<S.ht1 - S.ht0, kThreads, smt, st>>>(F, S.ht0)); }
+  if (S.ur1 > S.ur0) { LAUNCH(KK_UPDROW, st, k_updrow<Tc><<<S.ur1 - S.ur0, kThreads, sm, st>>>(F, S.ur0)); }
   return nk;
+}
+}  // namespace
+
+int launch_step(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
+                const FactorArgs &F, const StepRange &S, int K, const Plan &PL, Prof *prof) {
+  return F.mixed ? launch_step_t<float>(st, side, ev_fork, ev_join, F, S, K, PL, prof)
+                 : launch_step_t<double>(st, side, ev_fork, ev_join, F, S, K, PL, prof);
 }
 
 // --- a17: y = L x (field simulation Z = L xi) ------------------------------
@@ -1201,15 +1326,97 @@ __global__ void k_permute_out(const double *__restrict__ y, const int32_t *__res
 void launch_lower_matvec(cudaStream_t st, const FactorArgs &F, const int32_t *lr_ids, int nlr,
                          const int32_t *row0, const int32_t *rblocks, int nleaf,
                          const double *x, double *y, double *t) {
-  const int smt = std::max(kGemmSmem + F.b * F.b, kTnSmem) * (int)sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_lmv_t, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (kGemmSmem + kMaxLeaf * kMaxLeaf) * (int)sizeof(double));
-    attr = true;
-  }
+  const int smt = kTnSmem * (int)sizeof(double);
   if (nlr > 0) k_lmv_t<<<nlr, kThreads, smt, st>>>(F, lr_ids, x, t);
   k_lmv_rows<<<nleaf, kThreads, 0, st>>>(F, row0, rblocks, x, t, y);
+}
+
+void launch_solve(cudaStream_t st, const FactorArgs &F0, const Plan &PL, const int32_t *wpan_rhs) {
+  FactorArgs F = F0;
+  F.wpan = wpan_rhs;
+  const int sm = (kGemmSmem + F.b * F.b) * (int)sizeof(double);
+  const int smt = std::max(kGemmSmem + F.b * F.b, kTnSmem) * (int)sizeof(double);
+  for (int K = 0; K < PL.nleaf; ++K) {
+    const StepRange &S = PL.steps[K];
+    k_wsolve<<<dim3(1, 1), kThreads, sm, st>>>(F, 0, S.dns0);
+    const int h0 = PL.ht_rhs0[K], h1 = PL.ht_rhs0[K + 1];
+    if (h1 > h0) k_htask<double><<<h1 - h0, kThreads, smt, st>>>(F, h0);
+    const int u0 = PL.ur_rhs0[K], u1 = PL.ur_rhs0[K + 1];
+    if (u1 > u0) k_updrow<double><<<u1 - u0, kThreads, sm, st>>>(F, u0);
+  }
+}
+
+// --- a11: backward solve v = L^{-T} w --------------------------------------
+// L^T is block upper triangular, so the leaves are solved in reverse order:
+// v_K = L_KK^{-T} (w_K - sum over blocks A below the diagonal block of leaf K
+// of A^T v[rows A]).  Once v_K is final, every block whose rows start at
+// leaf K has all its rows final and pushes A^T v[rows A] into its columns.
+
+// v_K <- L_KK^{-T} v_K by back substitution (one thread; m <= 128)
+__global__ void k_bw_diag(FactorArgs F, int dblk, double *__restrict__ v) {
+  const BlockDesc D = F.blocks[dblk];
+  const int m = D.rend - D.rbeg, b = F.b;
+  const double *L = F.D + D.off_d;   // column-major, leading dimension b
+  if (threadIdx.x == 0) {
+    for (int i = m - 1; i >= 0; --i) {
+      double s = v[D.rbeg + i];
+      for (int l = i + 1; l < m; ++l) s = fma(-L[l + (int64_t)i * b], v[D.rbeg + l], s);
+      v[D.rbeg + i] = s / L[i + (int64_t)i * b];
+    }
+  }
+}
+
+// h_A = U_A^T v[rows A] for the low-rank blocks whose rows start at this leaf
+__global__ void __launch_bounds__(kThreads) k_bw_h(FactorArgs F, const int32_t *blks,
+                                                   const double *__restrict__ v,
+                                                   double *__restrict__ h) {
+  extern __shared__ double smem[];
+  Acc a(F);
+  const int blk = blks[blockIdx.x];
+  const BlockDesc A = F.blocks[blk];
+  cta_gemm_tn(
+      F.rank_l[blk], 1, A.rend - A.rbeg, [&](int k, int i) { return a.U(A, A.rbeg + k, i); },
+      [&](int k, int j) { return v[A.rbeg + k]; },
+      [&](int i, int j, double val) { h[(int64_t)blockIdx.x * F.kcap + i] = val; }, smem);
+}
+
+// v[J] -= sum over the entries of column leaf J, in a fixed order: W_A[J] h_A
+// for a low-rank block, D_A^T v[rows A] for a dense one.
+__global__ void __launch_bounds__(kThreads) k_bw_upd(FactorArgs F, const UpdRow *rows,
+                                                     const UpdEntry *ents,
+                                                     const double *__restrict__ h,
+                                                     double *__restrict__ v) {
+  Acc a(F);
+  const UpdRow R = rows[blockIdx.x];
+  const int J0 = F.leaf_beg[R.leaf], J1 = F.leaf_beg[R.leaf + 1];
+  for (int j = J0 + threadIdx.x; j < J1; j += blockDim.x) {
+    double acc = 0.0;
+    for (int q = R.e0; q < R.e1; ++q) {
+      const UpdEntry E = ents[q];
+      const BlockDesc A = F.blocks[E.a];
+      if (E.hoff < 0) {
+        for (int i = 0; i < A.rend - A.rbeg; ++i)
+          acc = fma(a.U(A, A.rbeg + i, j - A.cbeg), v[A.rbeg + i], acc);
+      } else {
+        const double *hA = h + E.hoff * F.kcap;
+        for (int k = 0; k < F.rank_l[E.a]; ++k) acc = fma(a.W(A, j, k), hA[k], acc);
+      }
+    }
+    v[j] -= acc;
+  }
+}
+
+void launch_backward(cudaStream_t st, const FactorArgs &F, const Plan &PL, double *v,
+                     const int32_t *bh_blocks, const UpdRow *bupd, const UpdEntry *bents,
+                     double *hbuf) {
+  const int smt = kTnSmem * (int)sizeof(double);
+  for (int K = PL.nleaf - 1; K >= 0; --K) {
+    k_bw_diag<<<1, 32, 0, st>>>(F, PL.diag_of_leaf[K], v);
+    const int h0 = PL.bh0[K], h1 = PL.bh0[K + 1];
+    if (h1 > h0) k_bw_h<<<h1 - h0, kThreads, smt, st>>>(F, bh_blocks + h0, v, hbuf);
+    const int u0 = PL.bupd0[K], u1 = PL.bupd0[K + 1];
+    if (u1 > u0) k_bw_upd<<<u1 - u0, kThreads, 0, st>>>(F, bupd + u0, bents, hbuf, v);
+  }
 }
 
 void launch_permute_out(cudaStream_t st, const double *y, const int32_t *perm, int64_t n,

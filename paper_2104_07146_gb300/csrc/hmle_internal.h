@@ -186,9 +186,27 @@ struct Plan {
   std::vector<UpdRow> urows;
   std::vector<UpdEntry> uents;
   std::vector<StepRange> steps;
+  // forward solve of a new right-hand side through a finished factor: per
+  // step, the deferred updates restricted to the right-hand-side panel
+  std::vector<HTask> hts_rhs;
+  std::vector<UpdRow> urows_rhs;
+  std::vector<UpdEntry> uents_rhs;
+  std::vector<int32_t> ht_rhs0, ur_rhs0;   // per step ranges (nleaf + 1 entries)
+  // backward solve v = L^{-T} w (reverse sweep).  At step K (leaves in
+  // reverse order), after v_K is solved, every block A whose row cluster
+  // starts at K pushes v[cols A] -= A^T v[rows A]: low-rank blocks through
+  // h_A = U_A^T v[rows A] (bh_blocks), then per column leaf J the entries
+  // touching it (bupd rows: UpdRow with panel unused, entries UpdEntry with
+  // hoff = index into the h workspace, or -1 for a dense block).
+  std::vector<int32_t> bh_blocks, bh0;      // per step: LR blocks whose rows start at K
+  std::vector<UpdRow> bupd;
+  std::vector<UpdEntry> bents;
+  std::vector<int32_t> bupd0;               // per step ranges of bupd
   // triangular H-matvec y = L x (simulation): per leaf row, the blocks of L
   // covering it (diagonal first)
   std::vector<int32_t> mv_row0, mv_blocks;
+  // per leaf I: off-diagonal blocks whose columns cover I (symmetric C x)
+  std::vector<int32_t> mvt_row0, mvt_blocks;
   int64_t ws_max;
   int64_t n_lr_blocks, n_dense_blocks;
 };

@@ -27,6 +27,7 @@ struct AsmArgs {
   int32_t *rank_c;
   double *cnorm;           // |C_block|_F estimate of every admissible block
   int *flags;
+  const ThetaDev *thd;     // the same theta in device memory (read by captured kernels)
 };
 
 // Everything the sweep kernels read; device pointers.
@@ -73,15 +74,13 @@ struct FactorArgs {
   uint64_t seed;
   int b, kcap, kc, r;
   int osamp;               // oversampling of the randomised compression
+  int mixed;               // 1: the Schur-update and panel-update products in FP32
 };
 
 void launch_matern_table(cudaStream_t st, double nu, double *tab);
 void launch_matern_eval(cudaStream_t st, const double *tab, const double *x, int64_t m,
                         double *out);
 void launch_aca(cudaStream_t st, const AsmArgs &A, int n_lr);
-void launch_hmatvec(cudaStream_t st, const AsmArgs &A, const int32_t *dense_ids, int nd,
-                    int n_lr, const double *x, double *y);
-
 // Kernel kinds of the sweep (for per-kernel timing and flop tallies).
 enum KernelKind {
   KK_GRAM = 0, KK_SIDE_T, KK_SIDE_S, KK_ROWS, KK_TSQR_PART, KK_TSQR_FINAL, KK_TALL_APPLY,
@@ -99,6 +98,8 @@ struct Prof {
   double ms = 0.0;
   int64_t launches = 0;
   double flops = 0.0;
+  int failed = 0;               // event pairs whose elapsed time could not be read
+  int first_err = 0;            // the cudaError_t of the first such pair
 };
 void prof_mark(Prof *p, cudaStream_t s);
 // after a stream synchronisation: add the elapsed times of the first nev
@@ -120,6 +121,17 @@ void launch_permute_in(cudaStream_t st, const double *z, const int32_t *perm, in
 void launch_lower_matvec(cudaStream_t st, const FactorArgs &F, const int32_t *lr_ids, int nlr,
                          const int32_t *row0, const int32_t *rblocks, int nleaf,
                          const double *x, double *y, double *t);
+// Forward solve w <- L^{-1} w on the right-hand-side panel of a finished
+// factor (F's task pointers set to the rhs-only lists: hts/urows/uents;
+// wpan must hold the rhs panel index at position 0).
+void launch_solve(cudaStream_t st, const FactorArgs &F, const Plan &PL, const int32_t *wpan_rhs);
+// Backward solve v <- L^{-T} v in place on a vector v (cluster order), by the
+// reverse leaf sweep; hbuf: workspace of kcap doubles per low-rank block of
+// the largest step.  bh_blocks / bupd / bents: device copies of the plan's
+// backward lists.
+void launch_backward(cudaStream_t st, const FactorArgs &F, const Plan &PL, double *v,
+                     const int32_t *bh_blocks, const UpdRow *bupd, const UpdEntry *bents,
+                     double *hbuf);
 // out[perm[k]] = y[k]
 void launch_permute_out(cudaStream_t st, const double *y, const int32_t *perm, int64_t n,
                         double *out);
@@ -127,5 +139,34 @@ void launch_permute_out(cudaStream_t st, const double *y, const int32_t *perm, i
 void launch_finalize(cudaStream_t st, const double *parts, int N, const double *w, int64_t n,
                      double *out);
 int factor_smem_setup(int b, int kcap);
+
+// Fixed-order lists of the symmetric H-matvec y = C x (device pointers):
+// per leaf I, the blocks whose rows cover I (row0 / rblocks, diagonal block
+// first) and the off-diagonal blocks whose columns cover I (col0 / cblocks);
+// lr_slot[blk] = index of blk among the admissible blocks, -1 if dense.
+struct CmvLists {
+  int nleaf;
+  const int32_t *leaf_beg, *row0, *rblocks, *col0, *cblocks, *lr_slot;
+};
+// y = C x in cluster order (FP64; dense entries generated from the table);
+// t: 2 kc doubles per admissible block.
+void launch_cmatvec(cudaStream_t st, const AsmArgs &A, int n_lr, const CmvLists &L,
+                    const double *x, double *t, double *y);
+// doubles of workspace pcg_quad needs
+int64_t pcg_words(int64_t n, int n_lr, int kc, int hmax);
+// q = b^T x with C x = b solved by PCG: operator launch_cmatvec, preconditioner
+// the factor of Fs (F's task pointers set to the right-hand-side lists) applied
+// through the right-hand-side panel `panel` (overwritten).  b: n doubles,
+// cluster order.  Stops when |r| <= tol |b| or after maxit iterations.
+// The two launch sequences (set-up, one iteration) are captured as CUDA
+// graphs into *g_init / *g_iter on first use when those are not NULL (the
+// pointers and theta they read are fixed per buffer set; theta is read from
+// device memory) and replayed afterwards.
+cudaError_t pcg_quad(cudaStream_t st, const AsmArgs &A, int n_lr, const CmvLists &L,
+                     const FactorArgs &Fs, const Plan &PL, const int32_t *wpan_rhs,
+                     const int32_t *bh_blocks, const UpdRow *bupd, const UpdEntry *bents,
+                     double *panel, const double *b, int64_t n, double tol, int maxit,
+                     double *pool, double *q_out, int *iters, double *relres,
+                     cudaGraphExec_t *g_init, cudaGraphExec_t *g_iter);
 
 }  // namespace hmle

@@ -1,0 +1,266 @@
+// a14 (mixed form): the quadratic form Z^T C~^{-1} Z won back to FP64
+// accuracy by preconditioned conjugate gradients.  The operator is the FP64
+// H-matrix of C (dense near-field entries generated from the Matern table,
+// admissible blocks as their ACA factors U V^T); the preconditioner is the
+// H-Cholesky factor of the mixed form, applied as a forward and a backward
+// sweep (M^{-1} = L~^{-T} L~^{-1}).  Everything is in cluster order.
+//
+// All reductions run in a fixed order, so a PCG run is deterministic.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "hmle_internal.h"
+#include "kernels.cuh"
+#include "matern.cuh"
+
+namespace hmle {
+namespace {
+
+constexpr int kDotCtas = 152;   // first-stage CTAs of a dot product (one per SM)
+constexpr int kThreadsMv = 128;
+
+// --- y = C x, deterministic ------------------------------------------------
+// Stage 1: per admissible block of C, t1 = V^T x[cols], t2 = U^T x[rows].
+__global__ void __launch_bounds__(kThreadsMv) k_cmv_t(AsmArgs A, const double *__restrict__ x,
+                                                      double *__restrict__ t) {
+  __shared__ double red[32];
+  const int blk = A.lr_ids[blockIdx.x];
+  const BlockDesc B = A.blocks[blk];
+  const int m = B.rend - B.rbeg, p = B.cend - B.cbeg, kc = A.kc;
+  const int k = A.rank_c[blk];
+  const double *U = A.uc + B.off_uc, *V = A.uc + B.off_vc;
+  double *t1 = t + (int64_t)blockIdx.x * 2 * kc, *t2 = t1 + kc;
+  for (int l = 0; l < k; ++l) {
+    double a = 0.0, c = 0.0;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) a = fma(V[(int64_t)l * p + j], x[B.cbeg + j], a);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) c = fma(U[(int64_t)l * m + i], x[B.rbeg + i], c);
+    a = block_sum(a, red);
+    c = block_sum(c, red);
+    if (threadIdx.x == 0) { t1[l] = a; t2[l] = c; }
+  }
+}
+
+// Stage 2: one CTA per leaf I; thread i sums, in list order, the blocks whose
+// rows cover I (C x[cols], U t1) and then those whose columns cover I
+// (C^T x[rows], V t2).  lr_slot[blk]: the block's index among the admissible
+// blocks (its t1/t2 slot), -1 for a dense block.
+__global__ void __launch_bounds__(kThreadsMv) k_cmv_rows(AsmArgs A, const int32_t *__restrict__ leaf_beg,
+                                                         const int32_t *__restrict__ row0,
+                                                         const int32_t *__restrict__ rblocks,
+                                                         const int32_t *__restrict__ col0,
+                                                         const int32_t *__restrict__ cblocks,
+                                                         const int32_t *__restrict__ lr_slot,
+                                                         const double *__restrict__ x,
+                                                         const double *__restrict__ t,
+                                                         double *__restrict__ y) {
+  const int I = blockIdx.x;
+  const int I0 = leaf_beg[I], I1 = leaf_beg[I + 1];
+  const int kc = A.kc;
+  const double inv_ell = A.thd->inv_ell, sigma2 = A.thd->sigma2, tau2 = A.thd->tau2;
+  for (int i = I0 + threadIdx.x; i < I1; i += blockDim.x) {
+    double acc = 0.0;
+    for (int q = row0[I]; q < row0[I + 1]; ++q) {
+      const int blk = rblocks[q];
+      const BlockDesc B = A.blocks[blk];
+      const int s = lr_slot[blk];
+      if (s < 0) {
+        for (int j = B.cbeg; j < B.cend; ++j)
+          acc = fma(cov_entry(A.tab, A.xyz, A.n, A.d, i, j, inv_ell, sigma2, tau2), x[j], acc);
+      } else {
+        const int m = B.rend - B.rbeg, k = A.rank_c[blk];
+        const double *U = A.uc + B.off_uc;
+        const double *t1 = t + (int64_t)s * 2 * kc;
+        for (int l = 0; l < k; ++l) acc = fma(U[(int64_t)l * m + (i - B.rbeg)], t1[l], acc);
+      }
+    }
+    for (int q = col0[I]; q < col0[I + 1]; ++q) {
+      const int blk = cblocks[q];
+      const BlockDesc B = A.blocks[blk];
+      const int s = lr_slot[blk];
+      if (s < 0) {
+        for (int j = B.rbeg; j < B.rend; ++j)
+          acc = fma(cov_entry(A.tab, A.xyz, A.n, A.d, j, i, inv_ell, sigma2, tau2), x[j], acc);
+      } else {
+        const int p = B.cend - B.cbeg, k = A.rank_c[blk];
+        const double *V = A.uc + B.off_vc;
+        const double *t2 = t + (int64_t)s * 2 * kc + kc;
+        for (int l = 0; l < k; ++l) acc = fma(V[(int64_t)l * p + (i - B.cbeg)], t2[l], acc);
+      }
+    }
+    y[i] = acc;
+  }
+}
+
+// --- dot products: fixed partition, fixed order -----------------------------
+__global__ void k_dot_part(const double *__restrict__ a, const double *__restrict__ b, int64_t n,
+                           double *__restrict__ part) {
+  __shared__ double red[32];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  double s = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) s = fma(a[i], b[i], s);
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_dot_final(const double *__restrict__ part, int np, double *__restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// --- the scalar recurrences and vector updates ------------------------------
+// sc: [0] r.z  [1] p.q  [2] alpha  [3] r.z (new)  [4] beta  [5] r.r  [6] b.b  [7] b.x
+__global__ void k_pcg_alpha(double *sc) { sc[2] = sc[0] / sc[1]; }
+__global__ void k_pcg_beta(double *sc) {
+  sc[4] = sc[3] / sc[0];
+  sc[0] = sc[3];
+}
+
+__global__ void k_pcg_xr(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                         const double *__restrict__ q, const double *__restrict__ sc, int64_t n) {
+  const double alpha = sc[2];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    x[i] = fma(alpha, p[i], x[i]);
+    r[i] = fma(-alpha, q[i], r[i]);
+  }
+}
+
+__global__ void k_pcg_p(double *__restrict__ p, const double *__restrict__ z,
+                        const double *__restrict__ sc, int64_t n) {
+  const double beta = sc[4];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = fma(beta, p[i], z[i]);
+}
+
+void dot(cudaStream_t st, const double *a, const double *b, int64_t n, double *part, double *out) {
+  k_dot_part<<<kDotCtas, 256, 0, st>>>(a, b, n, part);
+  k_dot_final<<<1, 256, 0, st>>>(part, kDotCtas, out);
+}
+
+unsigned grid1(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+int64_t pcg_words(int64_t n, int n_lr, int kc, int hmax) {
+  return 5 * n + (int64_t)std::max(n_lr, 1) * 2 * kc + (int64_t)hmax + kDotCtas + 16;
+}
+
+void launch_cmatvec(cudaStream_t st, const AsmArgs &A, int n_lr, const CmvLists &L,
+                    const double *x, double *t, double *y) {
+  if (n_lr > 0) k_cmv_t<<<n_lr, kThreadsMv, 0, st>>>(A, x, t);
+  k_cmv_rows<<<L.nleaf, kThreadsMv, 0, st>>>(A, L.leaf_beg, L.row0, L.rblocks, L.col0, L.cblocks,
+                                             L.lr_slot, x, t, y);
+}
+
+namespace {
+
+struct PcgBufs {
+  double *x, *r, *z, *p, *qv, *t, *hbuf, *part, *sc;
+};
+
+PcgBufs carve(double *pool, int64_t n, int n_lr, int kc, const Plan &PL) {
+  PcgBufs B;
+  B.x = pool; B.r = B.x + n; B.z = B.r + n; B.p = B.z + n; B.qv = B.p + n;
+  B.t = B.qv + n;
+  B.hbuf = B.t + (int64_t)std::max(n_lr, 1) * 2 * kc;
+  int hmax = 1;
+  for (int K = 0; K < PL.nleaf; ++K) hmax = std::max(hmax, PL.bh0[K + 1] - PL.bh0[K]);
+  B.part = B.hbuf + (int64_t)hmax * PL.kcap;
+  B.sc = B.part + kDotCtas;
+  return B;
+}
+
+// z = M^{-1} r = L~^{-T} L~^{-1} r through the right-hand-side panel
+void precond(cudaStream_t st, const FactorArgs &Fs, const Plan &PL, const int32_t *wpan_rhs,
+             const int32_t *bh_blocks, const UpdRow *bupd, const UpdEntry *bents, double *panel,
+             const double *r, double *z, double *hbuf, int64_t n) {
+  cudaMemcpyAsync(panel, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  launch_solve(st, Fs, PL, wpan_rhs);
+  launch_backward(st, Fs, PL, panel, bh_blocks, bupd, bents, hbuf);
+  cudaMemcpyAsync(z, panel, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+}
+
+// Run seq() directly, or through a graph captured into *g on first use.
+template <class Seq>
+cudaError_t run_seq(cudaStream_t st, cudaGraphExec_t *g, Seq seq) {
+  if (!g) { seq(); return cudaGetLastError(); }
+  if (!*g) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaGetLastError(); seq(); return cudaGetLastError(); }
+    seq();
+    e = cudaStreamEndCapture(st, &graph);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(g, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { *g = nullptr; return e; }
+  }
+  return cudaGraphLaunch(*g, st);
+}
+
+}  // namespace
+
+cudaError_t pcg_quad(cudaStream_t st, const AsmArgs &A, int n_lr, const CmvLists &L,
+                     const FactorArgs &Fs, const Plan &PL, const int32_t *wpan_rhs,
+                     const int32_t *bh_blocks, const UpdRow *bupd, const UpdEntry *bents,
+                     double *panel, const double *b, int64_t n, double tol, int maxit,
+                     double *pool, double *q_out, int *iters, double *relres,
+                     cudaGraphExec_t *g_init, cudaGraphExec_t *g_iter) {
+  const PcgBufs B = carve(pool, n, n_lr, A.kc, PL);
+  // x = 0, r = b, z = M^{-1} r, p = z, sc[0] = r.z, sc[6] = b.b
+  cudaError_t e = run_seq(st, g_init, [&] {
+    cudaMemsetAsync(B.x, 0, sizeof(double) * n, st);
+    cudaMemcpyAsync(B.r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    precond(st, Fs, PL, wpan_rhs, bh_blocks, bupd, bents, panel, B.r, B.z, B.hbuf, n);
+    cudaMemcpyAsync(B.p, B.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    dot(st, B.r, B.z, n, B.part, B.sc + 0);
+    dot(st, b, b, n, B.part, B.sc + 6);
+  });
+  if (e != cudaSuccess) return e;
+  double h[2];
+  e = cudaMemcpyAsync(h, B.sc + 6, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  const double bb = h[0];
+  int it = 0;
+  double rel = 1.0;
+  while (it < maxit) {
+    // one iteration; the preconditioner of the next one runs even when this
+    // one converges (its result is then unused)
+    e = run_seq(st, g_iter, [&] {
+      launch_cmatvec(st, A, n_lr, L, B.p, B.t, B.qv);
+      dot(st, B.p, B.qv, n, B.part, B.sc + 1);
+      k_pcg_alpha<<<1, 1, 0, st>>>(B.sc);
+      k_pcg_xr<<<grid1(n), 256, 0, st>>>(B.x, B.r, B.p, B.qv, B.sc, n);
+      dot(st, B.r, B.r, n, B.part, B.sc + 5);
+      precond(st, Fs, PL, wpan_rhs, bh_blocks, bupd, bents, panel, B.r, B.z, B.hbuf, n);
+      dot(st, B.r, B.z, n, B.part, B.sc + 3);
+      k_pcg_beta<<<1, 1, 0, st>>>(B.sc);
+      k_pcg_p<<<grid1(n), 256, 0, st>>>(B.p, B.z, B.sc, n);
+    });
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(h, B.sc + 5, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    ++it;
+    rel = bb > 0.0 ? std::sqrt(h[0] / bb) : 0.0;
+    if (!(rel > tol)) break;   // converged (or not finite: stop and report it)
+  }
+  dot(st, b, B.x, n, B.part, B.sc + 7);
+  e = cudaMemcpyAsync(h, B.sc + 7, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  *q_out = h[0];
+  *iters = it;
+  *relres = rel;
+  return cudaGetLastError();
+}
+
+}  // namespace hmle

@@ -183,6 +183,21 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
     P.mv_blocks.insert(P.mv_blocks.end(), Bd.rowlist[I].begin(), Bd.rowlist[I].end());
   }
   P.mv_row0[N] = (int32_t)P.mv_blocks.size();
+  {
+    std::vector<std::vector<int32_t>> collist(N);
+    for (size_t x = 0; x < P.blocks.size(); ++x) {
+      const BlockDesc &B = P.blocks[x];
+      if (B.kind == kDense && B.rleaf == B.cleaf) continue;
+      for (int J = B.cleaf; J < B.cleaf + Bd.span(B); ++J) collist[J].push_back((int32_t)x);
+    }
+    P.mvt_row0.assign(N + 1, 0);
+    P.mvt_blocks.clear();
+    for (int I = 0; I < N; ++I) {
+      P.mvt_row0[I] = (int32_t)P.mvt_blocks.size();
+      P.mvt_blocks.insert(P.mvt_blocks.end(), collist[I].begin(), collist[I].end());
+    }
+    P.mvt_row0[N] = (int32_t)P.mvt_blocks.size();
+  }
 
   // blocks grouped by first column leaf / by last column leaf
   std::vector<std::vector<int32_t>> starts(N), ends(N);
@@ -422,6 +437,67 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
     st.ws_words = ws;
     P.ws_max = std::max(P.ws_max, ws);
     P.steps.push_back(st);
+  }
+  // the right-hand-side panel's share of the deferred updates
+  P.hts_rhs.clear(); P.urows_rhs.clear(); P.uents_rhs.clear();
+  P.ht_rhs0.assign(N + 1, 0);
+  P.ur_rhs0.assign(N + 1, 0);
+  for (int K = 0; K < N; ++K) {
+    const StepRange &st = P.steps[K];
+    P.ht_rhs0[K] = (int32_t)P.hts_rhs.size();
+    for (int q = st.ht0; q < st.ht1; ++q)
+      if (P.hts[q].panel == P.rhs_panel) P.hts_rhs.push_back(P.hts[q]);
+    P.ur_rhs0[K] = (int32_t)P.urows_rhs.size();
+    for (int q = st.ur0; q < st.ur1; ++q) {
+      if (P.urows[q].panel != P.rhs_panel) continue;
+      UpdRow u = P.urows[q];
+      const int e0 = (int32_t)P.uents_rhs.size();
+      P.uents_rhs.insert(P.uents_rhs.end(), P.uents.begin() + u.e0, P.uents.begin() + u.e1);
+      u.e0 = e0;
+      u.e1 = (int32_t)P.uents_rhs.size();
+      P.urows_rhs.push_back(u);
+    }
+  }
+  P.ht_rhs0[N] = (int32_t)P.hts_rhs.size();
+  P.ur_rhs0[N] = (int32_t)P.urows_rhs.size();
+
+  // backward solve: blocks grouped by the first leaf of their rows
+  {
+    std::vector<std::vector<int32_t>> rstart(N);
+    for (size_t x = 0; x < P.blocks.size(); ++x) {
+      const BlockDesc &B = P.blocks[x];
+      if (B.kind == kDense && B.rleaf == B.cleaf) continue;  // diagonal
+      rstart[B.rleaf].push_back((int32_t)x);
+    }
+    P.bh_blocks.clear(); P.bh0.assign(N + 1, 0);
+    P.bupd.clear(); P.bents.clear(); P.bupd0.assign(N + 1, 0);
+    for (int K = 0; K < N; ++K) {
+      P.bh0[K] = (int32_t)P.bh_blocks.size();
+      std::map<int32_t, std::vector<UpdEntry>> cols;   // column leaf -> entries
+      for (int32_t x : rstart[K]) {
+        const BlockDesc &A = P.blocks[x];
+        UpdEntry ue{};
+        ue.a = x;
+        ue.hoff = -1;
+        if (A.kind == kLowRank) {
+          ue.hoff = (int64_t)(P.bh_blocks.size() - P.bh0[K]);
+          P.bh_blocks.push_back(x);
+        }
+        for (int J = A.cleaf; J < A.cleaf + Bd.span(A); ++J) cols[J].push_back(ue);
+      }
+      P.bupd0[K] = (int32_t)P.bupd.size();
+      for (auto &kv : cols) {
+        UpdRow u{};
+        u.panel = -1;
+        u.leaf = kv.first;
+        u.e0 = (int32_t)P.bents.size();
+        P.bents.insert(P.bents.end(), kv.second.begin(), kv.second.end());
+        u.e1 = (int32_t)P.bents.size();
+        P.bupd.push_back(u);
+      }
+    }
+    P.bh0[N] = (int32_t)P.bh_blocks.size();
+    P.bupd0[N] = (int32_t)P.bupd.size();
   }
   return "";
 }

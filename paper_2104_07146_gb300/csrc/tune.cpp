@@ -1,0 +1,77 @@
+// a15: the autotuner of the batched form (no counterpart in the paper).
+//
+// For one point set and one theta it times hmle_loglik_batch over a small
+// grid of leaf sizes (the tile of the leaf sweep: dense blocks are b x b,
+// every step of the sweep handles one leaf) and concurrencies (evaluations
+// in flight, each on its own streams and captured graph), and returns the
+// pair with the most evaluations per second.  It uses only the public C ABI.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstring>
+#include <vector>
+
+#include "../../include/hmle.h"
+
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+extern "C" hmle_status hmle_autotune(hmle_ctx *ctx, const double *locs, int64_t n, int32_t d,
+                                     const hmle_opts *base, const hmle_theta *theta,
+                                     const double *Z, int32_t max_concurrency,
+                                     hmle_tune_result *best, hmle_tune_result *trials,
+                                     int32_t max_trials, int32_t *ntrials) {
+  if (!ctx || !locs || !base || !theta || !Z || !best || n <= 0) return HMLE_ERR_INVALID_ARG;
+  if (max_concurrency <= 0) max_concurrency = 16;
+  if (max_concurrency > 64) max_concurrency = 64;
+  const int32_t leaves[] = {32, 64, 128};
+  std::memset(best, 0, sizeof(*best));
+  int32_t nt = 0;
+  hmle_status first = HMLE_OK;
+  for (int32_t leaf : leaves) {
+    if ((int64_t)leaf > n) continue;
+    hmle_opts o = *base;
+    o.leaf_size = leaf;
+    hmle_tree *t = nullptr;
+    hmle_status s = hmle_build_tree(ctx, locs, n, d, &o, &t);
+    if (s != HMLE_OK) { if (first == HMLE_OK) first = s; continue; }
+    double prev = 0.0;
+    for (int32_t c = 1; c <= max_concurrency; c *= 2) {
+      std::vector<hmle_theta> th(c, *theta);
+      std::vector<double> ll(c);
+      std::vector<int32_t> st(c);
+      // warm-up: allocates the c buffers and captures their graphs
+      s = hmle_loglik_batch(ctx, t, th.data(), c, Z, c, ll.data(), st.data());
+      double t0 = now_s();
+      if (s == HMLE_OK) s = hmle_loglik_batch(ctx, t, th.data(), c, Z, c, ll.data(), st.data());
+      const double dt = now_s() - t0;
+      bool ok = (s == HMLE_OK);
+      for (int32_t k = 0; k < c && ok; ++k) ok = (st[k] == HMLE_OK);
+      if (!ok) {   // this candidate fails (e.g. a rank overflow): record it, try the next leaf size
+        if (first == HMLE_OK) first = (s != HMLE_OK ? s : (hmle_status)st[0]);
+        cudaGetLastError();
+        hmle_tune_result r{leaf, c, 0.0, 0};
+        if (trials && nt < max_trials) trials[nt] = r;
+        ++nt;
+        break;
+      }
+      hmle_tune_result r{leaf, c, dt > 0.0 ? c / dt : 0.0, 0};
+      if (trials && nt < max_trials) trials[nt] = r;
+      ++nt;
+      if (r.evals_per_s > best->evals_per_s) *best = r;
+      if (r.evals_per_s < 1.05 * prev) break;   // saturated
+      prev = r.evals_per_s;
+    }
+    hmle_tree_destroy(t);
+  }
+  best->trials = nt;
+  if (ntrials) *ntrials = nt;
+  if (best->leaf_size == 0) return first != HMLE_OK ? first : HMLE_ERR_INVALID_ARG;
+  return HMLE_OK;
+}

@@ -26,10 +26,15 @@ class HmleError(RuntimeError):
         self.status = status
 
 
+HMLE_FP64 = 0
+HMLE_MIXED_FP32 = 1
+
+
 class Opts(C.Structure):
     _fields_ = [("leaf_size", C.c_int32), ("eta", C.c_double), ("aca_eps", C.c_double),
                 ("max_rank", C.c_int32), ("oversample", C.c_int32), ("precision", C.c_int32),
-                ("seed", C.c_uint64), ("leaf_lowrank", C.c_int32)]
+                ("seed", C.c_uint64), ("leaf_lowrank", C.c_int32), ("pcg_tol", C.c_double),
+                ("pcg_max_iter", C.c_int32)]
 
 
 class FitOpts(C.Structure):
@@ -49,11 +54,21 @@ class TreeInfo(C.Structure):
                 ("device_bytes", C.c_int64)]
 
 
+class Task(C.Structure):
+    _fields_ = [("tree", C.c_void_p), ("theta", Theta), ("Z", C.c_void_p)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("leaf_size", C.c_int32), ("concurrency", C.c_int32), ("evals_per_s", C.c_double),
+                ("trials", C.c_int32)]
+
+
 class EvalInfo(C.Structure):
     _fields_ = [("logdet", C.c_double), ("quad", C.c_double), ("loglik", C.c_double),
                 ("max_rank_c", C.c_int32), ("max_rank_l", C.c_int32),
                 ("mean_rank_l", C.c_double), ("status", C.c_int32),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("pcg_iters", C.c_int32),
+                ("pcg_relres", C.c_double)]
 
 
 _LIB = None
@@ -88,6 +103,23 @@ def lib():
             "hmle_profile_select": ([P, C.c_char_p], C.c_int),
             "hmle_simulate": ([P, P, P, P, P], C.c_int),
             "hmle_loglik_batch": ([P, P, P, C.c_int32, P, C.c_int32, P, P], C.c_int),
+            "hmle_solve": ([P, P, P, P], C.c_int),
+            "hmle_loglik_multi": ([P, P, C.c_int32, C.c_int32, P, P], C.c_int),
+            "hmle_theta_to_x": ([P, P], C.c_int),
+            "hmle_x_to_theta": ([P, P], C.c_int),
+            "hmle_features": ([P, P, C.c_int64, C.c_int32, P, P], C.c_int),
+            "hmle_mlp_nparams": ([], C.c_int32),
+            "hmle_mlp_create": ([P, C.c_uint64, P], C.c_int),
+            "hmle_mlp_destroy": ([P], None),
+            "hmle_mlp_set": ([P, P, P, P, P], C.c_int),
+            "hmle_mlp_get": ([P, P, P, P, P], C.c_int),
+            "hmle_mlp_forward": ([P, P, P, C.c_int32, P], C.c_int),
+            "hmle_mlp_grad": ([P, P, P, P, C.c_int32, P, P], C.c_int),
+            "hmle_mlp_adam_step": ([P, P, P, C.c_float], C.c_int),
+            "hmle_mlp_train": ([P, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_uint64,
+                                P, P], C.c_int),
+            "hmle_autotune": ([P, P, C.c_int64, C.c_int32, P, P, P, C.c_int32, P, P, C.c_int32, P],
+                              C.c_int),
             "hmle_matern_eval_noalloc": ([P, P, C.c_int32, P, C.c_int64, P], C.c_int),
             "hmle_profile_read": ([P, P, P, P], C.c_int),
         }
@@ -106,7 +138,10 @@ def exported_symbols():
             "hmle_tree_permutation", "hmle_assemble", "hmle_hmatrix_destroy",
             "hmle_hmatrix_matvec", "hmle_factor", "hmle_factor_destroy", "hmle_loglik",
             "hmle_loglik_eval", "hmle_fit", "hmle_matern_eval", "hmle_profile_select",
-            "hmle_profile_read", "hmle_simulate", "hmle_loglik_batch",
+            "hmle_profile_read", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_loglik_multi", "hmle_autotune",
+            "hmle_theta_to_x", "hmle_x_to_theta", "hmle_features", "hmle_mlp_nparams",
+            "hmle_mlp_create", "hmle_mlp_destroy", "hmle_mlp_set", "hmle_mlp_get",
+            "hmle_mlp_forward", "hmle_mlp_grad", "hmle_mlp_adam_step", "hmle_mlp_train",
             "hmle_matern_eval_noalloc"]
 
 
@@ -133,10 +168,49 @@ class Context:
         if st != HMLE_OK:
             raise HmleError(st, "hmle_ctx_create")
 
+    def last_error(self) -> str:
+        msg = lib().hmle_last_error(self._h)
+        return msg.decode() if msg else ""
+
     def check(self, st, what=""):
         if st != HMLE_OK:
             msg = lib().hmle_last_error(self._h)
             raise HmleError(st, (what + ": " if what else "") + (msg.decode() if msg else ""))
+
+    def loglik_multi(self, tasks, concurrency=8):
+        """Evaluations over several trees at once: tasks = [(tree, theta, Z), ...].
+        Returns (L array, status array)."""
+        tasks = list(tasks)
+        m = len(tasks)
+        keep = []
+        arr = (Task * max(m, 1))()
+        for i, (tree, th, Z) in enumerate(tasks):
+            p, k = _ptr(Z)
+            keep.append(k)
+            arr[i].tree = tree._h
+            arr[i].theta = _theta(th)
+            arr[i].Z = p.value
+        ll = np.empty(m, dtype=np.float64)
+        stt = np.empty(m, dtype=np.int32)
+        self.check(lib().hmle_loglik_multi(self._h, arr, m, int(concurrency), P(ll.ctypes.data),
+                                           P(stt.ctypes.data)), "hmle_loglik_multi")
+        return ll, stt
+
+    def autotune(self, locs, theta, Z, max_concurrency=16, **opts):
+        """hmle_autotune: returns (best dict, list of trial dicts)."""
+        locs = np.ascontiguousarray(locs, dtype=np.float64)
+        n, d = locs.shape
+        o = default_opts(**opts)
+        best = TuneResult()
+        trials = (TuneResult * 64)()
+        nt = C.c_int32()
+        p, keep = _ptr(Z)
+        self.check(lib().hmle_autotune(self._h, P(locs.ctypes.data), n, d, C.byref(o),
+                                       C.byref(_theta(theta)), p, int(max_concurrency),
+                                       C.byref(best), trials, 64, C.byref(nt)), "hmle_autotune")
+        conv = lambda r: {"leaf_size": r.leaf_size, "concurrency": r.concurrency,
+                          "evals_per_s": r.evals_per_s}
+        return conv(best), [conv(trials[i]) for i in range(min(nt.value, 64))]
 
     def close(self):
         if self._h:
@@ -343,14 +417,21 @@ class Factor:
         ctx.check(lib().hmle_factor(ctx._h, hm._h, p, C.byref(self._h)), "hmle_factor")
 
     def loglik(self, Z=None):
-        """(L, log|C~|, Z^T C~^{-1} Z)."""
-        Z = self._Z if Z is None else Z
-        p, keep = _ptr(Z)
+        """(L, log|C~|, Z^T C~^{-1} Z); Z = None uses the solve fused into the factor."""
+        p, keep = _ptr(Z) if Z is not None else (None, None)
         ll, ld, q = C.c_double(), C.c_double(), C.c_double()
         ctx = self.hm.tree.ctx
         ctx.check(lib().hmle_loglik(ctx._h, self._h, p, C.byref(ll), C.byref(ld), C.byref(q)),
                   "hmle_loglik")
         return ll.value, ld.value, q.value
+
+    def solve(self, Z) -> np.ndarray:
+        """X = C~^{-1} Z (forward and backward sweeps through the factor)."""
+        Z = np.ascontiguousarray(Z, dtype=np.float64)
+        X = np.empty_like(Z)
+        ctx = self.hm.tree.ctx
+        ctx.check(lib().hmle_solve(ctx._h, self._h, P(Z.ctypes.data), P(X.ctypes.data)), "hmle_solve")
+        return X
 
     def close(self):
         if self._h:

@@ -1,0 +1,207 @@
+"""a16: the learned start of the MLE (Sec. 7 suggests precomputing the
+optimiser's initial guess).
+
+Thin driver over the C ABI (every numerical step runs in the library's
+kernels): field statistics (``hmle_features``), the perceptron
+(``hmle_mlp_*``), training data simulated by the H-Cholesky factor itself
+(``hmle_simulate``, Sec. 2 factorisation used as Z = L~ xi), and the
+comparison against the default start.
+
+The perceptron predicts the transformed coordinates of Sec. 5 (mu) and log
+initial simplex steps (s).  ``LearnedStart.start`` turns them into a theta
+and steps for ``hmle_fit``; if the prediction is not finite or leaves the
+admissible range it falls back to the default start (theta0 =
+(0.2, 1.0, 0.5, 0.05), unit steps).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import time
+
+import numpy as np
+
+from . import hmle, synth
+from .hmle import P, lib
+
+NF = 35
+DEFAULT_THETA0 = (0.2, 1.0, 0.5, 0.05)
+
+# prior box of the simulated training fields (theta order ell, nu, sigma2, tau2)
+PRIOR = {"ell": (0.02, 0.3), "nu": (0.3, 2.0), "sigma2": (0.25, 4.0), "tau2": (1e-3, 0.1)}
+
+
+def theta_to_x(theta):
+    x = (C.c_double * 4)()
+    st = lib().hmle_theta_to_x(C.byref(hmle._theta(theta)), x)
+    if st != 0:
+        raise hmle.HmleError(st, "hmle_theta_to_x")
+    return np.array(list(x))
+
+
+def x_to_theta(x):
+    xa = (C.c_double * 4)(*[float(v) for v in x])
+    th = hmle.Theta()
+    st = lib().hmle_x_to_theta(xa, C.byref(th))
+    if st != 0:
+        return None
+    return (th.ell, th.nu, th.sigma2, th.tau2)
+
+
+def features(ctx: hmle.Context, locs, Z) -> np.ndarray:
+    locs = np.ascontiguousarray(locs, dtype=np.float64)
+    n, d = locs.shape
+    f = np.zeros(NF, dtype=np.float32)
+    pz, keep = hmle._ptr(np.ascontiguousarray(Z, dtype=np.float64))
+    ctx.check(lib().hmle_features(ctx._h, P(locs.ctypes.data), n, d, pz, P(f.ctypes.data)),
+              "hmle_features")
+    return f
+
+
+class LearnedStart:
+    """The perceptron of the learned start (owns an hmle_mlp)."""
+
+    def __init__(self, ctx: hmle.Context, seed: int = 1):
+        self.ctx = ctx
+        self._h = P()
+        ctx.check(lib().hmle_mlp_create(ctx._h, C.c_uint64(seed), C.byref(self._h)),
+                  "hmle_mlp_create")
+        self.nparams = lib().hmle_mlp_nparams()
+
+    def close(self):
+        if self._h:
+            lib().hmle_mlp_destroy(self._h)
+            self._h = P()
+
+    def __del__(self):
+        import sys
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get(self):
+        p = np.zeros(self.nparams, dtype=np.float32)
+        mu = np.zeros(NF, dtype=np.float32)
+        sd = np.zeros(NF, dtype=np.float32)
+        self.ctx.check(lib().hmle_mlp_get(self.ctx._h, self._h, P(p.ctypes.data), P(mu.ctypes.data),
+                                          P(sd.ctypes.data)), "hmle_mlp_get")
+        return p, mu, sd
+
+    def set(self, params=None, mu=None, sd=None):
+        def ptr(a):
+            if a is None:
+                return None, None
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            return P(a.ctypes.data), a
+        (pp, k1), (pm, k2), (ps, k3) = ptr(params), ptr(mu), ptr(sd)
+        self.ctx.check(lib().hmle_mlp_set(self.ctx._h, self._h, pp, pm, ps), "hmle_mlp_set")
+
+    def forward(self, feats) -> np.ndarray:
+        F = np.ascontiguousarray(np.atleast_2d(feats), dtype=np.float32)
+        out = np.zeros((F.shape[0], 8), dtype=np.float32)
+        self.ctx.check(lib().hmle_mlp_forward(self.ctx._h, self._h, P(F.ctypes.data), F.shape[0],
+                                              P(out.ctypes.data)), "hmle_mlp_forward")
+        return out
+
+    def grad(self, feats, targets):
+        F = np.ascontiguousarray(feats, dtype=np.float32)
+        T = np.ascontiguousarray(targets, dtype=np.float32)
+        g = np.zeros(self.nparams, dtype=np.float32)
+        loss = C.c_float()
+        self.ctx.check(lib().hmle_mlp_grad(self.ctx._h, self._h, P(F.ctypes.data), P(T.ctypes.data),
+                                           F.shape[0], P(g.ctypes.data), C.byref(loss)),
+                       "hmle_mlp_grad")
+        return g, loss.value
+
+    def adam_step(self, grad, lr):
+        g = np.ascontiguousarray(grad, dtype=np.float32)
+        self.ctx.check(lib().hmle_mlp_adam_step(self.ctx._h, self._h, P(g.ctypes.data),
+                                                C.c_float(lr)), "hmle_mlp_adam_step")
+
+    def train(self, feats, targets, epochs=200, batch=64, lr=3e-3, seed=7):
+        F = np.ascontiguousarray(feats, dtype=np.float32)
+        T = np.ascontiguousarray(targets, dtype=np.float32)
+        l0, l1 = C.c_float(), C.c_float()
+        self.ctx.check(lib().hmle_mlp_train(self.ctx._h, self._h, P(F.ctypes.data), P(T.ctypes.data),
+                                            F.shape[0], epochs, batch, C.c_float(lr),
+                                            C.c_uint64(seed), C.byref(l0), C.byref(l1)),
+                       "hmle_mlp_train")
+        return l0.value, l1.value
+
+    def start(self, locs, Z):
+        """(theta0, steps, used_fallback) for hmle_fit on this field."""
+        y = self.forward(features(self.ctx, locs, Z))[0].astype(np.float64)
+        mu, s = y[:4], y[4:]
+        th = x_to_theta(mu) if np.all(np.isfinite(y)) else None
+        if th is None or not (1e-4 <= th[0] <= 1e3 and 0.05 <= th[1] <= 20.0):
+            return DEFAULT_THETA0, [1.0, 1.0, 1.0, 1.0], True
+        steps = [float(min(2.0, max(0.05, math.exp(v)))) for v in s]
+        return th, steps, False
+
+
+def draw_theta(seed: int, i: int):
+    """theta of training field i: log-uniform ell, sigma2, tau2; uniform nu."""
+    u = synth.uniform(seed * 1_000_003 + i, 4)
+    lo, hi = PRIOR["ell"]
+    ell = lo * (hi / lo) ** u[0]
+    nu = PRIOR["nu"][0] + (PRIOR["nu"][1] - PRIOR["nu"][0]) * u[1]
+    lo, hi = PRIOR["sigma2"]
+    s2 = lo * (hi / lo) ** u[2]
+    lo, hi = PRIOR["tau2"]
+    t2 = lo * (hi / lo) ** u[3]
+    return (float(ell), float(nu), float(s2), float(t2))
+
+
+def field(ctx, seed: int, i: int, n: int):
+    """Field i of a seeded family: point set (uniform or blob mixture,
+    alternating), theta from the prior, Z = L~ xi simulated by the
+    H-Cholesky factor at eps 1e-9."""
+    th = draw_theta(seed, i)
+    if i % 2 == 0:
+        locs = synth.locations_uniform(n, 2, seed=seed * 7919 + i)
+    else:
+        locs = synth.locations_blobs(n, 2, 0.3, 8, 0.03, seed=seed * 7919 + i)
+    tree = hmle.Tree(ctx, locs, leaf_size=32, aca_eps=1e-9, max_rank=48, oversample=16)
+    Z = tree.simulate(th, synth.normal(seed * 104729 + i, n))
+    tree.close()
+    return locs, Z, th
+
+
+def training_set(ctx, count: int, seed: int = 11, n_range=(600, 2400)):
+    """count simulated fields -> (features count x 35, targets count x 4)."""
+    F = np.zeros((count, NF), dtype=np.float32)
+    T = np.zeros((count, 4), dtype=np.float32)
+    for i in range(count):
+        u = synth.uniform(seed * 31337 + i, 1)[0]
+        n = int(n_range[0] + (n_range[1] - n_range[0]) * u)
+        locs, Z, th = field(ctx, seed, i, n)
+        F[i] = features(ctx, locs, Z)
+        T[i] = theta_to_x(th)
+    return F, T
+
+
+def compare_starts(ctx, model: LearnedStart, fields, **fit_kw):
+    """Fit every (locs, Z, theta) field from the default start and from the
+    learned start.  Returns per-field records and totals."""
+    rows = []
+    for locs, Z, th in fields:
+        tree = hmle.Tree(ctx, locs, leaf_size=32, aca_eps=1e-8, max_rank=48, oversample=16)
+        t0 = time.time()
+        th_d, ll_d, it_d, ev_d, st_d = tree.fit(Z, DEFAULT_THETA0, **fit_kw)
+        t_d = time.time() - t0
+        th0, steps, fb = model.start(locs, Z)
+        t0 = time.time()
+        th_l, ll_l, it_l, ev_l, st_l = tree.fit(Z, th0, step=steps, **fit_kw)
+        t_l = time.time() - t0
+        tree.close()
+        rows.append({"n": int(locs.shape[0]), "theta": th, "fallback": fb,
+                     "default": {"theta": th_d, "L": ll_d, "iters": it_d, "evals": ev_d,
+                                 "status": st_d, "s": t_d},
+                     "learned": {"theta0": th0, "theta": th_l, "L": ll_l, "iters": it_l,
+                                 "evals": ev_l, "status": st_l, "s": t_l}})
+    tot = {k: {f: sum(r[k][f] for r in rows) for f in ("iters", "evals", "s")}
+           for k in ("default", "learned")}
+    return rows, tot

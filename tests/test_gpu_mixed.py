@@ -1,0 +1,84 @@
+"""Mixed form (FP32 Schur-update products, FP64 recompression / POTRF /
+log-det, quadratic form by PCG) through the C ABI, against the CPU oracle.
+
+Stated bounds of the mixed form: the quadratic form is won back by PCG to
+the FP64 bound |dq| / n <= 1e-6; the log-determinant carries the FP32
+rounding of the Schur complements, |d logdet| / n <= 1e-5, and so does L.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_07146_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+MIXED = 1
+
+
+@pytest.fixture(scope="module")
+def ctx(hmle_lib):
+    from paper_2104_07146_gb300 import hmle
+    return hmle.Context()
+
+
+def _tree(ctx, locs, **kw):
+    from paper_2104_07146_gb300 import hmle
+    return hmle.Tree(ctx, locs, **kw)
+
+
+def _mixed_parity(ctx, locs, theta, leaf, eps, zseed, field=True, **kw):
+    n = locs.shape[0]
+    Z = synth.normal(zseed, n)
+    if field:
+        Z = oracle.simulate(locs, theta, Z)
+    t = _tree(ctx, locs, leaf_size=leaf, aca_eps=eps, precision=MIXED, **kw)
+    ll, info = t.loglik(theta, Z)
+    ref, ld, q = oracle.loglik_dense(locs, Z, theta)
+    assert info.pcg_iters >= 1 and info.pcg_relres <= 1e-10, (info.pcg_iters, info.pcg_relres)
+    assert abs(info.quad - q) / n <= 1e-6, (info.quad, q)
+    assert abs(info.logdet - ld) / n <= 1e-5, (info.logdet, ld)
+    assert abs(ll - ref) / n <= 1e-5, (ll, ref)
+    return info
+
+
+def test_mixed_small_config(ctx):
+    locs = synth.locations_uniform(2000, 2, seed=1000)
+    _mixed_parity(ctx, locs, (0.1, 0.5, 1.0, 0.01), 32, 1e-8, 1001)
+
+
+def test_mixed_white_noise_ragged(ctx):
+    # white-noise Z on a smooth field (q ~ 43 n): the FP64 form needs its
+    # factor truncated at 1e-10 for this quadratic form; the mixed factor
+    # stays at its 1e-7 floor and the PCG on the ACA operator (eps 1e-10)
+    # carries the quadratic form
+    locs = synth.locations_uniform(3001, 2, seed=21)
+    _mixed_parity(ctx, locs, (0.15, 1.3, 0.8, 0.02), 32, 1e-10, 22, field=False,
+                  max_rank=48, oversample=16)
+
+
+@pytest.mark.parametrize("nu,eps", [(0.5, 1e-6), (1.5, 1e-7)])
+def test_mixed_blob_mixture_leaf64(ctx, nu, eps):
+    locs = synth.locations_blobs(4096, 2, 0.3, 8, 0.03, seed=23)
+    _mixed_parity(ctx, locs, (0.05, nu, 1.0, 1e-3), 64, eps, 24, max_rank=48, oversample=16)
+
+
+def test_mixed_batch_matches_single(ctx):
+    locs = synth.locations_uniform(2500, 2, seed=61)
+    Z = synth.normal(62, 2500)
+    t = _tree(ctx, locs, leaf_size=32, aca_eps=1e-8, precision=MIXED)
+    thetas = [(0.1, 0.5, 1.0, 0.01), (0.12, 0.6, 0.9, 0.02), (0.08, 0.7, 1.1, 0.01)]
+    ll, st = t.loglik_batch(thetas, Z, concurrency=3)
+    assert all(s == 0 for s in st), list(st)
+    for th, v in zip(thetas, ll):
+        assert v == t.loglik(th, Z)[0]
+
+
+def test_pcg_not_converged_is_reported(ctx):
+    from paper_2104_07146_gb300 import hmle
+    locs = synth.locations_uniform(800, 2, seed=63)
+    t = _tree(ctx, locs, leaf_size=32, aca_eps=1e-8, precision=MIXED, pcg_tol=1e-30,
+              pcg_max_iter=1)
+    with pytest.raises(hmle.HmleError) as e:
+        t.loglik((0.1, 0.5, 1.0, 0.01), synth.normal(64, 800))
+    assert e.value.status == 7

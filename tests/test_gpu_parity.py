@@ -92,6 +92,13 @@ def test_loglik_smooth_white_noise_tight_eps(ctx):
     _parity(ctx, locs, (0.15, 1.3, 0.8, 0.02), 32, 1e-10, 22, max_rank=48, oversample=16)
 
 
+def test_loglik_leaf128(ctx):
+    # the largest leaf (128): dense blocks and shared-memory tiles at their
+    # maximum size, 3001 points (ragged leaves)
+    locs = synth.locations_uniform(3001, 2, seed=25)
+    _parity(ctx, locs, (0.1, 0.5, 1.0, 0.01), 128, 1e-8, 26, field=True)
+
+
 @pytest.mark.parametrize("nu,eps", [(0.5, 1e-6), (0.8, 1e-6), (1.5, 1e-7), (2.5, 1e-8)])
 def test_loglik_blob_mixture_leaf64(ctx, nu, eps):
     # the medium workload's geometry and theta at n = 4096, Z = L xi.  The
@@ -115,8 +122,32 @@ def test_factor_api_matches_fused_eval(ctx):
     t = _tree(ctx, locs, leaf_size=32, aca_eps=1e-8)
     ll1, info = t.loglik(th, Z)
     f = t.assemble(th).factor(Z)
-    ll2, ld, q = f.loglik(Z)
+    ll2, ld, q = f.loglik(None)                      # the fused solve
     assert ll1 == ll2 and ld == info.logdet and q == info.quad
+    ll3, ld3, q3 = f.loglik(Z)                       # a separate solve sweep
+    assert ld3 == ld and abs(q3 - q) <= 1e-12 * q
+    Z2 = synth.normal(29, 1500)                      # a new right-hand side
+    ll4, _, q4 = f.loglik(Z2)
+    assert abs(ll4 - t.loglik(th, Z2)[0]) <= 1e-9 * abs(ll4)
+
+
+def test_solve_matches_dense(ctx):
+    # X = C~^{-1} Z through the forward and backward sweeps against the dense
+    # FP64 solve of the oracle's C; Z^T X must equal the quadratic form of
+    # the forward solve, |L~^{-1} P Z|^2.
+    n = 1800                                   # several leaves of 32 and a ragged tail
+    locs = synth.locations_uniform(n, 2, seed=51)
+    th = (0.1, 0.8, 1.0, 0.02)
+    Z = synth.normal(52, n)
+    t = _tree(ctx, locs, leaf_size=32, aca_eps=1e-10, max_rank=48, oversample=16)
+    f = t.assemble(th).factor(Z)
+    X = f.solve(Z)
+    Xd = np.linalg.solve(oracle.matern_matrix(locs, th), Z)
+    assert np.linalg.norm(X - Xd) <= 1e-6 * np.linalg.norm(Xd)
+    _, _, q = f.loglik(None)
+    assert abs(Z @ X - q) <= 1e-10 * q
+    X2 = f.solve(synth.normal(53, n))           # a second right-hand side, same factor
+    assert np.isfinite(X2).all()
 
 
 def test_non_spd_is_reported(ctx):
@@ -221,6 +252,35 @@ def test_batched_evaluations_match_single(ctx):
         assert st[k] == 0
         assert ll[k] == t.loglik(th, Z)[0]
     assert st[-1] == 2 and ll[-1] == -math.inf       # sigma2 = tau2 = 0: NOT_SPD
+
+
+def test_multi_instance_tasks_match_single(ctx):
+    # tasks over two trees of uneven n (1500 ragged, 2600) and several thetas,
+    # in waves of 3: each result equals its one-at-a-time evaluation
+    la = synth.locations_uniform(1500, 2, seed=71)
+    lb = synth.locations_blobs(2600, 2, 0.3, 8, 0.03, seed=72)
+    za, zb = synth.normal(73, 1500), synth.normal(74, 2600)
+    ta = _tree(ctx, la, leaf_size=32, aca_eps=1e-8)
+    tb = _tree(ctx, lb, leaf_size=64, aca_eps=1e-7)
+    tasks = [(ta, (0.1, 0.5, 1.0, 0.01), za), (tb, (0.05, 0.5, 1.0, 1e-3), zb),
+             (ta, (0.15, 0.9, 1.1, 0.02), za), (tb, (0.07, 0.8, 0.9, 1e-3), zb),
+             (tb, (0.04, 0.5, 1.2, 2e-3), zb), (ta, (0.1, 0.5, 0.0, 0.0), za)]
+    ll, st = ctx.loglik_multi(tasks, concurrency=3)
+    for k, (t, th, z) in enumerate(tasks[:-1]):
+        assert st[k] == 0
+        assert ll[k] == t.loglik(th, z)[0]
+    assert st[-1] == 2 and ll[-1] == -math.inf
+
+
+def test_autotune_picks_a_timed_trial(ctx):
+    locs = synth.locations_uniform(3000, 2, seed=75)
+    Z = synth.normal(76, 3000)
+    best, trials = ctx.autotune(locs, (0.1, 0.5, 1.0, 0.01), Z, max_concurrency=4, aca_eps=1e-8)
+    assert trials and best in trials
+    assert best["evals_per_s"] == max(t["evals_per_s"] for t in trials) > 0
+    assert all(t["evals_per_s"] > 0 for t in trials)      # no candidate failed
+    assert {t["leaf_size"] for t in trials} <= {32, 64, 128}
+    assert all(t["concurrency"] in (1, 2, 4) for t in trials)
 
 
 @pytest.mark.slow
