@@ -236,6 +236,13 @@ def run_gpu(args):
                              "in one evaluation bracketed by CUDA events on its launching "
                              "stream, " + dom["mode"],
                      **({"graph_note": dom["graph_note"]} if "graph_note" in dom else {})},
+        "step_roofline": {
+            "bound": "alu", "flops_per_eval": info.flops,
+            "achieved": info.flops * value / ws / 1e9 if info.flops else None,
+            "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": (info.flops * value / ws / 1e9 / FP64_PEAK_GFLOPS) if info.flops else None,
+            "note": "whole batched step on one GPU: algorithmic flops of one evaluation (plan "
+                    "x ranks) x evaluations/s, against the FP64 ALU peak"},
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
@@ -321,7 +328,7 @@ def main():
     ap.add_argument("--batch", type=int, default=16,
                     help="concurrent theta evaluations per step (hmle_loglik_batch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--roofline-kernel", default="k_tsqr_final",
+    ap.add_argument("--roofline-kernel", default="k_rows",
                     help="sweep kernel whose launches are timed for the roofline line")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -139,6 +139,9 @@ typedef struct {
   int64_t kernel_launches; /* CUDA kernels this evaluation launched */
   int32_t pcg_iters;    /* mixed form: PCG iterations (0 in FP64) */
   double pcg_relres;    /* mixed form: final |r| / |Z| */
+  double flops;         /* algorithmic flops of the factorisation sweep (the plan's
+                           products at this evaluation's ranks; FP32 ones included
+                           in the mixed form) */
 } hmle_eval_info;
 
 typedef struct hmle_ctx hmle_ctx;

@@ -6,8 +6,9 @@
 //    kernel (partial pivoting: the next row pivot is the largest entry of the
 //    last column outside the rows already used).  Stops when
 //    |u_k| |v_k| <= eps |S_k|_F, with |S_k|_F^2 updated from the new cross
-//    and its inner products with the previous ones.  Dense leaf blocks are
-//    not stored: the factorisation generates their entries on the fly.
+//    and its inner products with the previous ones.
+//  * k_assemble_dense: the dense near-field blocks of C, stored per theta
+//    (read by the factorisation's dense targets and by the H-matvec).
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -191,6 +192,29 @@ void launch_matern_eval(cudaStream_t st, const double *tab, const double *x, int
 }
 void launch_aca(cudaStream_t st, const AsmArgs &A, int n_lr) {
   if (n_lr > 0) k_aca<<<n_lr, 256, 0, st>>>(A);
+}
+
+// a3: the dense near field.  One CTA per dense block (all leaf-level blocks
+// of the lower triangle kept dense, the diagonal ones included, both
+// triangles of those): C(i, j) = sigma^2 M_nu(|s_i - s_j| / ell) + tau^2 [i == j]
+// into the block's b x b slot (ld b, column-major: consecutive threads write
+// consecutive rows), padding rows and columns zero.
+__global__ void k_assemble_dense(AsmArgs A, const int32_t *__restrict__ dense_ids, int b,
+                                 double *__restrict__ Cd) {
+  const BlockDesc B = A.blocks[dense_ids[blockIdx.x]];
+  const int m = B.rend - B.rbeg, p = B.cend - B.cbeg;
+  double *out = Cd + B.off_d;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e % b, j = e / b;
+    out[e] = (i < m && j < p) ? cov_entry(A.tab, A.xyz, A.n, A.d, B.rbeg + i, B.cbeg + j, A.inv_ell,
+                                          A.sigma2, A.tau2)
+                              : 0.0;
+  }
+}
+
+void launch_assemble_dense(cudaStream_t st, const AsmArgs &A, const int32_t *dense_ids, int nd,
+                           int b, double *Cd) {
+  if (nd > 0) k_assemble_dense<<<nd, 256, 0, st>>>(A, dense_ids, b, Cd);
 }
 
 }  // namespace hmle

@@ -85,6 +85,7 @@ struct hmle_hmatrix {
   hmle_theta th{};
   double *tab = nullptr;
   double *uc = nullptr;
+  double *Cd = nullptr;       // dense near-field blocks of C (b x b at each dense block's off_d)
   int32_t *rank_c = nullptr;
   double *cnorm = nullptr;
   ThetaDev *thd = nullptr;
@@ -110,6 +111,7 @@ struct hmle_hfactor {
   double mean_rank_l = 0.0;
   bool owned = true;
   double *pcg = nullptr;      // mixed form: right-hand side + PCG workspace
+  double *pcg_host = nullptr; // pinned scalars read back by the PCG
   cudaGraphExec_t pcg_init = nullptr, pcg_iter = nullptr;   // its captured sequences
   int pcg_iters = 0;
   double pcg_relres = 0.0;
@@ -187,11 +189,12 @@ bool theta_ok(const hmle_theta *t) {
 void free_hm(cudaStream_t st, hmle_hmatrix *h) {
   if (h->tab) cudaFreeAsync(h->tab, st);
   if (h->uc) cudaFreeAsync(h->uc, st);
+  if (h->Cd) cudaFreeAsync(h->Cd, st);
   if (h->rank_c) cudaFreeAsync(h->rank_c, st);
   if (h->cnorm) cudaFreeAsync(h->cnorm, st);
   if (h->thd) cudaFreeAsync(h->thd, st);
   if (h->flags) cudaFreeAsync(h->flags, st);
-  h->tab = nullptr; h->uc = nullptr; h->rank_c = nullptr; h->cnorm = nullptr;
+  h->tab = nullptr; h->uc = nullptr; h->Cd = nullptr; h->rank_c = nullptr; h->cnorm = nullptr;
   h->thd = nullptr; h->flags = nullptr;
 }
 
@@ -200,6 +203,8 @@ void free_f(cudaStream_t st, hmle_hfactor *f) {
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, st);
   f->D = f->U = f->W = f->ws = f->pcg = nullptr;
+  if (f->pcg_host) cudaFreeHost(f->pcg_host);
+  f->pcg_host = nullptr;
   if (f->pcg_init) cudaGraphExecDestroy(f->pcg_init);
   if (f->pcg_iter) cudaGraphExecDestroy(f->pcg_iter);
   f->pcg_init = f->pcg_iter = nullptr;
@@ -227,6 +232,7 @@ hmle_status alloc_hm(hmle_ctx *ctx, const hmle_tree *t, hmle_hmatrix *h) {
   h->tree = t;
   CK(cudaMallocAsync(&h->tab, sizeof(double) * kTableWords, st), "alloc table");
   CK(cudaMallocAsync(&h->uc, sizeof(double) * std::max<int64_t>(P.uc_words, 1), st), "alloc C factors");
+  CK(cudaMallocAsync(&h->Cd, sizeof(double) * std::max<int64_t>(P.dense_words, 1), st), "alloc dense near field");
   CK(cudaMallocAsync(&h->rank_c, sizeof(int32_t) * std::max<size_t>(P.blocks.size(), 1), st), "alloc ranks");
   CK(cudaMallocAsync(&h->cnorm, sizeof(double) * std::max<size_t>(P.blocks.size(), 1), st), "alloc norms");
   CK(cudaMemsetAsync(h->cnorm, 0, sizeof(double) * std::max<size_t>(P.blocks.size(), 1), st), "memset");
@@ -278,6 +284,7 @@ hmle_status do_assemble(hmle_ctx *ctx, const hmle_tree *t, const hmle_theta *th,
   A.cnorm = h->cnorm;
   A.flags = h->flags;
   launch_aca(st, A, (int)t->lr_ids.size());
+  launch_assemble_dense(st, A, t->dp.dense_ids, (int)t->dense_ids.size(), P.b, h->Cd);
   CK(cudaGetLastError(), "assemble launch");
   return HMLE_OK;
 }
@@ -295,7 +302,7 @@ FactorArgs make_fargs(const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f
   F.brow_ent = d.brow_ent; F.dns = d.dns; F.dpairs = d.dpairs; F.wpan = d.wpan;
   F.dpair_tr = d.dpair_tr; F.dpair_tc = d.dpair_tc;
   F.hts = d.hts; F.urows = d.urows; F.uents = d.uents; F.leaf_beg = d.leaf_beg;
-  F.D = f->D; F.uc = h->uc; F.rank_c = h->rank_c; F.cnorm = h->cnorm; F.U = f->U; F.W = f->W; F.ws = f->ws;
+  F.D = f->D; F.uc = h->uc; F.Cd = h->Cd; F.rank_c = h->rank_c; F.cnorm = h->cnorm; F.U = f->U; F.W = f->W; F.ws = f->ws;
   F.rank_l = f->rank_l; F.kept = f->kept; F.logdet_parts = f->ldp; F.flags = f->flags;
   F.xyz = t->T.xyz; F.n = t->n; F.d = t->d; F.tab = h->tab; F.th = h->thd;
   F.eps = t->opts.aca_eps; F.seed = t->opts.seed;
@@ -314,8 +321,8 @@ FactorArgs make_fargs(const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f
 // the FP32 rounding of the factor; it is replaced by b^T x with C x = b solved
 // by PCG (FP64 operator, the mixed factor as preconditioner).  zdev: Z in the
 // caller's order, on the device.
-hmle_status mixed_quad(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f,
-                       const double *zdev) {
+hmle_status mixed_prepare(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f,
+                          const double *zdev, PcgRun &R) {
   cudaStream_t st = ctx->st;
   const Plan &P = t->plan;
   const int nlr = (int)t->lr_ids.size();
@@ -326,34 +333,57 @@ hmle_status mixed_quad(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h,
     cudaError_t e = cudaMallocAsync(&f->pcg, sizeof(double) * words, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pcg workspace");
   }
+  if (!f->pcg_host) {
+    cudaError_t e = cudaMallocHost(&f->pcg_host, 4 * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pcg host scalars");
+  }
   double *b = f->pcg;
   launch_permute_in(st, zdev, t->T.perm, t->n, b);
   AsmArgs A{};
   A.blocks = t->dp.blocks; A.lr_ids = t->dp.lr_ids; A.xyz = t->T.xyz; A.n = t->n; A.d = t->d;
   A.tab = h->tab; A.inv_ell = 1.0 / h->th.ell; A.sigma2 = h->th.sigma2; A.tau2 = h->th.tau2;
   A.kc = P.kc; A.uc = h->uc; A.rank_c = h->rank_c; A.cnorm = h->cnorm; A.flags = h->flags;
-  A.thd = h->thd;
-  CmvLists L{P.nleaf, t->dp.leaf_beg, t->dp.mv_row0, t->dp.mv_blocks, t->dp.mvt_row0,
-             t->dp.mvt_blocks, t->dp.lr_slot};
+  A.thd = h->thd; A.Cd = h->Cd; A.b = P.b;
   FactorArgs Fs = make_fargs(t, h, f);
   Fs.hts = t->dp.hts_rhs;
   Fs.urows = t->dp.urows_rhs;
   Fs.uents = t->dp.uents_rhs;
-  double q = 0.0, rel = 0.0;
-  int it = 0;
   const PanelDesc &rp = P.panels[P.rhs_panel];
-  cudaError_t e = pcg_quad(st, A, nlr, L, Fs, P, t->dp.wpan_rhs, t->dp.bh_blocks, t->dp.bupd,
-                           t->dp.bents, f->W + rp.off, b, t->n, t->opts.pcg_tol,
-                           t->opts.pcg_max_iter, f->pcg + t->n, &q, &it, &rel,
-                           t->graphs ? &f->pcg_init : nullptr, t->graphs ? &f->pcg_iter : nullptr);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "pcg");
-  f->quad = q;
-  f->pcg_iters = it;
-  f->pcg_relres = rel;
+  R = PcgRun{};
+  R.st = st; R.A = A; R.n_lr = nlr;
+  R.L = CmvLists{P.nleaf, t->dp.leaf_beg, t->dp.mv_row0, t->dp.mv_blocks, t->dp.mvt_row0,
+                 t->dp.mvt_blocks, t->dp.lr_slot};
+  R.Fs = Fs; R.PL = &P; R.wpan_rhs = t->dp.wpan_rhs; R.bh_blocks = t->dp.bh_blocks;
+  R.bupd = t->dp.bupd; R.bents = t->dp.bents; R.panel = f->W + rp.off; R.b = b; R.n = t->n;
+  R.tol = t->opts.pcg_tol; R.maxit = t->opts.pcg_max_iter; R.pool = f->pcg + t->n;
+  R.host = f->pcg_host;
+  R.g_init = t->graphs ? &f->pcg_init : nullptr;
+  R.g_iter = t->graphs ? &f->pcg_iter : nullptr;
+  return HMLE_OK;
+}
+
+hmle_status mixed_result(hmle_ctx *ctx, const hmle_tree *t, hmle_hfactor *f, const PcgRun &R) {
+  f->quad = R.q;
+  f->pcg_iters = R.it;
+  f->pcg_relres = R.rel;
   f->has_rhs = true;
-  if (!(rel <= t->opts.pcg_tol) || !std::isfinite(q))
+  if (!(R.rel <= t->opts.pcg_tol) || !std::isfinite(R.q))
     return fail(ctx, HMLE_ERR_NOT_CONVERGED, "PCG: relative residual above pcg_tol after pcg_max_iter");
   return HMLE_OK;
+}
+
+// a14: in the mixed form the quadratic form of the fused forward solve carries
+// the FP32 rounding of the factor; it is replaced by b^T x with C x = b solved
+// by PCG (FP64 operator, the mixed factor as preconditioner).  zdev: Z in the
+// caller's order, on the device.
+hmle_status mixed_quad(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f,
+                       const double *zdev) {
+  PcgRun R;
+  hmle_status s = mixed_prepare(ctx, t, h, f, zdev, R);
+  if (s != HMLE_OK) return s;
+  cudaError_t e = pcg_quad(R);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "pcg");
+  return mixed_result(ctx, t, f, R);
 }
 
 // The launch sequence of one factorisation (sweep + finalize) on stream st.
@@ -790,7 +820,7 @@ hmle_status hmle_hmatrix_matvec(hmle_ctx *ctx, const hmle_hmatrix *h, const doub
   A.blocks = t->dp.blocks; A.lr_ids = t->dp.lr_ids; A.xyz = t->T.xyz; A.n = n; A.d = t->d;
   A.tab = h->tab; A.inv_ell = 1.0 / h->th.ell; A.sigma2 = h->th.sigma2; A.tau2 = h->th.tau2;
   A.kc = P.kc; A.uc = h->uc; A.rank_c = h->rank_c; A.cnorm = h->cnorm; A.flags = h->flags;
-  A.thd = h->thd;
+  A.thd = h->thd; A.Cd = h->Cd; A.b = P.b;
   CmvLists L{P.nleaf, t->dp.leaf_beg, t->dp.mv_row0, t->dp.mv_blocks, t->dp.mvt_row0,
              t->dp.mvt_blocks, t->dp.lr_slot};
   launch_cmatvec(st, A, nlr, L, xp, tb, yp);
@@ -954,6 +984,23 @@ hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tc, const hmle_thet
     info->kernel_launches = w.F.launches;
     info->pcg_iters = w.F.pcg_iters;
     info->pcg_relres = w.F.pcg_relres;
+    info->flops = 0.0;
+    if (s == HMLE_OK) {   // algorithmic flops of the sweep, from the plan and this evaluation's ranks
+      const Plan &P = t->plan;
+      std::vector<int32_t> rc(P.blocks.size()), rl(P.blocks.size()), kp(std::max<size_t>(P.lrt.size(), 1));
+      double jf = 0.0;
+      cudaStream_t st = ctx->st;
+      cudaError_t e = cudaMemcpyAsync(rc.data(), w.H.rank_c, sizeof(int32_t) * rc.size(), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(rl.data(), w.F.rank_l, sizeof(int32_t) * rl.size(), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(kp.data(), w.F.kept, sizeof(int32_t) * kp.size(), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&jf, ctx->d_jacobi, sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e == cudaSuccess)
+        for (int k = 0; k < KK_COUNT; ++k)
+          info->flops += tally_flops(P, k, rc, rl, kp, t->opts.oversample, jf);
+      else
+        cudaGetLastError();
+    }
     double mr = 0;
     int mx = 0;
     if (rank_stats(ctx, t, w.H.rank_c, &mx, &mr) == HMLE_OK) info->max_rank_c = mx;
@@ -1042,14 +1089,54 @@ hmle_status run_waves(hmle_ctx *ctx, const std::vector<TaskRef> &tasks, int W, c
       if (s != HMLE_OK) { if (status) status[i0 + k] = s; if (first == HMLE_OK) { first = s; ctx->err = wc.err; } }
       else if (status) status[i0 + k] = HMLE_OK;
     }
-    // collect
+    // collect the factorisations; mixed-form evaluations then run their PCG
+    // solves interleaved across the wave's streams
+    std::vector<hmle_status> fs(cnt, HMLE_OK);
+    std::vector<PcgRun> runs(cnt);
+    std::vector<int> live;
+    std::vector<std::string> errs(cnt);
     for (int k = 0; k < cnt; ++k) {
       const TaskRef &T = tasks[i0 + k];
       Work *w = ws[k];
       hmle_ctx wc;
       wc.st = w->st; wc.side = w->side;
-      hmle_status s = finish_factor(&wc, T.t, &w->H, &w->F);
-      if (s == HMLE_OK && T.t->opts.precision == HMLE_MIXED_FP32) s = mixed_quad(&wc, T.t, &w->H, &w->F, T.zd);
+      fs[k] = finish_factor(&wc, T.t, &w->H, &w->F);
+      if (fs[k] == HMLE_OK && T.t->opts.precision == HMLE_MIXED_FP32) {
+        fs[k] = mixed_prepare(&wc, T.t, &w->H, &w->F, T.zd, runs[k]);
+        if (fs[k] == HMLE_OK) {
+          cudaError_t e = pcg_start(runs[k]);
+          if (e != cudaSuccess) fs[k] = cuda_fail(&wc, e, "pcg");
+          else live.push_back(k);
+        }
+      }
+      errs[k] = wc.err;
+    }
+    while (!live.empty()) {
+      std::vector<int> next;
+      for (int k : live) {
+        bool fin = false;
+        cudaError_t e = cudaStreamSynchronize(runs[k].st);
+        if (e == cudaSuccess) e = pcg_poll(runs[k], &fin);
+        if (e != cudaSuccess) {
+          hmle_ctx wc;
+          fs[k] = cuda_fail(&wc, e, "pcg");
+          errs[k] = wc.err;
+        } else if (fin) {
+          hmle_ctx wc;
+          fs[k] = mixed_result(&wc, tasks[i0 + k].t, &ws[k]->F, runs[k]);
+          errs[k] = wc.err;
+        } else {
+          next.push_back(k);
+        }
+      }
+      live.swap(next);
+    }
+    for (int k = 0; k < cnt; ++k) {
+      const TaskRef &T = tasks[i0 + k];
+      Work *w = ws[k];
+      hmle_ctx wc;
+      wc.err = errs[k];
+      hmle_status s = fs[k];
       const int i = i0 + k;
       const double nn = (double)T.t->n;
       ll[i] = (s == HMLE_OK) ? -0.5 * nn * std::log(2.0 * M_PI) - 0.5 * w->F.logdet - 0.5 * w->F.quad

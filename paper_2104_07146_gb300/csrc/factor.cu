@@ -17,7 +17,8 @@
 //      sigma_i^2 <= eps^2 max(|S_T|_F^2, |C_T|_F^2): U_T = Q V_k,
 //      W_T = Z V_k (the start of the forward solve of W_T).
 //  P6  k_dense       S_IK = C_IK - sum_pairs U_A G_AB U_B^T for the dense
-//      blocks of column K (diagonal first); C entries from the Matern table.
+//      blocks of column K (diagonal first); C_IK from the assembled dense
+//      near field.
 //  P7  k_potrf       L_KK = chol(S_KK); log-det part 2 sum log L_ii.
 //  P8  k_trsm        L_IK = S_IK L_KK^{-T}.
 //  P9  k_wsolve      rows of leaf K of every open W-panel: W <- L_KK^{-1} W.
@@ -294,49 +295,120 @@ __global__ void __launch_bounds__(kThreads) k_side_t(FactorArgs F, int e0, int n
   }
 }
 
-// --- P2b / P4b: s_X = sum over the entry's pairs of G (or G^T) t_partner ---
+// --- P2b / P4b: s_X = sum over the entry's pairs of L_q t_q ----------------
+// Each pair q of the entry contributes a left factor L_q (rows of X x K_q)
+// times the partner's t_q (K_q x r).  The pairs are concatenated along K (in
+// chunks of at most kMaxRowK columns and kSidePairs pairs) into one product
+// per CTA (the small-output, long-K product: rows of X x samples), in Tc
+// arithmetic.
+//   !trans (X = A, partner B)         trans (X = B, partner A)
+//   LR/LR       L = G_AB                L = G_AB^T
+//   A dense     L(i,k) = W_B(J0_A+i,k)   L(i,k) = W_B(J0_A+k,i)
+//   B dense     L(i,k) = W_A(J0_B+k,i)   L(i,k) = W_A(J0_B+i,k)
+//   both dense  L = I (the overlapping columns)
+// Rows of a low-rank X beyond its rank are zero.
+constexpr int kSidePairs = 256;
+enum { kLG = 0, kLGt = 1, kLWik = 2, kLWki = 3, kLI = 4 };
+
+template <class Tc>
 __global__ void __launch_bounds__(kThreads) k_side_s(FactorArgs F, int e0, int trans) {
+  extern __shared__ double smem[];
+  __shared__ int kb[kSidePairs + 1];
+  __shared__ int pcase[kSidePairs], pnr[kSidePairs], pky[kSidePairs], pwld[kSidePairs];
+  __shared__ int64_t pmat[kSidePairs], ptoff[kSidePairs];
+  __shared__ short kmap[kMaxRowK];
+  __shared__ int s_q1, s_nc;
   Acc a(F);
   const int kc = F.kcap;
   const SideEntry E = trans ? F.bent[e0 + blockIdx.x] : F.aent[e0 + blockIdx.x];
   const int r = sample_width(F, F.lrt[E.target].blk);
   const BlockDesc X = F.blocks[E.blk];
   const int kx = a.kof(X), kxe = a.keff(E.blk, X);
+  const int M = X.kind == kDense ? kx : kxe;   // rows of s that can be nonzero
   double *s = F.ws + E.soff;
   const int32_t *plist = trans ? F.bpair : F.apair;
-  // each thread owns outputs (i, j) of s (kx x r, only the first kxe rows
-  // can be nonzero) and accumulates all the entry's pairs in order
-  for (int o = threadIdx.x; o < kx * r; o += blockDim.x) {
-    const int i = o % kx, j = o / kx;
-    double acc = 0.0;
-    if (i < kxe || X.kind == kDense) {
-      for (int q = E.p0; q < E.p1; ++q) {
+  for (int o = threadIdx.x; o < kx * r; o += blockDim.x)
+    if (o % kx >= M || E.p1 == E.p0) s[o] = 0.0;
+  int q0 = E.p0;
+  bool first = true;
+  while (q0 < E.p1) {
+    if (threadIdx.x == 0) {   // describe the next chunk of pairs
+      int k = 0, c = 0, q = q0;
+      for (; q < E.p1 && c < kSidePairs; ++q) {
         const LrPair P = F.lrpairs[plist[q]];
         const int oe = trans ? P.ae : P.be;
         const SideEntry O = trans ? F.aent[oe] : F.bent[oe];
         const BlockDesc Y = F.blocks[O.blk];
         const BlockDesc &A = trans ? Y : X;
         const BlockDesc &B = trans ? X : Y;
-        const int ky = a.kof(Y), kye = a.keff(O.blk, Y);
-        const double *t = F.ws + O.toff + (int64_t)j * ky;   // column j of the partner's t
+        const int kye = a.keff(O.blk, Y);
+        int cs, K, nr = 0, wld = 0;
+        int64_t mat = 0;
         if (A.kind == kLowRank && B.kind == kLowRank) {
-          const double *G = F.ws + P.goff;
-          if (!trans) { for (int k = 0; k < kye; ++k) acc = fma(G[i + k * kc], t[k], acc); }
-          else { for (int k = 0; k < kye; ++k) acc = fma(G[k + i * kc], t[k], acc); }
-        } else if (A.kind == kDense && B.kind == kLowRank) {
-          const int J0 = A.cbeg, nj = A.cend - A.cbeg;
-          if (!trans) { if (i < nj) for (int k = 0; k < kye; ++k) acc = fma(a.W(B, J0 + i, k), t[k], acc); }
-          else { for (int k = 0; k < nj; ++k) acc = fma(a.W(B, J0 + k, i), t[k], acc); }
-        } else if (A.kind == kLowRank && B.kind == kDense) {
-          const int J0 = B.cbeg, nj = B.cend - B.cbeg;
-          if (!trans) { for (int k = 0; k < nj; ++k) acc = fma(a.W(A, J0 + k, i), t[k], acc); }
-          else { if (i < nj) for (int k = 0; k < kye; ++k) acc = fma(a.W(A, J0 + i, k), t[k], acc); }
+          cs = trans ? kLGt : kLG; K = kye; mat = P.goff;
+        } else if (A.kind == kDense && B.kind == kDense) {
+          cs = kLI; K = 0; nr = A.cend - A.cbeg;   // added directly after the product
         } else {
-          if (i < A.cend - A.cbeg) acc += t[i];
+          const BlockDesc &Wb = (A.kind == kDense) ? B : A;   // the low-rank block holding W
+          const PanelDesc PW = F.panels[Wb.panel];
+          wld = PW.rend - PW.rbeg;
+          const int J0 = (A.kind == kDense) ? A.cbeg : B.cbeg;
+          const int nj = (A.kind == kDense) ? A.cend - A.cbeg : B.cend - B.cbeg;
+          mat = PW.off + (int64_t)Wb.slot * wld + (J0 - PW.rbeg);   // W(J0 + x, y) = W[mat + x + y wld]
+          const bool ik = (A.kind == kDense) != (trans != 0);      // L(i,k) = W(J0+i, k)?
+          cs = ik ? kLWik : kLWki;
+          K = ik ? kye : nj;
+          nr = ik ? nj : 0;
         }
+        if (k + K > kMaxRowK && c > 0) break;
+        kb[c] = k; pcase[c] = cs; pnr[c] = nr; pmat[c] = mat; pwld[c] = wld;
+        ptoff[c] = O.toff; pky[c] = a.kof(Y);
+        k += K;
+        ++c;
       }
+      kb[c] = k;
+      s_nc = c;
+      s_q1 = q;
     }
-    s[i + (int64_t)j * kx] = acc;
+    __syncthreads();
+    const int nc = s_nc, K = min(kb[nc], kMaxRowK);
+    for (int c = 0; c < nc; ++c)
+      for (int k = kb[c] + threadIdx.x; k < min(kb[c + 1], K); k += blockDim.x) kmap[k] = (short)c;
+    __syncthreads();
+    const bool acc = !first;
+    cta_gemm_tn<Tc>(
+        M, r, K,
+        [&](int k, int i) -> double {
+          const int c = kmap[k], kk = k - kb[c];
+          switch (pcase[c]) {
+            case kLG: return F.ws[pmat[c] + i + (int64_t)kk * kc];
+            case kLGt: return F.ws[pmat[c] + kk + (int64_t)i * kc];
+            case kLWik: return i < pnr[c] ? F.W[pmat[c] + i + (int64_t)kk * pwld[c]] : 0.0;
+            case kLWki: return F.W[pmat[c] + kk + (int64_t)i * pwld[c]];
+            default: return 0.0;   // identity pairs take no columns
+          }
+        },
+        [&](int k, int j) -> double {
+          const int c = kmap[k];
+          return F.ws[ptoff[c] + (k - kb[c]) + (int64_t)j * pky[c]];
+        },
+        [&](int i, int j, double v) {
+          double *o = s + i + (int64_t)j * kx;
+          *o = acc ? *o + v : v;
+        },
+        smem);
+    __syncthreads();
+    // identity pairs (both blocks dense): s(i, j) += t_q(i, j), in pair order
+    for (int o = threadIdx.x; o < M * r; o += blockDim.x) {
+      const int i = o % M, j = o / M;
+      double v = s[i + (int64_t)j * kx];
+      for (int c = 0; c < nc; ++c)
+        if (pcase[c] == kLI && i < pnr[c]) v += F.ws[ptoff[c] + i + (int64_t)j * pky[c]];
+      s[i + (int64_t)j * kx] = v;
+    }
+    __syncthreads();
+    q0 = s_q1;
+    first = false;
   }
 }
 
@@ -405,40 +477,46 @@ __global__ void __launch_bounds__(kThreads) k_rows(FactorArgs F, int rt0, int tr
 // --- tall QR (R factor only) and SVD of the small R -----------------------
 constexpr int kQrRows = 64;
 
-// Householder QR of the h x r column-major matrix A (ld h, h >= r) in shared
-// memory, in place: on return rows 0..r-1 hold R in their upper triangle
-// (the entries below the diagonal hold reflector data).
+// R factor of the stacked h x r matrix A = [R; X] (ld h) in shared memory, in
+// place: R (rows 0..r-1) is upper triangular with zeros below its diagonal,
+// X holds rows r..h-1.  On return rows 0..r-1 hold the R factor of A; rows
+// r..h-1 are overwritten.  Column j's reflector only involves row j and the
+// rows of X (the rows of R below j are zero), so only those rows are read.
+// The reflector is applied without being stored: w_c = A(j,c) + scal
+// sum_i A(i,j) A(i,c), A(j,c) -= tau w_c, A(i,c) -= tau w_c scal A(i,j).
+// Every warp computes the scalars of a column itself (lane 0, broadcast by
+// shuffle), so a column costs one block reduction and one barrier.
 __device__ void smem_householder(double *A, int h, int r, double *red) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int j = 0; j < r && j < h; ++j) {
+  for (int j = 0; j < r; ++j) {
     double s = 0.0;
-    for (int i = j + 1 + threadIdx.x; i < h; i += blockDim.x) s = fma(A[i + j * h], A[i + j * h], s);
-    s = block_sum(s, red);
-    if (!(s > 0.0)) continue;  // nothing below the diagonal (uniform branch)
-    if (threadIdx.x == 0) {    // reflector scalars, computed once
+    for (int i = r + threadIdx.x; i < h; i += blockDim.x) s = fma(A[i + j * h], A[i + j * h], s);
+    s = block_sum(s, red);               // ends with a barrier: column j is final
+    if (!(s > 0.0)) continue;            // nothing below the diagonal (uniform branch)
+    double tau = 0.0, scal = 0.0, beta = 0.0;
+    if (lane == 0) {                     // reflector scalars, once per warp
       const double alpha = A[j + j * h];
       const double nrm = sqrt(fma(alpha, alpha, s));
-      const double beta = alpha >= 0.0 ? -nrm : nrm;
-      red[0] = (beta - alpha) / beta;
-      red[1] = 1.0 / (alpha - beta);
-      red[2] = beta;
+      beta = alpha >= 0.0 ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
     }
-    __syncthreads();
-    const double tau = red[0], scal = red[1], beta = red[2];
-    for (int i = j + 1 + threadIdx.x; i < h; i += blockDim.x) A[i + j * h] *= scal;
-    __syncthreads();
+    tau = __shfl_sync(0xffffffffu, tau, 0);
+    scal = __shfl_sync(0xffffffffu, scal, 0);
+    beta = __shfl_sync(0xffffffffu, beta, 0);
     for (int c = j + 1 + warp; c < r; c += nw) {
       double w = 0.0;
-      for (int i = j + 1 + lane; i < h; i += 32) w = fma(A[i + j * h], A[i + c * h], w);
+      for (int i = r + lane; i < h; i += 32) w = fma(A[i + j * h], A[i + c * h], w);
       w = warp_sum(w);
-      w = tau * (w + A[j + c * h]);
+      w = tau * fma(scal, w, A[j + c * h]);
       if (lane == 0) A[j + c * h] -= w;
-      for (int i = j + 1 + lane; i < h; i += 32) A[i + c * h] = fma(-w, A[i + j * h], A[i + c * h]);
+      const double ws = w * scal;
+      for (int i = r + lane; i < h; i += 32) A[i + c * h] = fma(-ws, A[i + j * h], A[i + c * h]);
     }
-    __syncthreads();
+    __syncthreads();                     // every column c > j is updated
     if (threadIdx.x == 0) A[j + j * h] = beta;
-    __syncthreads();
   }
+  __syncthreads();
 }
 
 // R factor of one row group of a target's Y (which = 0) or Z (which = 1):
@@ -486,6 +564,104 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_part(FactorArgs F, int t0, in
 // values above 1e-14 of the largest (zero columns otherwise).  mode 1
 // (truncate): k = smallest rank whose tail energy sum_{i>=k} sigma_i^2 is
 // <= eps^2 max(sum sigma_i^2, |C_T|_F^2); M = V_k (r x kcap); rank to rank_l.
+// Column-pivoted Householder QR of the r x r matrix B (ld lb) in shared
+// memory, in place: B P = Q R.  At step j the remaining column of largest
+// norm is swapped in; the sweep stops where that norm falls below 1e-14 of
+// the first pivot's (the rest is numerically zero).  On return rows 0..k1-1
+// hold R in their upper triangle, piv the permutation (column j of B P is
+// column piv[j] of B), and the result is k1.  Reflector scalars are computed
+// once by thread 0; a column with nothing below its diagonal is left as it
+// is (H = I).
+struct PqrShared {
+  int p, k1;
+  double first, tau, beta;
+};
+
+__device__ int smem_pivoted_qr(double *B, int lb, int r, int *piv, double *cn, PqrShared &S) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = threadIdx.x; c < r; c += blockDim.x) piv[c] = c;
+  for (int c = warp; c < r; c += nw) {     // initial column norms, a warp per column
+    double v = 0.0;
+    for (int i = lane; i < r; i += 32) v = fma(B[i + c * lb], B[i + c * lb], v);
+    v = warp_sum(v);
+    if (lane == 0) cn[c] = v;
+  }
+  if (threadIdx.x == 0) { S.k1 = r; S.first = 0.0; }
+  __syncthreads();
+  for (int j = 0; j < r; ++j) {
+    if (warp == 0) {   // pivot: largest remaining norm (ties -> lowest index)
+      double bv = -1.0;
+      int bi = j;
+      for (int c = j + lane; c < r; c += 32)
+        if (cn[c] > bv) { bv = cn[c]; bi = c; }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) {
+        if (j == 0) S.first = bv;
+        S.p = bi;
+        if (!(bv > 1e-28 * S.first) || !(bv > 0.0)) S.k1 = j;   // the rest is rank deficient
+      }
+    }
+    __syncthreads();
+    if (S.k1 == j) break;
+    const int p = S.p;
+    if (p != j) {   // swap columns j and p (all rows), their norms and permutation entries
+      for (int i = threadIdx.x; i < r; i += blockDim.x) {
+        double t = B[i + j * lb]; B[i + j * lb] = B[i + p * lb]; B[i + p * lb] = t;
+      }
+      if (threadIdx.x == 0) {
+        int t = piv[j]; piv[j] = piv[p]; piv[p] = t;
+        double u = cn[j]; cn[j] = cn[p]; cn[p] = u;
+      }
+      __syncthreads();
+    }
+    if (warp == 0) {   // reflector for column j, rows j..r-1
+      double s2 = 0.0;
+      for (int i = j + 1 + lane; i < r; i += 32) s2 = fma(B[i + j * lb], B[i + j * lb], s2);
+      s2 = warp_sum(s2);
+      const double alpha = B[j + j * lb];
+      double scal = 0.0;
+      if (s2 > 0.0) {
+        const double nrm = sqrt(fma(alpha, alpha, s2));
+        const double beta = alpha >= 0.0 ? -nrm : nrm;
+        scal = 1.0 / (alpha - beta);
+        if (lane == 0) { S.beta = beta; S.tau = (beta - alpha) / beta; }
+      } else if (lane == 0) {   // nothing below the diagonal: H = I
+        S.beta = alpha;
+        S.tau = 0.0;
+      }
+      for (int i = j + 1 + lane; i < r; i += 32) B[i + j * lb] *= scal;
+    }
+    __syncthreads();
+    const double tau = S.tau;
+    // apply to the columns right of j, a warp per column; the same pass gives
+    // each column's norm over rows j+1.. for the next pivot choice
+    for (int c = j + 1 + warp; c < r; c += nw) {
+      double w = 0.0;
+      for (int i = j + 1 + lane; i < r; i += 32) w = fma(B[i + j * lb], B[i + c * lb], w);
+      w = tau * (warp_sum(w) + B[j + c * lb]);
+      double v2 = 0.0;
+      for (int i = j + 1 + lane; i < r; i += 32) {
+        const double x = fma(-w, B[i + j * lb], B[i + c * lb]);
+        B[i + c * lb] = x;
+        v2 = fma(x, x, v2);
+      }
+      v2 = warp_sum(v2);
+      if (lane == 0) {
+        B[j + c * lb] -= w;
+        cn[c] = v2;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) B[j + j * lb] = S.beta;
+    __syncthreads();
+  }
+  return S.k1;
+}
+
 __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, int which, int mode) {
   extern __shared__ double smem[];
   __shared__ double red[32];
@@ -525,71 +701,13 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, i
     V[i + c * lb] = (i == c) ? 1.0 : 0.0;
   }
   __syncthreads();
+  __shared__ int piv[kMaxSample + 2];
+  __shared__ double cn[kMaxSample + 2];
+  __shared__ PqrShared pq;
+  const int k1 = smem_pivoted_qr(B, lb, r, piv, cn, pq);
   if (mode == 0) {
-    // Orthonormalisation: column-pivoted Householder QR of R (R P = Q_r R_p),
-    // stopped where the pivot column's norm falls below 1e-14 of the first;
-    // Q1 = Y P_{:,1:k1} R_p11^{-1} (the CholQR pass that follows restores
-    // orthogonality to rounding level).
-    __shared__ int piv[kMaxSample + 2];
-    __shared__ double cn[kMaxSample + 2];
-    __shared__ int s_p, s_k1;
-    __shared__ double s_first, s_tau, s_beta;
-    for (int c = threadIdx.x; c < r; c += blockDim.x) piv[c] = c;
-    if (threadIdx.x == 0) { s_k1 = r; s_first = 0.0; }
-    __syncthreads();
-    for (int j = 0; j < r; ++j) {
-      for (int c = j + threadIdx.x; c < r; c += blockDim.x) {   // remaining column norms
-        double v = 0.0;
-        for (int i = j; i < r; ++i) v = fma(B[i + c * lb], B[i + c * lb], v);
-        cn[c] = v;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        int p = j;
-        for (int c = j + 1; c < r; ++c) if (cn[c] > cn[p]) p = c;
-        if (j == 0) s_first = cn[p];
-        s_p = p;
-        if (!(cn[p] > 1e-28 * s_first) || !(cn[p] > 0.0)) s_k1 = j;   // the rest is rank deficient
-      }
-      __syncthreads();
-      if (s_k1 == j) break;
-      const int p = s_p;
-      if (p != j) {   // swap columns j and p (entries of all rows) and the permutation
-        for (int i = threadIdx.x; i < r; i += blockDim.x) {
-          double t = B[i + j * lb]; B[i + j * lb] = B[i + p * lb]; B[i + p * lb] = t;
-        }
-        if (threadIdx.x == 0) { int t = piv[j]; piv[j] = piv[p]; piv[p] = t; }
-        __syncthreads();
-      }
-      if (threadIdx.x == 0) {   // reflector for column j, rows j..r-1
-        double alpha = B[j + j * lb], s2 = 0.0;
-        for (int i = j + 1; i < r; ++i) s2 = fma(B[i + j * lb], B[i + j * lb], s2);
-        if (s2 > 0.0) {
-          double nrm = sqrt(fma(alpha, alpha, s2));
-          double beta = alpha >= 0.0 ? -nrm : nrm;
-          s_beta = beta;
-          s_tau = (beta - alpha) / beta;
-          double scal = 1.0 / (alpha - beta);
-          for (int i = j + 1; i < r; ++i) B[i + j * lb] *= scal;
-        } else {   // nothing below the diagonal: H = I
-          s_beta = alpha;
-          s_tau = 0.0;
-        }
-      }
-      __syncthreads();
-      const double tau = s_tau;
-      for (int c = j + 1 + threadIdx.x; c < r; c += blockDim.x) {
-        double w = B[j + c * lb];
-        for (int i = j + 1; i < r; ++i) w = fma(B[i + j * lb], B[i + c * lb], w);
-        w *= tau;
-        B[j + c * lb] -= w;
-        for (int i = j + 1; i < r; ++i) B[i + c * lb] = fma(-w, B[i + j * lb], B[i + c * lb]);
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) B[j + j * lb] = s_beta;
-      __syncthreads();
-    }
-    const int k1 = s_k1;
+    // Orthonormalisation: Q1 = Y P_{:,1:k1} R_p11^{-1} (the CholQR pass that
+    // follows restores orthogonality to rounding level).
     // V <- R_p11^{-1} (upper triangular, k1 x k1), one thread per column
     for (int c = threadIdx.x; c < k1; c += blockDim.x) {
       for (int i = k1 - 1; i >= 0; --i) {
@@ -609,12 +727,26 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, i
     if (threadIdx.x == 0) F.kept[t0 + blockIdx.x] = k1;
     return;
   }
-  // one-sided Jacobi on the columns of B (R V = B).  A round rotates the
-  // disjoint column pairs of a round-robin tournament; each pair is handled
-  // by a group of g lanes (all four warps busy, so all four FP64 pipes of the
-  // SM), the group's lanes split the rows, and the rotation parameters are
-  // computed once per group and broadcast.
-  const int rp = r + (r & 1), half = rp / 2;
+  // mode 1: the SVD of R from the pivoted factor (R P = Q_r R_p): one-sided
+  // Jacobi on the columns of X = R_p^T (its first k1 columns; the rest is
+  // numerically zero).  The columns of X become U_X Sigma with R_p = V_X
+  // Sigma U_X^T, so the right singular vectors of R are P U_X: no rotation
+  // needs to be accumulated, and the pivoting leaves X's columns nearly
+  // orthogonal, so few sweeps are needed.
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {   // X = R_p^T into V (scratch)
+    const int c = e % r, i = e / r;                         // X(c, i) = R_p(i, c)
+    V[c + i * lb] = (i < k1 && i <= c) ? B[i + c * lb] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) B[e % r + (e / r) * lb] = V[e % r + (e / r) * lb];
+  __syncthreads();
+  // A round rotates the disjoint column pairs of a round-robin tournament;
+  // each pair is handled by a group of g lanes (all four warps busy, so all
+  // four FP64 pipes of the SM), the group's lanes split the rows, and the
+  // rotation parameters are computed once per group and broadcast.
+  const int nc = k1;
+  const int rp = nc + (nc & 1), half = rp / 2;
   double fro = 0.0;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     double v = B[e % r + (e / r) * lb];
@@ -625,9 +757,8 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, i
   int g = 1;                            // lanes per pair: largest power of 2 with half * g <= 128
   while (g < 32 && half * g * 2 <= kThreads) g *= 2;
   const int grp = threadIdx.x / g, gl = threadIdx.x % g;
-  const unsigned gmask = (g == 32) ? 0xffffffffu : (((1u << g) - 1u) << ((threadIdx.x & 31) / g * g));
   double jf = 0.0;
-  for (int sweep = 0; sweep < 40; ++sweep) {
+  for (int sweep = 0; sweep < 40 && nc > 1; ++sweep) {
     __syncthreads();                    // every thread has read the previous flag
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
@@ -638,7 +769,7 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, i
         p = (grp == 0) ? 0 : 1 + (grp - 1 + round) % (rp - 1);
         q = 1 + (rp - 2 - grp + round) % (rp - 1);
         if (p > q) { int t = p; p = q; q = t; }
-        active = q < r;
+        active = q < nc;
       }
       double al = 0.0, be = 0.0, ga = 0.0;
       if (active) {
@@ -674,26 +805,28 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, i
           double bp = B[i + p * lb], bq = B[i + q * lb];
           B[i + p * lb] = c * bp - sn * bq;
           B[i + q * lb] = sn * bp + c * bq;
-          double vp = V[i + p * lb], vq = V[i + q * lb];
-          V[i + p * lb] = c * vp - sn * vq;
-          V[i + q * lb] = sn * vp + c * vq;
         }
         if (gl == 0) {
           s_rot = 1;
-          jf += 12.0 * r;
+          jf += 6.0 * r;
         }
       }
       __syncthreads();
     }
     if (s_rot == 0) break;
   }
-  (void)gmask;
   jf = block_sum(jf, red);
   if (threadIdx.x == 0 && F.jacobi_flops) atomicAdd(F.jacobi_flops, jf);
-  for (int c = threadIdx.x; c < r; c += blockDim.x) {
+  // V(piv[c], j) = X(c, j) / sigma_j: the right singular vectors of R
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
     double s = 0.0;
-    for (int i = 0; i < r; ++i) s = fma(B[i + c * lb], B[i + c * lb], s);
-    sig[c] = sqrt(s);
+    for (int i = 0; i < r; ++i) s = fma(B[i + j * lb], B[i + j * lb], s);
+    sig[j] = sqrt(s);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int c = e % r, j = e / r;
+    V[piv[c] + j * lb] = (sig[j] > 0.0) ? B[c + j * lb] / sig[j] : 0.0;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -704,14 +837,14 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, i
         if (sig[ord[j]] > sig[ord[best]]) best = j;
       int t = ord[i]; ord[i] = ord[best]; ord[best] = t;
     }
-    if (mode == 1) {
+    {
       // truncate relative to the larger of |S| and |C_block|: C~ itself is
       // only accurate to eps |C_block| (ACA), so smaller singular values of
       // the updated block are noise
       double total = 0.0;
       for (int i = 0; i < r; ++i) total += sig[i] * sig[i];
-      const double cn = F.cnorm[L.blk];
-      const double thr = F.eps * F.eps * fmax(total, cn * cn);
+      const double cnb = F.cnorm[L.blk];
+      const double thr = F.eps * F.eps * fmax(total, cnb * cnb);
       int k = r;
       double tail = 0.0;
       while (k > 0) {
@@ -730,24 +863,7 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, i
   }
   __syncthreads();
   double *M = F.ws + L.soff + ldm * ldm;
-  if (mode == 0) {
-    __shared__ double rinv[kMaxSample + 2];
-    const double smax = sig[ord[0]];
-    for (int c = threadIdx.x; c < r; c += blockDim.x) {   // one reciprocal per column
-      double sc = sig[ord[c]];
-      rinv[c] = (sc > 1e-14 * smax && sc > 0.0) ? 1.0 / sc : 0.0;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {      // kept columns come first (descending order)
-      int k1 = 0;
-      while (k1 < r && rinv[k1] != 0.0) ++k1;
-      F.kept[t0 + blockIdx.x] = k1;
-    }
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-      int i = e % r, c = e / r;
-      M[i + c * ldm] = V[i + ord[c] * lb] * rinv[c];
-    }
-  } else {
+  {
     const int k = s_rank, kc = F.kcap;
     for (int e = threadIdx.x; e < r * kc; e += blockDim.x) {
       int i = e % r, c = e / r;
@@ -935,12 +1051,12 @@ __global__ void __launch_bounds__(kThreads) k_dense_reduce(FactorArgs F, int d0,
   const int m = T.rend - T.rbeg, p = T.cend - T.cbeg;
   const int q0 = F.dns[d0].p0;
   double *S = F.D + T.off_d;
-  const ThetaDev th = *F.th;
+  const double *Cb = F.Cd + T.off_d;
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     int i = e % b, j = e / b;
     double v = 0.0;
     if (i < m && j < p) {
-      v = cov_entry(F.tab, F.xyz, F.n, F.d, T.rbeg + i, T.cbeg + j, th.inv_ell, th.sigma2, th.tau2);
+      v = Cb[e];
       for (int q = DT.p0; q < DT.p1; ++q) v -= F.ws[dpws + (int64_t)(q - q0) * b * b + e];
     }
     S[e] = v;
@@ -1061,7 +1177,8 @@ __global__ void __launch_bounds__(kThreads) k_htask(FactorArgs F, int h0) {
   const PanelDesc PA = F.panels[A.panel];
   const int lda = PA.rend - PA.rbeg;
   const double *wa = F.W + PA.off + (int64_t)A.slot * lda + (A.cbeg - PA.rbeg);
-  for (int j0 = 0; j0 < P.width; j0 += kTnMaxMN - kMaxRank) {
+  // column chunk blockIdx.y of the panel (chunks run in parallel CTAs)
+  for (int j0 = blockIdx.y * (kTnMaxMN - kMaxRank); j0 < P.width; j0 += gridDim.y * (kTnMaxMN - kMaxRank)) {
     const int nj = min(kTnMaxMN - kMaxRank, P.width - j0);
     cta_gemm_tn<Tc>(
         ka, nj, A.cend - A.cbeg, [&](int k, int i) { return wa[k + (int64_t)i * lda]; },
@@ -1138,7 +1255,8 @@ int factor_smem_setup(int b, int kcap) {
   SETA(k_gram<float>, g_smem_bytes);
   SETA(k_side_t<double>, g_smem_bytes);
   SETA(k_side_t<float>, g_smem_bytes);
-  SETA(k_side_s, g_smem_bytes);
+  SETA(k_side_s<double>, kTnSmem * (int)sizeof(double));
+  SETA(k_side_s<float>, kTnSmem * (int)sizeof(double));
   SETA(k_rows<double>, g_smem_bytes);
   SETA(k_rows<float>, g_smem_bytes);
   SETA(k_tsqr_part, (kMaxSample + kQrRows) * kMaxSample * (int)sizeof(double));
@@ -1207,6 +1325,7 @@ int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaE
   const int sm = (kGemmSmem + F.b * F.b) * (int)sizeof(double);
   const int smt = std::max(kGemmSmem + F.b * F.b, kTnSmem) * (int)sizeof(double);
   const int smd = (kGemmSmem + std::max(F.b, F.kcap) * F.b) * (int)sizeof(double);
+  const int stn = kTnSmem * (int)sizeof(double);    // a small-output product and nothing else
   const int r = F.r;
   if (S.gch1 > S.gch0) { LAUNCH(KK_GRAM, st, k_gram<Tc><<<S.gch1 - S.gch0, kThreads, smt, st>>>(F, S.gch0)); }
   if (S.gred1 > S.gred0) { LAUNCH(KK_GRAM, st, k_gram_reduce<<<S.gred1 - S.gred0, kThreads, 0, st>>>(F, S.gred0)); }
@@ -1238,7 +1357,7 @@ int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaE
     const int cq_smem = 2 * r * r * (int)sizeof(double);
     // Y = S Omega
     LAUNCH(KK_SIDE_T, st, k_side_t<Tc><<<(S.bent1 - S.bent0) + nt, kThreads, smt, st>>>(F, S.bent0, S.bent1 - S.bent0, S.lrt0, 0));
-    if (S.aent1 > S.aent0) LAUNCH(KK_SIDE_S, st, k_side_s<<<S.aent1 - S.aent0, kThreads, sm, st>>>(F, S.aent0, 0));
+    if (S.aent1 > S.aent0) LAUNCH(KK_SIDE_S, st, k_side_s<Tc><<<S.aent1 - S.aent0, kThreads, stn, st>>>(F, S.aent0, 0));
     LAUNCH(KK_ROWS, st, k_rows<Tc><<<S.arow1 - S.arow0, kThreads, sm, st>>>(F, S.arow0, 0));
     // Q = orth(Y): R of Y, SVD, Q1 = Y V Sigma^{-1}, then CholQR
     LAUNCH(KK_TSQR_PART, st, k_tsqr_part<<<dim3(nt, maxgm), kThreads, qr_smem, st>>>(F, S.lrt0, 0));
@@ -1249,7 +1368,7 @@ int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaE
     LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch), kThreads, sm, st>>>(F, S.lrt0, 0));
     // Z = S^T Q
     LAUNCH(KK_SIDE_T, st, k_side_t<Tc><<<(S.aent1 - S.aent0) + nt, kThreads, smt, st>>>(F, S.aent0, S.aent1 - S.aent0, S.lrt0, 1));
-    if (S.bent1 > S.bent0) LAUNCH(KK_SIDE_S, st, k_side_s<<<S.bent1 - S.bent0, kThreads, sm, st>>>(F, S.bent0, 1));
+    if (S.bent1 > S.bent0) LAUNCH(KK_SIDE_S, st, k_side_s<Tc><<<S.bent1 - S.bent0, kThreads, stn, st>>>(F, S.bent0, 1));
     LAUNCH(KK_ROWS, st, k_rows<Tc><<<S.brow1 - S.brow0, kThreads, sm, st>>>(F, S.brow0, 1));
     LAUNCH(KK_TSQR_PART, st, k_tsqr_part<<<dim3(nt, maxgp), kThreads, qr_smem, st>>>(F, S.lrt0, 1));
     LAUNCH(KK_TSQR_FINAL, st, k_tsqr_final<<<nt, kThreads, qrf_smem, st>>>(F, S.lrt0, 1, 1));
@@ -1265,7 +1384,12 @@ int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaE
     LAUNCH(KK_WSOLVE, st, k_wsolve<<<dim3(S.wpan1 - S.wpan0, (maxw + kThreads - 1) / kThreads), kThreads, sm, st>>>(
         F, S.wpan0, S.dns0));
   }
-  if (S.ht1 > S.ht0) { LAUNCH(KK_HTASK, st, k_htask<Tc><<<S.ht1 - S.ht0, kThreads, smt, st>>>(F, S.ht0)); }
+  if (S.ht1 > S.ht0) {
+    int maxw = 1;
+    for (int q = S.ht0; q < S.ht1; ++q) maxw = std::max(maxw, PL.panels[PL.hts[q].panel].width);
+    const int ny = (maxw + (kTnMaxMN - kMaxRank) - 1) / (kTnMaxMN - kMaxRank);
+    LAUNCH(KK_HTASK, st, k_htask<Tc><<<dim3(S.ht1 - S.ht0, ny), kThreads, smt, st>>>(F, S.ht0));
+  }
   if (S.ur1 > S.ur0) { LAUNCH(KK_UPDROW, st, k_updrow<Tc><<<S.ur1 - S.ur0, kThreads, sm, st>>>(F, S.ur0)); }
   return nk;
 }

@@ -28,6 +28,8 @@ struct AsmArgs {
   double *cnorm;           // |C_block|_F estimate of every admissible block
   int *flags;
   const ThetaDev *thd;     // the same theta in device memory (read by captured kernels)
+  const double *Cd;        // dense near-field blocks (b x b at each dense block's off_d)
+  int b;                   // leaf size (leading dimension of the Cd blocks)
 };
 
 // Everything the sweep kernels read; device pointers.
@@ -54,6 +56,7 @@ struct FactorArgs {
   // pools
   double *D;               // dense blocks of L (b x b each, ld b)
   const double *uc;        // ACA factors of C
+  const double *Cd;        // dense near-field blocks of C (b x b at each dense block's off_d)
   const int32_t *rank_c;
   const double *cnorm;     // |C_block|_F of the admissible blocks (ACA)
   double *U;               // U factors of L
@@ -81,6 +84,9 @@ void launch_matern_table(cudaStream_t st, double nu, double *tab);
 void launch_matern_eval(cudaStream_t st, const double *tab, const double *x, int64_t m,
                         double *out);
 void launch_aca(cudaStream_t st, const AsmArgs &A, int n_lr);
+// dense near-field blocks of C into Cd (the dense blocks' b x b slots, off_d)
+void launch_assemble_dense(cudaStream_t st, const AsmArgs &A, const int32_t *dense_ids, int nd,
+                           int b, double *Cd);
 // Kernel kinds of the sweep (for per-kernel timing and flop tallies).
 enum KernelKind {
   KK_GRAM = 0, KK_SIDE_T, KK_SIDE_S, KK_ROWS, KK_TSQR_PART, KK_TSQR_FINAL, KK_TALL_APPLY,
@@ -158,15 +164,42 @@ int64_t pcg_words(int64_t n, int n_lr, int kc, int hmax);
 // the factor of Fs (F's task pointers set to the right-hand-side lists) applied
 // through the right-hand-side panel `panel` (overwritten).  b: n doubles,
 // cluster order.  Stops when |r| <= tol |b| or after maxit iterations.
-// The two launch sequences (set-up, one iteration) are captured as CUDA
-// graphs into *g_init / *g_iter on first use when those are not NULL (the
-// pointers and theta they read are fixed per buffer set; theta is read from
-// device memory) and replayed afterwards.
-cudaError_t pcg_quad(cudaStream_t st, const AsmArgs &A, int n_lr, const CmvLists &L,
-                     const FactorArgs &Fs, const Plan &PL, const int32_t *wpan_rhs,
-                     const int32_t *bh_blocks, const UpdRow *bupd, const UpdEntry *bents,
-                     double *panel, const double *b, int64_t n, double tol, int maxit,
-                     double *pool, double *q_out, int *iters, double *relres,
-                     cudaGraphExec_t *g_init, cudaGraphExec_t *g_iter);
+// One PCG solve C x = b (b: n doubles, cluster order) with q = b^T x:
+// operator launch_cmatvec, preconditioner the factor of Fs (task pointers set
+// to the right-hand-side lists) applied through the right-hand-side panel
+// `panel` (overwritten); stops when |r| <= tol |b| or after maxit
+// iterations.  The set-up and one iteration are captured as CUDA graphs into
+// *g_init / *g_iter on first use when those are not NULL (the pointers and
+// theta they read are fixed per buffer set; theta is read from device
+// memory) and replayed afterwards.  host: 3 doubles of pinned memory for the
+// scalars read back.  pcg_start launches the set-up and the first iteration;
+// after each synchronisation of st, pcg_poll reads the residual and launches
+// the next iteration or the final dot (then *finished once q is in).  Several
+// solves on different streams can so run interleaved.
+struct PcgRun {
+  cudaStream_t st;
+  AsmArgs A;
+  int n_lr;
+  CmvLists L;
+  FactorArgs Fs;
+  const Plan *PL;
+  const int32_t *wpan_rhs, *bh_blocks;
+  const UpdRow *bupd;
+  const UpdEntry *bents;
+  double *panel;
+  const double *b;
+  int64_t n;
+  double tol;
+  int maxit;
+  double *pool;
+  double *host;
+  cudaGraphExec_t *g_init, *g_iter;
+  // results
+  int it = 0, state = 0;
+  double rel = 1.0, q = 0.0;
+};
+cudaError_t pcg_start(PcgRun &R);
+cudaError_t pcg_poll(PcgRun &R, bool *finished);
+cudaError_t pcg_quad(PcgRun &R);   // start, then synchronise and poll until finished
 
 }  // namespace hmle

@@ -1,7 +1,7 @@
 // a14 (mixed form): the quadratic form Z^T C~^{-1} Z won back to FP64
 // accuracy by preconditioned conjugate gradients.  The operator is the FP64
-// H-matrix of C (dense near-field entries generated from the Matern table,
-// admissible blocks as their ACA factors U V^T); the preconditioner is the
+// H-matrix of C (the assembled dense near-field blocks, admissible blocks as
+// their ACA factors U V^T); the preconditioner is the
 // H-Cholesky factor of the mixed form, applied as a forward and a backward
 // sweep (M^{-1} = L~^{-T} L~^{-1}).  Everything is in cluster order.
 //
@@ -59,16 +59,15 @@ __global__ void __launch_bounds__(kThreadsMv) k_cmv_rows(AsmArgs A, const int32_
   const int I = blockIdx.x;
   const int I0 = leaf_beg[I], I1 = leaf_beg[I + 1];
   const int kc = A.kc;
-  const double inv_ell = A.thd->inv_ell, sigma2 = A.thd->sigma2, tau2 = A.thd->tau2;
   for (int i = I0 + threadIdx.x; i < I1; i += blockDim.x) {
     double acc = 0.0;
     for (int q = row0[I]; q < row0[I + 1]; ++q) {
       const int blk = rblocks[q];
       const BlockDesc B = A.blocks[blk];
       const int s = lr_slot[blk];
-      if (s < 0) {
-        for (int j = B.cbeg; j < B.cend; ++j)
-          acc = fma(cov_entry(A.tab, A.xyz, A.n, A.d, i, j, inv_ell, sigma2, tau2), x[j], acc);
+      if (s < 0) {   // dense: row i - rbeg of the stored block
+        const double *Cb = A.Cd + B.off_d + (i - B.rbeg);
+        for (int j = 0; j < B.cend - B.cbeg; ++j) acc = fma(Cb[(int64_t)j * A.b], x[B.cbeg + j], acc);
       } else {
         const int m = B.rend - B.rbeg, k = A.rank_c[blk];
         const double *U = A.uc + B.off_uc;
@@ -80,9 +79,9 @@ __global__ void __launch_bounds__(kThreadsMv) k_cmv_rows(AsmArgs A, const int32_
       const int blk = cblocks[q];
       const BlockDesc B = A.blocks[blk];
       const int s = lr_slot[blk];
-      if (s < 0) {
-        for (int j = B.rbeg; j < B.rend; ++j)
-          acc = fma(cov_entry(A.tab, A.xyz, A.n, A.d, j, i, inv_ell, sigma2, tau2), x[j], acc);
+      if (s < 0) {   // dense, transposed: column i - cbeg of the stored block
+        const double *Cb = A.Cd + B.off_d + (int64_t)(i - B.cbeg) * A.b;
+        for (int j = 0; j < B.rend - B.rbeg; ++j) acc = fma(Cb[j], x[B.rbeg + j], acc);
       } else {
         const int p = B.cend - B.cbeg, k = A.rank_c[blk];
         const double *V = A.uc + B.off_vc;
@@ -207,60 +206,82 @@ cudaError_t run_seq(cudaStream_t st, cudaGraphExec_t *g, Seq seq) {
 
 }  // namespace
 
-cudaError_t pcg_quad(cudaStream_t st, const AsmArgs &A, int n_lr, const CmvLists &L,
-                     const FactorArgs &Fs, const Plan &PL, const int32_t *wpan_rhs,
-                     const int32_t *bh_blocks, const UpdRow *bupd, const UpdEntry *bents,
-                     double *panel, const double *b, int64_t n, double tol, int maxit,
-                     double *pool, double *q_out, int *iters, double *relres,
-                     cudaGraphExec_t *g_init, cudaGraphExec_t *g_iter) {
-  const PcgBufs B = carve(pool, n, n_lr, A.kc, PL);
-  // x = 0, r = b, z = M^{-1} r, p = z, sc[0] = r.z, sc[6] = b.b
-  cudaError_t e = run_seq(st, g_init, [&] {
-    cudaMemsetAsync(B.x, 0, sizeof(double) * n, st);
-    cudaMemcpyAsync(B.r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-    precond(st, Fs, PL, wpan_rhs, bh_blocks, bupd, bents, panel, B.r, B.z, B.hbuf, n);
-    cudaMemcpyAsync(B.p, B.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-    dot(st, B.r, B.z, n, B.part, B.sc + 0);
-    dot(st, b, b, n, B.part, B.sc + 6);
+namespace {
+
+cudaError_t launch_iteration(PcgRun &R) {
+  const PcgBufs B = carve(R.pool, R.n, R.n_lr, R.A.kc, *R.PL);
+  cudaStream_t st = R.st;
+  const int64_t n = R.n;
+  // one iteration; the preconditioner of the next one runs even when this
+  // one converges (its result is then unused)
+  cudaError_t e = run_seq(st, R.g_iter, [&] {
+    launch_cmatvec(st, R.A, R.n_lr, R.L, B.p, B.t, B.qv);
+    dot(st, B.p, B.qv, n, B.part, B.sc + 1);
+    k_pcg_alpha<<<1, 1, 0, st>>>(B.sc);
+    k_pcg_xr<<<grid1(n), 256, 0, st>>>(B.x, B.r, B.p, B.qv, B.sc, n);
+    dot(st, B.r, B.r, n, B.part, B.sc + 5);
+    precond(st, R.Fs, *R.PL, R.wpan_rhs, R.bh_blocks, R.bupd, R.bents, R.panel, B.r, B.z, B.hbuf, n);
+    dot(st, B.r, B.z, n, B.part, B.sc + 3);
+    k_pcg_beta<<<1, 1, 0, st>>>(B.sc);
+    k_pcg_p<<<grid1(n), 256, 0, st>>>(B.p, B.z, B.sc, n);
   });
   if (e != cudaSuccess) return e;
-  double h[2];
-  e = cudaMemcpyAsync(h, B.sc + 6, sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return e;
-  const double bb = h[0];
-  int it = 0;
-  double rel = 1.0;
-  while (it < maxit) {
-    // one iteration; the preconditioner of the next one runs even when this
-    // one converges (its result is then unused)
-    e = run_seq(st, g_iter, [&] {
-      launch_cmatvec(st, A, n_lr, L, B.p, B.t, B.qv);
-      dot(st, B.p, B.qv, n, B.part, B.sc + 1);
-      k_pcg_alpha<<<1, 1, 0, st>>>(B.sc);
-      k_pcg_xr<<<grid1(n), 256, 0, st>>>(B.x, B.r, B.p, B.qv, B.sc, n);
-      dot(st, B.r, B.r, n, B.part, B.sc + 5);
-      precond(st, Fs, PL, wpan_rhs, bh_blocks, bupd, bents, panel, B.r, B.z, B.hbuf, n);
-      dot(st, B.r, B.z, n, B.part, B.sc + 3);
-      k_pcg_beta<<<1, 1, 0, st>>>(B.sc);
-      k_pcg_p<<<grid1(n), 256, 0, st>>>(B.p, B.z, B.sc, n);
-    });
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(h, B.sc + 5, sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return e;
-    ++it;
-    rel = bb > 0.0 ? std::sqrt(h[0] / bb) : 0.0;
-    if (!(rel > tol)) break;   // converged (or not finite: stop and report it)
+  return cudaMemcpyAsync(R.host + 1, B.sc + 5, sizeof(double), cudaMemcpyDeviceToHost, st);
+}
+
+}  // namespace
+
+cudaError_t pcg_start(PcgRun &R) {
+  const PcgBufs B = carve(R.pool, R.n, R.n_lr, R.A.kc, *R.PL);
+  cudaStream_t st = R.st;
+  const int64_t n = R.n;
+  R.it = 0;
+  R.rel = 1.0;
+  R.state = 0;
+  // x = 0, r = b, z = M^{-1} r, p = z, sc[0] = r.z, sc[6] = b.b
+  cudaError_t e = run_seq(st, R.g_init, [&] {
+    cudaMemsetAsync(B.x, 0, sizeof(double) * n, st);
+    cudaMemcpyAsync(B.r, R.b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    precond(st, R.Fs, *R.PL, R.wpan_rhs, R.bh_blocks, R.bupd, R.bents, R.panel, B.r, B.z, B.hbuf, n);
+    cudaMemcpyAsync(B.p, B.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    dot(st, B.r, B.z, n, B.part, B.sc + 0);
+    dot(st, R.b, R.b, n, B.part, B.sc + 6);
+  });
+  if (e == cudaSuccess) e = cudaMemcpyAsync(R.host + 0, B.sc + 6, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && R.maxit > 0) e = launch_iteration(R);
+  return e;
+}
+
+cudaError_t pcg_poll(PcgRun &R, bool *finished) {
+  *finished = false;
+  if (R.state == 2) { *finished = true; return cudaSuccess; }
+  const PcgBufs B = carve(R.pool, R.n, R.n_lr, R.A.kc, *R.PL);
+  if (R.state == 1) {   // the final dot has completed
+    R.q = R.host[2];
+    R.state = 2;
+    *finished = true;
+    return cudaGetLastError();
   }
-  dot(st, b, B.x, n, B.part, B.sc + 7);
-  e = cudaMemcpyAsync(h, B.sc + 7, sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return e;
-  *q_out = h[0];
-  *iters = it;
-  *relres = rel;
-  return cudaGetLastError();
+  if (R.maxit > 0) {    // an iteration has completed
+    ++R.it;
+    const double bb = R.host[0];
+    R.rel = bb > 0.0 ? std::sqrt(R.host[1] / bb) : 0.0;
+  }
+  if (R.it < R.maxit && R.rel > R.tol) return launch_iteration(R);
+  // converged, out of iterations or not finite: q = b.x
+  dot(R.st, R.b, B.x, R.n, B.part, B.sc + 7);
+  R.state = 1;
+  return cudaMemcpyAsync(R.host + 2, B.sc + 7, sizeof(double), cudaMemcpyDeviceToHost, R.st);
+}
+
+cudaError_t pcg_quad(PcgRun &R) {
+  cudaError_t e = pcg_start(R);
+  bool fin = false;
+  while (e == cudaSuccess && !fin) {
+    e = cudaStreamSynchronize(R.st);
+    if (e == cudaSuccess) e = pcg_poll(R, &fin);
+  }
+  return e;
 }
 
 }  // namespace hmle

@@ -68,7 +68,7 @@ class EvalInfo(C.Structure):
                 ("max_rank_c", C.c_int32), ("max_rank_l", C.c_int32),
                 ("mean_rank_l", C.c_double), ("status", C.c_int32),
                 ("kernel_launches", C.c_int64), ("pcg_iters", C.c_int32),
-                ("pcg_relres", C.c_double)]
+                ("pcg_relres", C.c_double), ("flops", C.c_double)]
 
 
 _LIB = None

@@ -1,6 +1,7 @@
 """Per-kernel time and algorithmic FP64 throughput of one evaluation.
 
     python -m paper_2104_07146_gb300.profile_kernels [--n 65536] [--leaf 64] [--eps 1e-6] [--nu 0.5]
+                                                     [--precision 0|1] [--single]
 
 For every kernel kind of the factorisation sweep, one evaluation is run with
 that kernel's launches bracketed by CUDA events on their own stream
@@ -29,10 +30,14 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--nu", type=float, default=0.5)
     ap.add_argument("--leaf-lowrank", type=int, default=0)
+    ap.add_argument("--precision", type=int, default=0, help="0 FP64, 1 mixed FP32 + PCG")
+    ap.add_argument("--single", action="store_true",
+                    help="one warm-up and one timed evaluation only (for an external profiler)")
     a = ap.parse_args()
     ctx = hmle.Context()
     locs = synth.medium_locations(a.n)
-    tree = hmle.Tree(ctx, locs, leaf_size=a.leaf, aca_eps=a.eps, leaf_lowrank=a.leaf_lowrank)
+    tree = hmle.Tree(ctx, locs, leaf_size=a.leaf, aca_eps=a.eps, leaf_lowrank=a.leaf_lowrank,
+                     precision=a.precision)
     Z = synth.normal(7, a.n)
     th = (0.05, a.nu, 1.0, 1e-3)
     tree.loglik(th, Z)
@@ -40,6 +45,8 @@ def main():
     ll, info = tree.loglik(th, Z)
     wall = time.time() - t0
     print("n %d  one evaluation %.3f s  %d kernel launches  L = %.6f" % (a.n, wall, info.kernel_launches, ll))
+    if a.single:
+        return
     rows, tot = [], 0.0
     for name in KERNELS:
         p = hmle.Profiler(ctx, name)
