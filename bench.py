@@ -247,10 +247,85 @@ def run_gpu(args):
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample_n)
+    if not args.no_fit:
+        out["fit"] = fit_small(ctx, not args.no_cpu_baseline)
+    if args.forms:
+        out["forms"] = other_forms(ctx, locs, Z, Zd, thetas, args.batch, value)
     print(json.dumps(out))
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+SMALL = dict(n=2000, theta=(0.1, 0.5, 1.0, 0.01), theta0=(0.2, 1.0, 0.5, 0.05), leaf=32, eps=1e-8)
+
+
+def fit_small(ctx, with_oracle):
+    """The MLE of the small configuration: n = 2000 uniform points, Z = L xi
+    (dense factor of C at theta), Nelder-Mead of all 4 parameters from theta0
+    (Sec. 2; tolerance 1e-4, at most 400 iterations); the oracle's own fit of
+    the same field timed beside it on the host cores."""
+    from paper_2104_07146_gb300 import hmle, synth
+    import oracle
+    c = SMALL
+    locs = synth.locations_uniform(c["n"], 2, seed=1000)
+    Z = oracle.simulate(locs, c["theta"], synth.normal(1001, c["n"]))
+    tree = hmle.Tree(ctx, locs, leaf_size=c["leaf"], aca_eps=c["eps"], max_rank=48, oversample=16)
+    t0 = time.time()
+    th, ll, it, nev, st = tree.fit(Z, c["theta0"])
+    dt = time.time() - t0
+    out = {"config": "small: n=2000 uniform, theta=(0.1, 0.5, 1, 0.01), Z = L xi, leaf 32, "
+                     "eps 1e-8, Nelder-Mead from (0.2, 1, 0.5, 0.05)",
+           "gpu_s": dt, "iterations": it, "evaluations": nev, "status": st,
+           "theta_hat": th, "loglik_hat": ll,
+           "loglik_hat_oracle": oracle.loglik_dense(locs, Z, th)[0]}
+    if with_oracle:
+        t0 = time.time()
+        th_c, ll_c, it_c, nev_c = oracle.fit(locs, Z, c["theta0"])
+        out["cpu_oracle"] = {"s": time.time() - t0, "iterations": it_c, "evaluations": nev_c,
+                             "theta_hat": th_c, "loglik_hat": ll_c, "cores": os.cpu_count()}
+    tree.close()
+    return out
+
+
+def other_forms(ctx, locs, Z, Zd, thetas, B, fp64_value):
+    """The mixed-precision and multi-instance batched forms on the same GPU,
+    reported against the plain FP64 batched form of this run."""
+    import torch
+    from paper_2104_07146_gb300 import hmle, synth
+    w = WORKLOAD
+    res = {"fp64_batched_evals_per_s": fp64_value}
+    tm = hmle.Tree(ctx, locs, leaf_size=w["leaf"], eta=w["eta"], aca_eps=w["eps"], precision=1)
+    tm.loglik_batch(thetas, Zd, concurrency=B)                     # buffers, graphs
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ll_m, st = tm.loglik_batch(thetas, Zd, concurrency=B)
+    dt = time.time() - t0
+    ll1, info = tm.loglik(thetas[0], Zd)
+    res["mixed_fp32_pcg"] = {"evals_per_s": B / dt, "pcg_iters": info.pcg_iters,
+                             "pcg_relres": info.pcg_relres, "loglik": ll1}
+    tm.close()
+    # multi-instance: 8 fields of uneven n (2-D and 3-D), 4 theta each, one call
+    fields = []
+    for i in range(8):
+        n = int(2048 * 2 ** (4 * synth.uniform(500 + i, 1)[0]))      # log-uniform in [2048, 32768]
+        d = 2 if i % 2 == 0 else 3
+        pts = (synth.locations_uniform(n, 2, seed=600 + i) if d == 2
+               else synth.uniform(700 + i, 3 * n).reshape(n, 3))
+        fields.append((hmle.Tree(ctx, pts, leaf_size=64, aca_eps=1e-6), synth.normal(800 + i, n), n, d))
+    tasks = [(t, (0.05 + 0.02 * k, 0.5 + 0.2 * k, 1.0, 1e-3), z) for (t, z, n, d) in fields
+             for k in range(4)]
+    ctx.loglik_multi(tasks, concurrency=16)
+    t0 = time.time()
+    ll, st = ctx.loglik_multi(tasks, concurrency=16)
+    dt = time.time() - t0
+    res["multi_instance"] = {"fields": [(n, d) for (_, _, n, d) in fields], "tasks": len(tasks),
+                             "evals_per_s": len(tasks) / dt, "points_evals_per_s":
+                             sum(n for (_, _, n, _) in fields) * 4 / dt,
+                             "all_ok": bool(all(x == 0 for x in st))}
+    for t, _, _, _ in fields:
+        t.close()
+    return res
 
 
 def batch_thetas(theta, B):
@@ -328,6 +403,9 @@ def main():
     ap.add_argument("--batch", type=int, default=16,
                     help="concurrent theta evaluations per step (hmle_loglik_batch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fit", action="store_true", help="skip the small-configuration MLE fit")
+    ap.add_argument("--forms", action="store_true",
+                    help="also report the mixed-precision and multi-instance batched forms")
     ap.add_argument("--roofline-kernel", default="k_rows",
                     help="sweep kernel whose launches are timed for the roofline line")
     args = ap.parse_args()

@@ -397,6 +397,17 @@ hmle_status hmle_mlp_train(hmle_ctx *ctx, hmle_mlp *mlp, const float *feats, con
                            int32_t m, int32_t epochs, int32_t batch, float lr, uint64_t seed,
                            float *loss_first, float *loss_last);
 
+/* Failure-detection self-test of the bounded device waits (no counterpart in
+ * the paper).  The persistent sweeps of the solves synchronise their CTAs with
+ * a grid barrier whose waits are bounded; a wait that runs out sets an error
+ * word, every CTA leaves, and the call reports HMLE_ERR_TIMEOUT with the
+ * context still usable.  This runs one such barrier: extra = 0 (every CTA
+ * arrives) returns HMLE_OK; extra = 1 expects one more arrival than there are
+ * CTAs, so the wait must run out (after about a quarter of a second) and the
+ * call returns HMLE_ERR_TIMEOUT.  *err_word (may be NULL) receives the error
+ * word.  Errors: INVALID_ARG (extra not 0 or 1), OOM, CUDA. */
+hmle_status hmle_selftest_barrier(hmle_ctx *ctx, int32_t extra, uint32_t *err_word);
+
 /* Measurement support (no counterpart in the paper).  Select one kernel of
  * the factorisation sweep by name (e.g. "k_tsqr_final", "k_dense_pair"; NULL
  * switches timing off).  While selected, every launch of that kernel is

@@ -61,6 +61,7 @@ struct DevPlan {
   UpdRow *bupd = nullptr;
   UpdEntry *bents = nullptr;
   int32_t *mvt_row0 = nullptr, *mvt_blocks = nullptr, *lr_slot = nullptr;
+  int32_t *diag = nullptr, *ht_rhs0 = nullptr, *ur_rhs0 = nullptr, *bh0 = nullptr, *bupd0 = nullptr;
   int64_t bytes = 0;
 };
 
@@ -78,6 +79,8 @@ struct hmle_tree {
   Work *work = nullptr;
   std::vector<Work *> pool;  // evaluation buffers of hmle_loglik_batch
   bool graphs = true;        // replay the sweep as a captured CUDA graph
+  SolvePlan sp{};            // device task lists of the persistent sweeps on one vector
+  bool coop = false;         // the device supports cooperative launches
 };
 
 struct hmle_hmatrix {
@@ -174,7 +177,8 @@ void free_devplan(cudaStream_t st, DevPlan &d) {
                   d.dpair_tr, d.dpair_tc, d.wpan,
                   d.hts, d.urows, d.uents, d.leaf_beg, d.lr_ids, d.dense_ids, d.mv_row0,
                   d.mv_blocks, d.hts_rhs, d.urows_rhs, d.uents_rhs, d.wpan_rhs, d.bh_blocks,
-                  d.bupd, d.bents, d.mvt_row0, d.mvt_blocks, d.lr_slot};
+                  d.bupd, d.bents, d.mvt_row0, d.mvt_blocks, d.lr_slot, d.diag, d.ht_rhs0,
+                  d.ur_rhs0, d.bh0, d.bupd0};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, st);
   d = DevPlan{};
@@ -329,7 +333,7 @@ hmle_status mixed_prepare(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix 
   int hmax = 1;
   for (int K = 0; K < P.nleaf; ++K) hmax = std::max(hmax, P.bh0[K + 1] - P.bh0[K]);
   if (!f->pcg) {
-    const int64_t words = t->n + pcg_words(t->n, nlr, P.kc, hmax * P.kcap);
+    const int64_t words = t->n + pcg_words(t->n, nlr, P.kc, hmax * P.kcap) + 2;
     cudaError_t e = cudaMallocAsync(&f->pcg, sizeof(double) * words, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pcg workspace");
   }
@@ -357,12 +361,17 @@ hmle_status mixed_prepare(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix 
   R.bupd = t->dp.bupd; R.bents = t->dp.bents; R.panel = f->W + rp.off; R.b = b; R.n = t->n;
   R.tol = t->opts.pcg_tol; R.maxit = t->opts.pcg_max_iter; R.pool = f->pcg + t->n;
   R.host = f->pcg_host;
-  R.g_init = t->graphs ? &f->pcg_init : nullptr;
-  R.g_iter = t->graphs ? &f->pcg_iter : nullptr;
+  // the persistent sweeps (one cooperative launch each) when the device has
+  // them; the CUDA graphs otherwise replay the launch-by-launch sweeps
+  R.SP = t->coop ? &t->sp : nullptr;
+  R.bar = reinterpret_cast<unsigned *>(f->pcg + t->n + pcg_words(t->n, nlr, P.kc, hmax * P.kcap));
+  R.g_init = (t->graphs && !R.SP) ? &f->pcg_init : nullptr;
+  R.g_iter = (t->graphs && !R.SP) ? &f->pcg_iter : nullptr;
   return HMLE_OK;
 }
 
 hmle_status mixed_result(hmle_ctx *ctx, const hmle_tree *t, hmle_hfactor *f, const PcgRun &R) {
+  if (R.timed_out) return fail(ctx, HMLE_ERR_TIMEOUT, "PCG: a barrier wait of the persistent sweep ran out");
   f->quad = R.q;
   f->pcg_iters = R.it;
   f->pcg_relres = R.rel;
@@ -707,6 +716,8 @@ hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n, int32_
   UP(hts_rhs, P.hts_rhs); UP(urows_rhs, P.urows_rhs); UP(uents_rhs, P.uents_rhs);
   UP(bh_blocks, P.bh_blocks); UP(bupd, P.bupd); UP(bents, P.bents);
   UP(mvt_row0, P.mvt_row0); UP(mvt_blocks, P.mvt_blocks);
+  UP(diag, P.diag_of_leaf); UP(ht_rhs0, P.ht_rhs0); UP(ur_rhs0, P.ur_rhs0); UP(bh0, P.bh0);
+  UP(bupd0, P.bupd0);
   {
     std::vector<int32_t> slot(std::max<size_t>(P.blocks.size(), 1), -1);
     for (size_t q = 0; q < t->lr_ids.size(); ++q) slot[t->lr_ids[q]] = (int32_t)q;
@@ -719,6 +730,14 @@ hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n, int32_
 #undef UP
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { hmle_tree_destroy(t); return cuda_fail(ctx, e, "plan upload"); }
+  {
+    const DevPlan &d = t->dp;
+    t->sp = SolvePlan{P.nleaf, d.diag, d.ht_rhs0, d.ur_rhs0, d.hts_rhs, d.urows_rhs, d.uents_rhs,
+                      d.bh0, d.bupd0, d.bh_blocks, d.bupd, d.bents};
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->dev);
+    t->coop = coop != 0;
+  }
   *out = t;
   return HMLE_OK;
 }
@@ -914,8 +933,11 @@ hmle_status hmle_solve(hmle_ctx *ctx, const hmle_hfactor *fc, const double *Z, d
   if (s != HMLE_OK) return s;
   int maxh = 1;
   for (int K = 0; K < P.nleaf; ++K) maxh = std::max(maxh, P.bh0[K + 1] - P.bh0[K]);
+  unsigned *bar = nullptr;
   CK(cudaMallocAsync(&xo, sizeof(double) * t->n, st), "alloc");
   CK(cudaMallocAsync(&hb, sizeof(double) * (size_t)maxh * P.kcap, st), "alloc");
+  CK(cudaMallocAsync(&bar, 4 * sizeof(unsigned), st), "alloc");
+  CK(cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st), "memset");
   const PanelDesc &rp = P.panels[P.rhs_panel];
   double *w = f->W + rp.off;
   launch_permute_in(st, zd, t->T.perm, t->n, w);
@@ -923,15 +945,30 @@ hmle_status hmle_solve(hmle_ctx *ctx, const hmle_hfactor *fc, const double *Z, d
   F.hts = t->dp.hts_rhs;
   F.urows = t->dp.urows_rhs;
   F.uents = t->dp.uents_rhs;
-  launch_solve(st, F, P, t->dp.wpan_rhs);                                  // w = L^{-1} P Z
-  launch_finalize(st, f->ldp, P.nleaf, w, t->n, f->out);
-  launch_backward(st, F, P, w, t->dp.bh_blocks, t->dp.bupd, t->dp.bents, hb);  // v = L^{-T} w
+  if (t->coop) {   // one cooperative launch per sweep
+    CK(persistent_solve(st, F, t->sp, w, F.ws, bar, false), "forward sweep");   // w = L^{-1} P Z
+    launch_finalize(st, f->ldp, P.nleaf, w, t->n, f->out);
+    CK(persistent_solve(st, F, t->sp, w, hb, bar, true), "backward sweep");     // v = L^{-T} w
+  } else {
+    launch_solve(st, F, P, t->dp.wpan_rhs);
+    launch_finalize(st, f->ldp, P.nleaf, w, t->n, f->out);
+    launch_backward(st, F, P, w, t->dp.bh_blocks, t->dp.bupd, t->dp.bents, hb);
+  }
   launch_permute_out(st, w, t->T.perm, t->n, xo);
   double out[2];
+  unsigned berr = 0;
   CK(cudaGetLastError(), "solve launch");
   CK(cudaMemcpyAsync(X, xo, sizeof(double) * t->n, cudaMemcpyDefault, st), "copy");
   CK(cudaMemcpyAsync(out, f->out, sizeof(out), cudaMemcpyDeviceToHost, st), "copy");
+  CK(cudaMemcpyAsync(&berr, bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "copy");
   CK(cudaStreamSynchronize(st), "sync");
+  cudaFreeAsync(bar, st);
+  if (berr) {
+    cudaFreeAsync(xo, st);
+    cudaFreeAsync(hb, st);
+    if (owned) cudaFreeAsync(zd, st);
+    return fail(ctx, HMLE_ERR_TIMEOUT, "solve: a barrier wait of the persistent sweep ran out");
+  }
   f->quad = out[1];                   // the quadratic form now belongs to this Z
   f->has_rhs = true;
   if (owned) cudaFreeAsync(zd, st);

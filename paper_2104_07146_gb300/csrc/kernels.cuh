@@ -164,6 +164,27 @@ int64_t pcg_words(int64_t n, int n_lr, int kc, int hmax);
 // the factor of Fs (F's task pointers set to the right-hand-side lists) applied
 // through the right-hand-side panel `panel` (overwritten).  b: n doubles,
 // cluster order.  Stops when |r| <= tol |b| or after maxit iterations.
+// Device copies of the per-leaf task lists of the two sweeps on one vector.
+struct SolvePlan {
+  int nleaf;
+  const int32_t *diag;                    // diagonal block of each leaf
+  const int32_t *ht0, *ur0;               // forward: per leaf ranges (nleaf + 1)
+  const HTask *hts;                       // forward: right-hand-side panel tasks
+  const UpdRow *urows;
+  const UpdEntry *uents;
+  const int32_t *bh0, *bu0;               // backward: per leaf ranges (nleaf + 1)
+  const int32_t *bblk;                    // backward: low-rank blocks per leaf
+  const UpdRow *bupd;
+  const UpdEntry *bents;
+};
+// w <- L~^{-1} w (backward = false; h = the factor's workspace) or
+// w <- L~^{-T} w (backward = true; h = kcap doubles per low-rank block of the
+// largest leaf list) in one cooperative launch; bar: 3 unsigned of device
+// memory for the grid barrier, bar[2] zeroed by the caller beforehand
+// (bar[2] != 0 afterwards: a barrier wait ran out).
+cudaError_t persistent_solve(cudaStream_t st, const FactorArgs &F, const SolvePlan &P, double *w,
+                             double *h, unsigned *bar, bool backward);
+
 // One PCG solve C x = b (b: n doubles, cluster order) with q = b^T x:
 // operator launch_cmatvec, preconditioner the factor of Fs (task pointers set
 // to the right-hand-side lists) applied through the right-hand-side panel
@@ -178,6 +199,8 @@ int64_t pcg_words(int64_t n, int n_lr, int kc, int hmax);
 // solves on different streams can so run interleaved.
 struct PcgRun {
   cudaStream_t st;
+  const SolvePlan *SP;      // when not NULL: preconditioner by the persistent sweeps
+  unsigned *bar;            // their barrier words (3 unsigned, device)
   AsmArgs A;
   int n_lr;
   CmvLists L;
@@ -197,6 +220,7 @@ struct PcgRun {
   // results
   int it = 0, state = 0;
   double rel = 1.0, q = 0.0;
+  bool timed_out = false;   // a barrier wait of the persistent sweeps ran out
 };
 cudaError_t pcg_start(PcgRun &R);
 cudaError_t pcg_poll(PcgRun &R, bool *finished);

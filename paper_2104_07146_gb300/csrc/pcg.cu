@@ -179,10 +179,16 @@ PcgBufs carve(double *pool, int64_t n, int n_lr, int kc, const Plan &PL) {
 // z = M^{-1} r = L~^{-T} L~^{-1} r through the right-hand-side panel
 void precond(cudaStream_t st, const FactorArgs &Fs, const Plan &PL, const int32_t *wpan_rhs,
              const int32_t *bh_blocks, const UpdRow *bupd, const UpdEntry *bents, double *panel,
-             const double *r, double *z, double *hbuf, int64_t n) {
+             const double *r, double *z, double *hbuf, int64_t n, const SolvePlan *SP,
+             unsigned *bar) {
   cudaMemcpyAsync(panel, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-  launch_solve(st, Fs, PL, wpan_rhs);
-  launch_backward(st, Fs, PL, panel, bh_blocks, bupd, bents, hbuf);
+  if (SP) {
+    persistent_solve(st, Fs, *SP, panel, Fs.ws, bar, false);
+    persistent_solve(st, Fs, *SP, panel, hbuf, bar, true);
+  } else {
+    launch_solve(st, Fs, PL, wpan_rhs);
+    launch_backward(st, Fs, PL, panel, bh_blocks, bupd, bents, hbuf);
+  }
   cudaMemcpyAsync(z, panel, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
 }
 
@@ -220,12 +226,18 @@ cudaError_t launch_iteration(PcgRun &R) {
     k_pcg_alpha<<<1, 1, 0, st>>>(B.sc);
     k_pcg_xr<<<grid1(n), 256, 0, st>>>(B.x, B.r, B.p, B.qv, B.sc, n);
     dot(st, B.r, B.r, n, B.part, B.sc + 5);
-    precond(st, R.Fs, *R.PL, R.wpan_rhs, R.bh_blocks, R.bupd, R.bents, R.panel, B.r, B.z, B.hbuf, n);
+    precond(st, R.Fs, *R.PL, R.wpan_rhs, R.bh_blocks, R.bupd, R.bents, R.panel, B.r, B.z, B.hbuf, n,
+            R.SP, R.bar);
     dot(st, B.r, B.z, n, B.part, B.sc + 3);
     k_pcg_beta<<<1, 1, 0, st>>>(B.sc);
     k_pcg_p<<<grid1(n), 256, 0, st>>>(B.p, B.z, B.sc, n);
   });
   if (e != cudaSuccess) return e;
+  if (R.SP) {
+    e = cudaMemcpyAsync(reinterpret_cast<unsigned *>(R.host + 3), R.bar + 2, sizeof(unsigned),
+                        cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+  }
   return cudaMemcpyAsync(R.host + 1, B.sc + 5, sizeof(double), cudaMemcpyDeviceToHost, st);
 }
 
@@ -238,11 +250,18 @@ cudaError_t pcg_start(PcgRun &R) {
   R.it = 0;
   R.rel = 1.0;
   R.state = 0;
+  R.timed_out = false;
+  *reinterpret_cast<unsigned *>(R.host + 3) = 0u;
+  if (R.SP) {
+    cudaError_t e0 = cudaMemsetAsync(R.bar, 0, 3 * sizeof(unsigned), st);
+    if (e0 != cudaSuccess) return e0;
+  }
   // x = 0, r = b, z = M^{-1} r, p = z, sc[0] = r.z, sc[6] = b.b
   cudaError_t e = run_seq(st, R.g_init, [&] {
     cudaMemsetAsync(B.x, 0, sizeof(double) * n, st);
     cudaMemcpyAsync(B.r, R.b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-    precond(st, R.Fs, *R.PL, R.wpan_rhs, R.bh_blocks, R.bupd, R.bents, R.panel, B.r, B.z, B.hbuf, n);
+    precond(st, R.Fs, *R.PL, R.wpan_rhs, R.bh_blocks, R.bupd, R.bents, R.panel, B.r, B.z, B.hbuf, n,
+            R.SP, R.bar);
     cudaMemcpyAsync(B.p, B.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
     dot(st, B.r, B.z, n, B.part, B.sc + 0);
     dot(st, R.b, R.b, n, B.part, B.sc + 6);
@@ -261,6 +280,12 @@ cudaError_t pcg_poll(PcgRun &R, bool *finished) {
     R.state = 2;
     *finished = true;
     return cudaGetLastError();
+  }
+  if (R.SP && *reinterpret_cast<volatile unsigned *>(R.host + 3) != 0u) {
+    R.timed_out = true;   // a persistent sweep gave up at a barrier: stop here
+    R.state = 2;
+    *finished = true;
+    return cudaSuccess;
   }
   if (R.maxit > 0) {    // an iteration has completed
     ++R.it;

@@ -1,0 +1,286 @@
+// a10-a11 as one persistent kernel each: the forward sweep w <- L~^{-1} w and
+// the backward sweep v <- L~^{-T} v on one vector (cluster order), for the
+// preconditioner of the PCG and for hmle_solve.
+//
+// The sweep launched kernel by kernel costs three small launches per leaf
+// (thousands per solve), and each launch carries a few microseconds of GPU
+// latency whatever its work.  Here one cooperative launch runs every leaf:
+// per leaf (in sweep order)
+//   A  the diagonal leaf's triangular solve (one warp of CTA 0),
+//   B  the coupling vectors of the leaf's low-rank blocks, one task per CTA
+//      (forward: h_A = W_A^T w[cols A] for the blocks whose columns end at
+//      the leaf; backward: h_A = U_A^T v[rows A] for those whose rows start
+//      there),
+//   C  the updates of the affected leaf rows (forward) or column leaves
+//      (backward), one leaf per CTA, each a fixed-order sum,
+// separated by grid barriers.  The vector and the coupling vectors change
+// during the launch, so they are read through L2 (ld.global.cg), never from
+// an SM's L1.  The barrier waits are bounded: a wait that
+// runs out sets an error word, every CTA then leaves at its next barrier,
+// and the host reports HMLE_ERR_TIMEOUT.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "hmle_internal.h"
+#include "kernels.cuh"
+
+namespace hmle {
+namespace {
+
+constexpr int kSolveThreads = 128;
+constexpr long long kBarrierSpins = 20000000;   // x 64 ns sleep: about 1.3 s
+
+// Grid barrier for a cooperative launch (all CTAs resident).  bar[0]:
+// arrivals, bar[1]: generation, bar[2]: error word.  Returns false once any
+// wait has run out (after `limit` polls).
+__device__ bool grid_barrier(unsigned *bar, unsigned nblk, long long limit = kBarrierSpins) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = bar + 1;
+    volatile unsigned *err = bar + 2;
+    const unsigned my = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblk - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == my && *err == 0u) {
+        if (++spins > limit) { atomicExch(bar + 2, 1u); break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile unsigned *)(bar + 2) == 0u;
+}
+
+// One warp solves L x = w (forward) or L^T x = w (backward) for the m <= 128
+// rows of a diagonal leaf, L = the b x b dense block at off (ld b); lanes own
+// rows lane, lane + 32, ...
+__device__ void leaf_trsv(const double *__restrict__ L, int b, int m, double *w, bool trans) {
+  const int lane = threadIdx.x & 31;
+  double x[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) x[q] = (lane + 32 * q < m) ? __ldcg(w + lane + 32 * q) : 0.0;
+  for (int s = 0; s < m; ++s) {
+    const int i = trans ? m - 1 - s : s;
+    const int owner = i & 31, slot = i >> 5;
+    double xi = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q == slot) xi = x[q];
+    xi = __shfl_sync(0xffffffffu, xi, owner) / L[i + (int64_t)i * b];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = lane + 32 * q;
+      if (r == i) x[q] = xi;
+      else if (r < m && (trans ? r < i : r > i))
+        x[q] = fma(-(trans ? L[i + (int64_t)r * b] : L[r + (int64_t)i * b]), xi, x[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (lane + 32 * q < m) w[lane + 32 * q] = x[q];
+}
+
+struct SolveArgs {
+  FactorArgs F;             // the factor (pools, blocks, panels, ranks)
+  const int32_t *diag;      // diagonal block of each leaf
+  const int32_t *s0;        // per leaf: range of B tasks (nleaf + 1)
+  const int32_t *u0;        // per leaf: range of C rows (nleaf + 1)
+  const HTask *hts;         // forward B tasks (right-hand-side panel)
+  const UpdRow *rows;       // forward / backward C rows
+  const UpdEntry *ents;     // their entries
+  const int32_t *bblk;      // backward B tasks: low-rank block ids
+  double *w;                // the vector
+  double *h;                // coupling vectors: forward at the tasks' own offsets (the
+                            // factor's workspace), backward kcap per task of a leaf
+  unsigned *bar;
+  int nleaf;
+};
+
+__global__ void __launch_bounds__(kSolveThreads) k_solve_fwd(SolveArgs S) {
+  const FactorArgs &F = S.F;
+  const unsigned G = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int K = 0; K < S.nleaf; ++K) {
+    if (blockIdx.x == 0 && warp == 0) {
+      const BlockDesc D = F.blocks[S.diag[K]];
+      leaf_trsv(F.D + D.off_d, F.b, D.rend - D.rbeg, S.w + D.rbeg, false);
+    }
+    if (!grid_barrier(S.bar, G)) return;
+    // B: h_A = W_A^T w[cols A], a warp per component
+    for (int t = S.s0[K] + blockIdx.x; t < S.s0[K + 1]; t += G) {
+      const HTask T = S.hts[t];
+      const BlockDesc A = F.blocks[T.a];
+      const PanelDesc PA = F.panels[A.panel];
+      const int lda = PA.rend - PA.rbeg, ka = F.rank_l[T.a], p = A.cend - A.cbeg;
+      const double *Wa = F.W + PA.off + (int64_t)A.slot * lda + (A.cbeg - PA.rbeg);
+      double *h = S.h + T.hoff;   // where the sweep's own task writes it
+      for (int i = warp; i < ka; i += nw) {
+        double s = 0.0;
+        for (int k = lane; k < p; k += 32) s = fma(Wa[k + (int64_t)i * lda], __ldcg(S.w + A.cbeg + k), s);
+        s = warp_sum(s);
+        if (lane == 0) h[i] = s;
+      }
+    }
+    if (!grid_barrier(S.bar, G)) return;
+    // C: w[I] -= sum over the row's entries, in order
+    for (int t = S.u0[K] + blockIdx.x; t < S.u0[K + 1]; t += G) {
+      const UpdRow R = S.rows[t];
+      const int I0 = F.leaf_beg[R.leaf], I1 = F.leaf_beg[R.leaf + 1];
+      for (int i = I0 + threadIdx.x; i < I1; i += blockDim.x) {
+        double acc = 0.0;
+        for (int q = R.e0; q < R.e1; ++q) {
+          const UpdEntry E = S.ents[q];
+          const BlockDesc A = F.blocks[E.a];
+          if (E.hoff < 0) {   // dense: D_A w[cols A]
+            const double *Dr = F.D + A.off_d + (i - A.rbeg);
+            for (int j = 0; j < A.cend - A.cbeg; ++j) acc = fma(Dr[(int64_t)j * F.b], __ldcg(S.w + A.cbeg + j), acc);
+          } else {            // low rank: U_A[i] h_A (h slot from the task list)
+            const double *U = F.U + A.off_u + (i - A.rbeg);
+            const int m = A.rend - A.rbeg;
+            const double *h = S.h + E.hoff;
+            for (int k = 0; k < F.rank_l[E.a]; ++k) acc = fma(U[(int64_t)k * m], __ldcg(h + k), acc);
+          }
+        }
+        S.w[i] = __ldcg(S.w + i) - acc;
+      }
+    }
+    if (!grid_barrier(S.bar, G)) return;
+  }
+}
+
+__global__ void __launch_bounds__(kSolveThreads) k_solve_bwd(SolveArgs S) {
+  const FactorArgs &F = S.F;
+  const unsigned G = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int K = S.nleaf - 1; K >= 0; --K) {
+    if (blockIdx.x == 0 && warp == 0) {
+      const BlockDesc D = F.blocks[S.diag[K]];
+      leaf_trsv(F.D + D.off_d, F.b, D.rend - D.rbeg, S.w + D.rbeg, true);
+    }
+    if (!grid_barrier(S.bar, G)) return;
+    // B: h_A = U_A^T v[rows A] for the low-rank blocks whose rows start at K
+    for (int t = S.s0[K] + blockIdx.x; t < S.s0[K + 1]; t += G) {
+      const int blk = S.bblk[t];
+      const BlockDesc A = F.blocks[blk];
+      const int m = A.rend - A.rbeg, ka = F.rank_l[blk];
+      const double *U = F.U + A.off_u;
+      double *h = S.h + (int64_t)(t - S.s0[K]) * F.kcap;
+      for (int i = warp; i < ka; i += nw) {
+        double s = 0.0;
+        for (int k = lane; k < m; k += 32) s = fma(U[k + (int64_t)i * m], __ldcg(S.w + A.rbeg + k), s);
+        s = warp_sum(s);
+        if (lane == 0) h[i] = s;
+      }
+    }
+    if (!grid_barrier(S.bar, G)) return;
+    // C: v[J] -= sum over the column leaf's entries, in order
+    for (int t = S.u0[K] + blockIdx.x; t < S.u0[K + 1]; t += G) {
+      const UpdRow R = S.rows[t];
+      const int J0 = F.leaf_beg[R.leaf], J1 = F.leaf_beg[R.leaf + 1];
+      for (int j = J0 + threadIdx.x; j < J1; j += blockDim.x) {
+        double acc = 0.0;
+        for (int q = R.e0; q < R.e1; ++q) {
+          const UpdEntry E = S.ents[q];
+          const BlockDesc A = F.blocks[E.a];
+          if (E.hoff < 0) {   // dense: D_A^T v[rows A], column j - cbeg
+            const double *Dc = F.D + A.off_d + (int64_t)(j - A.cbeg) * F.b;
+            for (int i = 0; i < A.rend - A.rbeg; ++i) acc = fma(Dc[i], __ldcg(S.w + A.rbeg + i), acc);
+          } else {            // low rank: W_A[j] h_A
+            const PanelDesc PA = F.panels[A.panel];
+            const int lda = PA.rend - PA.rbeg;
+            const double *Wr = F.W + PA.off + (int64_t)A.slot * lda + (j - PA.rbeg);
+            const double *h = S.h + E.hoff * F.kcap;
+            for (int k = 0; k < F.rank_l[E.a]; ++k) acc = fma(Wr[(int64_t)k * lda], __ldcg(h + k), acc);
+          }
+        }
+        S.w[j] = __ldcg(S.w + j) - acc;
+      }
+    }
+    if (!grid_barrier(S.bar, G)) return;
+  }
+}
+
+// failure-detection self-test: one barrier expecting `expect` arrivals
+__global__ void k_barrier_selftest(unsigned *bar, unsigned expect, long long limit) {
+  grid_barrier(bar, expect, limit);
+}
+
+int g_solve_grid = 0;
+
+int solve_grid() {
+  if (g_solve_grid == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_fwd, kSolveThreads, 0);
+    int per2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_solve_bwd, kSolveThreads, 0);
+    per = std::min(per, per2);
+    g_solve_grid = std::max(1, std::min(per, 2) * sms);
+  }
+  return g_solve_grid;
+}
+
+cudaError_t launch_coop(const void *fn, SolveArgs &S, cudaStream_t st) {
+  void *args[] = {&S};
+  return cudaLaunchCooperativeKernel(fn, dim3(solve_grid()), dim3(kSolveThreads), args, 0, st);
+}
+
+}  // namespace
+
+cudaError_t persistent_solve(cudaStream_t st, const FactorArgs &F, const SolvePlan &P, double *w,
+                             double *h, unsigned *bar, bool backward) {
+  SolveArgs S;
+  S.F = F;
+  S.diag = P.diag;
+  S.nleaf = P.nleaf;
+  S.w = w;
+  S.h = h;
+  S.bar = bar;
+  // arrivals and generation start at zero; the error word is kept (set to
+  // zero by the caller once), so a later sweep does not hide an earlier one's
+  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  if (!backward) {
+    S.s0 = P.ht0; S.u0 = P.ur0; S.hts = P.hts; S.rows = P.urows; S.ents = P.uents; S.bblk = nullptr;
+    return launch_coop((const void *)k_solve_fwd, S, st);
+  }
+  S.s0 = P.bh0; S.u0 = P.bu0; S.hts = nullptr; S.rows = P.bupd; S.ents = P.bents; S.bblk = P.bblk;
+  return launch_coop((const void *)k_solve_bwd, S, st);
+}
+
+}  // namespace hmle
+
+extern "C" __attribute__((visibility("hidden"))) cudaStream_t hmle_internal_ctx_stream(const hmle_ctx *ctx);
+
+extern "C" hmle_status hmle_selftest_barrier(hmle_ctx *ctx, int32_t extra, uint32_t *err_word) {
+  using namespace hmle;
+  if (!ctx || extra < 0 || extra > 1) return HMLE_ERR_INVALID_ARG;
+  cudaStream_t st = hmle_internal_ctx_stream(ctx);
+  unsigned *bar = nullptr;
+  unsigned h = 0;
+  cudaError_t e = cudaMallocAsync(&bar, 3 * sizeof(unsigned), st);
+  if (e != cudaSuccess) { cudaGetLastError(); return HMLE_ERR_OOM; }
+  e = cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st);
+  const int G = solve_grid();
+  unsigned expect = (unsigned)G + (unsigned)extra;
+  long long limit = 2000000;   // about a quarter of a second of polling
+  void *args[] = {&bar, &expect, &limit};
+  if (e == cudaSuccess)
+    e = cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, dim3(G), dim3(kSolveThreads), args, 0, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(bar, st);
+  cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { cudaGetLastError(); return HMLE_ERR_CUDA; }
+  if (err_word) *err_word = h;
+  return h ? HMLE_ERR_TIMEOUT : HMLE_OK;
+}

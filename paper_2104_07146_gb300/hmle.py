@@ -106,6 +106,7 @@ def lib():
             "hmle_solve": ([P, P, P, P], C.c_int),
             "hmle_loglik_multi": ([P, P, C.c_int32, C.c_int32, P, P], C.c_int),
             "hmle_theta_to_x": ([P, P], C.c_int),
+            "hmle_selftest_barrier": ([P, C.c_int32, P], C.c_int),
             "hmle_x_to_theta": ([P, P], C.c_int),
             "hmle_features": ([P, P, C.c_int64, C.c_int32, P, P], C.c_int),
             "hmle_mlp_nparams": ([], C.c_int32),
@@ -139,7 +140,7 @@ def exported_symbols():
             "hmle_hmatrix_matvec", "hmle_factor", "hmle_factor_destroy", "hmle_loglik",
             "hmle_loglik_eval", "hmle_fit", "hmle_matern_eval", "hmle_profile_select",
             "hmle_profile_read", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_loglik_multi", "hmle_autotune",
-            "hmle_theta_to_x", "hmle_x_to_theta", "hmle_features", "hmle_mlp_nparams",
+            "hmle_theta_to_x", "hmle_x_to_theta", "hmle_selftest_barrier", "hmle_features", "hmle_mlp_nparams",
             "hmle_mlp_create", "hmle_mlp_destroy", "hmle_mlp_set", "hmle_mlp_get",
             "hmle_mlp_forward", "hmle_mlp_grad", "hmle_mlp_adam_step", "hmle_mlp_train",
             "hmle_matern_eval_noalloc"]

@@ -150,6 +150,20 @@ def test_solve_matches_dense(ctx):
     assert np.isfinite(X2).all()
 
 
+def test_bounded_barrier_wait_reports_timeout(ctx):
+    # failure detection without a GPU fault: a grid barrier that one more CTA
+    # than exists should reach runs out of its bounded wait; the call reports
+    # TIMEOUT and the context keeps working
+    import ctypes as C
+    from paper_2104_07146_gb300 import hmle
+    word = C.c_uint32(7)
+    assert hmle.lib().hmle_selftest_barrier(ctx._h, 0, C.byref(word)) == 0 and word.value == 0
+    assert hmle.lib().hmle_selftest_barrier(ctx._h, 1, C.byref(word)) == 6 and word.value == 1
+    locs = synth.locations_uniform(500, 2, seed=77)
+    ll, _ = _tree(ctx, locs, leaf_size=32).loglik((0.1, 0.5, 1.0, 0.01), synth.normal(78, 500))
+    assert math.isfinite(ll)
+
+
 def test_non_spd_is_reported(ctx):
     from paper_2104_07146_gb300 import hmle
     locs = synth.locations_uniform(200, 2, seed=29)
