@@ -105,13 +105,37 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _dist():
+def _dist(backend="nccl"):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
         return None, 0, 1
     import torch.distributed as dist
-    dist.init_process_group("nccl")
+    dist.init_process_group(backend)
     return dist, dist.get_rank(), ws
+
+
+def reduce_max(dist, values, device="cpu"):
+    """The per-rank timings combined as their maximum over ranks (the slowest
+    replica sets the whole job's time); no-op on one process."""
+    if not dist:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_rate(ws, units_per_rank, ms_max):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return ws * units_per_rank / (ms_max / 1e3)
+
+
+def shard(n_tasks, rank, ws):
+    """The contiguous range of tasks (fields / theta points) of one rank when
+    a batched workload is split over ranks: no data exchange is needed."""
+    per, extra = divmod(n_tasks, ws)
+    lo = rank * per + min(rank, extra)
+    return lo, lo + per + (1 if rank < extra else 0)
 
 
 def _workload_inputs(n):
@@ -198,17 +222,14 @@ def run_gpu(args):
     torch.cuda.synchronize()
     ms_e2e = e2.elapsed_time(e3)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms, ms_e2e], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
+    ms, ms_e2e = reduce_max(dist, [ms, ms_e2e], device=f"cuda:{local}")
     if rank != 0:
         if dist:
             dist.barrier()
             dist.destroy_process_group()
         return
-    value = ws * args.steps * args.batch / (ms / 1e3)
-    e2e = ws * args.steps * args.batch / (ms_e2e / 1e3)
+    value = job_rate(ws, args.steps * args.batch, ms)
+    e2e = job_rate(ws, args.steps * args.batch, ms_e2e)
     achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] > 0 else None
     peaks = _peaks()
     out = {
@@ -258,6 +279,7 @@ def run_gpu(args):
 
 
 SMALL = dict(n=2000, theta=(0.1, 0.5, 1.0, 0.01), theta0=(0.2, 1.0, 0.5, 0.05), leaf=32, eps=1e-8)
+# (default rank capacity 32 and oversampling 8, as the small-configuration parity tests use)
 
 
 def fit_small(ctx, with_oracle):
@@ -270,7 +292,7 @@ def fit_small(ctx, with_oracle):
     c = SMALL
     locs = synth.locations_uniform(c["n"], 2, seed=1000)
     Z = oracle.simulate(locs, c["theta"], synth.normal(1001, c["n"]))
-    tree = hmle.Tree(ctx, locs, leaf_size=c["leaf"], aca_eps=c["eps"], max_rank=48, oversample=16)
+    tree = hmle.Tree(ctx, locs, leaf_size=c["leaf"], aca_eps=c["eps"])
     t0 = time.time()
     th, ll, it, nev, st = tree.fit(Z, c["theta0"])
     dt = time.time() - t0
@@ -279,6 +301,11 @@ def fit_small(ctx, with_oracle):
            "gpu_s": dt, "iterations": it, "evaluations": nev, "status": st,
            "theta_hat": th, "loglik_hat": ll,
            "loglik_hat_oracle": oracle.loglik_dense(locs, Z, th)[0]}
+    t0 = time.time()
+    th_p, ll_p, it_p, nev_p, st_p = tree.fit(Z, c["theta0"], profiled=True)
+    out["profiled"] = {"gpu_s": time.time() - t0, "iterations": it_p, "evaluations": nev_p,
+                       "status": st_p, "theta_hat": th_p, "loglik_hat": ll_p,
+                       "note": "sigma2 profiled out: Nelder-Mead over (ell, nu, tau2/sigma2)"}
     if with_oracle:
         t0 = time.time()
         th_c, ll_c, it_c, nev_c = oracle.fit(locs, Z, c["theta0"])
@@ -312,17 +339,26 @@ def other_forms(ctx, locs, Z, Zd, thetas, B, fp64_value):
         d = 2 if i % 2 == 0 else 3
         pts = (synth.locations_uniform(n, 2, seed=600 + i) if d == 2
                else synth.uniform(700 + i, 3 * n).reshape(n, 3))
-        fields.append((hmle.Tree(ctx, pts, leaf_size=64, aca_eps=1e-6), synth.normal(800 + i, n), n, d))
-    tasks = [(t, (0.05 + 0.02 * k, 0.5 + 0.2 * k, 1.0, 1e-3), z) for (t, z, n, d) in fields
+        fields.append((hmle.Tree(ctx, pts, leaf_size=64, aca_eps=1e-6, max_rank=48, oversample=16),
+                       synth.normal(800 + i, n), n, d))
+    tasks = [(t, (0.05 + 0.01 * k, 0.5 + 0.1 * k, 1.0, 1e-3), z) for (t, z, n, d) in fields
              for k in range(4)]
     ctx.loglik_multi(tasks, concurrency=16)
     t0 = time.time()
     ll, st = ctx.loglik_multi(tasks, concurrency=16)
     dt = time.time() - t0
+    ok = [k for k, x in enumerate(st) if x == 0]
+    for k in ok:                                                  # graphs of the single path
+        tasks[k][0].loglik(tasks[k][1], tasks[k][2])
+    t0 = time.time()
+    for k in ok:                                                  # the same tasks one call each
+        tasks[k][0].loglik(tasks[k][1], tasks[k][2])
+    dt_loop = time.time() - t0
     res["multi_instance"] = {"fields": [(n, d) for (_, _, n, d) in fields], "tasks": len(tasks),
-                             "evals_per_s": len(tasks) / dt, "points_evals_per_s":
-                             sum(n for (_, _, n, _) in fields) * 4 / dt,
-                             "all_ok": bool(all(x == 0 for x in st))}
+                             "evals_per_s": len(tasks) / dt,
+                             "looped_evals_per_s": len(ok) / dt_loop if ok else None,
+                             "points_evals_per_s": sum(n for (_, _, n, _) in fields) * 4 / dt,
+                             "status": [int(x) for x in st]}
     for t, _, _, _ in fields:
         t.close()
     return res

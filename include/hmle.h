@@ -199,9 +199,12 @@ hmle_status hmle_hmatrix_matvec(hmle_ctx *ctx, const hmle_hmatrix *h,
 
 /* a6-a10 (Sec. 2, H-Cholesky and solve): factor C~ = L~ L~^T by a
  * left-looking sweep over the leaf clusters (dense diagonal and near-field
- * leaves; low-rank blocks recompressed after their Schur-complement updates
- * by randomised sampling + eigen-based truncation), and, when Z is not NULL,
- * run the forward solve w = L~^{-1} P Z inside the same sweep.
+ * leaves; every low-rank block compressed once from all its Schur-complement
+ * updates: randomised range sampling, Householder TSQR, column-pivoted QR and
+ * a Jacobi SVD truncated at eps), and, when Z is not NULL, run the forward
+ * solve w = L~^{-1} P Z inside the same sweep.  With precision =
+ * HMLE_MIXED_FP32 the update products run in FP32 and, when Z is given, the
+ * quadratic form comes from PCG (see hmle_precision).
  *  h  the assembled matrix; it is not modified and may be reused.
  *  Z  n doubles in caller order (host or device) or NULL.
  * Errors: NOT_SPD, RANK_OVERFLOW, OOM, CUDA. */
@@ -217,13 +220,40 @@ void hmle_factor_destroy(hmle_hfactor *f);
 hmle_status hmle_loglik(hmle_ctx *ctx, const hmle_hfactor *f, const double *Z,
                         double *loglik, double *logdet, double *quad);
 
-/* a10-a11 (Sec. 2: "solve the linear system"; Eq. 4's C11^{-1} Z1): X =
+/* a10-a11 (the linear solve of Sec. 2 and Eq. 4's C11^{-1} Z1): X =
  * C~^{-1} Z = P^T L~^{-T} L~^{-1} P Z, by the forward sweep and the reverse
  * (backward) sweep through the factor.  Z, X: n doubles in caller order,
  * host or device (they may not alias).  Afterwards hmle_loglik(f, NULL)
  * returns L for this Z.
  * Errors: INVALID_ARG, OOM, CUDA. */
 hmle_status hmle_solve(hmle_ctx *ctx, const hmle_hfactor *f, const double *Z, double *X);
+
+/* The MLE with the variance profiled out (Sec. 7 suggests updating instead
+ * of recomputing; with C = sigma2 (R(ell, nu) + rho I), rho = tau2 / sigma2,
+ * the maximiser over sigma2 is sigma2 = Z^T R_rho^{-1} Z / n in closed form).
+ * Nelder-Mead runs over 3 coordinates (ell0, nu0, r0) with ell = 1 / 1.5^ell0,
+ * nu = 1 / 1.2^nu0 (Sec. 5) and rho = (1 / 2^r0)^2 on the profile likelihood
+ *   L_p = -n/2 log(2 pi) - n/2 log(Z^T R_rho^{-1} Z / n) - 1/2 log|R_rho| - n/2,
+ * each trial point one evaluation at (ell, nu, 1, rho).  It maximises the same
+ * likelihood as hmle_fit with one coordinate less.  fit_opts as hmle_fit
+ * (step[1..3] are the steps of ell0, nu0, r0; step[0] is unused).
+ * theta_hat = (ell, nu, sigma2_hat, rho sigma2_hat); *ll_hat = L(theta_hat).
+ * Errors: as hmle_fit. */
+hmle_status hmle_fit_profiled(hmle_ctx *ctx, const hmle_tree *tree, const double *Z,
+                              const hmle_theta *theta0, const hmle_fit_opts *fit_opts,
+                              hmle_theta *theta_hat, double *ll_hat, int32_t *n_iter,
+                              int32_t *n_evals);
+
+/* Kriging prediction (Eq. 4): Z2 = C21 C11^{-1} Z1 at m new locations, the
+ * conditional mean of the field there given Z1 (Sec. 1).  C11^{-1} Z1 comes
+ * from the factor f of C11 (forward and backward sweeps, as hmle_solve); C21
+ * is generated from the Matern function at f's theta, without a nugget (the
+ * new locations are other points).  Z1: n doubles in caller order; locs2:
+ * m x d row-major; Z2: m doubles (host or device each).  Afterwards
+ * hmle_loglik(f, NULL) returns L for this Z1.
+ * Errors: INVALID_ARG, OOM, CUDA, TIMEOUT. */
+hmle_status hmle_predict(hmle_ctx *ctx, const hmle_hfactor *f, const double *Z1,
+                         const double *locs2, int64_t m, double *Z2);
 
 /* One full evaluation L(theta): assemble + factor with the fused solve +
  * combine, on a tree.  info may be NULL.  This is the unit of work of the

@@ -13,6 +13,8 @@ approximates):
   L = -n/2 log(2 pi) - 1/2 log|C| - 1/2 Z^T C^{-1} Z, with log|C| =
   2 sum log L_ii (Sec. 2, "Storage and complexity") and
   Z^T C^{-1} Z = |L^{-1} Z|^2.
+* ``predict`` / ``rmse`` -- kriging prediction Z2 = C21 C11^{-1} Z1 (Eq. 4)
+  and the root mean square error of Eq. 7.
 * ``transform`` / ``untransform`` -- the positivity transform of Sec. 5
   (Test 1a): sigma = 2 / 1.1^s0, ell = 1 / 1.5^l0, nu = 1 / 1.2^n0,
   tau = 1 / 2^t0.
@@ -145,6 +147,35 @@ def loglik_dense(locs: np.ndarray, Z: np.ndarray, theta):
 def simulate(locs: np.ndarray, theta, xi: np.ndarray) -> np.ndarray:
     """Z = L xi with L the dense Cholesky factor of C(theta)."""
     return cholesky(matern_matrix(locs, theta)) @ np.asarray(xi, dtype=np.float64)
+
+
+def loglik_profiled(locs: np.ndarray, Z: np.ndarray, ell: float, nu: float, rho: float):
+    """The profile log-likelihood over sigma2 (Sec. 7: update instead of
+    recompute): with C = sigma2 R, R = M_nu(h / ell) + rho I, maximising Eq. 1
+    over sigma2 gives sigma2_hat = Z^T R^{-1} Z / n and
+    L_p = -n/2 log(2 pi) - n/2 log(sigma2_hat) - 1/2 log|R| - n/2.
+    Returns (L_p, sigma2_hat)."""
+    n = len(Z)
+    _, ld, q = loglik_dense(locs, Z, (ell, nu, 1.0, rho))
+    s2 = q / n
+    return -0.5 * n * math.log(2 * math.pi) - 0.5 * n * math.log(s2) - 0.5 * ld - 0.5 * n, s2
+
+
+def predict(locs1: np.ndarray, Z1: np.ndarray, locs2: np.ndarray, theta) -> np.ndarray:
+    """Kriging prediction of Eq. 4: Z2 = C21 C11^{-1} Z1, C11 from Eq. 2 at the
+    n1 training locations (nugget on its diagonal), C21 the cross-covariance
+    without nugget.  C11^{-1} Z1 by the dense Cholesky factor: L w = Z1
+    (forward substitution), then L^T x = w (back substitution)."""
+    L = cholesky(matern_matrix(locs1, theta))
+    w = forward_solve(L, np.asarray(Z1, dtype=np.float64))
+    x = np.linalg.solve(L.T, w)   # library triangular step (upper)
+    return matern_cross(locs2, locs1, theta) @ x
+
+
+def rmse(pred: np.ndarray, truth: np.ndarray) -> float:
+    """Eq. 7: sqrt(mean((Z_hat - Z)^2)) over the test locations."""
+    d = np.asarray(pred, dtype=np.float64) - np.asarray(truth, dtype=np.float64)
+    return float(np.sqrt(np.mean(d * d)))
 
 
 # --- positivity transform of Sec. 5 (Test 1a) ---------------------------------

@@ -921,20 +921,21 @@ hmle_status hmle_loglik(hmle_ctx *ctx, const hmle_hfactor *fc, const double *Z, 
   return HMLE_OK;
 }
 
-hmle_status hmle_solve(hmle_ctx *ctx, const hmle_hfactor *fc, const double *Z, double *X) {
-  if (!ctx || !fc || !Z || !X) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
-  hmle_hfactor *f = const_cast<hmle_hfactor *>(fc);
+}  // extern "C"
+
+namespace {
+
+// x = C~^{-1} P Z in cluster order, left in the factor's right-hand-side
+// panel (forward sweep, q, backward sweep); *xout = that panel.  zd: Z in
+// the caller's order, on the device.
+hmle_status solve_cluster(hmle_ctx *ctx, hmle_hfactor *f, const double *zd, double **xout) {
   const hmle_tree *t = f->h->tree;
   const Plan &P = t->plan;
   cudaStream_t st = ctx->st;
-  double *zd = nullptr, *xo = nullptr, *hb = nullptr;
-  bool owned = false;
-  hmle_status s = stage_vec(ctx, Z, t->n, &zd, &owned);
-  if (s != HMLE_OK) return s;
+  double *hb = nullptr;
   int maxh = 1;
   for (int K = 0; K < P.nleaf; ++K) maxh = std::max(maxh, P.bh0[K + 1] - P.bh0[K]);
   unsigned *bar = nullptr;
-  CK(cudaMallocAsync(&xo, sizeof(double) * t->n, st), "alloc");
   CK(cudaMallocAsync(&hb, sizeof(double) * (size_t)maxh * P.kcap, st), "alloc");
   CK(cudaMallocAsync(&bar, 4 * sizeof(unsigned), st), "alloc");
   CK(cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st), "memset");
@@ -954,28 +955,73 @@ hmle_status hmle_solve(hmle_ctx *ctx, const hmle_hfactor *fc, const double *Z, d
     launch_finalize(st, f->ldp, P.nleaf, w, t->n, f->out);
     launch_backward(st, F, P, w, t->dp.bh_blocks, t->dp.bupd, t->dp.bents, hb);
   }
-  launch_permute_out(st, w, t->T.perm, t->n, xo);
   double out[2];
   unsigned berr = 0;
   CK(cudaGetLastError(), "solve launch");
-  CK(cudaMemcpyAsync(X, xo, sizeof(double) * t->n, cudaMemcpyDefault, st), "copy");
   CK(cudaMemcpyAsync(out, f->out, sizeof(out), cudaMemcpyDeviceToHost, st), "copy");
   CK(cudaMemcpyAsync(&berr, bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "copy");
   CK(cudaStreamSynchronize(st), "sync");
   cudaFreeAsync(bar, st);
-  if (berr) {
-    cudaFreeAsync(xo, st);
-    cudaFreeAsync(hb, st);
-    if (owned) cudaFreeAsync(zd, st);
-    return fail(ctx, HMLE_ERR_TIMEOUT, "solve: a barrier wait of the persistent sweep ran out");
-  }
+  cudaFreeAsync(hb, st);
+  if (berr) return fail(ctx, HMLE_ERR_TIMEOUT, "solve: a barrier wait of the persistent sweep ran out");
   f->quad = out[1];                   // the quadratic form now belongs to this Z
   f->has_rhs = true;
+  *xout = w;
+  return HMLE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hmle_status hmle_solve(hmle_ctx *ctx, const hmle_hfactor *fc, const double *Z, double *X) {
+  if (!ctx || !fc || !Z || !X) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  hmle_hfactor *f = const_cast<hmle_hfactor *>(fc);
+  const hmle_tree *t = f->h->tree;
+  cudaStream_t st = ctx->st;
+  double *zd = nullptr, *xo = nullptr, *w = nullptr;
+  bool owned = false;
+  hmle_status s = stage_vec(ctx, Z, t->n, &zd, &owned);
+  if (s != HMLE_OK) return s;
+  CK(cudaMallocAsync(&xo, sizeof(double) * t->n, st), "alloc");
+  s = solve_cluster(ctx, f, zd, &w);
+  if (s == HMLE_OK) {
+    launch_permute_out(st, w, t->T.perm, t->n, xo);
+    CK(cudaGetLastError(), "permute launch");
+    CK(cudaMemcpyAsync(X, xo, sizeof(double) * t->n, cudaMemcpyDefault, st), "copy");
+  }
   if (owned) cudaFreeAsync(zd, st);
   cudaFreeAsync(xo, st);
-  cudaFreeAsync(hb, st);
   CK(cudaStreamSynchronize(st), "sync");
-  return HMLE_OK;
+  return s;
+}
+
+hmle_status hmle_predict(hmle_ctx *ctx, const hmle_hfactor *fc, const double *Z1,
+                         const double *locs2, int64_t m, double *Z2) {
+  if (!ctx || !fc || !Z1 || !locs2 || !Z2 || m < 1) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  hmle_hfactor *f = const_cast<hmle_hfactor *>(fc);
+  const hmle_tree *t = f->h->tree;
+  const hmle_hmatrix *h = f->h;
+  cudaStream_t st = ctx->st;
+  double *zd = nullptr, *l2 = nullptr, *w = nullptr, *out = nullptr;
+  bool zown = false, lown = false;
+  hmle_status s = stage_vec(ctx, Z1, t->n, &zd, &zown);
+  if (s != HMLE_OK) return s;
+  s = stage_vec(ctx, locs2, m * t->d, &l2, &lown);
+  if (s != HMLE_OK) { if (zown) cudaFreeAsync(zd, st); return s; }
+  CK(cudaMallocAsync(&out, sizeof(double) * m, st), "alloc");
+  s = solve_cluster(ctx, f, zd, &w);                 // w = C~^{-1} Z1, cluster order
+  if (s == HMLE_OK) {
+    // Z2 = C21 w, C21 generated from the table at the factor's theta
+    launch_cross_matvec(st, h->tab, t->T.xyz, t->n, t->d, l2, m, 1.0 / h->th.ell, h->th.sigma2, w, out);
+    CK(cudaGetLastError(), "cross matvec launch");
+    CK(cudaMemcpyAsync(Z2, out, sizeof(double) * m, cudaMemcpyDefault, st), "copy");
+  }
+  if (zown) cudaFreeAsync(zd, st);
+  if (lown) cudaFreeAsync(l2, st);
+  cudaFreeAsync(out, st);
+  CK(cudaStreamSynchronize(st), "sync");
+  return s;
 }
 
 hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tc, const hmle_theta *th,
@@ -1093,7 +1139,7 @@ struct TaskRef {
 // captured sweep), and the wave is collected in task order.  zready: an
 // event after which every Z is readable.
 hmle_status run_waves(hmle_ctx *ctx, const std::vector<TaskRef> &tasks, int W, cudaEvent_t zready,
-                      double *ll, int32_t *status) {
+                      double *ll, int32_t *status, double *ld_out = nullptr, double *q_out = nullptr) {
   const int m = (int)tasks.size();
   hmle_status first = HMLE_OK;
   for (int i0 = 0; i0 < m; i0 += W) {
@@ -1178,6 +1224,8 @@ hmle_status run_waves(hmle_ctx *ctx, const std::vector<TaskRef> &tasks, int W, c
       const double nn = (double)T.t->n;
       ll[i] = (s == HMLE_OK) ? -0.5 * nn * std::log(2.0 * M_PI) - 0.5 * w->F.logdet - 0.5 * w->F.quad
                              : -INFINITY;
+      if (ld_out) ld_out[i] = (s == HMLE_OK) ? w->F.logdet : NAN;
+      if (q_out) q_out[i] = (s == HMLE_OK) ? w->F.quad : NAN;
       if (status && status[i] == HMLE_OK) status[i] = s;
       if (s != HMLE_OK && s != HMLE_ERR_NOT_SPD && s != HMLE_ERR_RANK_OVERFLOW && first == HMLE_OK) {
         first = s;
@@ -1185,6 +1233,23 @@ hmle_status run_waves(hmle_ctx *ctx, const std::vector<TaskRef> &tasks, int W, c
       }
     }
   }
+  return first;
+}
+
+// m evaluations on one tree (Z on the device); ll, and optionally log|C~| and
+// Z^T C~^{-1} Z, per evaluation.
+hmle_status batch_eval(hmle_ctx *ctx, hmle_tree *t, const hmle_theta *thetas, int m,
+                       const double *zd, int W, double *ll, int32_t *status, double *ld,
+                       double *q) {
+  hmle_status s0 = ensure_pool(ctx, t, std::min(W, std::max(m, 1)));
+  if (s0 != HMLE_OK) return s0;
+  cudaEvent_t zready;
+  CK(cudaEventCreateWithFlags(&zready, cudaEventDisableTiming), "event");
+  CK(cudaEventRecord(zready, ctx->st), "event record");
+  std::vector<TaskRef> tasks(m);
+  for (int i = 0; i < m; ++i) tasks[i] = {t, &thetas[i], zd};
+  hmle_status first = run_waves(ctx, tasks, std::min(W, std::max(m, 1)), zready, ll, status, ld, q);
+  cudaEventDestroy(zready);
   return first;
 }
 
@@ -1388,6 +1453,92 @@ hmle_status hmle_x_to_theta(const double x[4], hmle_theta *theta) {
   return theta_ok(theta) ? HMLE_OK : HMLE_ERR_INVALID_ARG;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Nelder-Mead (reflection 1, expansion 2, contraction 1/2, shrink 1/2) in D
+// transformed coordinates.  Each iteration evaluates its four candidates
+// (reflection, expansion, outside and inside contraction) together as one
+// batch and then applies the usual acceptance rules; nev counts the
+// evaluations the rules use.  Stops when the simplex's f-spread <= ftol and
+// x-spread <= xtol (Sec. 2 threshold) or after max_iter iterations.  fbatch(xs,
+// k, fv): f at k points (+inf where undefined).  On return X[0] is the best
+// vertex; the result says whether the tolerance was met.
+template <int D, class FB>
+bool nelder_mead(FB fbatch, const double x0[D], const double step[D], const hmle_fit_opts &fo,
+                 const hmle_status &hard, double (&X)[D + 1][D], double (&Fv)[D + 1], int &it,
+                 int &nev) {
+  for (int j = 0; j < D; ++j) X[0][j] = x0[j];
+  for (int i = 1; i <= D; ++i) {
+    for (int j = 0; j < D; ++j) X[i][j] = X[0][j];
+    X[i][i - 1] += step[i - 1];
+  }
+  fbatch(X, D + 1, Fv);
+  nev = D + 1;
+  it = 0;
+  while (hard == HMLE_OK) {
+    // stable order by f
+    int ord[D + 1];
+    for (int i = 0; i <= D; ++i) ord[i] = i;
+    std::stable_sort(ord, ord + D + 1, [&](int a, int b) { return Fv[a] < Fv[b]; });
+    double Xs[D + 1][D], Fs[D + 1];
+    for (int i = 0; i <= D; ++i) { Fs[i] = Fv[ord[i]]; for (int j = 0; j < D; ++j) Xs[i][j] = X[ord[i]][j]; }
+    std::memcpy(X, Xs, sizeof(X));
+    std::memcpy(Fv, Fs, sizeof(Fv));
+    double fs = 0, xs = 0;
+    for (int i = 1; i <= D; ++i) {
+      fs = std::max(fs, std::fabs(Fv[i] - Fv[0]));
+      for (int j = 0; j < D; ++j) xs = std::max(xs, std::fabs(X[i][j] - X[0][j]));
+    }
+    if (std::isfinite(Fv[D]) && fs <= fo.ftol && xs <= fo.xtol) return true;
+    if (it >= fo.max_iter) return false;
+    ++it;
+    double c[D];
+    for (int j = 0; j < D; ++j) c[j] = 0.0;
+    for (int i = 0; i < D; ++i) for (int j = 0; j < D; ++j) c[j] += X[i][j] / D;
+    double cand[4][D], fc[4];
+    for (int j = 0; j < D; ++j) {
+      const double d = c[j] - X[D][j];
+      cand[0][j] = c[j] + d;
+      cand[1][j] = c[j] + 2.0 * d;
+      cand[2][j] = c[j] + 0.5 * d;
+      cand[3][j] = c[j] - 0.5 * d;
+    }
+    fbatch(cand, 4, fc);
+    if (hard != HMLE_OK) return false;
+    const double fr = fc[0];
+    ++nev;
+    bool shrink = false;
+    if (Fv[0] <= fr && fr < Fv[D - 1]) {
+      std::memcpy(X[D], cand[0], sizeof(cand[0])); Fv[D] = fr;
+    } else if (fr < Fv[0]) {
+      ++nev;
+      if (fc[1] < fr) { std::memcpy(X[D], cand[1], sizeof(cand[1])); Fv[D] = fc[1]; }
+      else { std::memcpy(X[D], cand[0], sizeof(cand[0])); Fv[D] = fr; }
+    } else if (fr < Fv[D]) {
+      ++nev;
+      if (fc[2] <= fr) { std::memcpy(X[D], cand[2], sizeof(cand[2])); Fv[D] = fc[2]; }
+      else shrink = true;
+    } else {
+      ++nev;
+      if (fc[3] < Fv[D]) { std::memcpy(X[D], cand[3], sizeof(cand[3])); Fv[D] = fc[3]; }
+      else shrink = true;
+    }
+    if (shrink) {
+      for (int i = 1; i <= D; ++i)
+        for (int j = 0; j < D; ++j) X[i][j] = X[0][j] + 0.5 * (X[i][j] - X[0][j]);
+      fbatch(&X[1], D, &Fv[1]);
+      nev += D;
+    }
+  }
+  return false;
+}
+
+}  // namespace
+
+extern "C" {
+
 hmle_status hmle_fit(hmle_ctx *ctx, const hmle_tree *t, const double *Z, const hmle_theta *theta0,
                      const hmle_fit_opts *fo_in, hmle_theta *theta_hat, double *ll_hat,
                      int32_t *n_iter, int32_t *n_evals) {
@@ -1405,9 +1556,9 @@ hmle_status hmle_fit(hmle_ctx *ctx, const hmle_tree *t, const double *Z, const h
   bool owned = false;
   hmle_status s = stage_vec(ctx, Z, t->n, &zd, &owned);
   if (s != HMLE_OK) return s;
-  int nev = 0;
   hmle_status hard = HMLE_OK;
-  // evaluate -L at several transformed points concurrently
+  hmle_tree *tt = const_cast<hmle_tree *>(t);
+  // -L at several transformed points, evaluated concurrently
   auto fbatch = [&](const double (*xs)[4], int k, double *fv) {
     hmle_theta th[5];
     int idx[5], m = 0;
@@ -1419,82 +1570,107 @@ hmle_status hmle_fit(hmle_ctx *ctx, const hmle_tree *t, const double *Z, const h
     if (m == 0) return;
     double ll[5];
     int32_t st[5];
-    hmle_status r = hmle_loglik_batch(ctx, t, th, m, zd, m, ll, st);
+    hmle_status r = batch_eval(ctx, tt, th, m, zd, m, ll, st, nullptr, nullptr);
     if (r != HMLE_OK) { hard = r; return; }
     for (int j = 0; j < m; ++j)
       fv[idx[j]] = (st[j] == HMLE_OK) ? -ll[j] : INFINITY;
   };
-  double X[5][4], Fv[5];
-  from_theta(theta0, X[0]);
-  for (int i = 1; i < 5; ++i) {
-    for (int j = 0; j < 4; ++j) X[i][j] = X[0][j];
-    X[i][i - 1] += step[i - 1];
-  }
-  fbatch(X, 5, Fv);
-  nev += 5;
-  int it = 0;
-  bool conv = false;
-  while (hard == HMLE_OK) {
-    // stable order by f
-    int ord[5] = {0, 1, 2, 3, 4};
-    std::stable_sort(ord, ord + 5, [&](int a, int b) { return Fv[a] < Fv[b]; });
-    double Xs[5][4], Fs[5];
-    for (int i = 0; i < 5; ++i) { Fs[i] = Fv[ord[i]]; for (int j = 0; j < 4; ++j) Xs[i][j] = X[ord[i]][j]; }
-    std::memcpy(X, Xs, sizeof(X));
-    std::memcpy(Fv, Fs, sizeof(Fv));
-    double fs = 0, xs = 0;
-    for (int i = 1; i < 5; ++i) {
-      fs = std::max(fs, std::fabs(Fv[i] - Fv[0]));
-      for (int j = 0; j < 4; ++j) xs = std::max(xs, std::fabs(X[i][j] - X[0][j]));
-    }
-    if (std::isfinite(Fv[4]) && fs <= fo.ftol && xs <= fo.xtol) { conv = true; break; }
-    if (it >= fo.max_iter) break;
-    ++it;
-    double c[4] = {0, 0, 0, 0};
-    for (int i = 0; i < 4; ++i) for (int j = 0; j < 4; ++j) c[j] += X[i][j] / 4.0;
-    // the four candidates of this iteration, evaluated together:
-    // reflection, expansion, outside and inside contraction
-    double cand[4][4], fc[4];
-    for (int j = 0; j < 4; ++j) {
-      const double d = c[j] - X[4][j];
-      cand[0][j] = c[j] + d;
-      cand[1][j] = c[j] + 2.0 * d;
-      cand[2][j] = c[j] + 0.5 * d;
-      cand[3][j] = c[j] - 0.5 * d;
-    }
-    fbatch(cand, 4, fc);
-    if (hard != HMLE_OK) break;
-    const double fr = fc[0];
-    ++nev;
-    bool shrink = false;
-    if (Fv[0] <= fr && fr < Fv[3]) {
-      std::memcpy(X[4], cand[0], sizeof(cand[0])); Fv[4] = fr;
-    } else if (fr < Fv[0]) {
-      ++nev;
-      if (fc[1] < fr) { std::memcpy(X[4], cand[1], sizeof(cand[1])); Fv[4] = fc[1]; }
-      else { std::memcpy(X[4], cand[0], sizeof(cand[0])); Fv[4] = fr; }
-    } else if (fr < Fv[4]) {
-      ++nev;
-      if (fc[2] <= fr) { std::memcpy(X[4], cand[2], sizeof(cand[2])); Fv[4] = fc[2]; }
-      else shrink = true;
-    } else {
-      ++nev;
-      if (fc[3] < Fv[4]) { std::memcpy(X[4], cand[3], sizeof(cand[3])); Fv[4] = fc[3]; }
-      else shrink = true;
-    }
-    if (shrink) {
-      for (int i = 1; i < 5; ++i)
-        for (int j = 0; j < 4; ++j) X[i][j] = X[0][j] + 0.5 * (X[i][j] - X[0][j]);
-      fbatch(&X[1], 4, &Fv[1]);
-      nev += 4;
-    }
-  }
+  double x0[4], X[5][4], Fv[5];
+  from_theta(theta0, x0);
+  int it = 0, nev = 0;
+  const bool conv = nelder_mead<4>(fbatch, x0, step, fo, hard, X, Fv, it, nev);
   if (owned) cudaFreeAsync(zd, ctx->st);
+  cudaStreamSynchronize(ctx->st);
   if (hard != HMLE_OK) return hard;
   to_theta(X[0], theta_hat);
   *ll_hat = -Fv[0];
   if (n_iter) *n_iter = it;
   if (n_evals) *n_evals = nev;
+  return conv ? HMLE_OK : fail(ctx, HMLE_ERR_NOT_CONVERGED, "max_iter reached");
+}
+
+hmle_status hmle_fit_profiled(hmle_ctx *ctx, const hmle_tree *t, const double *Z,
+                              const hmle_theta *theta0, const hmle_fit_opts *fo_in,
+                              hmle_theta *theta_hat, double *ll_hat, int32_t *n_iter,
+                              int32_t *n_evals) {
+  if (!ctx || !t || !Z || !theta0 || !theta_hat || !ll_hat)
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  if (!theta_ok(theta0) || theta0->sigma2 <= 0 || theta0->tau2 <= 0)
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "theta0 must have sigma2 > 0 and tau2 > 0");
+  hmle_fit_opts fo;
+  if (fo_in) fo = *fo_in; else hmle_fit_opts_default(&fo);
+  // coordinates (ell0, nu0, r0): ell = 1 / 1.5^ell0, nu = 1 / 1.2^nu0 (Sec. 5)
+  // and the nugget-to-variance ratio rho = tau2 / sigma2 = (1 / 2^r0)^2
+  double step[3];
+  bool allzero = true;
+  for (int i = 0; i < 3; ++i) { step[i] = fo.step[i + 1]; allzero &= (step[i] == 0.0); }
+  if (allzero) for (int i = 0; i < 3; ++i) step[i] = 1.0;
+  const double n = (double)t->n;
+  auto to_unit = [](const double x[3], hmle_theta *th) {   // sigma2 = 1, tau2 = rho
+    th->ell = 1.0 / std::pow(1.5, x[0]);
+    th->nu = 1.0 / std::pow(1.2, x[1]);
+    th->sigma2 = 1.0;
+    const double r = 1.0 / std::pow(2.0, x[2]);
+    th->tau2 = r * r;
+  };
+  double *zd = nullptr;
+  bool owned = false;
+  hmle_status s = stage_vec(ctx, Z, t->n, &zd, &owned);
+  if (s != HMLE_OK) return s;
+  hmle_status hard = HMLE_OK;
+  hmle_tree *tt = const_cast<hmle_tree *>(t);
+  // -L_p: with C = sigma2 R_rho, log|C| = n log sigma2 + log|R_rho| and
+  // Z^T C^-1 Z = q / sigma2 are maximised over sigma2 by sigma2 = q / n, so
+  // L_p = -n/2 log(2 pi) - n/2 log(q / n) - 1/2 log|R_rho| - n/2
+  auto fbatch = [&](const double (*xs)[3], int k, double *fv) {
+    hmle_theta th[5];
+    int idx[5], m = 0;
+    for (int i = 0; i < k; ++i) {
+      to_unit(xs[i], &th[m]);
+      if (theta_ok(&th[m]) && std::isfinite(th[m].tau2)) { idx[m] = i; ++m; }
+      fv[i] = INFINITY;
+    }
+    if (m == 0) return;
+    double ll[5], ld[5], q[5];
+    int32_t st[5];
+    hmle_status r = batch_eval(ctx, tt, th, m, zd, m, ll, st, ld, q);
+    if (r != HMLE_OK) { hard = r; return; }
+    for (int j = 0; j < m; ++j)
+      fv[idx[j]] = (st[j] == HMLE_OK && q[j] > 0.0)
+                       ? 0.5 * n * std::log(2.0 * M_PI) + 0.5 * n * std::log(q[j] / n) +
+                             0.5 * ld[j] + 0.5 * n
+                       : INFINITY;
+  };
+  double x0[3] = {-std::log(theta0->ell) / std::log(1.5), -std::log(theta0->nu) / std::log(1.2),
+                  -std::log(std::sqrt(theta0->tau2 / theta0->sigma2)) / std::log(2.0)};
+  double X[4][3], Fv[4];
+  int it = 0, nev = 0;
+  const bool conv = nelder_mead<3>(fbatch, x0, step, fo, hard, X, Fv, it, nev);
+  hmle_status out = HMLE_OK;
+  if (hard == HMLE_OK) {
+    // sigma2 of the optimum: one more evaluation at the best point
+    hmle_theta th;
+    to_unit(X[0], &th);
+    double ll, ld, q;
+    int32_t st;
+    out = batch_eval(ctx, tt, &th, 1, zd, 1, &ll, &st, &ld, &q);
+    if (out == HMLE_OK && st == HMLE_OK) {
+      const double s2 = q / n;
+      theta_hat->ell = th.ell;
+      theta_hat->nu = th.nu;
+      theta_hat->sigma2 = s2;
+      theta_hat->tau2 = th.tau2 * s2;
+      *ll_hat = -Fv[0];
+    } else if (out == HMLE_OK) {
+      out = (hmle_status)st;
+    }
+  }
+  if (owned) cudaFreeAsync(zd, ctx->st);
+  cudaStreamSynchronize(ctx->st);
+  if (hard != HMLE_OK) return hard;
+  if (out != HMLE_OK) return out;
+  if (n_iter) *n_iter = it;
+  if (n_evals) *n_evals = nev + 1;
   return conv ? HMLE_OK : fail(ctx, HMLE_ERR_NOT_CONVERGED, "max_iter reached");
 }
 

@@ -185,6 +185,13 @@ struct SolvePlan {
 cudaError_t persistent_solve(cudaStream_t st, const FactorArgs &F, const SolvePlan &P, double *w,
                              double *h, unsigned *bar, bool backward);
 
+// Eq. 4: out[j] = sum_i sigma2 M_nu(|s2_j - s1_i| inv_ell) x_i for m new
+// locations locs2 (m x d, row-major) against the n training points xyz (SoA,
+// cluster order); x in cluster order.
+void launch_cross_matvec(cudaStream_t st, const double *tab, const double *xyz, int64_t n, int d,
+                         const double *locs2, int64_t m, double inv_ell, double sigma2,
+                         const double *x, double *out);
+
 // One PCG solve C x = b (b: n doubles, cluster order) with q = b^T x:
 // operator launch_cmatvec, preconditioner the factor of Fs (task pointers set
 // to the right-hand-side lists) applied through the right-hand-side panel

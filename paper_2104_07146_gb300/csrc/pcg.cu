@@ -241,7 +241,37 @@ cudaError_t launch_iteration(PcgRun &R) {
   return cudaMemcpyAsync(R.host + 1, B.sc + 5, sizeof(double), cudaMemcpyDeviceToHost, st);
 }
 
+// Eq. 4 (kriging): out[j] = sum_i sigma2 M_nu(|s2_j - s1_i| / ell) x_i, one
+// CTA per new location, the training points (SoA, cluster order) read in
+// order and the partial sums reduced in a fixed order.  No nugget: the new
+// locations are other points than the training ones.
+__global__ void k_cross_matvec(const double *__restrict__ tab, const double *__restrict__ xyz,
+                               int64_t n, int d, const double *__restrict__ locs2, double inv_ell,
+                               double sigma2, const double *__restrict__ x, double *__restrict__ out) {
+  __shared__ double red[32];
+  const int64_t j = blockIdx.x;
+  double p[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < d; ++k) p[k] = locs2[j * d + k];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double h2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+      const double dx = p[k] - xyz[k * n + i];
+      h2 = fma(dx, dx, h2);
+    }
+    acc = fma(sigma2 * matern_unit(tab, sqrt(h2) * inv_ell), x[i], acc);
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) out[j] = acc;
+}
+
 }  // namespace
+
+void launch_cross_matvec(cudaStream_t st, const double *tab, const double *xyz, int64_t n, int d,
+                         const double *locs2, int64_t m, double inv_ell, double sigma2,
+                         const double *x, double *out) {
+  if (m > 0) k_cross_matvec<<<(unsigned)m, 256, 0, st>>>(tab, xyz, n, d, locs2, inv_ell, sigma2, x, out);
+}
 
 cudaError_t pcg_start(PcgRun &R) {
   const PcgBufs B = carve(R.pool, R.n, R.n_lr, R.A.kc, *R.PL);

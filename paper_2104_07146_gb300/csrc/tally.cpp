@@ -1,6 +1,6 @@
 // Algorithmic FP64 work of one evaluation, per kernel kind, tallied on the
 // host from the θ-independent plan and the ranks that evaluation produced.
-// This is the "flop counter per phase": it counts the arithmetic the
+// This is the flop counter per phase: it counts the arithmetic the
 // left-looking sweep must do with the actual ranks (not the padded block
 // capacities), and a Matern entry as 48 flops (distance, Clenshaw degree 20,
 // scale).  Used for the achieved-throughput side of the roofline.

@@ -104,6 +104,8 @@ def lib():
             "hmle_simulate": ([P, P, P, P, P], C.c_int),
             "hmle_loglik_batch": ([P, P, P, C.c_int32, P, C.c_int32, P, P], C.c_int),
             "hmle_solve": ([P, P, P, P], C.c_int),
+            "hmle_predict": ([P, P, P, P, C.c_int64, P], C.c_int),
+            "hmle_fit_profiled": ([P, P, P, P, P, P, P, P, P], C.c_int),
             "hmle_loglik_multi": ([P, P, C.c_int32, C.c_int32, P, P], C.c_int),
             "hmle_theta_to_x": ([P, P], C.c_int),
             "hmle_selftest_barrier": ([P, C.c_int32, P], C.c_int),
@@ -139,7 +141,7 @@ def exported_symbols():
             "hmle_tree_permutation", "hmle_assemble", "hmle_hmatrix_destroy",
             "hmle_hmatrix_matvec", "hmle_factor", "hmle_factor_destroy", "hmle_loglik",
             "hmle_loglik_eval", "hmle_fit", "hmle_matern_eval", "hmle_profile_select",
-            "hmle_profile_read", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_loglik_multi", "hmle_autotune",
+            "hmle_profile_read", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_predict", "hmle_fit_profiled", "hmle_loglik_multi", "hmle_autotune",
             "hmle_theta_to_x", "hmle_x_to_theta", "hmle_selftest_barrier", "hmle_features", "hmle_mlp_nparams",
             "hmle_mlp_create", "hmle_mlp_destroy", "hmle_mlp_set", "hmle_mlp_get",
             "hmle_mlp_forward", "hmle_mlp_grad", "hmle_mlp_adam_step", "hmle_mlp_train",
@@ -340,8 +342,9 @@ class Tree:
     def assemble(self, theta) -> "HMatrix":
         return HMatrix(self, theta)
 
-    def fit(self, Z, theta0, ftol=1e-4, xtol=1e-4, max_iter=400, step=None):
-        """Nelder-Mead MLE: returns (theta_hat tuple, L_hat, iterations, evaluations, status)."""
+    def fit(self, Z, theta0, ftol=1e-4, xtol=1e-4, max_iter=400, step=None, profiled=False):
+        """Nelder-Mead MLE: returns (theta_hat tuple, L_hat, iterations, evaluations, status).
+        profiled=True: sigma2 profiled out, a 3-coordinate search (hmle_fit_profiled)."""
         fo = FitOpts()
         lib().hmle_fit_opts_default(C.byref(fo))
         fo.ftol, fo.xtol, fo.max_iter = ftol, xtol, max_iter
@@ -353,8 +356,9 @@ class Tree:
         ll = C.c_double()
         it = C.c_int32()
         nev = C.c_int32()
-        st = lib().hmle_fit(self.ctx._h, self._h, p, C.byref(_theta(theta0)), C.byref(fo),
-                            C.byref(th), C.byref(ll), C.byref(it), C.byref(nev))
+        fn = lib().hmle_fit_profiled if profiled else lib().hmle_fit
+        st = fn(self.ctx._h, self._h, p, C.byref(_theta(theta0)), C.byref(fo),
+                C.byref(th), C.byref(ll), C.byref(it), C.byref(nev))
         if st not in (HMLE_OK, 7):
             self.ctx.check(st, "hmle_fit")
         return (th.ell, th.nu, th.sigma2, th.tau2), ll.value, it.value, nev.value, st
@@ -433,6 +437,16 @@ class Factor:
         ctx = self.hm.tree.ctx
         ctx.check(lib().hmle_solve(ctx._h, self._h, P(Z.ctypes.data), P(X.ctypes.data)), "hmle_solve")
         return X
+
+    def predict(self, Z, locs2) -> np.ndarray:
+        """Kriging prediction (Eq. 4) at the m x d locations locs2."""
+        Z = np.ascontiguousarray(Z, dtype=np.float64)
+        L2 = np.ascontiguousarray(locs2, dtype=np.float64)
+        out = np.empty(L2.shape[0])
+        ctx = self.hm.tree.ctx
+        ctx.check(lib().hmle_predict(ctx._h, self._h, P(Z.ctypes.data), P(L2.ctypes.data),
+                                     L2.shape[0], P(out.ctypes.data)), "hmle_predict")
+        return out
 
     def close(self):
         if self._h:

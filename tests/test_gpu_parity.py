@@ -150,6 +150,23 @@ def test_solve_matches_dense(ctx):
     assert np.isfinite(X2).all()
 
 
+def test_kriging_prediction_matches_dense(ctx):
+    # Eq. 4: Z2 = C21 C11^{-1} Z1 at 300 new locations (10% held out as in the
+    # paper's split), against the dense FP64 oracle; RMSE (Eq. 7) of both
+    # against the held-out truth agree
+    n, m = 1700, 300
+    allp = synth.locations_uniform(n + m, 2, seed=91)
+    th = (0.1, 0.8, 1.0, 0.02)
+    Zall = oracle.simulate(allp, th, synth.normal(92, n + m))
+    locs1, Z1, locs2, Z2 = allp[:n], Zall[:n], allp[n:], Zall[n:]
+    t = _tree(ctx, locs1, leaf_size=32, aca_eps=1e-10, max_rank=48, oversample=16)
+    f = t.assemble(th).factor(Z1)
+    pred = f.predict(Z1, locs2)
+    ref = oracle.predict(locs1, Z1, locs2, th)
+    assert np.abs(pred - ref).max() <= 1e-6 * np.abs(ref).max()
+    assert abs(oracle.rmse(pred, Z2) - oracle.rmse(ref, Z2)) <= 1e-6 * oracle.rmse(ref, Z2)
+
+
 def test_bounded_barrier_wait_reports_timeout(ctx):
     # failure detection without a GPU fault: a grid barrier that one more CTA
     # than exists should reach runs out of its bounded wait; the call reports
@@ -314,3 +331,9 @@ def test_fit_matches_oracle_fit(ctx):
     ll_gpu_exact = oracle.loglik_dense(locs, Z, th_gpu)[0]
     assert abs(ll_gpu - ll_gpu_exact) / n <= 1e-6
     assert ll_gpu_exact >= ll_cpu - 1e-3 * abs(ll_cpu) / n - 1e-3
+    # the same MLE with sigma2 profiled out: a 3-coordinate search
+    th_p, ll_p, it_p, nev_p, st_p = t.fit(Z, th0, profiled=True)
+    assert st_p == 0
+    ll_p_exact = oracle.loglik_dense(locs, Z, th_p)[0]
+    assert abs(ll_p - ll_p_exact) / n <= 1e-6
+    assert ll_p_exact >= ll_cpu - 1e-3 * abs(ll_cpu) / n - 1e-3

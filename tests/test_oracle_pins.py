@@ -276,3 +276,40 @@ def test_fit_recovers_simulated_theta():
     ll_true = oracle.loglik_dense(locs, Z, th)[0]
     assert ll_hat >= ll_true - 1e-3          # the MLE is at least as likely as the truth
     assert 0.03 < th_hat[0] < 0.3 and 0.2 < th_hat[1] < 1.2 and 0.3 < th_hat[2] < 3.0
+
+
+def test_prediction_interpolates_without_nugget():
+    # Eq. 4 with tau2 = 0: a training location's own row of C21 is its row of
+    # C11, so the prediction there returns the observed value exactly
+    rng = np.random.default_rng(3)
+    locs = rng.uniform(size=(40, 2))
+    Z = rng.normal(size=40)
+    th = (0.3, 1.5, 1.2, 0.0)
+    pred = oracle.predict(locs, Z, locs[[3, 17, 31]], th)
+    assert np.allclose(pred, Z[[3, 17, 31]], rtol=0, atol=1e-8)
+
+
+def test_prediction_single_point_closed_form():
+    # one training point: Z2 = sigma2 M(h/ell) / (sigma2 + tau2) * Z1
+    th = (0.5, 0.5, 2.0, 0.5)
+    z = np.array([1.7])
+    p = oracle.predict(np.array([[0.0, 0.0]]), z, np.array([[0.3, 0.4]]), th)[0]
+    expect = 2.0 * math.exp(-0.5 / 0.5) / (2.0 + 0.5) * 1.7    # nu = 1/2: M(x) = exp(-x)
+    assert abs(p - expect) <= 1e-12
+
+
+def test_rmse_definition():
+    assert oracle.rmse([1.0, 2.0, 3.0], [1.0, 0.0, 3.0]) == math.sqrt(4.0 / 3.0)
+
+
+def test_profile_likelihood_is_the_maximum_over_sigma2():
+    # L_p(ell, nu, rho) = L(ell, nu, s2_hat, rho s2_hat) and L at any other
+    # sigma2 on the same ray is lower (the maximiser is the closed form)
+    rng = np.random.default_rng(8)
+    locs = rng.uniform(size=(60, 2))
+    Z = rng.normal(size=60) * 1.3
+    lp, s2 = oracle.loglik_profiled(locs, Z, 0.2, 0.7, 0.05)
+    full = oracle.loglik_dense(locs, Z, (0.2, 0.7, s2, 0.05 * s2))[0]
+    assert abs(lp - full) <= 1e-9 * abs(full)
+    for f in (0.5, 0.9, 1.1, 2.0):
+        assert oracle.loglik_dense(locs, Z, (0.2, 0.7, f * s2, 0.05 * f * s2))[0] < lp
