@@ -3,7 +3,7 @@ second (Eq. 1 with the Matern covariance of Eq. 2) on one GB300.
 
 One evaluation = Matern tables + ACA assembly of the admissible blocks + the
 H-Cholesky leaf sweep with the fused forward solve + log-det / quadratic
-form.  One step = one batch of B evaluations at B distinct theta (the
+form.  One step = one batch of B = 32 evaluations at B distinct theta (the
 workload theta and its neighbours in the transformed coordinates of Sec. 5,
 as an optimiser's simplex would ask for), run concurrently through
 hmle_loglik_batch, for the medium workload: n = 65,536 points in
@@ -436,7 +436,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-sample-n", type=int, default=8192)
-    ap.add_argument("--batch", type=int, default=16,
+    ap.add_argument("--batch", type=int, default=32,
                     help="concurrent theta evaluations per step (hmle_loglik_batch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fit", action="store_true", help="skip the small-configuration MLE fit")

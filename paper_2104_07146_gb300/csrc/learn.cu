@@ -75,9 +75,9 @@ __global__ void k_vario_spread(const double *__restrict__ P, int m, int d, doubl
     __syncthreads();
     if (lane == 0) { rmin[w] = lo; rmax[w] = hi; }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {   // lo / hi hold warp 0's extremes; fold in the other warps'
       for (int q = 1; q < nw; ++q) { lo = fmin(lo, rmin[q]); hi = fmax(hi, rmax[q]); }
-      const double wd = __dsub_rn(fmax(hi, rmax[0]), fmin(lo, rmin[0]));
+      const double wd = __dsub_rn(hi, lo);
       acc = __dadd_rn(acc, __dmul_rn(wd, wd));
     }
   }
