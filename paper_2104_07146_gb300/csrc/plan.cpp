@@ -20,6 +20,7 @@
 // covering rows X and Y and overlapping columns: U_A G_AB U_B^T with
 // G_AB = W_A[ov]^T W_B[ov] (a dense leaf block acts as U = D, W = I).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -331,8 +332,15 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
       L.zoff = ws; ws += (int64_t)L.p * r;
       L.soff = ws; ws += 4LL * r * r;
       L.tcoff = ws; ws += (int64_t)std::max(kc, r) * r;
-      L.gm = std::max(1, std::min(32, (L.m + 1023) / 1024));
-      L.gp = std::max(1, std::min(32, (L.p + 1023) / 1024));
+      // TSQR row groups: a group streams its rows 64 at a time through one
+      // CTA, and the final combine stacks the groups' R factors one after
+      // another, so about sqrt(rows / 64) groups balance the two chains
+      auto groups = [](int rows) {
+        int g = (int)std::ceil(std::sqrt((double)rows / 64.0));
+        return std::max(1, std::min(32, g));
+      };
+      L.gm = groups(L.m);
+      L.gp = groups(L.p);
       L.roff = ws; ws += (int64_t)std::max(L.gm, L.gp) * r * r;
       P.lrt.push_back(L);
     }

@@ -82,3 +82,21 @@ def test_pcg_not_converged_is_reported(ctx):
     with pytest.raises(hmle.HmleError) as e:
         t.loglik((0.1, 0.5, 1.0, 0.01), synth.normal(64, 800))
     assert e.value.status == 7
+
+
+@pytest.mark.slow
+def test_mixed_medium_workload_subset_16384(ctx):
+    # the medium workload's first 16,384 points at its theta (nu = 1/2, leaf 64,
+    # eps 1e-6), Z = L xi from the dense oracle: the mixed form against the
+    # oracle and against the FP64 form on the same tree geometry
+    locs = synth.medium_locations(65536)[:16384]
+    th = (0.05, 0.5, 1.0, 1e-3)
+    info = _mixed_parity(ctx, locs, th, 64, 1e-6, 53)
+    Z = oracle.simulate(locs, th, synth.normal(53, 16384))
+    ll64, i64 = _tree(ctx, locs, leaf_size=64, aca_eps=1e-6).loglik(th, Z)
+    assert abs(info.logdet - i64.logdet) / 16384 <= 1e-5
+
+
+def test_mixed_three_dimensional(ctx):
+    locs = synth.locations_uniform(2500, 3, seed=25)
+    _mixed_parity(ctx, locs, (0.2, 1.0, 1.0, 0.01), 32, 1e-7, 26, max_rank=48, oversample=16)

@@ -167,6 +167,24 @@ def test_kriging_prediction_matches_dense(ctx):
     assert abs(oracle.rmse(pred, Z2) - oracle.rmse(ref, Z2)) <= 1e-6 * oracle.rmse(ref, Z2)
 
 
+def test_solve_and_prediction_leaf128(ctx):
+    # the persistent sweeps at the largest leaf (128): X = C~^{-1} Z and the
+    # kriging prediction against the dense oracle
+    n, m = 1800, 200
+    allp = synth.locations_uniform(n + m, 2, seed=97)
+    th = (0.1, 0.8, 1.0, 0.02)
+    Zall = oracle.simulate(allp, th, synth.normal(98, n + m))
+    locs1, Z1, locs2 = allp[:n], Zall[:n], allp[n:]
+    t = _tree(ctx, locs1, leaf_size=128, aca_eps=1e-10, max_rank=48, oversample=16)
+    f = t.assemble(th).factor(Z1)
+    X = f.solve(Z1)
+    Xd = np.linalg.solve(oracle.matern_matrix(locs1, th), Z1)
+    assert np.linalg.norm(X - Xd) <= 1e-5 * np.linalg.norm(Xd)
+    pred = f.predict(Z1, locs2)
+    ref = oracle.predict(locs1, Z1, locs2, th)
+    assert np.abs(pred - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
 def test_bounded_barrier_wait_reports_timeout(ctx):
     # failure detection without a GPU fault: a grid barrier that one more CTA
     # than exists should reach runs out of its bounded wait; the call reports
