@@ -294,6 +294,7 @@ hmle_status do_assemble(hmle_ctx *ctx, const hmle_tree *t, const hmle_theta *th,
 }
 
 constexpr double kMixedTruncEps = 1e-7;  // truncation floor of the mixed factor
+constexpr int kAssemblyLaunches = 3;      // Matern table, ACA, dense near field of one assembly
 
 FactorArgs make_fargs(const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f) {
   const Plan &P = t->plan;
@@ -422,7 +423,7 @@ hmle_status launch_factor_async(hmle_ctx *ctx, const hmle_tree *t, const hmle_hm
   launch_permute_in(st, zdev, t->T.perm, t->n, f->W + rp.off);
   f->has_rhs = true;
   if (!w) {
-    f->launches = launch_sweep(ctx, t, h, f, nullptr) + 2;
+    f->launches = launch_sweep(ctx, t, h, f, nullptr) + kAssemblyLaunches;
   } else if (!w->exec || w->graph_kind != -1) {
     if (w->exec) { cudaGraphExecDestroy(w->exec); w->exec = nullptr; }
     cudaGraph_t g = nullptr;
@@ -435,7 +436,7 @@ hmle_status launch_factor_async(hmle_ctx *ctx, const hmle_tree *t, const hmle_hm
     if (e != cudaSuccess) { w->exec = nullptr; return cuda_fail(ctx, e, "graph instantiate"); }
     w->graph_kind = -1;
     w->graph_nev = 0;
-    f->launches = nk + 2;
+    f->launches = nk + kAssemblyLaunches;
   }
   if (w) CK(cudaGraphLaunch(w->exec, st), "graph launch");
   // no copy to host here: host_out is pageable, and a device-to-pageable copy
@@ -493,13 +494,13 @@ hmle_status do_factor(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h,
       if (e != cudaSuccess) { w->exec = nullptr; return cuda_fail(ctx, e, "graph instantiate"); }
       w->graph_kind = ctx->prof.kind;
       w->graph_nev = prof ? prof->used : 0;
-      f->launches = nk + 2;  // + matern table, ACA
+      f->launches = nk + kAssemblyLaunches;
     }
     CK(cudaGraphLaunch(w->exec, st), "graph launch");
     nev = w->graph_nev;
   } else {
     if (prof) prof->used = 0;
-    f->launches = launch_sweep(ctx, t, h, f, prof) + 2;
+    f->launches = launch_sweep(ctx, t, h, f, prof) + kAssemblyLaunches;
     nev = prof ? prof->used : 0;
   }
   CK(cudaGetLastError(), "factor launch");
