@@ -244,6 +244,16 @@ hmle_status hmle_fit_profiled(hmle_ctx *ctx, const hmle_tree *tree, const double
                               hmle_theta *theta_hat, double *ll_hat, int32_t *n_iter,
                               int32_t *n_evals);
 
+/* Cross-covariance products between the tree's n points and m new locations
+ * (the C21 / C12 blocks of Sec. 1, without a nugget) at theta:
+ *  trans = 0: y (m) = C21 x (x: n doubles, caller order);
+ *  trans = 1: y (n, caller order) = C12 x (x: m doubles).
+ * locs2: m x d row-major.  Every pointer host or device.  Used with hmle_solve
+ * for the prediction variances of Eq. 5-6.  Errors: INVALID_ARG, OOM, CUDA. */
+hmle_status hmle_cross_matvec(hmle_ctx *ctx, const hmle_tree *tree, const hmle_theta *theta,
+                              const double *locs2, int64_t m, int32_t trans, const double *x,
+                              double *y);
+
 /* Kriging prediction (Eq. 4): Z2 = C21 C11^{-1} Z1 at m new locations, the
  * conditional mean of the field there given Z1 (Sec. 1).  C11^{-1} Z1 comes
  * from the factor f of C11 (forward and backward sweeps, as hmle_solve); C21

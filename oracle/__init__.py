@@ -13,8 +13,9 @@ approximates):
   L = -n/2 log(2 pi) - 1/2 log|C| - 1/2 Z^T C^{-1} Z, with log|C| =
   2 sum log L_ii (Sec. 2, "Storage and complexity") and
   Z^T C^{-1} Z = |L^{-1} Z|^2.
-* ``predict`` / ``rmse`` -- kriging prediction Z2 = C21 C11^{-1} Z1 (Eq. 4)
-  and the root mean square error of Eq. 7.
+* ``predict`` / ``rmse`` / ``mloe_mmom`` -- kriging prediction
+  Z2 = C21 C11^{-1} Z1 (Eq. 4), the root mean square error of Eq. 7 and the
+  MLOE / MMOM measures of Eq. 5-6.
 * ``transform`` / ``untransform`` -- the positivity transform of Sec. 5
   (Test 1a): sigma = 2 / 1.1^s0, ell = 1 / 1.5^l0, nu = 1 / 1.2^n0,
   tau = 1 / 2^t0.
@@ -170,6 +171,29 @@ def predict(locs1: np.ndarray, Z1: np.ndarray, locs2: np.ndarray, theta) -> np.n
     w = forward_solve(L, np.asarray(Z1, dtype=np.float64))
     x = np.linalg.solve(L.T, w)   # library triangular step (upper)
     return matern_cross(locs2, locs1, theta) @ x
+
+
+def mloe_mmom(locs1: np.ndarray, locs2: np.ndarray, theta_t, theta_a):
+    """MLOE and MMOM of Eq. 5-6 with dense FP64 matrices.  For each test
+    location s_j the mean square errors of the kriging predictors under the
+    true (t) and approximated (a) models: with c = cross-covariance column,
+    C = training covariance, v = sigma2 + tau2 (the variance of Z(s_j)),
+    l_a = C_a^{-1} c_a:
+      E_t[(Z_t - Z)^2] = v_t - c_t^T C_t^{-1} c_t
+      E_a[(Z_a - Z)^2] = v_a - c_a^T l_a
+      E_t[(Z_a - Z)^2] = v_t - 2 l_a^T c_t + l_a^T C_t l_a
+    MLOE = mean(E_t[a] / E_t[t] - 1), MMOM = mean(E_a[a] / E_t[a] - 1)."""
+    Ct, Ca = matern_matrix(locs1, theta_t), matern_matrix(locs1, theta_a)
+    ct = matern_cross(locs1, locs2, theta_t)          # n x M columns c_t(j)
+    ca = matern_cross(locs1, locs2, theta_a)
+    lt = np.linalg.solve(Ct, ct)
+    la = np.linalg.solve(Ca, ca)
+    vt = float(theta_t[2]) + float(theta_t[3])
+    va = float(theta_a[2]) + float(theta_a[3])
+    e_tt = vt - np.sum(ct * lt, axis=0)
+    e_aa = va - np.sum(ca * la, axis=0)
+    e_ta = vt - 2.0 * np.sum(la * ct, axis=0) + np.sum(la * (Ct @ la), axis=0)
+    return float(np.mean(e_ta / e_tt - 1.0)), float(np.mean(e_aa / e_ta - 1.0))
 
 
 def rmse(pred: np.ndarray, truth: np.ndarray) -> float:

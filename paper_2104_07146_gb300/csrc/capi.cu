@@ -1398,6 +1398,42 @@ hmle_status hmle_matern_eval(hmle_ctx *ctx, double nu, const double *x, int64_t 
   return HMLE_OK;
 }
 
+hmle_status hmle_cross_matvec(hmle_ctx *ctx, const hmle_tree *t, const hmle_theta *th,
+                              const double *locs2, int64_t m, int32_t trans, const double *x,
+                              double *y) {
+  if (!ctx || !t || !th || !locs2 || !x || !y || m < 1 || (trans != 0 && trans != 1))
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  if (!theta_ok(th)) return fail(ctx, HMLE_ERR_INVALID_ARG, "theta out of range");
+  cudaStream_t st = ctx->st;
+  const int64_t n = t->n, nin = trans ? m : n, nout = trans ? n : m;
+  double *tab = nullptr, *l2 = nullptr, *xd = nullptr, *xp = nullptr, *od = nullptr, *oc = nullptr;
+  bool lown = false, xown = false;
+  hmle_status s = stage_vec(ctx, locs2, m * t->d, &l2, &lown);
+  if (s != HMLE_OK) return s;
+  s = stage_vec(ctx, x, nin, &xd, &xown);
+  if (s != HMLE_OK) { if (lown) cudaFreeAsync(l2, st); return s; }
+  CK(cudaMallocAsync(&tab, sizeof(double) * kTableWords, st), "alloc");
+  CK(cudaMallocAsync(&od, sizeof(double) * nout, st), "alloc");
+  launch_matern_table(st, th->nu, tab);
+  if (!trans) {            // y = C21 x: x to cluster order first
+    CK(cudaMallocAsync(&xp, sizeof(double) * n, st), "alloc");
+    launch_permute_in(st, xd, t->T.perm, n, xp);
+    launch_cross_matvec(st, tab, t->T.xyz, n, t->d, l2, m, 1.0 / th->ell, th->sigma2, xp, od);
+  } else {                 // y = C12 x: the result back to caller order
+    CK(cudaMallocAsync(&oc, sizeof(double) * n, st), "alloc");
+    launch_cross_matvec_t(st, tab, t->T.xyz, n, t->d, l2, m, 1.0 / th->ell, th->sigma2, xd, oc);
+    launch_permute_out(st, oc, t->T.perm, n, od);
+  }
+  CK(cudaGetLastError(), "cross matvec launch");
+  CK(cudaMemcpyAsync(y, od, sizeof(double) * nout, cudaMemcpyDefault, st), "copy");
+  CK(cudaStreamSynchronize(st), "sync");
+  for (double *p : {tab, od, xp, oc}) if (p) cudaFreeAsync(p, st);
+  if (lown) cudaFreeAsync(l2, st);
+  if (xown) cudaFreeAsync(xd, st);
+  CK(cudaStreamSynchronize(st), "sync");
+  return HMLE_OK;
+}
+
 hmle_status hmle_profile_select(hmle_ctx *ctx, const char *kernel) {
   if (!ctx) return HMLE_ERR_INVALID_ARG;
   Prof &p = ctx->prof;

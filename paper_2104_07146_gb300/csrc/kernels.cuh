@@ -191,6 +191,11 @@ cudaError_t persistent_solve(cudaStream_t st, const FactorArgs &F, const SolvePl
 void launch_cross_matvec(cudaStream_t st, const double *tab, const double *xyz, int64_t n, int d,
                          const double *locs2, int64_t m, double inv_ell, double sigma2,
                          const double *x, double *out);
+// out[i] = sum_j sigma2 M_nu(|s1_i - s2_j| inv_ell) y_j (the transposed product;
+// out in cluster order).
+void launch_cross_matvec_t(cudaStream_t st, const double *tab, const double *xyz, int64_t n, int d,
+                           const double *locs2, int64_t m, double inv_ell, double sigma2,
+                           const double *y, double *out);
 
 // One PCG solve C x = b (b: n doubles, cluster order) with q = b^T x:
 // operator launch_cmatvec, preconditioner the factor of Fs (task pointers set

@@ -267,10 +267,41 @@ __global__ void k_cross_matvec(const double *__restrict__ tab, const double *__r
 
 }  // namespace
 
+// The transposed product: out[i] = sum_j sigma2 M_nu(|s1_i - s2_j| / ell) y_j,
+// one thread per training point (cluster order), the m new locations summed
+// in order.
+__global__ void k_cross_matvec_t(const double *__restrict__ tab, const double *__restrict__ xyz,
+                                 int64_t n, int d, const double *__restrict__ locs2, int64_t m,
+                                 double inv_ell, double sigma2, const double *__restrict__ y,
+                                 double *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double p[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < d; ++k) p[k] = xyz[k * n + i];
+  double acc = 0.0;
+  for (int64_t j = 0; j < m; ++j) {
+    double h2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+      const double dx = p[k] - locs2[j * d + k];
+      h2 = fma(dx, dx, h2);
+    }
+    acc = fma(sigma2 * matern_unit(tab, sqrt(h2) * inv_ell), y[j], acc);
+  }
+  out[i] = acc;
+}
+
 void launch_cross_matvec(cudaStream_t st, const double *tab, const double *xyz, int64_t n, int d,
                          const double *locs2, int64_t m, double inv_ell, double sigma2,
                          const double *x, double *out) {
   if (m > 0) k_cross_matvec<<<(unsigned)m, 256, 0, st>>>(tab, xyz, n, d, locs2, inv_ell, sigma2, x, out);
+}
+
+void launch_cross_matvec_t(cudaStream_t st, const double *tab, const double *xyz, int64_t n, int d,
+                           const double *locs2, int64_t m, double inv_ell, double sigma2,
+                           const double *y, double *out) {
+  if (n > 0)
+    k_cross_matvec_t<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(tab, xyz, n, d, locs2, m, inv_ell,
+                                                                 sigma2, y, out);
 }
 
 cudaError_t pcg_start(PcgRun &R) {

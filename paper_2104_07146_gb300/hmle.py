@@ -105,6 +105,7 @@ def lib():
             "hmle_loglik_batch": ([P, P, P, C.c_int32, P, C.c_int32, P, P], C.c_int),
             "hmle_solve": ([P, P, P, P], C.c_int),
             "hmle_predict": ([P, P, P, P, C.c_int64, P], C.c_int),
+            "hmle_cross_matvec": ([P, P, P, P, C.c_int64, C.c_int32, P, P], C.c_int),
             "hmle_fit_profiled": ([P, P, P, P, P, P, P, P, P], C.c_int),
             "hmle_loglik_multi": ([P, P, C.c_int32, C.c_int32, P, P], C.c_int),
             "hmle_theta_to_x": ([P, P], C.c_int),
@@ -141,7 +142,7 @@ def exported_symbols():
             "hmle_tree_permutation", "hmle_assemble", "hmle_hmatrix_destroy",
             "hmle_hmatrix_matvec", "hmle_factor", "hmle_factor_destroy", "hmle_loglik",
             "hmle_loglik_eval", "hmle_fit", "hmle_matern_eval", "hmle_profile_select",
-            "hmle_profile_read", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_predict", "hmle_fit_profiled", "hmle_loglik_multi", "hmle_autotune",
+            "hmle_profile_read", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_predict", "hmle_fit_profiled", "hmle_cross_matvec", "hmle_loglik_multi", "hmle_autotune",
             "hmle_theta_to_x", "hmle_x_to_theta", "hmle_selftest_barrier", "hmle_features", "hmle_mlp_nparams",
             "hmle_mlp_create", "hmle_mlp_destroy", "hmle_mlp_set", "hmle_mlp_get",
             "hmle_mlp_forward", "hmle_mlp_grad", "hmle_mlp_adam_step", "hmle_mlp_train",
@@ -338,6 +339,18 @@ class Tree:
         self.ctx.check(lib().hmle_simulate(self.ctx._h, self._h, C.byref(_theta(theta)),
                                            P(xi.ctypes.data), P(Z.ctypes.data)), "hmle_simulate")
         return Z
+
+    def cross_matvec(self, theta, locs2, x, trans=False) -> np.ndarray:
+        """C21 x (trans=False; x of length n) or C12 x (trans=True; x of length m)
+        between this tree's points and the m x d locations locs2."""
+        L2 = np.ascontiguousarray(locs2, dtype=np.float64)
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.empty(self.n if trans else L2.shape[0])
+        self.ctx.check(lib().hmle_cross_matvec(self.ctx._h, self._h, C.byref(_theta(theta)),
+                                               P(L2.ctypes.data), L2.shape[0], int(trans),
+                                               P(x.ctypes.data), P(y.ctypes.data)),
+                       "hmle_cross_matvec")
+        return y
 
     def assemble(self, theta) -> "HMatrix":
         return HMatrix(self, theta)

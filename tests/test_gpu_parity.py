@@ -185,6 +185,38 @@ def test_solve_and_prediction_leaf128(ctx):
     assert np.abs(pred - ref).max() <= 1e-5 * np.abs(ref).max()
 
 
+def test_cross_covariance_products_match_dense(ctx):
+    # C21 x and C12 y (Sec. 1 blocks, no nugget) against the oracle's dense
+    # cross-covariance, ragged sizes
+    n, m = 1301, 57
+    locs1 = synth.locations_uniform(n, 2, seed=101)
+    locs2 = synth.locations_uniform(m, 2, seed=102)
+    th = (0.12, 1.3, 0.8, 0.05)
+    t = _tree(ctx, locs1, leaf_size=32)
+    x, y = synth.normal(103, n), synth.normal(104, m)
+    C21 = oracle.matern_cross(locs2, locs1, th)
+    assert np.abs(t.cross_matvec(th, locs2, x) - C21 @ x).max() <= 1e-11 * np.abs(C21 @ x).max()
+    assert np.abs(t.cross_matvec(th, locs2, y, trans=True) - C21.T @ y).max() <= \
+        1e-11 * np.abs(C21.T @ y).max()
+
+
+def test_mloe_mmom_match_dense(ctx):
+    # Eq. 5-6 from the GPU solves, cross products and H-matvec against the
+    # dense oracle; both vanish when the two models coincide
+    from paper_2104_07146_gb300 import prediction
+    n, m = 900, 12
+    allp = synth.locations_uniform(n + m, 2, seed=105)
+    locs1, locs2 = allp[:n], allp[n:]
+    tht, tha = (0.1, 0.5, 1.0, 0.01), (0.13, 0.6, 0.9, 0.02)
+    t = _tree(ctx, locs1, leaf_size=32, aca_eps=1e-10, max_rank=48, oversample=16)
+    lo, mo = prediction.mloe_mmom(t, locs2, tht, tha)
+    lo_r, mo_r = oracle.mloe_mmom(locs1, locs2, tht, tha)
+    assert abs(lo - lo_r) <= 1e-6 + 1e-4 * abs(lo_r), (lo, lo_r)
+    assert abs(mo - mo_r) <= 1e-6 + 1e-4 * abs(mo_r), (mo, mo_r)
+    lo0, mo0 = prediction.mloe_mmom(t, locs2, tht, tht)
+    assert abs(lo0) <= 1e-6 and abs(mo0) <= 1e-6
+
+
 def test_bounded_barrier_wait_reports_timeout(ctx):
     # failure detection without a GPU fault: a grid barrier that one more CTA
     # than exists should reach runs out of its bounded wait; the call reports

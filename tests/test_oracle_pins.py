@@ -313,3 +313,18 @@ def test_profile_likelihood_is_the_maximum_over_sigma2():
     assert abs(lp - full) <= 1e-9 * abs(full)
     for f in (0.5, 0.9, 1.1, 2.0):
         assert oracle.loglik_dense(locs, Z, (0.2, 0.7, f * s2, 0.05 * f * s2))[0] < lp
+
+
+def test_mloe_mmom_vanish_for_the_true_model_and_mloe_is_nonnegative():
+    # Eq. 5-6: with the approximated model equal to the true one both
+    # measures are 0; the true model's predictor has the smallest mean square
+    # error under the true model, so MLOE >= 0 for any other model
+    rng = np.random.default_rng(12)
+    locs1 = rng.uniform(size=(120, 2))
+    locs2 = rng.uniform(size=(15, 2))
+    th = (0.15, 0.8, 1.0, 0.02)
+    lo, mo = oracle.mloe_mmom(locs1, locs2, th, th)
+    assert abs(lo) <= 1e-10 and abs(mo) <= 1e-10
+    for tha in [(0.3, 0.8, 1.0, 0.02), (0.15, 1.6, 2.0, 0.1), (0.08, 0.5, 0.5, 0.01)]:
+        lo, mo = oracle.mloe_mmom(locs1, locs2, th, tha)
+        assert lo >= -1e-12
