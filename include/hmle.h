@@ -93,7 +93,12 @@ typedef struct {
  *             are held low-rank like the coarser admissible blocks.
  *  pcg_tol, pcg_max_iter  mixed form only: PCG stops when |r| <= pcg_tol |Z|
  *             (default 1e-10) or fails with HMLE_ERR_NOT_CONVERGED after
- *             pcg_max_iter iterations (default 50). */
+ *             pcg_max_iter iterations (default 50).
+ *  fixed_rank 0 (default): fixed accuracy, every block at eps (Sec. 2, the
+ *             accuracy-fixed approximation); k in 1..max_rank: fixed rank,
+ *             every block of C~ and of L~ at most k (Sec. 2, the rank-fixed
+ *             approximation; the accuracy then varies from block to block and
+ *             no rank overflow is reported). */
 typedef struct {
   int32_t leaf_size;
   double eta;
@@ -105,6 +110,7 @@ typedef struct {
   int32_t leaf_lowrank;
   double pcg_tol;
   int32_t pcg_max_iter;
+  int32_t fixed_rank;
 } hmle_opts;
 
 /* Nelder-Mead options of hmle_fit (Sec. 2: threshold 1e-4, <= 400 iterations). */

@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(256) k_aca(AsmArgs A) {
     rank = k;
     tries = 0;
     if (sqrt(uu * vv) <= A.eps * sqrt(fabs(norm2))) { done = true; break; }
+    if (A.fixed_k > 0 && k >= A.fixed_k) { done = true; break; }   // fixed-rank mode
     if (k == kc) { overflow = true; break; }
     istar = inext;
     if (pu == 0.0) {

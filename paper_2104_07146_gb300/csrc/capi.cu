@@ -287,6 +287,7 @@ hmle_status do_assemble(hmle_ctx *ctx, const hmle_tree *t, const hmle_theta *th,
   A.rank_c = h->rank_c;
   A.cnorm = h->cnorm;
   A.flags = h->flags;
+  A.fixed_k = t->opts.fixed_rank;
   launch_aca(st, A, (int)t->lr_ids.size());
   launch_assemble_dense(st, A, t->dp.dense_ids, (int)t->dense_ids.size(), P.b, h->Cd);
   CK(cudaGetLastError(), "assemble launch");
@@ -314,6 +315,7 @@ FactorArgs make_fargs(const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f
   F.b = P.b; F.kcap = P.kcap; F.kc = P.kc; F.r = P.r;
   F.osamp = t->opts.oversample;
   F.mixed = t->opts.precision == HMLE_MIXED_FP32 ? 1 : 0;
+  F.fixed_k = t->opts.fixed_rank;
   // The FP32 products leave noise of about 1e-7 of |C_T| in a Schur
   // complement; truncating below that would keep noise as rank.  The mixed
   // factor is truncated at max(eps, 1e-7); the accuracy of the quadratic
@@ -577,6 +579,7 @@ hmle_status hmle_opts_default(hmle_opts *o) {
   o->pcg_max_iter = 50;
   o->seed = 0x5eed;
   o->leaf_lowrank = 0;
+  o->fixed_rank = 0;
   return HMLE_OK;
 }
 
@@ -638,6 +641,8 @@ hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n, int32_
     return fail(ctx, HMLE_ERR_INVALID_ARG, "eta > 0 and 0 < aca_eps < 1 required");
   if (o.max_rank < 8 || o.max_rank > 64 || (o.max_rank % 8) != 0)
     return fail(ctx, HMLE_ERR_INVALID_ARG, "max_rank must be a multiple of 8 in [8, 64]");
+  if (o.fixed_rank < 0 || o.fixed_rank > o.max_rank)
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "fixed_rank must be in [0, max_rank]");
   if (o.oversample < 4 || o.max_rank + o.oversample > 64)
     return fail(ctx, HMLE_ERR_INVALID_ARG, "oversample >= 4 and max_rank + oversample <= 64");
   if (o.precision != HMLE_FP64 && o.precision != HMLE_MIXED_FP32)

@@ -854,9 +854,17 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, i
         --k;
       }
       if (!(total > 0.0)) k = 0;
-      if (k > F.kcap) { raise_flag(F.flags, kFlagRankOverflow); k = F.kcap; }
-      // too few samples left to trust the numerical rank
-      if (k > r - F.osamp / 2) raise_flag(F.flags, kFlagRankOverflow);
+      if (F.fixed_k > 0) {
+        // fixed-rank mode (the rank-fixed approximation of Sec. 2): the
+        // leading fixed_k directions whatever the accuracy, never an overflow
+        k = 0;
+        while (k < r && sig[ord[k]] > 1e-14 * sig[ord[0]]) ++k;
+        k = min(k, min(F.fixed_k, F.kcap));
+      } else {
+        if (k > F.kcap) { raise_flag(F.flags, kFlagRankOverflow); k = F.kcap; }
+        // too few samples left to trust the numerical rank
+        if (k > r - F.osamp / 2) raise_flag(F.flags, kFlagRankOverflow);
+      }
       s_rank = k;
       F.rank_l[L.blk] = k;
     }

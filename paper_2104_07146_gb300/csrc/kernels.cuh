@@ -27,6 +27,7 @@ struct AsmArgs {
   int32_t *rank_c;
   double *cnorm;           // |C_block|_F estimate of every admissible block
   int *flags;
+  int fixed_k;             // > 0: fixed-rank mode, every block at most this rank
   const ThetaDev *thd;     // the same theta in device memory (read by captured kernels)
   const double *Cd;        // dense near-field blocks (b x b at each dense block's off_d)
   int b;                   // leaf size (leading dimension of the Cd blocks)
@@ -77,6 +78,7 @@ struct FactorArgs {
   uint64_t seed;
   int b, kcap, kc, r;
   int osamp;               // oversampling of the randomised compression
+  int fixed_k;             // > 0: fixed-rank mode (truncate at this rank, no overflow)
   int mixed;               // 1: the Schur-update and panel-update products in FP32
 };
 

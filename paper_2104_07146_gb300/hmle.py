@@ -34,7 +34,7 @@ class Opts(C.Structure):
     _fields_ = [("leaf_size", C.c_int32), ("eta", C.c_double), ("aca_eps", C.c_double),
                 ("max_rank", C.c_int32), ("oversample", C.c_int32), ("precision", C.c_int32),
                 ("seed", C.c_uint64), ("leaf_lowrank", C.c_int32), ("pcg_tol", C.c_double),
-                ("pcg_max_iter", C.c_int32)]
+                ("pcg_max_iter", C.c_int32), ("fixed_rank", C.c_int32)]
 
 
 class FitOpts(C.Structure):

@@ -217,6 +217,20 @@ def test_mloe_mmom_match_dense(ctx):
     assert abs(lo0) <= 1e-6 and abs(mo0) <= 1e-6
 
 
+def test_fixed_rank_mode(ctx):
+    # Sec. 2's rank-fixed approximation: every block of C~ and L~ at most k,
+    # no rank overflow; at k = 16 on the small configuration L stays close to
+    # the exact value
+    locs = synth.locations_uniform(2000, 2, seed=1000)
+    th = (0.1, 0.5, 1.0, 0.01)
+    Z = oracle.simulate(locs, th, synth.normal(1001, 2000))
+    t = _tree(ctx, locs, leaf_size=32, aca_eps=1e-8, fixed_rank=16)
+    ll, info = t.loglik(th, Z)
+    assert info.max_rank_c <= 16 and info.max_rank_l <= 16
+    ref = oracle.loglik_dense(locs, Z, th)[0]
+    assert abs(ll - ref) / 2000 <= 1e-3, (ll, ref)
+
+
 def test_bounded_barrier_wait_reports_timeout(ctx):
     # failure detection without a GPU fault: a grid barrier that one more CTA
     # than exists should reach runs out of its bounded wait; the call reports
