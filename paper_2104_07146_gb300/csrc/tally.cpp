@@ -2,8 +2,9 @@
 // host from the θ-independent plan and the ranks that evaluation produced.
 // This is the flop counter per phase: it counts the arithmetic the
 // left-looking sweep must do with the actual ranks (not the padded block
-// capacities), and a Matern entry as 48 flops (distance, Clenshaw degree 20,
-// scale).  Used for the achieved-throughput side of the roofline.
+// capacities).  The assembly (Matern entries, ACA) is not part of the sweep
+// and is not counted here.  Used for the achieved-throughput side of the
+// roofline.
 #include <algorithm>
 
 #include "hmle_internal.h"
@@ -70,10 +71,11 @@ double tally_flops(const Plan &P, int kind, const std::vector<int32_t> &rc,
         f += (std::ceil(L.m / 64.0) + L.gm + std::ceil(L.p / 64.0) + L.gp) * hh(rt + qr, rt);
       }
       break;
-    case 5:  // k_tsqr_final: QR of the stacked group factors + Jacobi sweeps
+    case 5:  // k_tsqr_final: QR of the stacked group factors, the pivoted QR of
+             // each r x r R (Y and Z), and the Jacobi sweeps (device count)
       for (const LrTarget &L : P.lrt) {
         const double rt = sw(L.blk);
-        f += (L.gm + L.gp) * hh(rt + qr, rt);
+        f += (L.gm + L.gp) * hh(rt + qr, rt) + 2.0 * hh(rt, rt);
       }
       f += jacobi_flops;
       break;
@@ -103,10 +105,10 @@ double tally_flops(const Plan &P, int kind, const std::vector<int32_t> &rc,
         }
       }
       break;
-    case 10:  // k_dense_reduce: Matern entries + subtractions
+    case 10:  // k_dense_reduce: the pair products subtracted from the assembled C_IK
       for (const DenseTarget &dt : P.dns) {
         const BlockDesc &T = P.blocks[dt.blk];
-        f += (double)(T.rend - T.rbeg) * (T.cend - T.cbeg) * (48.0 + (dt.p1 - dt.p0));
+        f += (double)(T.rend - T.rbeg) * (T.cend - T.cbeg) * (dt.p1 - dt.p0);
       }
       break;
     case 11:  // k_potrf
