@@ -254,7 +254,7 @@ hmle_status hmle_fit_profiled(hmle_ctx *ctx, const hmle_tree *tree, const double
  * (the C21 / C12 blocks of Sec. 1, without a nugget) at theta:
  *  trans = 0: y (m) = C21 x (x: n doubles, caller order);
  *  trans = 1: y (n, caller order) = C12 x (x: m doubles).
- * locs2: m x d row-major.  Every pointer host or device.  Used with hmle_solve
+ * locs2: m x d row-major, m >= 1.  Every pointer host or device.  Used with hmle_solve
  * for the prediction variances of Eq. 5-6.  Errors: INVALID_ARG, OOM, CUDA. */
 hmle_status hmle_cross_matvec(hmle_ctx *ctx, const hmle_tree *tree, const hmle_theta *theta,
                               const double *locs2, int64_t m, int32_t trans, const double *x,
@@ -265,7 +265,7 @@ hmle_status hmle_cross_matvec(hmle_ctx *ctx, const hmle_tree *tree, const hmle_t
  * from the factor f of C11 (forward and backward sweeps, as hmle_solve); C21
  * is generated from the Matern function at f's theta, without a nugget (the
  * new locations are other points).  Z1: n doubles in caller order; locs2:
- * m x d row-major; Z2: m doubles (host or device each).  Afterwards
+ * m x d row-major, m >= 1; Z2: m doubles (host or device each).  Afterwards
  * hmle_loglik(f, NULL) returns L for this Z1.
  * Errors: INVALID_ARG, OOM, CUDA, TIMEOUT. */
 hmle_status hmle_predict(hmle_ctx *ctx, const hmle_hfactor *f, const double *Z1,
@@ -283,7 +283,8 @@ hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tree,
  * `concurrency` of them in flight at once (0 means 8), each on its own
  * evaluation buffers, stream pair and captured graph, so that independent
  * trial points of the optimiser fill the GPU together.
- *  thetas  m parameter sets;  Z  n doubles (caller order, host or device),
+ *  thetas  m >= 0 parameter sets (m = 0 returns HMLE_OK at once);
+ *          Z  n doubles (caller order, host or device),
  *          shared by all evaluations;  ll  m outputs (-inf for a failed one);
  *  status  m per-evaluation statuses, or NULL.
  * Returns the first hard error (CUDA, OOM, INVALID_ARG), or HMLE_OK; NOT_SPD
@@ -299,7 +300,8 @@ hmle_status hmle_loglik_batch(hmle_ctx *ctx, const hmle_tree *tree, const hmle_t
  * trials); they run in waves of up to `concurrency` (0 means 8), each on a
  * buffer of its own tree, streams and captured graph as in
  * hmle_loglik_batch.  Z of a task: n_tree doubles in caller order, host or
- * device; tasks that pass the same Z pointer share one staged copy.
+ * device; tasks that pass the same Z pointer share one staged copy.  ntask
+ * = 0 returns HMLE_OK at once.
  * Outputs and errors as hmle_loglik_batch. */
 typedef struct {
   const hmle_tree *tree;

@@ -1269,6 +1269,7 @@ hmle_status hmle_loglik_batch(hmle_ctx *ctx, const hmle_tree *tc, const hmle_the
   if (concurrency > 64) concurrency = 64;
   for (int i = 0; i < m; ++i)
     if (!theta_ok(&thetas[i])) return fail(ctx, HMLE_ERR_INVALID_ARG, "theta out of range");
+  if (m == 0) return HMLE_OK;
   hmle_tree *t = const_cast<hmle_tree *>(tc);
   const int W = std::min<int>(concurrency, std::max(m, 1));
   hmle_status s0 = ensure_pool(ctx, t, W);
@@ -1299,6 +1300,7 @@ hmle_status hmle_loglik_multi(hmle_ctx *ctx, const hmle_task *tasks, int32_t m, 
     if (!tasks[i].tree || !tasks[i].Z) return fail(ctx, HMLE_ERR_INVALID_ARG, "null tree or Z in a task");
     if (!theta_ok(&tasks[i].theta)) return fail(ctx, HMLE_ERR_INVALID_ARG, "theta out of range");
   }
+  if (m == 0) return HMLE_OK;
   const int W = std::min<int>(concurrency, std::max(m, 1));
   // stage every distinct Z once
   std::vector<const double *> src;
