@@ -468,6 +468,25 @@ hmle_status hmle_profile_select(hmle_ctx *ctx, const char *kernel);
  * number of launches, algorithmic FP64 flops.  Any pointer may be NULL. */
 hmle_status hmle_profile_read(hmle_ctx *ctx, double *ms, int64_t *launches, double *flops);
 
+/* Measurement support (no counterpart in the paper): the algorithmic work of
+ * the two phases outside the factorisation sweep, for the factor f and the
+ * ranks its assembly and factorisation produced (Sec. 2, storage and
+ * complexity of the H-matrix):
+ *  asm_flops    FP64 flops of assembling C~ (a3, a4): every dense block's
+ *               m x p entries, and for an admissible block of ACA rank k
+ *               the k rows and columns the cross approximation generates,
+ *               (m + p)(k e + k (k - 1)) with the residual updates; e =
+ *               3 d + 68 flops per Matern entry (distance, scaling, the
+ *               degree-20 Clenshaw recurrence of the table, sigma^2);
+ *  solve_bytes  bytes of the factor that one forward and one backward sweep
+ *               (hmle_solve) must read: the lower triangle of each diagonal
+ *               leaf block, every entry of the other dense blocks, and U and
+ *               W of each low-rank block at its rank, 8 bytes per double,
+ *               twice; the vectors' own traffic is not counted.
+ * Either pointer may be NULL.  Errors: INVALID_ARG, CUDA. */
+hmle_status hmle_phase_work(hmle_ctx *ctx, const hmle_hfactor *f, double *asm_flops,
+                            double *solve_bytes);
+
 #ifdef __cplusplus
 }
 #endif

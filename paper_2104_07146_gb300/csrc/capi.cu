@@ -1465,6 +1465,36 @@ hmle_status hmle_profile_read(hmle_ctx *ctx, double *ms, int64_t *launches, doub
   return HMLE_OK;
 }
 
+hmle_status hmle_phase_work(hmle_ctx *ctx, const hmle_hfactor *f, double *asm_flops,
+                            double *solve_bytes) {
+  if (!ctx || !f || !f->h) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  const hmle_hmatrix *h = f->h;
+  const hmle_tree *t = h->tree;
+  const Plan &P = t->plan;
+  const size_t nb = P.blocks.size();
+  std::vector<int32_t> rc(nb), rl(nb);
+  CK(cudaMemcpyAsync(rc.data(), h->rank_c, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, ctx->st), "ranks");
+  CK(cudaMemcpyAsync(rl.data(), f->rank_l, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, ctx->st), "ranks");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  const double e = 3.0 * t->d + 68.0;   // flops per Matern entry
+  double fa = 0.0, words = 0.0;
+  for (size_t x = 0; x < nb; ++x) {
+    const BlockDesc &B = P.blocks[x];
+    const double m = B.rend - B.rbeg, p = B.cend - B.cbeg;
+    if (B.kind == kDense) {
+      fa += m * p * e;
+      words += (B.rbeg == B.cbeg) ? m * (m + 1.0) / 2.0 : m * p;
+    } else {
+      const double k = rc[x];
+      fa += (m + p) * (k * e + k * (k - 1.0));
+      words += (m + p) * rl[x];
+    }
+  }
+  if (asm_flops) *asm_flops = fa;
+  if (solve_bytes) *solve_bytes = 2.0 * 8.0 * words;
+  return HMLE_OK;
+}
+
 // --- MLE (Sec. 2; transform of Sec. 5) ----------------------------------
 static void to_theta(const double x[4], hmle_theta *t) {
   double sigma = 2.0 / std::pow(1.1, x[0]);

@@ -126,6 +126,7 @@ def lib():
                               C.c_int),
             "hmle_matern_eval_noalloc": ([P, P, C.c_int32, P, C.c_int64, P], C.c_int),
             "hmle_profile_read": ([P, P, P, P], C.c_int),
+            "hmle_phase_work": ([P, P, P, P], C.c_int),
         }
         for name, (argt, rest) in sigs.items():
             fn = getattr(L, name)
@@ -142,7 +143,7 @@ def exported_symbols():
             "hmle_tree_permutation", "hmle_assemble", "hmle_hmatrix_destroy",
             "hmle_hmatrix_matvec", "hmle_factor", "hmle_factor_destroy", "hmle_loglik",
             "hmle_loglik_eval", "hmle_fit", "hmle_matern_eval", "hmle_profile_select",
-            "hmle_profile_read", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_predict", "hmle_fit_profiled", "hmle_cross_matvec", "hmle_loglik_multi", "hmle_autotune",
+            "hmle_profile_read", "hmle_phase_work", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_predict", "hmle_fit_profiled", "hmle_cross_matvec", "hmle_loglik_multi", "hmle_autotune",
             "hmle_theta_to_x", "hmle_x_to_theta", "hmle_selftest_barrier", "hmle_features", "hmle_mlp_nparams",
             "hmle_mlp_create", "hmle_mlp_destroy", "hmle_mlp_set", "hmle_mlp_get",
             "hmle_mlp_forward", "hmle_mlp_grad", "hmle_mlp_adam_step", "hmle_mlp_train",
@@ -450,6 +451,14 @@ class Factor:
         ctx = self.hm.tree.ctx
         ctx.check(lib().hmle_solve(ctx._h, self._h, P(Z.ctypes.data), P(X.ctypes.data)), "hmle_solve")
         return X
+
+    def phase_work(self):
+        """(assembly FP64 flops, bytes of the factor read by one hmle_solve)."""
+        fa, sb = C.c_double(), C.c_double()
+        ctx = self.hm.tree.ctx
+        ctx.check(lib().hmle_phase_work(ctx._h, self._h, C.byref(fa), C.byref(sb)),
+                  "hmle_phase_work")
+        return fa.value, sb.value
 
     def predict(self, Z, locs2) -> np.ndarray:
         """Kriging prediction (Eq. 4) at the m x d locations locs2."""

@@ -118,3 +118,15 @@ def test_invalid_inputs_are_rejected_and_the_context_stays_usable(ctx):
     ll, _ = t.loglik(TH, Z)
     ref, _, _ = oracle.loglik_dense(ok, Z, TH)
     assert abs(ll - ref) / 200 <= 1e-6
+
+
+def test_phase_work_of_a_single_leaf(ctx):
+    # one dense diagonal block of m = n points: n^2 Matern entries of
+    # 3d + 68 flops, and a solve reads its lower triangle once per sweep
+    n = 40
+    locs = synth.locations_uniform(n, 2, seed=851)
+    Z = synth.normal(852, n)
+    f = _tree(ctx, locs, leaf_size=64).assemble(TH).factor(Z)
+    fa, sb = f.phase_work()
+    assert fa == n * n * (3 * 2 + 68)
+    assert sb == 2 * 8 * n * (n + 1) / 2
