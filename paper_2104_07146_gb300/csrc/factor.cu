@@ -6,17 +6,19 @@
 //  P2  k_side_t/s, k_rows   Y = S_T Omega for every low-rank target T whose
 //      column cluster starts at K, with S_T = C_T - sum_pairs U_A G_AB U_B^T
 //      and Omega a counter-based random sign matrix.
-//  P3  k_tsqr_part, k_tsqr_final, k_tall_apply (twice)   Q = orth(Y): the R
-//      factor of Y by Householder reflections over row groups (TSQR), the
-//      one-sided Jacobi SVD R = U Sigma V^T, and Q = Y V Sigma^{-1}
-//      (directions below 1e-14 of the largest singular value dropped); the
-//      second pass restores orthogonality to rounding level.
+//  P3  k_tsqr_part, k_tsqr_final, k_tall_apply, k_cholqr_part/final,
+//      k_tall_apply   Q = orth(Y): the R factor of Y by Householder
+//      reflections over row groups (TSQR), a column-pivoted QR of that R
+//      (R P = Q_r R_p, stopped where the pivot norm falls below 1e-14 of the
+//      first), Q1 = Y P R_p11^{-1}, then one CholQR pass that restores
+//      orthogonality to rounding level.
 //  P4  as P2 with S_T^T applied to Q: Z = S_T^T Q.
 //  P5  k_tsqr_part, k_tsqr_final (truncating), k_tall_apply   the SVD of Z
-//      from its R factor; keep the leading k with tail energy sum_{i>=k}
-//      sigma_i^2 <= eps^2 max(|S_T|_F^2, |C_T|_F^2): U_T = Q V_k,
-//      W_T = Z V_k (the start of the forward solve of W_T).
-//  P6  k_dense       S_IK = C_IK - sum_pairs U_A G_AB U_B^T for the dense
+//      from its R factor (pivoted QR, then one-sided Jacobi on R_p^T); keep
+//      the leading k with tail energy sum_{i>=k} sigma_i^2 <= eps^2
+//      max(|S_T|_F^2, |C_T|_F^2) (or the leading fixed_k in the fixed-rank
+//      mode): U_T = Q V_k, W_T = Z V_k (the start of the forward solve of W_T).
+//  P6  k_dense_pair, k_dense_reduce   S_IK = C_IK - sum_pairs U_A G_AB U_B^T for the dense
 //      blocks of column K (diagonal first); C_IK from the assembled dense
 //      near field.
 //  P7  k_potrf       L_KK = chol(S_KK); log-det part 2 sum log L_ii.
@@ -25,8 +27,10 @@
 //  P10 k_htask, k_updrow   blocks A whose columns end at K push
 //      W[rows A] -= U_A (W_A^T W[cols A]) (dense A: D_A W[cols A]) into every
 //      open panel containing them.
-// All FP64.  Every output element is written by exactly one thread, in a
-// fixed order: the sweep is deterministic.
+// All FP64, except that the mixed form runs the update products (k_gram,
+// k_side_t/s, k_rows, k_dense_pair, k_htask, k_updrow) in FP32 (template
+// parameter Tc).  Every output element is written by exactly one thread, in
+// a fixed order: the sweep is deterministic.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -474,7 +478,7 @@ __global__ void __launch_bounds__(kThreads) k_rows(FactorArgs F, int rt0, int tr
       [&](int i, int j, double v) { Y[(I0 - base + i) + (int64_t)j * ld] = v; }, smem);
 }
 
-// --- tall QR (R factor only) and SVD of the small R -----------------------
+// --- tall QR (R factor only), then pivoted QR / SVD of the small R --------
 constexpr int kQrRows = 64;
 
 // R factor of the stacked h x r matrix A = [R; X] (ld h) in shared memory, in
@@ -559,11 +563,6 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_part(FactorArgs F, int t0, in
   }
 }
 
-// Combine the row groups' R factors, then the one-sided Jacobi SVD
-// R = U Sigma V^T.  mode 0 (orthonormalise): M = V Sigma^{-1} on singular
-// values above 1e-14 of the largest (zero columns otherwise).  mode 1
-// (truncate): k = smallest rank whose tail energy sum_{i>=k} sigma_i^2 is
-// <= eps^2 max(sum sigma_i^2, |C_T|_F^2); M = V_k (r x kcap); rank to rank_l.
 // Column-pivoted Householder QR of the r x r matrix B (ld lb) in shared
 // memory, in place: B P = Q R.  At step j the remaining column of largest
 // norm is swapped in; the sweep stops where that norm falls below 1e-14 of
@@ -662,6 +661,14 @@ __device__ int smem_pivoted_qr(double *B, int lb, int r, int *piv, double *cn, P
   return S.k1;
 }
 
+// Combine the row groups' R factors of Y (which = 0) or Z (which = 1) into
+// one r x r R, then its column-pivoted QR R P = Q_r R_p with k1 kept pivots.
+// mode 0 (orthonormalise): M = P_{:,1:k1} R_p11^{-1}, so that Q1 = Y M.
+// mode 1 (truncate): the singular values and right singular vectors of R by
+// one-sided Jacobi on R_p^T; k = smallest rank whose tail energy
+// sum_{i>=k} sigma_i^2 is <= eps^2 max(sum sigma_i^2, |C_T|_F^2), or the
+// leading fixed_k directions in the fixed-rank mode; M = V_k (r x kcap),
+// k to rank_l.
 __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, int which, int mode) {
   extern __shared__ double smem[];
   __shared__ double red[32];
@@ -880,7 +887,7 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, i
   }
 }
 
-// Re-orthonormalisation of Q1 = Y V Sigma^{-1} (nearly orthonormal kept
+// Re-orthonormalisation of Q1 = Y P R_p11^{-1} (nearly orthonormal kept
 // columns): partial Grams Q1_g^T Q1_g of the row groups ...
 __global__ void __launch_bounds__(kThreads) k_cholqr_part(FactorArgs F, int t0) {
   extern __shared__ double smem[];
@@ -1367,7 +1374,7 @@ int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaE
     LAUNCH(KK_SIDE_T, st, k_side_t<Tc><<<(S.bent1 - S.bent0) + nt, kThreads, smt, st>>>(F, S.bent0, S.bent1 - S.bent0, S.lrt0, 0));
     if (S.aent1 > S.aent0) LAUNCH(KK_SIDE_S, st, k_side_s<Tc><<<S.aent1 - S.aent0, kThreads, stn, st>>>(F, S.aent0, 0));
     LAUNCH(KK_ROWS, st, k_rows<Tc><<<S.arow1 - S.arow0, kThreads, sm, st>>>(F, S.arow0, 0));
-    // Q = orth(Y): R of Y, SVD, Q1 = Y V Sigma^{-1}, then CholQR
+    // Q = orth(Y): R of Y, pivoted QR, Q1 = Y P R_p11^{-1}, then CholQR
     LAUNCH(KK_TSQR_PART, st, k_tsqr_part<<<dim3(nt, maxgm), kThreads, qr_smem, st>>>(F, S.lrt0, 0));
     LAUNCH(KK_TSQR_FINAL, st, k_tsqr_final<<<nt, kThreads, qrf_smem, st>>>(F, S.lrt0, 0, 0));
     LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch), kThreads, sm, st>>>(F, S.lrt0, 0));
