@@ -13,6 +13,10 @@ approximates):
   L = -n/2 log(2 pi) - 1/2 log|C| - 1/2 Z^T C^{-1} Z, with log|C| =
   2 sum log L_ii (Sec. 2, "Storage and complexity") and
   Z^T C^{-1} Z = |L^{-1} Z|^2.
+* ``ldlt`` / ``loglik_ldlt`` -- the square-root-free factorisation
+  C = L D L^T of Sec. 2 (L unit lower triangular, D diagonal, related to the
+  Cholesky factor by L_chol = L D^(1/2)); log|C| = sum log d_i and
+  Z^T C^{-1} Z = sum (L^{-1} Z)_i^2 / d_i.
 * ``predict`` / ``rmse`` / ``mloe_mmom`` -- kriging prediction
   Z2 = C21 C11^{-1} Z1 (Eq. 4), the root mean square error of Eq. 7 and the
   MLOE / MMOM measures of Eq. 5-6.
@@ -138,6 +142,48 @@ def loglik_from_matrix(C: np.ndarray, Z: np.ndarray):
         q += v * v
     ll = -0.5 * n * math.log(2.0 * math.pi) - 0.5 * logdet - 0.5 * q
     return ll, logdet, q
+
+
+def ldlt(C: np.ndarray):
+    """C = L D L^T without pivoting (Sec. 2, the factorisation that extracts
+    no square roots): column j gives d_j = C_jj - sum_{k<j} L_jk^2 d_k, then
+    L_ij = (C_ij - sum_{k<j} L_ik L_jk d_k) / d_j for i > j.  Returns
+    (L unit lower triangular, d).  It exists whenever every leading minor of
+    C is non-zero, so it also runs on symmetric indefinite matrices; a zero
+    pivot raises numpy.linalg.LinAlgError."""
+    C = np.asarray(C, dtype=np.float64)
+    n = C.shape[0]
+    L = np.eye(n)
+    d = np.zeros(n)
+    for j in range(n):
+        d[j] = C[j, j] - np.dot(L[j, :j] ** 2, d[:j])
+        if d[j] == 0.0:
+            raise np.linalg.LinAlgError("zero pivot in LDL^T")
+        for i in range(j + 1, n):
+            L[i, j] = (C[i, j] - np.dot(L[i, :j] * L[j, :j], d[:j])) / d[j]
+    return L, d
+
+
+def loglik_ldlt(C: np.ndarray, Z: np.ndarray):
+    """(L, log|C|, Z^T C^{-1} Z) of Eq. 1 through C = L D L^T: w solves the
+    unit lower triangular system L w = Z by forward substitution, log|C| =
+    sum log d_i and q = sum w_i^2 / d_i (sequential sums in index order).
+    The Gaussian density needs C positive definite, so a pivot d_i <= 0
+    raises numpy.linalg.LinAlgError, as the Cholesky route does."""
+    L, d = ldlt(C)
+    if not np.all(d > 0.0):
+        raise np.linalg.LinAlgError("non-positive pivot in LDL^T: C is not positive definite")
+    n = len(d)
+    Z = np.asarray(Z, dtype=np.float64)
+    w = np.empty(n)
+    for i in range(n):
+        w[i] = Z[i] - np.dot(L[i, :i], w[:i])
+    logdet = 0.0
+    q = 0.0
+    for i in range(n):
+        logdet += math.log(d[i])
+        q += w[i] * w[i] / d[i]
+    return -0.5 * n * math.log(2.0 * math.pi) - 0.5 * logdet - 0.5 * q, logdet, q
 
 
 def loglik_dense(locs: np.ndarray, Z: np.ndarray, theta):

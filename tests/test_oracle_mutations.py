@@ -61,3 +61,28 @@ def test_sqrt2nu_scaling_fails_half_integer_pin():
     x = 0.7
     alt = oracle.matern_unit(1.5, math.sqrt(3.0) * x)
     assert abs(alt - (1 + x) * math.exp(-x)) > 1e-2
+
+
+def _ll_ldlt(C, Z, drop_d=False, sqrt_d=False):
+    # Eq. 1 through C = L D L^T with a planted mistake: q without the 1/d_i
+    # weights, or log|C| from sqrt(d_i) as if d held Cholesky diagonals
+    n = C.shape[0]
+    L, d = oracle.ldlt(C)
+    w = np.linalg.solve(L, Z)
+    q = float(np.sum(w * w) if drop_d else np.sum(w * w / d))
+    logdet = float(np.sum(np.log(np.sqrt(d)) if sqrt_d else np.log(d)))
+    return -0.5 * n * LOG2PI - 0.5 * logdet - 0.5 * q
+
+
+def test_ldlt_mistakes_fail_nugget_and_cholesky_pins():
+    n, t2 = 40, 0.3
+    Z = synth.normal(6, n)
+    ref = -0.5 * n * LOG2PI - 0.5 * n * math.log(t2) - float(Z @ Z) / (2 * t2)
+    assert abs(_ll_ldlt(t2 * np.eye(n), Z) - ref) < 1e-10
+    assert abs(_ll_ldlt(t2 * np.eye(n), Z, drop_d=True) - ref) > 1.0
+    locs = synth.locations_uniform(60, 2, seed=7)
+    C = oracle.matern_matrix(locs, (0.2, 0.9, 1.0, 0.05))
+    Z = synth.normal(8, 60)
+    good = oracle.loglik_from_matrix(C, Z)[0]
+    assert abs(_ll_ldlt(C, Z) - good) < 1e-9 * abs(good)
+    assert abs(_ll_ldlt(C, Z, sqrt_d=True) - good) > 1.0

@@ -328,3 +328,55 @@ def test_mloe_mmom_vanish_for_the_true_model_and_mloe_is_nonnegative():
     for tha in [(0.3, 0.8, 1.0, 0.02), (0.15, 1.6, 2.0, 0.1), (0.08, 0.5, 0.5, 0.01)]:
         lo, mo = oracle.mloe_mmom(locs1, locs2, th, tha)
         assert lo >= -1e-12
+
+
+# --- LDL^T (Sec. 2: the factorisation without square roots) -------------------
+
+def test_ldlt_hand_examples():
+    # [[4, 2], [2, 3]]: d1 = 4, l21 = 2/4, d2 = 3 - (1/2)^2 4 = 2 (by hand)
+    L, d = oracle.ldlt(np.array([[4.0, 2.0], [2.0, 3.0]]))
+    assert L[1, 0] == 0.5 and list(d) == [4.0, 2.0] and L[0, 1] == 0.0 and L[1, 1] == 1.0
+    # indefinite [[1, 2], [2, 1]]: the factorisation exists, d = (1, -3), l21 = 2
+    L, d = oracle.ldlt(np.array([[1.0, 2.0], [2.0, 1.0]]))
+    assert L[1, 0] == 2.0 and list(d) == [1.0, -3.0]
+    # 3 x 3 by hand: [[2, -2, 0], [-2, 5, 3], [0, 3, 6]] -> d = (2, 3, 3),
+    # l21 = -1, l31 = 0, l32 = 1
+    L, d = oracle.ldlt(np.array([[2.0, -2.0, 0.0], [-2.0, 5.0, 3.0], [0.0, 3.0, 6.0]]))
+    assert list(d) == [2.0, 3.0, 3.0]
+    assert (L[1, 0], L[2, 0], L[2, 1]) == (-1.0, 0.0, 1.0)
+
+
+def test_ldlt_is_the_cholesky_factor_without_square_roots():
+    # L_chol = L D^(1/2) (Sec. 2), against LAPACK's Cholesky as a library routine
+    locs = synth.locations_uniform(50, 2, seed=61)
+    C = oracle.matern_matrix(locs, (0.2, 1.3, 1.5, 0.02))
+    L, d = oracle.ldlt(C)
+    Lc = np.linalg.cholesky(C)
+    assert np.abs(L * np.sqrt(d) - Lc).max() <= 1e-12
+    assert np.abs(L @ np.diag(d) @ L.T - C).max() <= 1e-13
+
+
+def test_loglik_ldlt_matches_closed_forms_and_the_cholesky_route():
+    # nugget only: L = I, d = tau2, the closed form of Eq. 1
+    n, t2 = 30, 0.3
+    Z = synth.normal(62, n)
+    ll, ld, q = oracle.loglik_ldlt(t2 * np.eye(n), Z)
+    assert abs(ld - n * math.log(t2)) <= 1e-12 * n
+    assert abs(q - Z @ Z / t2) <= 1e-12 * (Z @ Z / t2)
+    assert abs(ll - (-0.5 * n * math.log(2 * math.pi) - 0.5 * n * math.log(t2) - 0.5 * Z @ Z / t2)) <= 1e-10
+    # a Matern C: the same (L, log|C|, q) as the Cholesky route, and log|C|
+    # as numpy's slogdet (LU with pivoting, another library routine)
+    locs = synth.locations_uniform(80, 2, seed=63)
+    C = oracle.matern_matrix(locs, (0.15, 0.7, 1.0, 0.01))
+    Z = synth.normal(64, 80)
+    a = oracle.loglik_ldlt(C, Z)
+    b = oracle.loglik_from_matrix(C, Z)
+    sign, sld = np.linalg.slogdet(C)
+    assert sign == 1.0 and abs(a[1] - sld) <= 1e-10 * abs(sld)
+    for u, v in zip(a, b):
+        assert abs(u - v) <= 1e-10 * max(1.0, abs(v))
+
+
+def test_loglik_ldlt_rejects_an_indefinite_matrix():
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.loglik_ldlt(np.array([[1.0, 2.0], [2.0, 1.0]]), np.ones(2))
