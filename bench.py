@@ -228,6 +228,7 @@ def run_gpu(args):
             dist.barrier()
             dist.destroy_process_group()
         return
+    phases = phase_rooflines(tree, theta, Z, single_ms, info.flops)
     value = job_rate(ws, args.steps * args.batch, ms)
     e2e = job_rate(ws, args.steps * args.batch, ms_e2e)
     achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] > 0 else None
@@ -264,6 +265,7 @@ def run_gpu(args):
             "frac": (info.flops * value / ws / 1e9 / FP64_PEAK_GFLOPS) if info.flops else None,
             "note": "whole batched step on one GPU: algorithmic flops of one evaluation (plan "
                     "x ranks) x evaluations/s, against the FP64 ALU peak"},
+        "phases": phases,
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
@@ -362,6 +364,53 @@ def other_forms(ctx, locs, Z, Zd, thetas, B, fp64_value):
     for t, _, _, _ in fields:
         t.close()
     return res
+
+
+def phase_rooflines(tree, theta, Z, single_ms, sweep_flops):
+    """Time and algorithmic work of the phases of one evaluation: the
+    assembly of C~ (a3 + a4) and one solve through a stored factor (a10 +
+    a11, the persistent sweeps), each the median of three synchronised
+    library calls, with the work from hmle_phase_work; the factorisation
+    sweep with its fused forward solve (a5-a10) is the single evaluation
+    minus the assembly.  A failure here is reported in the line, not raised."""
+    import statistics
+    try:
+        hm = tree.assemble(theta)
+        f = hm.factor(Z)
+        f.solve(Z)                                   # warm-up of the persistent sweeps
+        fa, sb = f.phase_work()
+        ta, ts = [], []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            h2 = tree.assemble(theta)
+            ta.append(time.perf_counter() - t0)
+            h2.close()
+        for _ in range(3):
+            t0 = time.perf_counter()
+            f.solve(Z)
+            ts.append(time.perf_counter() - t0)
+        f.close()
+        hm.close()
+        t_a, t_s = statistics.median(ta), statistics.median(ts)
+        t_sw = single_ms / 1e3 - t_a
+        hbm = _peaks().get("hbm_gbs")
+
+        def row(sec, work, unit, peak, bound, **kw):
+            rate = work / sec / 1e9 if sec > 0 else None
+            return {"s": sec, "work": work, "achieved": rate, "unit": unit, "peak": peak,
+                    "frac": rate / peak if (rate and peak) else None, "bound": bound, **kw}
+        return {
+            "assembly": row(t_a, fa, "GFLOP/s", FP64_PEAK_GFLOPS, "alu",
+                            work_unit="FP64 flops (3d + 68 per Matern entry, ACA updates)"),
+            "sweep": row(t_sw, sweep_flops, "GFLOP/s", FP64_PEAK_GFLOPS, "alu",
+                         work_unit="FP64 flops (plan x ranks)"),
+            "solve": row(t_s, sb, "GB/s", hbm, "hbm",
+                         work_unit="bytes of the factor read by the forward and backward sweeps",
+                         note="limited by the grid barriers of the leaf chain, not by HBM"),
+            "note": "wall times of synchronised library calls (median of 3); sweep = single "
+                    "evaluation - assembly; solve peak = measured HBM copy (MEASURED_PEAKS.json)"}
+    except Exception as e:                           # keep the bench line
+        return {"error": repr(e)}
 
 
 def batch_thetas(theta, B):
