@@ -77,15 +77,19 @@ typedef struct {
 
 /* H-matrix options (the paper leaves the H-matrix construction to the
  * library it used; these are the knobs of this implementation).
- *  leaf_size  b: clusters with at most b points are leaves (8..128).
+ *  leaf_size  b: clusters with at most b points are leaves; a multiple of
+ *             16 in [16, 128].
  *  eta        admissibility: block (t, s) is low-rank when
  *             min(diam t, diam s) <= eta * dist(t, s) (bounding boxes).
- *  aca_eps    relative accuracy of every low-rank block: ACA of C stops at
- *             |u_k||v_k| <= eps |S_k|_F; truncation of the Schur-complement
- *             blocks keeps singular values above eps * |block|_F.
- *  max_rank   capacity (columns) of every low-rank block, 8..96.
+ *  aca_eps    relative accuracy of every low-rank block, in (0, 1): ACA of C
+ *             stops at |u_k||v_k| <= eps |S_k|_F; the truncation of a
+ *             Schur-complement block S drops the trailing singular values
+ *             whose energy sum is <= eps^2 max(|S|_F^2, |C_block|_F^2).
+ *  max_rank   capacity (columns) of every low-rank block of L~; a multiple
+ *             of 8 in [8, 64].  ACA of C may use up to max_rank + 16 (at
+ *             most 64).
  *  oversample extra random samples beyond max_rank for the compression of
- *             updated low-rank blocks (>= 4).
+ *             updated low-rank blocks; >= 4 with max_rank + oversample <= 64.
  *  seed       seed of the counter-based random signs used by that
  *             compression (the result is deterministic for a given seed).
  *  leaf_lowrank  0 (default): admissible blocks between two leaf clusters
@@ -156,8 +160,9 @@ typedef struct hmle_hmatrix hmle_hmatrix;
 typedef struct hmle_hfactor hmle_hfactor;
 
 /* Fill *opts with defaults: leaf 64, eta 2, aca_eps 1e-8, max_rank 32,
- * oversample 8, FP64, seed 0x5eed, leaf_lowrank 0.  Always HMLE_OK for
- * non-NULL opts. */
+ * oversample 8, FP64, seed 0x5eed, leaf_lowrank 0, pcg_tol 1e-10,
+ * pcg_max_iter 50, fixed_rank 0.  HMLE_OK for non-NULL opts, else
+ * INVALID_ARG. */
 hmle_status hmle_opts_default(hmle_opts *opts);
 
 /* Fill *opts with the paper's optimiser settings: ftol = xtol = 1e-4,
@@ -337,7 +342,10 @@ hmle_status hmle_autotune(hmle_ctx *ctx, const double *locs, int64_t n, int32_t 
 
 /* a13 (Sec. 2 and Sec. 5): maximise L over theta by Nelder-Mead in the
  * transformed coordinates sigma = 2/1.1^s0, ell = 1/1.5^l0, nu = 1/1.2^n0,
- * tau = 1/2^t0.  Trial points whose factorisation is not SPD score -inf.
+ * tau = 1/2^t0.  Trial points outside the admissible range of theta, or
+ * whose evaluation fails with NOT_SPD or RANK_OVERFLOW, score L = -inf.
+ * The candidates of one iteration (reflection, expansion, contractions) are
+ * evaluated together as one batch.
  *  theta0     start point; fopts may be NULL for hmle_fit_opts_default.
  *  theta_hat  best point found; loglik_hat its L; n_iter / n_evals may be NULL.
  * Returns HMLE_OK on convergence, HMLE_ERR_NOT_CONVERGED when max_iter was
