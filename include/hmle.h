@@ -495,6 +495,82 @@ hmle_status hmle_profile_read(hmle_ctx *ctx, double *ms, int64_t *launches, doub
 hmle_status hmle_phase_work(hmle_ctx *ctx, const hmle_hfactor *f, double *asm_flops,
                             double *solve_bytes);
 
+/* Host-only inspection of the factorisation schedule (no device work, no
+ * counterpart in the paper; for checking the planner and for tools).
+ * hmle_plan_build builds the θ-independent task lists of the left-looking
+ * leaf sweep (Sec. 2, H-Cholesky) for a given block partition, as
+ * hmle_build_tree does after its device trees:
+ *  n, d        points and dimension; the clusters are the halving of the
+ *              point range in cluster order down to leaves of at most
+ *              leaf_size points (depth = smallest with ceil(n / 2^depth) <=
+ *              leaf_size; cluster h of level l is heap entry 2^l - 1 + h and
+ *              splits at b + (e - b) / 2).
+ *  blocks      nblocks records of 4 int32 (level, i, j, kind): the block of
+ *              row cluster i and column cluster j of that level, j <= i;
+ *              kind 0 = dense (leaf level only), 1 = low-rank (i > j).  They
+ *              must tile the lower triangle, the diagonal leaf blocks
+ *              included, as the device block tree does.
+ *  max_rank, oversample  as in hmle_opts.
+ * Errors: INVALID_ARG (sizes, options, a record out of range, or a
+ * partition the planner rejects), OOM.
+ *
+ * hmle_plan_list copies one of the planner's lists as records of int64
+ * fields: *nrec records of *width fields each (either may be NULL).  With out
+ * = NULL only the sizes are returned; else cap (int64 slots) must hold
+ * nrec * width.  Indices are into the plan's own lists; offsets are in
+ * doubles.  Fields by list:
+ *  SCALARS    n, d, b, depth, nleaf, kcap, kc, r, rhs_panel, ws_max,
+ *             dense_words, uc_words, u_words, w_words
+ *  BLOCKS     kind, level, rbeg, rend, cbeg, cend, rleaf, cleaf, off_d,
+ *             off_uc, off_vc, off_u, panel, slot  (sorted by first column
+ *             leaf, dense before low-rank, then row leaf)
+ *  STEPS      per leaf K: gram0, gram1, gch0, gch1, gred0, gred1, lrt0, lrt1,
+ *             aent0, aent1, bent0, bent1, arow0, arow1, brow0, brow1, dns0,
+ *             dns1, wpan0, wpan1, ht0, ht1, ur0, ur1, dpws, ws_words
+ *  LRT        low-rank targets: blk, m, p, a0, a1, b0, b1, yoff, zoff, soff,
+ *             tcoff, gm, gp, roff
+ *  AENT/BENT  blocks covering a target's rows / columns left of it: target,
+ *             blk, toff, soff, p0, p1 (range in APAIR / BPAIR)
+ *  LRPAIRS    ae, be, goff (-1 unless both blocks are low-rank)
+ *  DNS        dense targets (diagonal first per step): blk, p0, p1
+ *  DPAIRS     a, b, goff
+ *  PANELS     W-panels (the last is the right-hand side): rbeg, rend, width,
+ *             leaf0, off
+ *  WPAN       panel ids solved per step (ranges wpan0..wpan1)
+ *  HTS        deferred-update products: a, panel, hoff
+ *  UROWS      deferred-update rows: panel, leaf, e0, e1 (range in UENTS)
+ *  UENTS      a, hoff (-1 for a dense block)
+ *  GRAMS      a, b, ovb, ove, goff;  GCHUNKS  g, r0, r1, out;
+ *  GREDS      g, nchunk, poff
+ *  AROW/BROW  row tasks of the samples Y / Z: target, leaf, e0, e1 (range in
+ *             AROW_ENT / BROW_ENT, which hold AENT / BENT indices)
+ *  *_RHS, HT_RHS0, UR_RHS0  the right-hand-side panel's share of HTS /
+ *             UROWS / UENTS and its per-step ranges (nleaf + 1 entries)
+ *  BH_BLOCKS, BH0, BUPD, BENTS, BUPD0  the backward sweep's lists: low-rank
+ *             blocks whose rows start at leaf K, per column leaf the entries
+ *             to push, and their per-step ranges
+ *  MV_ROW0, MV_BLOCKS    per leaf row, the blocks of L covering it (diagonal
+ *             first);  MVT_ROW0, MVT_BLOCKS  per leaf, the off-diagonal
+ *             blocks whose columns cover it.
+ * Errors: INVALID_ARG (unknown list, cap too small). */
+typedef enum {
+  HMLE_PLAN_SCALARS = 0, HMLE_PLAN_BLOCKS, HMLE_PLAN_STEPS, HMLE_PLAN_LRT, HMLE_PLAN_AENT,
+  HMLE_PLAN_BENT, HMLE_PLAN_LRPAIRS, HMLE_PLAN_DNS, HMLE_PLAN_DPAIRS, HMLE_PLAN_PANELS,
+  HMLE_PLAN_WPAN, HMLE_PLAN_HTS, HMLE_PLAN_UROWS, HMLE_PLAN_UENTS, HMLE_PLAN_GRAMS,
+  HMLE_PLAN_GCHUNKS, HMLE_PLAN_GREDS, HMLE_PLAN_AROW, HMLE_PLAN_BROW, HMLE_PLAN_AROW_ENT,
+  HMLE_PLAN_BROW_ENT, HMLE_PLAN_APAIR, HMLE_PLAN_BPAIR, HMLE_PLAN_HTS_RHS,
+  HMLE_PLAN_UROWS_RHS, HMLE_PLAN_UENTS_RHS, HMLE_PLAN_HT_RHS0, HMLE_PLAN_UR_RHS0,
+  HMLE_PLAN_BH_BLOCKS, HMLE_PLAN_BH0, HMLE_PLAN_BUPD, HMLE_PLAN_BENTS, HMLE_PLAN_BUPD0,
+  HMLE_PLAN_MV_ROW0, HMLE_PLAN_MV_BLOCKS, HMLE_PLAN_MVT_ROW0, HMLE_PLAN_MVT_BLOCKS
+} hmle_plan_list_id;
+typedef struct hmle_plan hmle_plan;
+hmle_status hmle_plan_build(int64_t n, int32_t d, int32_t leaf_size, const int32_t *blocks,
+                            int32_t nblocks, int32_t max_rank, int32_t oversample,
+                            hmle_plan **out);
+void hmle_plan_destroy(hmle_plan *plan);
+hmle_status hmle_plan_list(const hmle_plan *plan, int32_t which, int64_t *out, int64_t cap,
+                           int64_t *nrec, int32_t *width);
+
 #ifdef __cplusplus
 }
 #endif

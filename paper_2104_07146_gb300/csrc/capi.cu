@@ -657,17 +657,10 @@ hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n, int32_
   }
   cudaStream_t st = ctx->st;
   // cluster ranges (pure integer, host)
-  int depth = 0;
-  while (((n + (1LL << depth) - 1) >> depth) > o.leaf_size) ++depth;
+  const int depth = tree_depth(n, o.leaf_size);
   if (depth > kMaxLevels - 2) return fail(ctx, HMLE_ERR_INVALID_ARG, "tree too deep");
-  const int ncl = (2 << depth) - 1;
-  std::vector<int32_t> cb(ncl), ce(ncl);
-  cb[0] = 0; ce[0] = (int32_t)n;
-  for (int h = 0; h < (1 << depth) - 1; ++h) {
-    int32_t b = cb[h], e = ce[h], mid = b + (e - b) / 2;
-    cb[2 * h + 1] = b; ce[2 * h + 1] = mid;
-    cb[2 * h + 2] = mid; ce[2 * h + 2] = e;
-  }
+  std::vector<int32_t> cb, ce;
+  cluster_ranges(n, depth, cb, ce);
   hmle_tree *t = new (std::nothrow) hmle_tree();
   if (!t) return HMLE_ERR_OOM;
   t->ctx = ctx; t->n = n; t->d = d; t->opts = o;

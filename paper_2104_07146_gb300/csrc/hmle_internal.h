@@ -211,6 +211,13 @@ struct Plan {
   int64_t n_lr_blocks, n_dense_blocks;
 };
 
+// Depth of the cluster tree of n points with leaves of at most leaf_size
+// points (every level halves the clusters), and the clusters' point ranges
+// in heap order (cluster h splits at b + (e - b) / 2 into 2h + 1, 2h + 2).
+int32_t tree_depth(int64_t n, int32_t leaf_size);
+void cluster_ranges(int64_t n, int32_t depth, std::vector<int32_t> &cl_beg,
+                    std::vector<int32_t> &cl_end);
+
 // Build the plan from the cluster ranges and the block list (host).
 // Returns an empty string on success, else an error message.
 std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,

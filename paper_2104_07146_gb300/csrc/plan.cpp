@@ -66,6 +66,25 @@ struct Builder {
 
 }  // namespace
 
+int32_t tree_depth(int64_t n, int32_t leaf_size) {
+  int32_t depth = 0;
+  while (((n + (1LL << depth) - 1) >> depth) > leaf_size) ++depth;
+  return depth;
+}
+
+void cluster_ranges(int64_t n, int32_t depth, std::vector<int32_t> &cb, std::vector<int32_t> &ce) {
+  const int ncl = (2 << depth) - 1;
+  cb.assign(ncl, 0);
+  ce.assign(ncl, 0);
+  cb[0] = 0;
+  ce[0] = (int32_t)n;
+  for (int h = 0; h < (1 << depth) - 1; ++h) {
+    const int32_t b = cb[h], e = ce[h], mid = b + (e - b) / 2;
+    cb[2 * h + 1] = b; ce[2 * h + 1] = mid;
+    cb[2 * h + 2] = mid; ce[2 * h + 2] = e;
+  }
+}
+
 std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
                        const std::vector<int32_t> &cl_beg,
                        const std::vector<int32_t> &cl_end,

@@ -127,6 +127,10 @@ def lib():
             "hmle_matern_eval_noalloc": ([P, P, C.c_int32, P, C.c_int64, P], C.c_int),
             "hmle_profile_read": ([P, P, P, P], C.c_int),
             "hmle_phase_work": ([P, P, P, P], C.c_int),
+            "hmle_plan_build": ([C.c_int64, C.c_int32, C.c_int32, P, C.c_int32, C.c_int32,
+                                 C.c_int32, P], C.c_int),
+            "hmle_plan_destroy": ([P], None),
+            "hmle_plan_list": ([P, C.c_int32, P, C.c_int64, P, P], C.c_int),
         }
         for name, (argt, rest) in sigs.items():
             fn = getattr(L, name)
@@ -147,7 +151,8 @@ def exported_symbols():
             "hmle_theta_to_x", "hmle_x_to_theta", "hmle_selftest_barrier", "hmle_features", "hmle_mlp_nparams",
             "hmle_mlp_create", "hmle_mlp_destroy", "hmle_mlp_set", "hmle_mlp_get",
             "hmle_mlp_forward", "hmle_mlp_grad", "hmle_mlp_adam_step", "hmle_mlp_train",
-            "hmle_matern_eval_noalloc"]
+            "hmle_matern_eval_noalloc", "hmle_plan_build", "hmle_plan_destroy",
+            "hmle_plan_list"]
 
 
 def _ptr(a):
@@ -380,6 +385,54 @@ class Tree:
     def close(self):
         if self._h:
             lib().hmle_tree_destroy(self._h)
+            self._h = P()
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+PLAN_LISTS = ["scalars", "blocks", "steps", "lrt", "aent", "bent", "lrpairs", "dns", "dpairs",
+              "panels", "wpan", "hts", "urows", "uents", "grams", "gchunks", "greds", "arow",
+              "brow", "arow_ent", "brow_ent", "apair", "bpair", "hts_rhs", "urows_rhs",
+              "uents_rhs", "ht_rhs0", "ur_rhs0", "bh_blocks", "bh0", "bupd", "bents", "bupd0",
+              "mv_row0", "mv_blocks", "mvt_row0", "mvt_blocks"]
+
+
+class Plan:
+    """hmle_plan_build: the schedule of the leaf sweep for a given block
+    partition, built on the host (no device).  blocks: (level, i, j, kind)
+    rows; list(name) returns one of PLAN_LISTS as an int64 array of records
+    (fields as in include/hmle.h)."""
+
+    def __init__(self, n, d, leaf_size, blocks, max_rank=32, oversample=8):
+        b = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, 4)
+        self._h = P()
+        st = lib().hmle_plan_build(int(n), int(d), int(leaf_size), P(b.ctypes.data), b.shape[0],
+                                   int(max_rank), int(oversample), C.byref(self._h))
+        if st != HMLE_OK:
+            raise HmleError(st, "hmle_plan_build")
+
+    def list(self, name) -> np.ndarray:
+        which = PLAN_LISTS.index(name)
+        nrec, width = C.c_int64(), C.c_int32()
+        st = lib().hmle_plan_list(self._h, which, None, 0, C.byref(nrec), C.byref(width))
+        if st != HMLE_OK:
+            raise HmleError(st, "hmle_plan_list")
+        out = np.zeros((nrec.value, width.value), dtype=np.int64)
+        if out.size:
+            st = lib().hmle_plan_list(self._h, which, P(out.ctypes.data), out.size, None, None)
+            if st != HMLE_OK:
+                raise HmleError(st, "hmle_plan_list")
+        return out
+
+    def close(self):
+        if self._h:
+            lib().hmle_plan_destroy(self._h)
             self._h = P()
 
     def __del__(self):
