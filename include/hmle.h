@@ -355,6 +355,25 @@ hmle_status hmle_fit(hmle_ctx *ctx, const hmle_tree *tree, const double *Z,
                      hmle_theta *theta_hat, double *loglik_hat,
                      int32_t *n_iter, int32_t *n_evals);
 
+/* The optimiser of hmle_fit and hmle_fit_profiled (Sec. 2, maximisation of
+ * the log-likelihood; Nelder-Mead with reflection 1, expansion 2,
+ * contraction 1/2, shrink 1/2) on a caller's objective, on the host: it
+ * minimises f over dim coordinates (1 <= dim <= 8) from x0 with initial
+ * simplex steps step (dim values, NULL = 1 each).  fopts as hmle_fit (its
+ * step field is not used; NULL = hmle_fit_opts_default).  f(x, dim, user)
+ * may return +inf where it is undefined; NaN counts as +inf.  Each
+ * iteration asks f for all four candidates (reflection, expansion, outside
+ * and inside contraction) before the acceptance rules choose, as hmle_fit
+ * evaluates them as one batch; *n_evals counts the values the rules use.
+ * x_best (dim values) and *f_best receive the best vertex.
+ * Returns HMLE_OK when the tolerance was met, HMLE_ERR_NOT_CONVERGED after
+ * max_iter iterations, INVALID_ARG for a bad dim, NULL or non-finite x0 /
+ * step. */
+typedef double (*hmle_objective)(const double *x, int32_t dim, void *user);
+hmle_status hmle_nelder_mead(int32_t dim, hmle_objective f, void *user, const double *x0,
+                             const double *step, const hmle_fit_opts *fopts, double *x_best,
+                             double *f_best, int32_t *n_iter, int32_t *n_evals);
+
 /* Field simulation (the test-data generator of the large workloads): factor
  * C~(theta) and return Z = P^T L~ P xi, a sample of the zero-mean field with
  * covariance C~ (Eq. 1's model, Sec. 1), where xi is white noise.

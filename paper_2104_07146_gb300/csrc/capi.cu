@@ -1602,9 +1602,56 @@ bool nelder_mead(FB fbatch, const double x0[D], const double step[D], const hmle
   return false;
 }
 
+template <int D>
+hmle_status nelder_mead_host(hmle_objective f, void *user, const double *x0, const double *step,
+                             const hmle_fit_opts &fo, double *x_best, double *f_best,
+                             int32_t *n_iter, int32_t *n_evals) {
+  double st[D], x[D];
+  for (int j = 0; j < D; ++j) {
+    x[j] = x0[j];
+    st[j] = step ? step[j] : 1.0;
+  }
+  const hmle_status hard = HMLE_OK;
+  auto fbatch = [&](const double (*xs)[D], int k, double *fv) {
+    for (int i = 0; i < k; ++i) {
+      const double v = f(xs[i], D, user);
+      fv[i] = std::isnan(v) ? INFINITY : v;
+    }
+  };
+  double X[D + 1][D], Fv[D + 1];
+  int it = 0, nev = 0;
+  const bool conv = nelder_mead<D>(fbatch, x, st, fo, hard, X, Fv, it, nev);
+  for (int j = 0; j < D; ++j) x_best[j] = X[0][j];
+  if (f_best) *f_best = Fv[0];
+  if (n_iter) *n_iter = it;
+  if (n_evals) *n_evals = nev;
+  return conv ? HMLE_OK : HMLE_ERR_NOT_CONVERGED;
+}
+
 }  // namespace
 
 extern "C" {
+
+hmle_status hmle_nelder_mead(int32_t dim, hmle_objective f, void *user, const double *x0,
+                             const double *step, const hmle_fit_opts *fo_in, double *x_best,
+                             double *f_best, int32_t *n_iter, int32_t *n_evals) {
+  if (!f || !x0 || !x_best) return HMLE_ERR_INVALID_ARG;
+  for (int j = 0; j < dim; ++j)
+    if (!std::isfinite(x0[j]) || (step && !std::isfinite(step[j]))) return HMLE_ERR_INVALID_ARG;
+  hmle_fit_opts fo;
+  if (fo_in) fo = *fo_in; else hmle_fit_opts_default(&fo);
+  switch (dim) {
+    case 1: return nelder_mead_host<1>(f, user, x0, step, fo, x_best, f_best, n_iter, n_evals);
+    case 2: return nelder_mead_host<2>(f, user, x0, step, fo, x_best, f_best, n_iter, n_evals);
+    case 3: return nelder_mead_host<3>(f, user, x0, step, fo, x_best, f_best, n_iter, n_evals);
+    case 4: return nelder_mead_host<4>(f, user, x0, step, fo, x_best, f_best, n_iter, n_evals);
+    case 5: return nelder_mead_host<5>(f, user, x0, step, fo, x_best, f_best, n_iter, n_evals);
+    case 6: return nelder_mead_host<6>(f, user, x0, step, fo, x_best, f_best, n_iter, n_evals);
+    case 7: return nelder_mead_host<7>(f, user, x0, step, fo, x_best, f_best, n_iter, n_evals);
+    case 8: return nelder_mead_host<8>(f, user, x0, step, fo, x_best, f_best, n_iter, n_evals);
+    default: return HMLE_ERR_INVALID_ARG;
+  }
+}
 
 hmle_status hmle_fit(hmle_ctx *ctx, const hmle_tree *t, const double *Z, const hmle_theta *theta0,
                      const hmle_fit_opts *fo_in, hmle_theta *theta_hat, double *ll_hat,

@@ -73,6 +73,7 @@ class EvalInfo(C.Structure):
 
 _LIB = None
 P = C.c_void_p
+OBJECTIVE = C.CFUNCTYPE(C.c_double, C.POINTER(C.c_double), C.c_int32, C.c_void_p)
 
 
 def lib():
@@ -130,6 +131,7 @@ def lib():
             "hmle_plan_build": ([C.c_int64, C.c_int32, C.c_int32, P, C.c_int32, C.c_int32,
                                  C.c_int32, P], C.c_int),
             "hmle_plan_destroy": ([P], None),
+            "hmle_nelder_mead": ([C.c_int32, OBJECTIVE, P, P, P, P, P, P, P, P], C.c_int),
             "hmle_plan_list": ([P, C.c_int32, P, C.c_int64, P, P], C.c_int),
         }
         for name, (argt, rest) in sigs.items():
@@ -152,7 +154,7 @@ def exported_symbols():
             "hmle_mlp_create", "hmle_mlp_destroy", "hmle_mlp_set", "hmle_mlp_get",
             "hmle_mlp_forward", "hmle_mlp_grad", "hmle_mlp_adam_step", "hmle_mlp_train",
             "hmle_matern_eval_noalloc", "hmle_plan_build", "hmle_plan_destroy",
-            "hmle_plan_list"]
+            "hmle_plan_list", "hmle_nelder_mead"]
 
 
 def _ptr(a):
@@ -394,6 +396,31 @@ class Tree:
             self.close()
         except Exception:
             pass
+
+
+def nelder_mead(f, x0, step=None, ftol=1e-4, xtol=1e-4, max_iter=400):
+    """hmle_nelder_mead: minimise f(x) (x a numpy array) with the optimiser
+    of hmle_fit.  Returns (x_best, f_best, iterations, evaluations, status)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    dim = x0.size
+    st = None if step is None else np.ascontiguousarray(
+        np.broadcast_to(np.asarray(step, dtype=np.float64), (dim,)))
+    fo = FitOpts()
+    lib().hmle_fit_opts_default(C.byref(fo))
+    fo.ftol, fo.xtol, fo.max_iter = ftol, xtol, max_iter
+
+    def cb(x, d, user):
+        return float(f(np.ctypeslib.as_array(x, shape=(d,)).copy()))
+    fn = OBJECTIVE(cb)
+    xb = np.zeros(dim)
+    fb = C.c_double()
+    it, nev = C.c_int32(), C.c_int32()
+    status = lib().hmle_nelder_mead(dim, fn, None, P(x0.ctypes.data),
+                                    None if st is None else P(st.ctypes.data), C.byref(fo),
+                                    P(xb.ctypes.data), C.byref(fb), C.byref(it), C.byref(nev))
+    if status not in (HMLE_OK, 7):
+        raise HmleError(status, "hmle_nelder_mead")
+    return xb, fb.value, it.value, nev.value, status
 
 
 PLAN_LISTS = ["scalars", "blocks", "steps", "lrt", "aent", "bent", "lrpairs", "dns", "dpairs",
