@@ -380,3 +380,44 @@ def test_loglik_ldlt_matches_closed_forms_and_the_cholesky_route():
 def test_loglik_ldlt_rejects_an_indefinite_matrix():
     with pytest.raises(np.linalg.LinAlgError):
         oracle.loglik_ldlt(np.array([[1.0, 2.0], [2.0, 1.0]]), np.ones(2))
+
+
+def test_mloe_mmom_one_training_point_by_hand():
+    # One training point s1 and one test point s2 at distance h, nu = 1/2
+    # (M(x) = e^{-x}).  Kriging weight of model m: lam_m = c_m / v_m with
+    # c_m = sigma2_m e^{-h / ell_m} and v_m = sigma2_m + tau2_m.  Mean square
+    # errors: e_tt = v_t - c_t^2 / v_t, e_aa = v_a - c_a^2 / v_a and
+    # e_ta = v_t - 2 lam_a c_t + lam_a^2 v_t; MLOE = e_ta / e_tt - 1,
+    # MMOM = e_aa / e_ta - 1 (Eq. 5-6).
+    s1, s2 = np.array([[0.2, 0.3]]), np.array([[0.5, 0.7]])
+    h = 0.5                                           # |(0.3, 0.4)|
+    tt, ta = (0.3, 0.5, 1.2, 0.1), (0.15, 0.5, 0.8, 0.05)
+    def parts(th):
+        c = th[2] * math.exp(-h / th[0])
+        v = th[2] + th[3]
+        return c, v
+    ct, vt = parts(tt)
+    ca, va = parts(ta)
+    lam = ca / va
+    e_tt = vt - ct * ct / vt
+    e_aa = va - ca * ca / va
+    e_ta = vt - 2.0 * lam * ct + lam * lam * vt
+    lo, mo = oracle.mloe_mmom(s1, s2, tt, ta)
+    assert abs(lo - (e_ta / e_tt - 1.0)) <= 1e-13
+    assert abs(mo - (e_aa / e_ta - 1.0)) <= 1e-13
+
+
+def test_profile_likelihood_of_white_noise_in_closed_form():
+    # ell -> 0 with distinct points: R = (1 + rho) I, so sigma2_hat =
+    # Z^T Z / (n (1 + rho)) and L_p = -n/2 log 2 pi - n/2 log sigma2_hat
+    # - n/2 log(1 + rho) - n/2
+    rng = np.random.default_rng(9)
+    locs = rng.uniform(size=(40, 2))
+    Z = rng.normal(size=40) * 0.7
+    n, rho = 40, 0.3
+    lp, s2 = oracle.loglik_profiled(locs, Z, 1e-6, 0.5, rho)
+    s2_ref = float(Z @ Z) / (n * (1 + rho))
+    assert abs(s2 - s2_ref) <= 1e-12 * s2_ref
+    ref = -0.5 * n * math.log(2 * math.pi) - 0.5 * n * math.log(s2_ref) \
+        - 0.5 * n * math.log(1 + rho) - 0.5 * n
+    assert abs(lp - ref) <= 1e-10 * abs(ref)
