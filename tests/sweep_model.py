@@ -70,10 +70,21 @@ def block_tree(depth, boxes, eta):
     return out
 
 
-def execute(locs, Z, theta, leaf=32, eta=2.0, eps=1e-8, max_rank=48):
+def execute(locs, Z, theta, leaf=32, eta=2.0, eps=1e-8, max_rank=48, form="llt"):
     """Factor C~ by the planner's schedule (rank capacity max_rank per block).
-    Returns (log|C~|, |L~^{-1} P Z|^2, dense L~, C in cluster order,
-    permutation, number of low-rank blocks, largest rank)."""
+
+    form "llt": C~ = L L^T (H-Cholesky).  form "ldlt": C~ = L D L^T with L
+    unit lower triangular and D diagonal (Sec. 2, no square roots), on the
+    same schedule: every block is held as M = L D (the diagonal leaves as
+    their unit factors, d apart), and every product over a column index k
+    carries the weight 1 / d_k (M_X D^{-1} M_Y^T = L_X D L_Y^T).  The leaf
+    factorisation is a pivot-free LDL^T, the off-diagonal solves and W-panel
+    solves use the unit factors, log|C~| = sum log d and the quadratic form is
+    sum w_k^2 / d_k.
+
+    Returns (log|C~|, Z^T C~^{-1} Z, dense L~ (for "ldlt": L D^(1/2), the
+    Cholesky factor it equals), C in cluster order, permutation, number of
+    low-rank blocks, largest rank)."""
     n, d = locs.shape
     depth, perm, boxes = cluster_tree(locs, leaf)
     blocks = block_tree(depth, boxes, eta)
@@ -89,6 +100,8 @@ def execute(locs, Z, theta, leaf=32, eta=2.0, eps=1e-8, max_rank=48):
     rhs = len(panels) - 1
     panels[rhs]["W"][:, 0] = np.asarray(Z, dtype=np.float64)[perm]
     Dn, U, rank = {}, {}, {}
+    ldlt = form == "ldlt"
+    dinv = np.ones(n)                  # 1 / d_k (all ones for L L^T)
 
     def W_of(x):                       # right factor of a low-rank block, rows = its columns
         b = B[x]
@@ -108,7 +121,7 @@ def execute(locs, Z, theta, leaf=32, eta=2.0, eps=1e-8, max_rank=48):
             s0, s1 = max(Y["rb"], T["cb"]), min(Y["re"], T["ce"])
             LA, LY = L_dense(a), L_dense(c)
             S[r0 - T["rb"]:r1 - T["rb"], s0 - T["cb"]:s1 - T["cb"]] -= \
-                LA[r0 - A["rb"]:r1 - A["rb"], o0 - A["cb"]:o1 - A["cb"]] @ \
+                (LA[r0 - A["rb"]:r1 - A["rb"], o0 - A["cb"]:o1 - A["cb"]] * dinv[o0:o1]) @ \
                 LY[s0 - Y["rb"]:s1 - Y["rb"], o0 - Y["cb"]:o1 - Y["cb"]].T
         return S
 
@@ -137,17 +150,26 @@ def execute(locs, Z, theta, leaf=32, eta=2.0, eps=1e-8, max_rank=48):
             x = int(q[0])
             S = schur(x, [(int(p[0]), int(p[1])) for p in dp[q[1]:q[2]]])
             if Lkk is None:
-                Lkk = np.linalg.cholesky(S)
-                logdet += 2.0 * float(np.sum(np.log(np.diag(Lkk))))
-                Dn[x] = Lkk
+                if ldlt:
+                    Lkk, dk = oracle.ldlt(S)             # unit lower, pivots d
+                    assert np.all(dk > 0.0), "non-positive pivot"
+                    T = B[x]
+                    dinv[T["rb"]:T["re"]] = 1.0 / dk
+                    logdet += float(np.sum(np.log(dk)))
+                    Dn[x] = Lkk * dk[None, :]            # M = L D; the solves use Lkk
+                else:
+                    Lkk = np.linalg.cholesky(S)
+                    logdet += 2.0 * float(np.sum(np.log(np.diag(Lkk))))
+                    Dn[x] = Lkk
             else:
-                Dn[x] = sla.solve_triangular(Lkk, S.T, lower=True).T
+                Dn[x] = sla.solve_triangular(Lkk, S.T, lower=True, unit_diagonal=ldlt).T
         kb, ke = B[int(Ls["dns"][st[16]][0])]["rb"], B[int(Ls["dns"][st[16]][0])]["re"]
         # 3. rows of leaf K of every open W-panel: W <- L_KK^{-1} W
         for pi in Ls["wpan"][st[18]:st[19]]:
             P = panels[int(pi[0])]
             r0 = kb - P["rb"]
-            P["W"][r0:r0 + ke - kb] = sla.solve_triangular(Lkk, P["W"][r0:r0 + ke - kb], lower=True)
+            P["W"][r0:r0 + ke - kb] = sla.solve_triangular(Lkk, P["W"][r0:r0 + ke - kb], lower=True,
+                                                           unit_diagonal=ldlt)
         # 4. deferred updates by the blocks whose columns end at K
         for ur in Ls["urows"][st[22]:st[23]]:
             pi, I, e0, e1 = (int(v) for v in ur)
@@ -158,13 +180,17 @@ def execute(locs, Z, theta, leaf=32, eta=2.0, eps=1e-8, max_rank=48):
                 A = B[a]
                 LA = L_dense(a)
                 P["W"][ib - P["rb"]:ie - P["rb"]] -= \
-                    LA[ib - A["rb"]:ie - A["rb"]] @ P["W"][A["cb"] - P["rb"]:A["ce"] - P["rb"]]
+                    (LA[ib - A["rb"]:ie - A["rb"]] * dinv[A["cb"]:A["ce"]]) @ \
+                    P["W"][A["cb"] - P["rb"]:A["ce"] - P["rb"]]
     w = panels[rhs]["W"][:, 0]
     Ld = np.zeros((n, n))
     for x, b in enumerate(B):
         Ld[b["rb"]:b["re"], b["cb"]:b["ce"]] = L_dense(x)
     Ld = np.tril(Ld)                   # the diagonal leaves' upper triangles are zero already
-    return logdet, float(w @ w), Ld, C, perm, len(rank), max(rank.values(), default=0)
+    if ldlt:
+        Ld = Ld * np.sqrt(dinv)[None, :]   # M D^{-1/2} = L D^{1/2}
+    q = float(np.sum(w * w * dinv))
+    return logdet, q, Ld, C, perm, len(rank), max(rank.values(), default=0)
 
 
 def _leaf_range(Ls, I):

@@ -34,3 +34,29 @@ def test_schedule_computes_the_h_cholesky_factor(n, d, leaf, theta, geometry):
     # the schedule's forward solve is L~^{-1} P Z itself
     w = np.linalg.solve(L, Z[perm])
     assert abs(w @ w - q) <= 1e-9 * q
+
+
+@pytest.mark.parametrize("n,d,leaf,theta,geometry", [
+    (1200, 2, 32, (0.1, 0.8, 1.0, 0.01), "uniform"),
+    (900, 2, 16, (0.05, 0.5, 1.0, 1e-3), "blobs"),
+])
+def test_ldlt_form_on_the_same_schedule(n, d, leaf, theta, geometry):
+    # Sec. 2's factorisation without square roots run on the same lists: the
+    # blocks held as M = L D and every product over a column index weighted
+    # by 1 / d.  It must give the dense oracle's log|C| and q, and its
+    # L D^(1/2) must be the H-Cholesky factor of the L L^T form (the same
+    # truncations, so the same factor up to rounding).
+    if geometry == "blobs":
+        locs = synth.locations_blobs(n, d, 0.3, 8, 0.03, seed=31)
+    else:
+        locs = synth.locations_uniform(n, d, seed=32)
+    Z = synth.normal(33, n)
+    ld, q, L, C, perm, nlr, _ = sweep_model.execute(locs, Z, theta, leaf=leaf, eps=1e-9, form="ldlt")
+    assert nlr > 0
+    _, ld0, q0 = oracle.loglik_from_matrix(C, Z[perm])
+    assert abs(ld - ld0) / n <= 1e-6, (ld, ld0)
+    assert abs(q - q0) / n <= 1e-6, (q, q0)
+    assert np.linalg.norm(L @ L.T - C) <= 1e-7 * np.linalg.norm(C)
+    ld1, q1, L1, *_ = sweep_model.execute(locs, Z, theta, leaf=leaf, eps=1e-9, form="llt")
+    assert abs(ld - ld1) <= 1e-9 * n and abs(q - q1) <= 1e-9 * q1
+    assert np.linalg.norm(L - L1) <= 1e-6 * np.linalg.norm(L1)
