@@ -8,7 +8,6 @@ is impossible the import of ``lib()`` raises -- there is no CPU path.
 from __future__ import annotations
 
 import ctypes as C
-import os
 import sys
 
 import numpy as np

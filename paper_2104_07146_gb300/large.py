@@ -16,8 +16,6 @@ import argparse
 import json
 import time
 
-import numpy as np
-
 from . import hmle, synth
 
 

@@ -11,7 +11,6 @@ the CUDA kernels; the cluster and block trees are built here in numpy.
 """
 from __future__ import annotations
 
-import math
 
 import numpy as np
 import scipy.linalg as sla

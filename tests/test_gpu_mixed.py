@@ -5,7 +5,6 @@ Stated bounds of the mixed form: the quadratic form is won back by PCG to
 the FP64 bound |dq| / n <= 1e-6; the log-determinant carries the FP32
 rounding of the Schur complements, |d logdet| / n <= 1e-5, and so does L.
 """
-import numpy as np
 import pytest
 
 import oracle
