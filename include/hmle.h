@@ -28,8 +28,10 @@
  *    detected with cudaPointerGetAttributes.  The caller keeps ownership of
  *    every array it passes; the library copies what it keeps.
  *  - Handles (hmle_ctx, hmle_tree, hmle_hmatrix, hmle_hfactor) are owned by
- *    the library and released with the matching *_destroy call.  A handle
- *    must not be used concurrently from two host threads.
+ *    the library and released with the matching *_destroy call (NULL is a
+ *    no-op).  A tree refers to its context, an H-matrix to its tree and a
+ *    factor to its H-matrix: destroy them in the reverse order of creation.
+ *    A handle must not be used concurrently from two host threads.
  *  - theta is passed by name, in the order (ell, nu, sigma2, tau2).
  *  - Z is always given in the caller's point order; the internal cluster
  *    permutation never leaks out.
@@ -190,8 +192,10 @@ const char *hmle_last_error(const hmle_ctx *ctx);
 hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n,
                             int32_t d, const hmle_opts *opts, hmle_tree **out);
 void hmle_tree_destroy(hmle_tree *tree);
+/* Sizes of the trees and the schedule (host struct).  Errors: INVALID_ARG. */
 hmle_status hmle_tree_get_info(const hmle_tree *tree, hmle_tree_info *info);
-/* perm[k] = caller index of the point at cluster position k (host array of n). */
+/* perm[k] = caller index of the point at cluster position k (host array of
+ * n int32).  Errors: INVALID_ARG, CUDA. */
 hmle_status hmle_tree_permutation(const hmle_tree *tree, int32_t *perm);
 
 /* a3-a4 (Eq. 2; Sec. 2, low-rank approximation on the fly): assemble
