@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <tuple>
 #include <unordered_map>
@@ -60,6 +61,44 @@ struct Builder {
           out.push_back(x);
         }
       }
+    std::sort(out.begin(), out.end());
+  }
+
+  // Column overlaps through the cluster tree.  Block column ranges are
+  // clusters, which are nested or disjoint, so the blocks of a list whose
+  // columns overlap A's are those whose column cluster is A's, one of its
+  // ancestors, or a cluster inside A's.  index_columns() indexes a list;
+  // overlapping() returns the positions of the overlapping blocks in
+  // ascending order (the order a scan of the whole list would give).
+  int colcid(const BlockDesc &B) const {
+    return (1 << B.level) - 1 + (B.cleaf >> (P.depth - B.level));
+  }
+  std::unordered_map<int32_t, std::vector<int32_t>> bycol;   // column cluster -> positions
+  std::vector<std::pair<int32_t, int32_t>> byleaf;            // (first column leaf, position)
+  const std::vector<int32_t> *ilist = nullptr;
+  void index_columns(const std::vector<int32_t> &list) {
+    ilist = &list;
+    bycol.clear();
+    byleaf.clear();
+    for (size_t i = 0; i < list.size(); ++i) {
+      const BlockDesc &B = P.blocks[list[i]];
+      bycol[colcid(B)].push_back((int32_t)i);
+      byleaf.emplace_back(B.cleaf, (int32_t)i);
+    }
+    std::sort(byleaf.begin(), byleaf.end());
+  }
+  void overlapping(const BlockDesc &A, std::vector<int32_t> &out) const {
+    out.clear();
+    for (int h = colcid(A);; h = (h - 1) / 2) {
+      auto it = bycol.find(h);
+      if (it != bycol.end()) out.insert(out.end(), it->second.begin(), it->second.end());
+      if (h == 0) break;
+    }
+    const int32_t l1 = A.cleaf + span(A);
+    auto it = std::lower_bound(byleaf.begin(), byleaf.end(),
+                               std::make_pair(A.cleaf, std::numeric_limits<int32_t>::min()));
+    for (; it != byleaf.end() && it->first < l1; ++it)
+      if (P.blocks[(*ilist)[it->second]].level > A.level) out.push_back(it->second);
     std::sort(out.begin(), out.end());
   }
 };
@@ -173,16 +212,18 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
     ww += (int64_t)(pd.rend - pd.rbeg) * pd.width;
   }
   P.w_words = ww;
-  // panel span in leaves, by cluster heap id (without the rhs panel)
-  std::vector<int32_t> panel_level(P.panels.size(), 0);
-  std::vector<int32_t> panel_cid(P.panels.size(), 0);
-  for (int h = 0; h < 2 * N - 1; ++h)
-    if (panel_of[h] >= 0 && panel_of[h] != P.rhs_panel) {
-      int l = 0;
-      while ((1 << (l + 1)) - 1 <= h) ++l;
-      panel_level[panel_of[h]] = l;
-      panel_cid[panel_of[h]] = h;
+  // the panels of cluster h and of its ancestors, in panel order (cluster
+  // ranges are nested or disjoint, so these are exactly the panels whose
+  // range contains cluster h's); the root's panel is the right-hand side
+  std::vector<int32_t> pans, cand;
+  auto panels_above = [&](int h, std::vector<int32_t> &out) {
+    out.clear();
+    for (;; h = (h - 1) / 2) {
+      if (panel_of[h] >= 0) out.push_back(panel_of[h]);
+      if (h == 0) break;
     }
+    std::sort(out.begin(), out.end());
+  };
 
   Builder Bd(P);
   Bd.rowlist.assign(N, {});
@@ -298,10 +339,10 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
       L.b1 = (int32_t)P.bent.size();
       // pairs, grouped per A-entry and per B-entry
       std::vector<std::vector<int32_t>> pa(Aset.size()), pb(Bset.size());
-      for (size_t ia = 0; ia < Aset.size(); ++ia)
-        for (size_t ib = 0; ib < Bset.size(); ++ib) {
-          const BlockDesc &A = P.blocks[Aset[ia]], &C = P.blocks[Bset[ib]];
-          if (!Bd.overlap(A, C)) continue;
+      Bd.index_columns(Bset);
+      for (size_t ia = 0; ia < Aset.size(); ++ia) {
+        Bd.overlapping(P.blocks[Aset[ia]], cand);
+        for (int32_t ib : cand) {
           LrPair pr{};
           pr.ae = L.a0 + (int32_t)ia; pr.be = L.b0 + (int32_t)ib;
           pr.goff = gram(Aset[ia], Bset[ib]);
@@ -310,6 +351,7 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
           pa[ia].push_back(pi);
           pb[ib].push_back(pi);
         }
+      }
       for (size_t ia = 0; ia < Aset.size(); ++ia) {
         SideEntry &e = P.aent[L.a0 + ia];
         e.p0 = (int32_t)P.apair.size();
@@ -382,13 +424,16 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
       dt.p0 = (int32_t)P.dpairs.size();
       Bd.collect(T.rleaf, T.rleaf + 1, T.cbeg, Aset, Bd.stampA);
       Bd.collect(T.cleaf, T.cleaf + 1, T.cbeg, Bset, Bd.stampB);
-      for (int32_t a : Aset)
-        for (int32_t c : Bset) {
-          if (!Bd.overlap(P.blocks[a], P.blocks[c])) continue;
+      Bd.index_columns(Bset);
+      for (int32_t a : Aset) {
+        Bd.overlapping(P.blocks[a], cand);
+        for (int32_t q : cand) {
+          const int32_t c = Bset[q];
           DPair pr{};
           pr.a = a; pr.b = c; pr.goff = gram(a, c);
           P.dpairs.push_back(pr);
         }
+      }
       dt.p1 = (int32_t)P.dpairs.size();
       P.dns.push_back(dt);
     }
@@ -422,11 +467,8 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
 
     // 3. panels advanced by the forward solve of leaf K
     st.wpan0 = (int32_t)P.wpan.size();
-    for (size_t pi = 0; pi < P.panels.size(); ++pi) {
-      const PanelDesc &pd = P.panels[pi];
-      int sp = ((int)pi == P.rhs_panel) ? N : (1 << (depth - panel_level[pi]));
-      if (pd.leaf0 <= K && K < pd.leaf0 + sp) P.wpan.push_back((int32_t)pi);
-    }
+    panels_above(N - 1 + K, pans);   // the panels whose cluster holds leaf K
+    P.wpan.insert(P.wpan.end(), pans.begin(), pans.end());
     st.wpan1 = (int32_t)P.wpan.size();
 
     // 4. deferred updates by blocks whose columns end at leaf K
@@ -435,20 +477,23 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
     std::map<std::pair<int32_t, int32_t>, std::vector<UpdEntry>> rows;  // (panel, leaf)
     for (int32_t a : ends[K]) {
       const BlockDesc &A = P.blocks[a];
-      for (size_t pi = 0; pi < P.panels.size(); ++pi) {
-        const PanelDesc &pd = P.panels[pi];
-        if (!(pd.rbeg <= A.cbeg && A.rend <= pd.rend)) continue;
+      // the panels containing A: clusters holding both its rows and columns
+      int hr = cid(A.level, A.rleaf >> (depth - A.level));
+      int hc = cid(A.level, A.cleaf >> (depth - A.level));
+      while (hr != hc) { hr = (hr - 1) / 2; hc = (hc - 1) / 2; }
+      panels_above(hr, pans);
+      for (int32_t pi : pans) {
         UpdEntry ue{};
         ue.a = a; ue.hoff = -1;
         if (A.kind == kLowRank) {
           HTask h{};
-          h.a = a; h.panel = (int32_t)pi;
-          h.hoff = ws; ws += (int64_t)kcap * pd.width;
+          h.a = a; h.panel = pi;
+          h.hoff = ws; ws += (int64_t)kcap * P.panels[pi].width;
           P.hts.push_back(h);
           ue.hoff = h.hoff;
         }
         for (int I = A.rleaf; I < A.rleaf + Bd.span(A); ++I)
-          rows[{(int32_t)pi, I}].push_back(ue);
+          rows[{pi, I}].push_back(ue);
       }
     }
     st.ht1 = (int32_t)P.hts.size();
