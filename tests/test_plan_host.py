@@ -74,6 +74,7 @@ def depth_of(n, leaf):
 
 
 CASES = [  # n, leaf, max_rank, oversample, p_adm, leaf_lowrank, seed
+    (16, 16, 8, 4, 0.5, False, 9),         # one leaf: the diagonal block only
     (40, 32, 32, 8, 0.5, False, 1),
     (100, 16, 16, 8, 0.5, False, 2),
     (250, 16, 32, 8, 0.6, False, 3),
