@@ -408,9 +408,12 @@ hmle_status hmle_matern_eval(hmle_ctx *ctx, double nu, const double *x,
  * The work is enqueued on the context's stream and the call returns without
  * waiting: synchronise that stream before reading out.  The first call on a
  * device looks up the static array's device address (cudaGetSymbolAddress),
- * so make that first call before any stream capture begins.  Every call
- * shares the one array and overwrites it: calls whose work overlaps on the
- * GPU (other streams, other contexts) race, and must be serialised. */
+ * so make that first call before any stream capture begins.  The address
+ * is kept per device for the life of the process (a device reset inside the
+ * process invalidates it).  The context's device must be the current device,
+ * else INVALID_ARG.  Every call shares the one array and overwrites it: calls
+ * whose work overlaps on the GPU (other streams, other contexts) race, and
+ * must be serialised.  Errors go to hmle_last_error like every entry point. */
 hmle_status hmle_matern_eval_noalloc(hmle_ctx *ctx, const double *nus, int32_t nnu,
                                      const double *x, int64_t m, double *out);
 

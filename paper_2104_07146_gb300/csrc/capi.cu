@@ -567,6 +567,16 @@ __attribute__((visibility("hidden"))) cudaStream_t hmle_internal_ctx_stream(cons
   return c ? c->st : nullptr;
 }
 
+// device that owns a context's stream, and the context's error path, for the
+// other translation units of the library
+__attribute__((visibility("hidden"))) int hmle_internal_ctx_device(const hmle_ctx *c) {
+  return c ? c->dev : -1;
+}
+__attribute__((visibility("hidden"))) hmle_status hmle_internal_ctx_fail(hmle_ctx *c, hmle_status s,
+                                                                        const char *msg) {
+  return fail(c, s, msg ? msg : "");
+}
+
 hmle_status hmle_opts_default(hmle_opts *o) {
   if (!o) return HMLE_ERR_INVALID_ARG;
   o->leaf_size = 64;

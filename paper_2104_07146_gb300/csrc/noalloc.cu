@@ -35,25 +35,37 @@ double *g_scratch_ptr[kMaxDevices] = {nullptr};
 
 using namespace hmle;
 
-struct hmle_ctx;  // defined in capi.cu; only its stream is needed here
+struct hmle_ctx;  // defined in capi.cu; its stream, device and error path are used here
 extern "C" __attribute__((visibility("hidden"))) cudaStream_t hmle_internal_ctx_stream(const hmle_ctx *ctx);
+extern "C" __attribute__((visibility("hidden"))) int hmle_internal_ctx_device(const hmle_ctx *ctx);
+extern "C" __attribute__((visibility("hidden"))) hmle_status hmle_internal_ctx_fail(hmle_ctx *ctx, hmle_status s,
+                                                                                   const char *msg);
 
 extern "C" hmle_status hmle_matern_eval_noalloc(hmle_ctx *ctx, const double *nus, int32_t nnu,
                                                 const double *x, int64_t m, double *out) {
-  if (!ctx || !nus || !x || !out || m < 0) return HMLE_ERR_INVALID_ARG;
-  if (nnu < 1 || nnu > kStaticNu) return HMLE_ERR_INVALID_ARG;  // beyond the static scratch
+  if (!ctx) return HMLE_ERR_INVALID_ARG;
+  if (!nus || !x || !out || m < 0) return hmle_internal_ctx_fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+  if (nnu < 1 || nnu > kStaticNu)
+    return hmle_internal_ctx_fail(ctx, HMLE_ERR_INVALID_ARG, "between 1 and 16 values of nu per call");
   for (int j = 0; j < nnu; ++j)
-    if (!(nus[j] > 0.0) || !(nus[j] <= 20.0)) return HMLE_ERR_INVALID_ARG;
+    if (!(nus[j] > 0.0) || !(nus[j] <= 20.0))
+      return hmle_internal_ctx_fail(ctx, HMLE_ERR_INVALID_ARG, "nu out of range");
+  // the scratch address belongs to the device that owns the context's
+  // stream; a call made with another device current is refused
+  const int dev = hmle_internal_ctx_device(ctx);
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return hmle_internal_ctx_fail(ctx, HMLE_ERR_CUDA, "cudaGetDevice failed");
+  if (cur != dev || dev < 0 || dev >= kMaxDevices)
+    return hmle_internal_ctx_fail(ctx, HMLE_ERR_INVALID_ARG, "the context's device is not the current device");
   // inputs and outputs must already be on the device: nothing is staged
   cudaPointerAttributes ax, ao;
   if (cudaPointerGetAttributes(&ax, x) != cudaSuccess || cudaPointerGetAttributes(&ao, out) != cudaSuccess) {
     cudaGetLastError();
-    return HMLE_ERR_INVALID_ARG;
+    return hmle_internal_ctx_fail(ctx, HMLE_ERR_INVALID_ARG, "x and out must be device pointers");
   }
-  if (ax.type != cudaMemoryTypeDevice && ax.type != cudaMemoryTypeManaged) return HMLE_ERR_INVALID_ARG;
-  if (ao.type != cudaMemoryTypeDevice && ao.type != cudaMemoryTypeManaged) return HMLE_ERR_INVALID_ARG;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HMLE_ERR_CUDA;
+  if ((ax.type != cudaMemoryTypeDevice && ax.type != cudaMemoryTypeManaged) ||
+      (ao.type != cudaMemoryTypeDevice && ao.type != cudaMemoryTypeManaged))
+    return hmle_internal_ctx_fail(ctx, HMLE_ERR_INVALID_ARG, "x and out must be device pointers");
   double *scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -62,18 +74,21 @@ extern "C" hmle_status hmle_matern_eval_noalloc(hmle_ctx *ctx, const double *nus
       double *p = nullptr;
       if (cudaGetSymbolAddress((void **)&p, g_matern_scratch) != cudaSuccess || !p) {
         cudaGetLastError();
-        return HMLE_ERR_CUDA;
+        return hmle_internal_ctx_fail(ctx, HMLE_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
       }
       g_scratch_ptr[dev] = p;
     }
     scratch = g_scratch_ptr[dev];
   }
   cudaStream_t st = hmle_internal_ctx_stream(ctx);
+  cudaGetLastError();   // report only the launches below, not an earlier caller's error
   // every word of each table is written by its table kernel before the
   // evaluation kernel reads it, so nothing left by a previous call is used
   for (int j = 0; j < nnu; ++j) {
     launch_matern_table(st, nus[j], scratch + (int64_t)j * kTableWords);
     launch_matern_eval(st, scratch + (int64_t)j * kTableWords, x, m, out + (int64_t)j * m);
   }
-  return cudaGetLastError() == cudaSuccess ? HMLE_OK : HMLE_ERR_CUDA;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return hmle_internal_ctx_fail(ctx, HMLE_ERR_CUDA, cudaGetErrorString(e));
+  return HMLE_OK;
 }

@@ -133,6 +133,16 @@ std::string build_plan(Plan &P, int32_t n, int32_t d, int32_t b, int32_t depth,
   P.kcap = kcap; P.kc = kc; P.r = r;
   P.cl_beg = cl_beg; P.cl_end = cl_end;
   const int N = P.nleaf;
+  // The overlap searches below go through the cluster tree (nested or
+  // disjoint column clusters) instead of comparing point ranges.  The two
+  // agree only while no cluster is empty: an empty cluster nested inside
+  // another overlaps nothing by point range, yet the tree search would report
+  // it.  The halving rule with leaf_size >= 16 never empties a cluster, and a
+  // caller's partition that would is refused here.
+  if ((int)cl_beg.size() < (2 << depth) - 1 || (int)cl_end.size() < (2 << depth) - 1)
+    return "cluster arrays shorter than the tree";
+  for (int h = 0; h < (2 << depth) - 1; ++h)
+    if (!(cl_beg[h] < cl_end[h])) return "empty cluster";
 
   // --- blocks, in a fixed order: by column leaf, then dense before
   // low-rank, then row leaf (the device block tree is already deterministic;

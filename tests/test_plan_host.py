@@ -83,6 +83,15 @@ CASES = [  # n, leaf, max_rank, oversample, p_adm, leaf_lowrank, seed
     (1000, 32, 32, 8, 0.5, True, 6),
     (1023, 32, 24, 8, 0.3, False, 7),
     (4096, 64, 32, 8, 0.6, False, 8),      # overlaps above 512 points: chunked grams
+    # the smallest n of each leaf size at depth 1 and 2 (the smallest clusters)
+    (17, 16, 8, 4, 0.5, False, 10),
+    (33, 16, 8, 4, 0.5, True, 11),
+    (33, 32, 16, 8, 0.5, False, 12),
+    (65, 32, 16, 8, 0.5, True, 13),
+    (65, 64, 32, 8, 0.5, False, 14),
+    (129, 64, 32, 8, 0.5, True, 15),
+    (129, 128, 32, 8, 0.5, False, 16),
+    (257, 128, 32, 8, 0.5, True, 17),
 ]
 
 
@@ -163,6 +172,24 @@ def _rows(b):
 
 def _cols(b):
     return range(b["cleaf"], b["cleaf"] + b["span"])
+
+
+def test_cluster_nesting_agrees_with_point_ranges(case):
+    """The planner finds column overlaps through the cluster tree (nested or
+    disjoint clusters).  That equals the point-range definition
+    max(begin) < min(end) only if no cluster is empty: check both on every
+    pair of exported blocks, rows and columns."""
+    B, _, _ = _blocks(case)
+    for b in B:
+        assert b["rbeg"] < b["rend"] and b["cbeg"] < b["cend"]
+    for a in B:
+        for b in B:
+            by_points = max(a["cbeg"], b["cbeg"]) < min(a["cend"], b["cend"])
+            by_leaves = max(a["cleaf"], b["cleaf"]) < min(a["cleaf"] + a["span"], b["cleaf"] + b["span"])
+            assert by_points == by_leaves
+            by_points = max(a["rbeg"], b["rbeg"]) < min(a["rend"], b["rend"])
+            by_leaves = max(a["rleaf"], b["rleaf"]) < min(a["rleaf"] + a["span"], b["rleaf"] + b["span"])
+            assert by_points == by_leaves
 
 
 def test_targets_per_step(case):
