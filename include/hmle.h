@@ -60,16 +60,26 @@ typedef enum {
 /* Arithmetic of the factorisation.
  *  HMLE_FP64        every step in FP64.
  *  HMLE_MIXED_FP32  the mixed form: the products of the Schur-complement
- *                   updates and of the W-panel solves run in FP32 with FP32
- *                   accumulation; the QR / SVD recompression, the diagonal
- *                   POTRF, the TRSM, the log-determinant and the solves used
- *                   as a preconditioner stay FP64.  log|C~| comes from the
- *                   mixed factor; Z^T C~^{-1} Z is won back by preconditioned
- *                   conjugate gradients on the FP64 H-matrix of C with the
- *                   mixed factor as preconditioner (pcg_tol, pcg_max_iter).
- *                   The mixed factor is truncated at max(aca_eps, 1e-7): the
- *                   FP32 products leave noise near 1e-7 of a block's norm. */
-typedef enum { HMLE_FP64 = 0, HMLE_MIXED_FP32 = 1 } hmle_precision;
+ *                   updates, of the Grams and of the W-panel updates run on
+ *                   the tensor cores (tcgen05.mma, BF16 operands, FP32
+ *                   accumulation), every operand split into three BF16
+ *                   slices (24 bits, the FP32 significand; six products per
+ *                   step of k); the QR / SVD recompression, the diagonal
+ *                   POTRF, the TRSM, the W-panel triangular solves, the
+ *                   log-determinant and the solves used as a preconditioner
+ *                   stay FP64.  log|C~| comes from the mixed factor;
+ *                   Z^T C~^{-1} Z is won back by preconditioned conjugate
+ *                   gradients on the FP64 H-matrix of C with the mixed factor
+ *                   as preconditioner (pcg_tol, pcg_max_iter).  The mixed
+ *                   factor is truncated at max(aca_eps, 1e-7).
+ *  HMLE_MIXED_BF16  the same with every operand split into two BF16 slices
+ *                   (16 bits; three products per step of k); the factor is
+ *                   truncated at max(aca_eps, 1e-5).  A single BF16 slice
+ *                   (8 bits) is not offered: its error, about 2^-9 of the
+ *                   updates' norm, exceeds the smallest eigenvalues of the
+ *                   diagonal leaves of a covariance with a small nugget, and
+ *                   the POTRF of such a leaf would fail. */
+typedef enum { HMLE_FP64 = 0, HMLE_MIXED_FP32 = 1, HMLE_MIXED_BF16 = 2 } hmle_precision;
 
 /* Matern parameters of Eq. 2: range ell > 0, smoothness nu > 0,
  * variance sigma2 >= 0, nugget tau2 >= 0. */
@@ -489,6 +499,23 @@ hmle_status hmle_mlp_train(hmle_ctx *ctx, hmle_mlp *mlp, const float *feats, con
  * call returns HMLE_ERR_TIMEOUT.  *err_word (may be NULL) receives the error
  * word.  Errors: INVALID_ARG (extra not 0 or 1), OOM, CUDA. */
 hmle_status hmle_selftest_barrier(hmle_ctx *ctx, int32_t extra, uint32_t *err_word);
+
+/* Check of the tensor-core tile product of the mixed forms (no counterpart in
+ * the paper; the products it serves are the Schur-complement updates of the
+ * H-Cholesky factorisation, Sec. 2).  C = A B with every operand value split
+ * into nslices BF16 slices (1, 2 or 3; a = a_0 + a_1 + ..., a_p the BF16
+ * rounding of what the earlier slices leave of the FP32 rounding of a) and
+ * the products a_p b_q with p + q < nslices accumulated in FP32 in tensor
+ * memory (tcgen05.mma).  A: M x K row-major, B: K x N row-major (host
+ * doubles); C: copies x (M x N column-major) host doubles, one copy per CTA
+ * (copies CTAs run concurrently and must agree).  a_kfast / b_kfast select the
+ * staging order of the operand (the order in which threads gather it), not
+ * its layout: the result is the same.  1 <= M, N; 0 <= K; 1 <= copies <= 4096;
+ * each array at most 2^28 values.  Errors: INVALID_ARG, OOM, CUDA; TIMEOUT if
+ * a bounded wait for the tensor cores ran out. */
+hmle_status hmle_selftest_tc_gemm(hmle_ctx *ctx, int32_t nslices, int32_t a_kfast, int32_t b_kfast,
+                                  int32_t copies, int32_t M, int32_t N, int32_t K, const double *A,
+                                  const double *B, double *C);
 
 /* Measurement support (no counterpart in the paper).  Select one kernel of
  * the factorisation sweep by name (e.g. "k_tsqr_final", "k_dense_pair"; NULL

@@ -25,6 +25,12 @@ approximates):
   tau = 1 / 2^t0.
 * ``nelder_mead`` -- the MLE driver (Sec. 2, "Maximization of the
   log-likelihood"; threshold 1e-4 and at most 400 iterations).
+* ``kalman_exponential`` / ``simulate_exponential_line`` -- Eq. 1 and a
+  draw from the model, in O(n), for nu = 1/2 (C_ij = sigma^2 exp(-h/ell) +
+  tau^2 [i == j], Eq. 2) on sorted collinear points: the exponential kernel
+  is then an Ornstein-Uhlenbeck process, a Markov chain in x, so the
+  prediction-error decomposition of a scalar Kalman filter is exact.  This is
+  the reference at sizes where the dense factorisation cannot run.
 """
 from __future__ import annotations
 
@@ -194,6 +200,47 @@ def loglik_dense(locs: np.ndarray, Z: np.ndarray, theta):
 def simulate(locs: np.ndarray, theta, xi: np.ndarray) -> np.ndarray:
     """Z = L xi with L the dense Cholesky factor of C(theta)."""
     return cholesky(matern_matrix(locs, theta)) @ np.asarray(xi, dtype=np.float64)
+
+
+def kalman_exponential(x: np.ndarray, z: np.ndarray, ell: float, s2: float, t2: float) -> float:
+    """Exact Eq. 1 for nu = 1/2 on sorted collinear points x (Eq. 2 with
+    M_1/2(h) = exp(-h)): the latent state follows x_i = rho_i x_{i-1} + noise
+    with rho_i = exp(-(x_i - x_{i-1}) / ell) and stationary variance s2, each
+    observation adds t2; L is the sum over i of the Gaussian log-density of
+    the one-step prediction error."""
+    m, P = 0.0, s2                       # prior of the latent state at x_0
+    ll = 0.0
+    log2pi = math.log(2.0 * math.pi)
+    for i in range(len(x)):
+        if i > 0:
+            rho = math.exp(-(x[i] - x[i - 1]) / ell)
+            m, P = rho * m, rho * rho * P + s2 * (1.0 - rho * rho)
+        S = P + t2
+        e = z[i] - m
+        ll += -0.5 * (log2pi + math.log(S) + e * e / S)
+        K = P / S
+        m, P = m + K * e, (1.0 - K) * P
+    return ll
+
+
+def simulate_exponential_line(x: np.ndarray, theta, xi: np.ndarray, eta: np.ndarray) -> np.ndarray:
+    """A draw from the model of Eq. 2 with nu = 1/2 on sorted collinear
+    points x: the latent Ornstein-Uhlenbeck state u_0 = sigma xi_0,
+    u_i = rho_i u_{i-1} + sigma sqrt(1 - rho_i^2) xi_i (rho_i as above) is
+    L xi with L the Cholesky factor of sigma^2 exp(-|x_i - x_j| / ell), and
+    the observation adds the nugget, z = u + tau eta."""
+    ell, nu, s2, t2 = theta
+    assert nu == 0.5
+    x = np.asarray(x, dtype=np.float64)
+    xi = np.asarray(xi, dtype=np.float64)
+    sig = math.sqrt(s2)
+    rho = np.exp(-np.diff(x) / ell)
+    gain = sig * np.sqrt(1.0 - rho * rho)
+    u = np.empty_like(x)
+    u[0] = sig * xi[0]
+    for i in range(1, len(x)):
+        u[i] = rho[i - 1] * u[i - 1] + gain[i - 1] * xi[i]
+    return u + math.sqrt(t2) * np.asarray(eta, dtype=np.float64)
 
 
 def loglik_profiled(locs: np.ndarray, Z: np.ndarray, ell: float, nu: float, rho: float):

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libhmle.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["tree.cu", "assemble.cu", "factor.cu", "capi.cu", "plan.cpp", "tally.cpp", "noalloc.cu", "pcg.cu", "tune.cpp", "learn.cu", "solve.cu", "inspect.cpp"]
+SOURCES = ["tree.cu", "assemble.cu", "factor.cu", "capi.cu", "plan.cpp", "tally.cpp", "noalloc.cu", "pcg.cu", "tune.cpp", "learn.cu", "solve.cu", "inspect.cpp", "tc_check.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

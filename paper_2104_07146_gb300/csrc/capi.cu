@@ -294,7 +294,12 @@ hmle_status do_assemble(hmle_ctx *ctx, const hmle_tree *t, const hmle_theta *th,
   return HMLE_OK;
 }
 
-constexpr double kMixedTruncEps = 1e-7;  // truncation floor of the mixed factor
+// Truncation floor of the mixed factors: the tensor-core products carry
+// their operands to 24 bits (HMLE_MIXED_FP32, three BF16 slices) or 16 bits
+// (HMLE_MIXED_BF16, two slices) and leave noise near 1e-7 or 1e-5 of a
+// block's norm in a Schur complement.
+constexpr double kMixedTruncEps[3] = {0.0, 1e-7, 1e-5};
+inline bool is_mixed(int32_t precision) { return precision == HMLE_MIXED_FP32 || precision == HMLE_MIXED_BF16; }
 constexpr int kAssemblyLaunches = 3;      // Matern table, ACA, dense near field of one assembly
 
 FactorArgs make_fargs(const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f) {
@@ -314,13 +319,14 @@ FactorArgs make_fargs(const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f
   F.eps = t->opts.aca_eps; F.seed = t->opts.seed;
   F.b = P.b; F.kcap = P.kcap; F.kc = P.kc; F.r = P.r;
   F.osamp = t->opts.oversample;
-  F.mixed = t->opts.precision == HMLE_MIXED_FP32 ? 1 : 0;
+  F.mixed = is_mixed(t->opts.precision) ? t->opts.precision : 0;
   F.fixed_k = t->opts.fixed_rank;
-  // The FP32 products leave noise of about 1e-7 of |C_T| in a Schur
-  // complement; truncating below that would keep noise as rank.  The mixed
-  // factor is truncated at max(eps, 1e-7); the accuracy of the quadratic
-  // form comes from the FP64 operator of the PCG (ACA at eps).
-  if (F.mixed) F.eps = std::max(F.eps, kMixedTruncEps);
+  // The low-precision products leave noise of about 1e-7 (FP32-class) or
+  // 1e-5 (16-bit) of |C_T| in a Schur complement; truncating below that would
+  // keep noise as rank.  The mixed factor is truncated at max(eps, floor);
+  // the accuracy of the quadratic form comes from the FP64 operator of the
+  // PCG (ACA at eps).
+  if (F.mixed) F.eps = std::max(F.eps, kMixedTruncEps[F.mixed]);
   return F;
 }
 
@@ -457,6 +463,7 @@ hmle_status finish_factor(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix 
   f->logdet = f->host_out[0];
   f->quad = f->host_out[1];
   int fl = f->host_flags[0] | f->host_flags[1];
+  if (fl & kFlagTimeout) return fail(ctx, HMLE_ERR_TIMEOUT, "a tensor-core product did not complete in time");
   if (fl & kFlagNotSpd) return fail(ctx, HMLE_ERR_NOT_SPD, "non-positive pivot in a diagonal leaf");
   if (fl & kFlagRankOverflow)
     return fail(ctx, HMLE_ERR_RANK_OVERFLOW, "a low-rank block needed more than max_rank terms");
@@ -529,6 +536,7 @@ hmle_status do_factor(hmle_ctx *ctx, const hmle_tree *t, const hmle_hmatrix *h,
     prof->flops += tally_flops(P, prof->kind, rc, rl, kp, t->opts.oversample, jf);
   }
   int fl = flags[0] | flags[1];
+  if (fl & kFlagTimeout) return fail(ctx, HMLE_ERR_TIMEOUT, "a tensor-core product did not complete in time");
   if (fl & kFlagNotSpd) return fail(ctx, HMLE_ERR_NOT_SPD, "non-positive pivot in a diagonal leaf");
   if (fl & kFlagRankOverflow)
     return fail(ctx, HMLE_ERR_RANK_OVERFLOW, "a low-rank block needed more than max_rank terms");
@@ -655,9 +663,9 @@ hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n, int32_
     return fail(ctx, HMLE_ERR_INVALID_ARG, "fixed_rank must be in [0, max_rank]");
   if (o.oversample < 4 || o.max_rank + o.oversample > 64)
     return fail(ctx, HMLE_ERR_INVALID_ARG, "oversample >= 4 and max_rank + oversample <= 64");
-  if (o.precision != HMLE_FP64 && o.precision != HMLE_MIXED_FP32)
+  if (o.precision != HMLE_FP64 && !is_mixed(o.precision))
     return fail(ctx, HMLE_ERR_INVALID_ARG, "precision");
-  if (o.precision == HMLE_MIXED_FP32 && !(o.pcg_tol > 0.0 && o.pcg_max_iter >= 1))
+  if (is_mixed(o.precision) && !(o.pcg_tol > 0.0 && o.pcg_max_iter >= 1))
     return fail(ctx, HMLE_ERR_INVALID_ARG, "pcg_tol / pcg_max_iter");
   static bool smem_ok = false;
   if (!smem_ok) {
@@ -875,7 +883,7 @@ hmle_status hmle_factor(hmle_ctx *ctx, const hmle_hmatrix *h, const double *Z, h
   bool owned = false;
   if (s == HMLE_OK && Z) s = stage_vec(ctx, Z, t->n, &zd, &owned);
   if (s == HMLE_OK) s = do_factor(ctx, t, h, zd, f);
-  if (s == HMLE_OK && zd && t->opts.precision == HMLE_MIXED_FP32) s = mixed_quad(ctx, t, h, f, zd);
+  if (s == HMLE_OK && zd && is_mixed(t->opts.precision)) s = mixed_quad(ctx, t, h, f, zd);
   if (owned) cudaFreeAsync(zd, ctx->st);
   if (s == HMLE_OK) s = rank_stats(ctx, t, f->rank_l, &f->max_rank_l, &f->mean_rank_l);
   if (s != HMLE_OK) { free_f(ctx->st, f); delete f; return s; }
@@ -1064,7 +1072,7 @@ hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tc, const hmle_thet
   }
   s = do_assemble(ctx, t, th, &w.H);
   if (s == HMLE_OK) s = do_factor(ctx, t, &w.H, zd, &w.F, t->graphs ? &w : nullptr);
-  if (s == HMLE_OK && t->opts.precision == HMLE_MIXED_FP32) s = mixed_quad(ctx, t, &w.H, &w.F, zd);
+  if (s == HMLE_OK && is_mixed(t->opts.precision)) s = mixed_quad(ctx, t, &w.H, &w.F, zd);
   const double n = (double)t->n;
   double L = -0.5 * n * std::log(2.0 * M_PI) - 0.5 * w.F.logdet - 0.5 * w.F.quad;
   *ll = (s == HMLE_OK) ? L : -INFINITY;
@@ -1193,7 +1201,7 @@ hmle_status run_waves(hmle_ctx *ctx, const std::vector<TaskRef> &tasks, int W, c
       hmle_ctx wc;
       wc.st = w->st; wc.side = w->side;
       fs[k] = finish_factor(&wc, T.t, &w->H, &w->F);
-      if (fs[k] == HMLE_OK && T.t->opts.precision == HMLE_MIXED_FP32) {
+      if (fs[k] == HMLE_OK && is_mixed(T.t->opts.precision)) {
         fs[k] = mixed_prepare(&wc, T.t, &w->H, &w->F, T.zd, runs[k]);
         if (fs[k] == HMLE_OK) {
           cudaError_t e = pcg_start(runs[k]);

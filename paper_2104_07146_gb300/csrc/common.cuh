@@ -10,6 +10,7 @@ namespace hmle {
 constexpr int kFlagNotSpd = 1;
 constexpr int kFlagRankOverflow = 2;
 constexpr int kFlagNonFinite = 4;
+constexpr int kFlagTimeout = 8;    // a bounded wait on the tensor cores ran out
 
 __device__ __forceinline__ void raise_flag(int *flags, int f) { atomicOr(flags, f); }
 

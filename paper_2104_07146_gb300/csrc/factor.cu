@@ -34,11 +34,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "hmle_internal.h"
 #include "kernels.cuh"
 #include "matern.cuh"
+#include "tc_gemm.cuh"
 
 namespace hmle {
 
@@ -113,11 +115,37 @@ __device__ void cta_gemm_t(int M, int N, int K, FA fa, FB fb, FC fc, double *sme
   }
 }
 
-// cta_gemm_t with the output tile width picked from N.
+// Tc = tc::Split<NS>: the product runs on the tensor cores (tc_gemm.cuh)
+// with NS BF16 slices per operand and FP32 accumulation.
+template <class T> struct TcSlices { static constexpr int value = 0; };
+template <int NS> struct TcSlices<tc::Split<NS>> { static constexpr int value = NS; };
+
+// dynamic shared memory (doubles) of one product of arithmetic T
+template <class T> __host__ __device__ constexpr int gemm_words() {
+  return TcSlices<T>::value ? tc::smem_words<(TcSlices<T>::value ? TcSlices<T>::value : 1)>() : kGemmSmem;
+}
+template <class T> __host__ __device__ constexpr int tn_words();
+
+// Dynamic shared memory of a product kernel: what its FP64 form needs, and at
+// least the tensor-core product's stages for Tc = tc::Split.
+template <class Tc> inline int tc_smem(int bytes) {
+  return std::max(bytes, TcSlices<Tc>::value ? gemm_words<Tc>() * (int)sizeof(double) : 0);
+}
+
+
+// cta_gemm_t with the output tile width picked from N, or the tensor-core
+// product for Tc = tc::Split<NS> (flags: the error word its bounded waits
+// report to).
 template <bool A_KFAST, bool B_KFAST, class T = double, class FA, class FB, class FC>
-__device__ __forceinline__ void cta_gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem) {
-  if (N <= 32) cta_gemm_t<T, A_KFAST, B_KFAST, 32>(M, N, K, fa, fb, fc, smem);
-  else cta_gemm_t<T, A_KFAST, B_KFAST, 64>(M, N, K, fa, fb, fc, smem);
+__device__ __forceinline__ void cta_gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem,
+                                         int *flags = nullptr) {
+  constexpr int ns = TcSlices<T>::value;
+  if constexpr (ns > 0) {
+    tc::gemm<ns, A_KFAST, B_KFAST>(M, N, K, fa, fb, fc, smem, flags);
+  } else {
+    if (N <= 32) cta_gemm_t<T, A_KFAST, B_KFAST, 32>(M, N, K, fa, fb, fc, smem);
+    else cta_gemm_t<T, A_KFAST, B_KFAST, 64>(M, N, K, fa, fb, fc, smem);
+  }
 }
 
 // C(i, j) = sum_k A(k, i) B(k, j) for small outputs (M x N) and long K: the
@@ -128,7 +156,7 @@ __device__ __forceinline__ void cta_gemm(int M, int N, int K, FA fa, FB fb, FC f
 constexpr int kTnMaxMN = 192;
 constexpr int kTnSmem = 32 * kTnMaxMN + 4 * 512;
 template <class T = double, class FA, class FB, class FC>
-__device__ void cta_gemm_tn(int M, int N, int K, FA fa, FB fb, FC fc, double *smem) {
+__device__ void cta_gemm_tn_simt(int M, int N, int K, FA fa, FB fb, FC fc, double *smem) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   T *sA = reinterpret_cast<T *>(smem);  // 32 x M  (sA[k * M + i])
   T *sB = sA + 32 * M;                  // 32 x N
@@ -171,6 +199,24 @@ __device__ void cta_gemm_tn(int M, int N, int K, FA fa, FB fb, FC fc, double *sm
       fc(o % M, o / M, double(v));
     }
     __syncthreads();
+  }
+}
+
+template <class T> __host__ __device__ constexpr int tn_words() {
+  return TcSlices<T>::value ? tc::smem_words<(TcSlices<T>::value ? TcSlices<T>::value : 1)>() : kTnSmem;
+}
+
+// C(i, j) = sum_k A(k, i) B(k, j), both operands contiguous along k: the
+// small-output product above, or the tensor-core product for Tc = tc::Split.
+template <class T = double, class FA, class FB, class FC>
+__device__ __forceinline__ void cta_gemm_tn(int M, int N, int K, FA fa, FB fb, FC fc, double *smem,
+                                            int *flags = nullptr) {
+  constexpr int ns = TcSlices<T>::value;
+  if constexpr (ns > 0) {
+    tc::gemm<ns, true, true>(
+        M, N, K, [&](int i, int k) { return fa(k, i); }, fb, fc, smem, flags);
+  } else {
+    cta_gemm_tn_simt<T>(M, N, K, fa, fb, fc, smem);
   }
 }
 
@@ -227,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) k_gram(FactorArgs F, int c0) {
   cta_gemm_tn<Tc>(
       F.rank_l[g.a], F.rank_l[g.b], ch.r1 - ch.r0, [&](int k, int i) { return wa[k + (int64_t)i * lda]; },
       [&](int k, int j) { return wb[k + (int64_t)j * ldb]; },
-      [&](int i, int j, double v) { out[i + (int64_t)j * kc] = v; }, smem);
+      [&](int i, int j, double v) { out[i + (int64_t)j * kc] = v; }, smem, F.flags);
 }
 
 // Sum of the chunks of a gram, in chunk order.
@@ -267,12 +313,12 @@ __global__ void __launch_bounds__(kThreads) k_side_t(FactorArgs F, int e0, int n
       cta_gemm_tn<Tc>(
           ke, r, hi - lo, [&](int kk, int i) { return a.U(X, lo + kk, i); },
           [&](int kk, int j) { return Q[(lo + kk - cb) + (int64_t)j * L.m]; },
-          [&](int i, int j, double v) { t[i + (int64_t)j * k] = v; }, smem);
+          [&](int i, int j, double v) { t[i + (int64_t)j * k] = v; }, smem, F.flags);
     } else {
       cta_gemm_tn<Tc>(
           ke, r, hi - lo, [&](int kk, int i) { return a.U(X, lo + kk, i); },
           [&](int kk, int j) { return rademacher(seed, tb, lo + kk - cb, j); },
-          [&](int i, int j, double v) { t[i + (int64_t)j * k] = v; }, smem);
+          [&](int i, int j, double v) { t[i + (int64_t)j * k] = v; }, smem, F.flags);
     }
   } else {
     const LrTarget L = F.lrt[t0 + blockIdx.x - ne];
@@ -289,12 +335,12 @@ __global__ void __launch_bounds__(kThreads) k_side_t(FactorArgs F, int e0, int n
       cta_gemm_tn<Tc>(
           kce, r, L.m, [&](int kk, int i) { return UC[kk + (int64_t)i * ld]; },
           [&](int kk, int j) { return Q[kk + (int64_t)j * L.m]; },
-          [&](int i, int j, double v) { tc[i + (int64_t)j * kc] = v; }, smem);
+          [&](int i, int j, double v) { tc[i + (int64_t)j * kc] = v; }, smem, F.flags);
     } else {
       cta_gemm_tn<Tc>(
           kce, r, L.p, [&](int kk, int i) { return UC[kk + (int64_t)i * ld]; },
           [&](int kk, int j) { return rademacher(seed, tb, kk, j); },
-          [&](int i, int j, double v) { tc[i + (int64_t)j * kc] = v; }, smem);
+          [&](int i, int j, double v) { tc[i + (int64_t)j * kc] = v; }, smem, F.flags);
     }
   }
 }
@@ -400,7 +446,7 @@ __global__ void __launch_bounds__(kThreads) k_side_s(FactorArgs F, int e0, int t
           double *o = s + i + (int64_t)j * kx;
           *o = acc ? *o + v : v;
         },
-        smem);
+        smem, F.flags);
     __syncthreads();
     // identity pairs (both blocks dense): s(i, j) += t_q(i, j), in pair order
     for (int o = threadIdx.x; o < M * r; o += blockDim.x) {
@@ -475,7 +521,7 @@ __global__ void __launch_bounds__(kThreads) k_rows(FactorArgs F, int rt0, int tr
         if (q == 0) return tc[k + (int64_t)j * kc];
         return F.ws[esoff[q - 1] + (k - kbeg[q]) + (int64_t)j * ekx[q - 1]];
       },
-      [&](int i, int j, double v) { Y[(I0 - base + i) + (int64_t)j * ld] = v; }, smem);
+      [&](int i, int j, double v) { Y[(I0 - base + i) + (int64_t)j * ld] = v; }, smem, F.flags);
 }
 
 // --- tall QR (R factor only), then pivoted QR / SVD of the small R --------
@@ -1018,14 +1064,14 @@ __global__ void __launch_bounds__(kThreads) k_dense_pair(FactorArgs F, int q0, i
   // the target's rows and columns (point ranges), stored per pair
   const int tr0 = F.dpair_tr[q].x, m = F.dpair_tr[q].y - F.dpair_tr[q].x;
   const int tc0 = F.dpair_tc[q].x, p = F.dpair_tc[q].y - F.dpair_tc[q].x;
-  double *X = smem + kGemmSmem;  // up to max(kcap, b) x b, ld ldx
+  double *X = smem + gemm_words<Tc>();  // up to max(kcap, b) x b, ld ldx
   const int ldx = max(b, kc);
   auto put = [&](int i, int j, double v) { out[i + (int64_t)j * b] = v; };
   if (A.kind == kDense && B.kind == kDense) {
     const int nj = A.cend - A.cbeg;
     cta_gemm<false, true, Tc>(
         m, p, nj, [&](int i, int k) { return a.U(A, tr0 + i, k); },
-        [&](int k, int j) { return a.U(B, tc0 + j, k); }, put, smem);
+        [&](int k, int j) { return a.U(B, tc0 + j, k); }, put, smem, F.flags);
     return;
   }
   int kx;
@@ -1036,27 +1082,27 @@ __global__ void __launch_bounds__(kThreads) k_dense_pair(FactorArgs F, int q0, i
     cta_gemm<false, true, Tc>(
         kx, p, kb, [&](int i, int k) { return G[i + (int64_t)k * kc]; },
         [&](int k, int j) { return a.U(B, tc0 + j, k); },
-        [&](int i, int j, double v) { X[i + j * ldx] = v; }, smem);
+        [&](int i, int j, double v) { X[i + j * ldx] = v; }, smem, F.flags);
   } else if (A.kind == kDense) {  // B low-rank: X = W_B[J_A] U_B[K]^T
     kx = A.cend - A.cbeg;
     const int J0 = A.cbeg;
     cta_gemm<false, true, Tc>(
         kx, p, F.rank_l[Pq.b], [&](int i, int k) { return a.W(B, J0 + i, k); },
         [&](int k, int j) { return a.U(B, tc0 + j, k); },
-        [&](int i, int j, double v) { X[i + j * ldx] = v; }, smem);
+        [&](int i, int j, double v) { X[i + j * ldx] = v; }, smem, F.flags);
   } else {  // A low-rank, B dense: X = W_A[J_B]^T D_B^T
     kx = F.rank_l[Pq.a];
     const int J0 = B.cbeg, nj = B.cend - B.cbeg;
     cta_gemm<true, true, Tc>(
         kx, p, nj, [&](int i, int k) { return a.W(A, J0 + k, i); },
         [&](int k, int j) { return a.U(B, tc0 + j, k); },
-        [&](int i, int j, double v) { X[i + j * ldx] = v; }, smem);
+        [&](int i, int j, double v) { X[i + j * ldx] = v; }, smem, F.flags);
   }
   __syncthreads();
   const int kxx = kx;
   cta_gemm<false, false, Tc>(
       m, p, kxx, [&](int i, int k) { return a.U(A, tr0 + i, k); },
-      [&](int k, int j) { return X[k + j * ldx]; }, put, smem);
+      [&](int k, int j) { return X[k + j * ldx]; }, put, smem, F.flags);
 }
 
 __global__ void __launch_bounds__(kThreads) k_dense_reduce(FactorArgs F, int d0, int64_t dpws) {
@@ -1198,7 +1244,7 @@ __global__ void __launch_bounds__(kThreads) k_htask(FactorArgs F, int h0) {
     cta_gemm_tn<Tc>(
         ka, nj, A.cend - A.cbeg, [&](int k, int i) { return wa[k + (int64_t)i * lda]; },
         [&](int k, int j) { return Wp[(A.cbeg + k - P.rbeg) + (int64_t)(j0 + j) * ld]; },
-        [&](int i, int j, double v) { out[i + (int64_t)(j0 + j) * kc] = v; }, smem);
+        [&](int i, int j, double v) { out[i + (int64_t)(j0 + j) * kc] = v; }, smem, F.flags);
   }
 }
 
@@ -1222,12 +1268,12 @@ __global__ void __launch_bounds__(kThreads) k_updrow(FactorArgs F, int u0) {
       const int nj = A.cend - A.cbeg;
       cta_gemm<false, false, Tc>(
           mi, P.width, nj, [&](int i, int k) { return a.U(A, I0 + i, k); },
-          [&](int k, int j) { return Wp[(A.cbeg + k - P.rbeg) + (int64_t)j * ld]; }, sub, smem);
+          [&](int k, int j) { return Wp[(A.cbeg + k - P.rbeg) + (int64_t)j * ld]; }, sub, smem, F.flags);
     } else {
       const double *Hm = F.ws + E.hoff;
       cta_gemm<false, true, Tc>(
           mi, P.width, F.rank_l[E.a], [&](int i, int k) { return a.U(A, I0 + i, k); },
-          [&](int k, int j) { return Hm[k + (int64_t)j * kc]; }, sub, smem);
+          [&](int k, int j) { return Hm[k + (int64_t)j * kc]; }, sub, smem, F.flags);
     }
   }
 }
@@ -1266,28 +1312,29 @@ int factor_smem_setup(int b, int kcap) {
   g_smem_dense = (kGemmSmem + kx * b) * (int)sizeof(double);
   cudaError_t e = cudaSuccess;
 #define SETA(k, s) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, s); if (e != cudaSuccess) return (int)e
-  SETA(k_gram<double>, g_smem_bytes);
-  SETA(k_gram<float>, g_smem_bytes);
-  SETA(k_side_t<double>, g_smem_bytes);
-  SETA(k_side_t<float>, g_smem_bytes);
-  SETA(k_side_s<double>, kTnSmem * (int)sizeof(double));
-  SETA(k_side_s<float>, kTnSmem * (int)sizeof(double));
-  SETA(k_rows<double>, g_smem_bytes);
-  SETA(k_rows<float>, g_smem_bytes);
+  const int tn = kTnSmem * (int)sizeof(double);
+#define SETA_TC(kern, bytes)                      \
+  SETA(kern<double>, bytes);                      \
+  SETA(kern<tc::Split<3>>, tc_smem<tc::Split<3>>(bytes)); \
+  SETA(kern<tc::Split<2>>, tc_smem<tc::Split<2>>(bytes))
+  SETA_TC(k_gram, g_smem_bytes);
+  SETA_TC(k_side_t, g_smem_bytes);
+  SETA_TC(k_side_s, tn);
+  SETA_TC(k_rows, g_smem_bytes);
   SETA(k_tsqr_part, (kMaxSample + kQrRows) * kMaxSample * (int)sizeof(double));
   SETA(k_cholqr_part, kTnSmem * (int)sizeof(double));
   SETA(k_cholqr_final, 2 * kMaxSample * kMaxSample * (int)sizeof(double));
   SETA(k_tsqr_final, ((kMaxSample + kQrRows) * kMaxSample + 2 * (kMaxSample + 1) * kMaxSample) * (int)sizeof(double));
   SETA(k_tall_apply, g_smem_bytes);
   SETA(k_dense_pair<double>, g_smem_dense);
-  SETA(k_dense_pair<float>, g_smem_dense);
+  SETA(k_dense_pair<tc::Split<3>>, (gemm_words<tc::Split<3>>() + kx * b) * (int)sizeof(double));
+  SETA(k_dense_pair<tc::Split<2>>, (gemm_words<tc::Split<2>>() + kx * b) * (int)sizeof(double));
   SETA(k_potrf, g_smem_bytes);
   SETA(k_trsm, g_smem_bytes);
   SETA(k_wsolve, g_smem_bytes);
-  SETA(k_htask<double>, g_smem_bytes);
-  SETA(k_htask<float>, g_smem_bytes);
-  SETA(k_updrow<double>, g_smem_bytes);
-  SETA(k_updrow<float>, g_smem_bytes);
+  SETA_TC(k_htask, g_smem_bytes);
+  SETA_TC(k_updrow, g_smem_bytes);
+#undef SETA_TC
   SETA(k_bw_h, kTnSmem * (int)sizeof(double));
   SETA(k_lmv_t, kTnSmem * (int)sizeof(double));
 #undef SETA
@@ -1331,18 +1378,21 @@ void prof_collect(Prof *p, int nev) {
   } while (0)
 
 namespace {
-// One step of the sweep with the Schur-update products computed in T.
-template <class Tc>
+// One step of the sweep.  Tl: arithmetic of the products of the low-rank
+// targets' compression and of the deferred panel updates (k_side_t/s, k_rows,
+// k_htask, k_updrow); Td: that of the Grams and of the dense targets' products
+// (k_gram, k_dense_pair), the updates of the diagonal leaves.
+template <class Tl, class Td>
 int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
                   const FactorArgs &F, const StepRange &S, int K, const Plan &PL, Prof *prof) {
   const std::vector<LrTarget> &lrt_host = PL.lrt;
   int nk = 0;
   const int sm = (kGemmSmem + F.b * F.b) * (int)sizeof(double);
   const int smt = std::max(kGemmSmem + F.b * F.b, kTnSmem) * (int)sizeof(double);
-  const int smd = (kGemmSmem + std::max(F.b, F.kcap) * F.b) * (int)sizeof(double);
+  const int smd = (gemm_words<Td>() + std::max(F.b, F.kcap) * F.b) * (int)sizeof(double);
   const int stn = kTnSmem * (int)sizeof(double);    // a small-output product and nothing else
   const int r = F.r;
-  if (S.gch1 > S.gch0) { LAUNCH(KK_GRAM, st, k_gram<Tc><<<S.gch1 - S.gch0, kThreads, smt, st>>>(F, S.gch0)); }
+  if (S.gch1 > S.gch0) { LAUNCH(KK_GRAM, st, k_gram<Td><<<S.gch1 - S.gch0, kThreads, tc_smem<Td>(smt), st>>>(F, S.gch0)); }
   if (S.gred1 > S.gred0) { LAUNCH(KK_GRAM, st, k_gram_reduce<<<S.gred1 - S.gred0, kThreads, 0, st>>>(F, S.gred0)); }
   // the dense blocks of column K (P6-P8) only need the grams: fork them to
   // the side stream while the low-rank targets are compressed
@@ -1353,7 +1403,7 @@ int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaE
   }
   const int nd = S.dns1 - S.dns0;
   const int q0 = PL.dns[S.dns0].p0, q1 = PL.dns[S.dns1 - 1].p1;
-  if (q1 > q0) { LAUNCH(KK_DENSE_PAIR, sd, k_dense_pair<Tc><<<q1 - q0, kThreads, smd, sd>>>(F, q0, S.dpws)); }
+  if (q1 > q0) { LAUNCH(KK_DENSE_PAIR, sd, k_dense_pair<Td><<<q1 - q0, kThreads, smd, sd>>>(F, q0, S.dpws)); }
   LAUNCH(KK_DENSE_REDUCE, sd, k_dense_reduce<<<nd, kThreads, 0, sd>>>(F, S.dns0, S.dpws));
   LAUNCH(KK_POTRF, sd, k_potrf<<<1, kThreads, sm, sd>>>(F, S.dns0, K));
   if (nd > 1) { LAUNCH(KK_TRSM, sd, k_trsm<<<nd - 1, kThreads, sm, sd>>>(F, S.dns0, K)); }
@@ -1371,9 +1421,9 @@ int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaE
     const int qrf_smem = ((r + kQrRows) * r + 2 * (r | 1) * r) * (int)sizeof(double);
     const int cq_smem = 2 * r * r * (int)sizeof(double);
     // Y = S Omega
-    LAUNCH(KK_SIDE_T, st, k_side_t<Tc><<<(S.bent1 - S.bent0) + nt, kThreads, smt, st>>>(F, S.bent0, S.bent1 - S.bent0, S.lrt0, 0));
-    if (S.aent1 > S.aent0) LAUNCH(KK_SIDE_S, st, k_side_s<Tc><<<S.aent1 - S.aent0, kThreads, stn, st>>>(F, S.aent0, 0));
-    LAUNCH(KK_ROWS, st, k_rows<Tc><<<S.arow1 - S.arow0, kThreads, sm, st>>>(F, S.arow0, 0));
+    LAUNCH(KK_SIDE_T, st, k_side_t<Tl><<<(S.bent1 - S.bent0) + nt, kThreads, tc_smem<Tl>(smt), st>>>(F, S.bent0, S.bent1 - S.bent0, S.lrt0, 0));
+    if (S.aent1 > S.aent0) LAUNCH(KK_SIDE_S, st, k_side_s<Tl><<<S.aent1 - S.aent0, kThreads, tc_smem<Tl>(stn), st>>>(F, S.aent0, 0));
+    LAUNCH(KK_ROWS, st, k_rows<Tl><<<S.arow1 - S.arow0, kThreads, tc_smem<Tl>(sm), st>>>(F, S.arow0, 0));
     // Q = orth(Y): R of Y, pivoted QR, Q1 = Y P R_p11^{-1}, then CholQR
     LAUNCH(KK_TSQR_PART, st, k_tsqr_part<<<dim3(nt, maxgm), kThreads, qr_smem, st>>>(F, S.lrt0, 0));
     LAUNCH(KK_TSQR_FINAL, st, k_tsqr_final<<<nt, kThreads, qrf_smem, st>>>(F, S.lrt0, 0, 0));
@@ -1382,9 +1432,9 @@ int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaE
     LAUNCH(KK_CHOLQR_FINAL, st, k_cholqr_final<<<nt, kThreads, cq_smem, st>>>(F, S.lrt0));
     LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch), kThreads, sm, st>>>(F, S.lrt0, 0));
     // Z = S^T Q
-    LAUNCH(KK_SIDE_T, st, k_side_t<Tc><<<(S.aent1 - S.aent0) + nt, kThreads, smt, st>>>(F, S.aent0, S.aent1 - S.aent0, S.lrt0, 1));
-    if (S.bent1 > S.bent0) LAUNCH(KK_SIDE_S, st, k_side_s<Tc><<<S.bent1 - S.bent0, kThreads, stn, st>>>(F, S.bent0, 1));
-    LAUNCH(KK_ROWS, st, k_rows<Tc><<<S.brow1 - S.brow0, kThreads, sm, st>>>(F, S.brow0, 1));
+    LAUNCH(KK_SIDE_T, st, k_side_t<Tl><<<(S.aent1 - S.aent0) + nt, kThreads, tc_smem<Tl>(smt), st>>>(F, S.aent0, S.aent1 - S.aent0, S.lrt0, 1));
+    if (S.bent1 > S.bent0) LAUNCH(KK_SIDE_S, st, k_side_s<Tl><<<S.bent1 - S.bent0, kThreads, tc_smem<Tl>(stn), st>>>(F, S.bent0, 1));
+    LAUNCH(KK_ROWS, st, k_rows<Tl><<<S.brow1 - S.brow0, kThreads, tc_smem<Tl>(sm), st>>>(F, S.brow0, 1));
     LAUNCH(KK_TSQR_PART, st, k_tsqr_part<<<dim3(nt, maxgp), kThreads, qr_smem, st>>>(F, S.lrt0, 1));
     LAUNCH(KK_TSQR_FINAL, st, k_tsqr_final<<<nt, kThreads, qrf_smem, st>>>(F, S.lrt0, 1, 1));
     LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch), kThreads, sm, st>>>(F, S.lrt0, 1));
@@ -1403,17 +1453,20 @@ int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaE
     int maxw = 1;
     for (int q = S.ht0; q < S.ht1; ++q) maxw = std::max(maxw, PL.panels[PL.hts[q].panel].width);
     const int ny = (maxw + (kTnMaxMN - kMaxRank) - 1) / (kTnMaxMN - kMaxRank);
-    LAUNCH(KK_HTASK, st, k_htask<Tc><<<dim3(S.ht1 - S.ht0, ny), kThreads, smt, st>>>(F, S.ht0));
+    LAUNCH(KK_HTASK, st, k_htask<Tl><<<dim3(S.ht1 - S.ht0, ny), kThreads, tc_smem<Tl>(smt), st>>>(F, S.ht0));
   }
-  if (S.ur1 > S.ur0) { LAUNCH(KK_UPDROW, st, k_updrow<Tc><<<S.ur1 - S.ur0, kThreads, sm, st>>>(F, S.ur0)); }
+  if (S.ur1 > S.ur0) { LAUNCH(KK_UPDROW, st, k_updrow<Tl><<<S.ur1 - S.ur0, kThreads, tc_smem<Tl>(sm), st>>>(F, S.ur0)); }
   return nk;
 }
 }  // namespace
 
 int launch_step(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
                 const FactorArgs &F, const StepRange &S, int K, const Plan &PL, Prof *prof) {
-  return F.mixed ? launch_step_t<float>(st, side, ev_fork, ev_join, F, S, K, PL, prof)
-                 : launch_step_t<double>(st, side, ev_fork, ev_join, F, S, K, PL, prof);
+  // the mixed forms run every product on the tensor cores: FP32-class
+  // operands (three BF16 slices) or 16-bit operands (two slices)
+  if (F.mixed == 1) return launch_step_t<tc::Split<3>, tc::Split<3>>(st, side, ev_fork, ev_join, F, S, K, PL, prof);
+  if (F.mixed == 2) return launch_step_t<tc::Split<2>, tc::Split<2>>(st, side, ev_fork, ev_join, F, S, K, PL, prof);
+  return launch_step_t<double, double>(st, side, ev_fork, ev_join, F, S, K, PL, prof);
 }
 
 // --- a17: y = L x (field simulation Z = L xi) ------------------------------

@@ -27,6 +27,7 @@ class HmleError(RuntimeError):
 
 HMLE_FP64 = 0
 HMLE_MIXED_FP32 = 1
+HMLE_MIXED_BF16 = 2
 
 
 class Opts(C.Structure):
@@ -110,6 +111,8 @@ def lib():
             "hmle_loglik_multi": ([P, P, C.c_int32, C.c_int32, P, P], C.c_int),
             "hmle_theta_to_x": ([P, P], C.c_int),
             "hmle_selftest_barrier": ([P, C.c_int32, P], C.c_int),
+            "hmle_selftest_tc_gemm": ([P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                       C.c_int32, C.c_int32, P, P, P], C.c_int),
             "hmle_x_to_theta": ([P, P], C.c_int),
             "hmle_features": ([P, P, C.c_int64, C.c_int32, P, P], C.c_int),
             "hmle_mlp_nparams": ([], C.c_int32),
@@ -149,7 +152,7 @@ def exported_symbols():
             "hmle_hmatrix_matvec", "hmle_factor", "hmle_factor_destroy", "hmle_loglik",
             "hmle_loglik_eval", "hmle_fit", "hmle_matern_eval", "hmle_profile_select",
             "hmle_profile_read", "hmle_phase_work", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_predict", "hmle_fit_profiled", "hmle_cross_matvec", "hmle_loglik_multi", "hmle_autotune",
-            "hmle_theta_to_x", "hmle_x_to_theta", "hmle_selftest_barrier", "hmle_features", "hmle_mlp_nparams",
+            "hmle_theta_to_x", "hmle_x_to_theta", "hmle_selftest_barrier", "hmle_selftest_tc_gemm", "hmle_features", "hmle_mlp_nparams",
             "hmle_mlp_create", "hmle_mlp_destroy", "hmle_mlp_set", "hmle_mlp_get",
             "hmle_mlp_forward", "hmle_mlp_grad", "hmle_mlp_adam_step", "hmle_mlp_train",
             "hmle_matern_eval_noalloc", "hmle_plan_build", "hmle_plan_destroy",
@@ -243,6 +246,21 @@ class Context:
         self.check(lib().hmle_matern_eval(self._h, float(nu), P(x.ctypes.data), x.size,
                                           P(out.ctypes.data)), "hmle_matern_eval")
         return out
+
+    def tc_gemm(self, A, B, nslices: int, a_kfast: bool = True, b_kfast: bool = True,
+                copies: int = 1) -> np.ndarray:
+        """C = A B by the tensor-core tile product with nslices BF16 slices
+        per operand (hmle_selftest_tc_gemm); returns copies x M x N."""
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        M, K = A.shape
+        K2, N = B.shape
+        assert K == K2
+        out = np.empty((copies, N, M), dtype=np.float64)
+        self.check(lib().hmle_selftest_tc_gemm(self._h, nslices, int(a_kfast), int(b_kfast), copies, M, N, K,
+                                               P(A.ctypes.data), P(B.ctypes.data), P(out.ctypes.data)),
+                   "hmle_selftest_tc_gemm")
+        return out.transpose(0, 2, 1)
 
 
 class Profiler:

@@ -168,24 +168,6 @@ def test_loglik_permutation_invariant():
         assert abs(u - v) <= 1e-10 * max(1.0, abs(u))
 
 
-def _kalman_ou_loglik(x, z, ell, s2, t2):
-    """Exact L for C_ij = s2 exp(-|x_i - x_j|/ell) + t2 [i==j] on sorted x:
-    the exponential kernel is an Ornstein-Uhlenbeck process, so the
-    prediction-error decomposition of a scalar Kalman filter gives Eq. 1."""
-    m, P = 0.0, s2                       # prior of the latent state at x_0
-    ll = 0.0
-    for i in range(len(x)):
-        if i > 0:
-            rho = math.exp(-(x[i] - x[i - 1]) / ell)
-            m, P = rho * m, rho * rho * P + s2 * (1 - rho * rho)
-        S = P + t2
-        e = z[i] - m
-        ll += -0.5 * (LOG2PI + math.log(S) + e * e / S)
-        K = P / S
-        m, P = m + K * e, (1 - K) * P
-    return ll
-
-
 @pytest.mark.parametrize("t2", [0.0, 1e-3, 0.05])
 def test_loglik_exponential_on_a_line_matches_kalman(t2):
     n = 700
@@ -193,8 +175,23 @@ def test_loglik_exponential_on_a_line_matches_kalman(t2):
     Z = synth.normal(13, n)
     ell, s2 = 0.07, 1.4
     ll, _, _ = oracle.loglik_dense(locs, Z, (ell, 0.5, s2, t2))
-    ref = _kalman_ou_loglik(locs[:, 0], Z, ell, s2, t2)
+    ref = oracle.kalman_exponential(locs[:, 0], Z, ell, s2, t2)
     assert abs(ll - ref) <= 1e-9 * abs(ref), (ll, ref)
+
+
+def test_exponential_line_simulation_is_the_cholesky_factor():
+    """The O(n) Ornstein-Uhlenbeck recursion without nugget is L xi with L
+    the dense Cholesky factor of the exponential covariance on sorted points;
+    the nugget then adds tau eta."""
+    n = 300
+    locs = synth.locations_collinear(n, seed=14)
+    xi, eta = synth.normal(15, n), synth.normal(16, n)
+    th = (0.05, 0.5, 1.7, 0.0)
+    u = oracle.simulate_exponential_line(locs[:, 0], th, xi, eta)
+    assert np.max(np.abs(u - oracle.simulate(locs, th, xi))) <= 1e-11
+    th2 = (0.05, 0.5, 1.7, 0.02)
+    z = oracle.simulate_exponential_line(locs[:, 0], th2, xi, eta)
+    assert np.max(np.abs(z - u - math.sqrt(0.02) * eta)) <= 1e-14
 
 
 def test_loglik_tiny_range_is_white_noise():
