@@ -189,28 +189,19 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    launches = args.steps * args.batch * info.kernel_launches
-    # roofline kernel: its launches timed with CUDA events inside one
-    # evaluation's captured graph
+    # kernels of one step: the batch's sweep (each launch serves all B
+    # evaluations, gridDim.z = B) plus, per evaluation, the three assembly
+    # launches, the permutation of Z and the final reduction
+    launches = args.steps * (info.kernel_launches - 5 + 5 * args.batch)
+    # roofline kernel: every launch of it in one batched step (B evaluations
+    # per launch, the bench's launch configuration), bracketed by CUDA events
+    # on its launching stream; the step's sweep is then launched directly,
+    # since events inside a captured graph cannot be read back
     prof.enable(True)
-    tree.loglik(theta, Zd)
+    step(Zd)
     dom = prof.read()
     prof.enable(False)
-    dom["mode"] = "inside the captured graph"
-    if dom["launches"] == 0:
-        # event pairs inside the graph could not be read: time the same
-        # kernel on a tree whose sweep is launched directly (no graph)
-        dom["graph_note"] = ctx.last_error()
-        os.environ["HMLE_GRAPHS"] = "0"
-        tree_ng = hmle.Tree(ctx, locs, leaf_size=w["leaf"], eta=w["eta"], aca_eps=w["eps"])
-        os.environ.pop("HMLE_GRAPHS")
-        tree_ng.loglik(theta, Zd)
-        prof.enable(True)
-        tree_ng.loglik(theta, Zd)
-        dom.update(prof.read())
-        prof.enable(False)
-        dom["mode"] = "direct launches (no graph)"
-        tree_ng.close()
+    dom["mode"] = "one batched step of %d evaluations, direct launches" % args.batch
     # e2e: host Z (pinned) through the C ABI; the copy in and the result out
     # are inside the timed region
     e2 = torch.cuda.Event(enable_timing=True)
@@ -254,10 +245,9 @@ def run_gpu(args):
                      "frac": (achieved / FP64_PEAK_GFLOPS) if achieved else None,
                      "traffic": None,
                      "note": "FP64 ALU peak from 152 SMs x 2 FMA/clk x 2070 MHz "
-                             "(measured FMA loop: 1254.6 GFLOP/s); every launch of the kernel "
-                             "in one evaluation bracketed by CUDA events on its launching "
-                             "stream, " + dom["mode"],
-                     **({"graph_note": dom["graph_note"]} if "graph_note" in dom else {})},
+                             "(measured FMA loop: 1254.6 GFLOP/s); algorithmic FP64 flops of "
+                             "the kernel's launches (plan x ranks of every evaluation) over "
+                             "their summed CUDA-event durations: " + dom["mode"]},
         "step_roofline": {
             "bound": "alu", "flops_per_eval": info.flops,
             "achieved": info.flops * value / ws / 1e9 if info.flops else None,
@@ -324,16 +314,23 @@ def other_forms(ctx, locs, Z, Zd, thetas, B, fp64_value):
     from paper_2104_07146_gb300 import hmle, synth
     w = WORKLOAD
     res = {"fp64_batched_evals_per_s": fp64_value}
-    tm = hmle.Tree(ctx, locs, leaf_size=w["leaf"], eta=w["eta"], aca_eps=w["eps"], precision=1)
-    tm.loglik_batch(thetas, Zd, concurrency=B)                     # buffers, graphs
-    torch.cuda.synchronize()
-    t0 = time.time()
-    ll_m, st = tm.loglik_batch(thetas, Zd, concurrency=B)
-    dt = time.time() - t0
-    ll1, info = tm.loglik(thetas[0], Zd)
-    res["mixed_fp32_pcg"] = {"evals_per_s": B / dt, "pcg_iters": info.pcg_iters,
-                             "pcg_relres": info.pcg_relres, "loglik": ll1}
-    tm.close()
+    for prec, key in ((1, "mixed_fp32_pcg"), (2, "mixed_bf16_pcg")):
+        # the products on the tensor cores with three (24-bit) or two (16-bit)
+        # BF16 slices per operand; the quadratic form by PCG
+        tm = hmle.Tree(ctx, locs, leaf_size=w["leaf"], eta=w["eta"], aca_eps=w["eps"], precision=prec)
+        ll_m, st = tm.loglik_batch(thetas, Zd, concurrency=B)          # buffers, graphs
+        torch.cuda.synchronize()
+        t0 = time.time()
+        ll_m, st = tm.loglik_batch(thetas, Zd, concurrency=B)
+        dt = time.time() - t0
+        ll1, info = tm.loglik(thetas[0], Zd)
+        t0 = time.time()
+        ll1, info = tm.loglik(thetas[0], Zd)
+        single = time.time() - t0
+        res[key] = {"evals_per_s": B / dt, "single_eval_ms": single * 1e3, "pcg_iters": info.pcg_iters,
+                    "pcg_relres": info.pcg_relres, "loglik": ll1, "logdet": info.logdet,
+                    "status": [int(x) for x in st]}
+        tm.close()
     # multi-instance: 8 fields of uneven n (2-D and 3-D), 4 theta each, one call
     fields = []
     for i in range(8):

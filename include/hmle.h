@@ -114,7 +114,14 @@ typedef struct {
  *             accuracy-fixed approximation); k in 1..max_rank: fixed rank,
  *             every block of C~ and of L~ at most k (Sec. 2, the rank-fixed
  *             approximation; the accuracy then varies from block to block and
- *             no rank overflow is reported). */
+ *             no rank overflow is reported).
+ *  batch_size evaluations of hmle_loglik_batch served by one launch of every
+ *             sweep kernel (gridDim.z), in [1, 64]; default 4.  A batch of
+ *             concurrency evaluations runs as ceil(concurrency / batch_size)
+ *             such launches sequences on their own streams, side by side, and
+ *             the mixed forms' PCG solves all of them in one lockstep
+ *             iteration.  Results do not depend on it (hmle_autotune picks
+ *             it with the leaf size and the concurrency). */
 typedef struct {
   int32_t leaf_size;
   double eta;
@@ -127,6 +134,7 @@ typedef struct {
   double pcg_tol;
   int32_t pcg_max_iter;
   int32_t fixed_rank;
+  int32_t batch_size;
 } hmle_opts;
 
 /* Nelder-Mead options of hmle_fit (Sec. 2: threshold 1e-4, <= 400 iterations). */
@@ -173,7 +181,7 @@ typedef struct hmle_hfactor hmle_hfactor;
 
 /* Fill *opts with defaults: leaf 64, eta 2, aca_eps 1e-8, max_rank 32,
  * oversample 8, FP64, seed 0x5eed, leaf_lowrank 0, pcg_tol 1e-10,
- * pcg_max_iter 50, fixed_rank 0.  HMLE_OK for non-NULL opts, else
+ * pcg_max_iter 50, fixed_rank 0, batch_size 4.  HMLE_OK for non-NULL opts, else
  * INVALID_ARG. */
 hmle_status hmle_opts_default(hmle_opts *opts);
 
@@ -335,10 +343,12 @@ hmle_status hmle_loglik_multi(hmle_ctx *ctx, const hmle_task *tasks, int32_t nta
  * and theta it builds trees with leaf sizes 32, 64 and 128 (the tile of the
  * leaf sweep; other options from base) and times hmle_loglik_batch at
  * concurrency 1, 2, 4, ... up to max_concurrency (0 means 16), stopping a
- * leaf size once doubling the concurrency gains less than 5 %.  Each trial is
- * one warm-up batch (buffers, graph capture) and one timed batch.
- *  best    the fastest (leaf_size, concurrency, evals_per_s); best->trials =
- *          number of trials run.
+ * leaf size once doubling the concurrency gains less than 5 %; at each
+ * concurrency c it tries the batch sizes (evaluations per launch) c, c / 2
+ * and c / 4 (at least 1).  Each trial is one warm-up batch (buffers, graph
+ * capture) and one timed batch.
+ *  best    the fastest (leaf_size, concurrency, batch_size, evals_per_s);
+ *          best->trials = number of trials run.
  *  trials  if not NULL, up to max_trials trial results in run order;
  *          *ntrials (may be NULL) receives the number run.
  * The trees are destroyed before returning.  Errors: INVALID_ARG, OOM,
@@ -348,7 +358,12 @@ typedef struct {
   int32_t concurrency;
   double evals_per_s;
   int32_t trials;
+  int32_t batch_size;
 } hmle_tune_result;
+
+/* a15: set the evaluations per launch (opts.batch_size, 1..64) of a tree's
+ * later hmle_loglik_batch calls.  Errors: INVALID_ARG. */
+hmle_status hmle_tree_set_batch_size(hmle_tree *tree, int32_t batch_size);
 hmle_status hmle_autotune(hmle_ctx *ctx, const double *locs, int64_t n, int32_t d,
                           const hmle_opts *base, const hmle_theta *theta, const double *Z,
                           int32_t max_concurrency, hmle_tune_result *best,
@@ -436,10 +451,15 @@ hmle_status hmle_theta_to_x(const hmle_theta *theta, double x[4]);
 hmle_status hmle_x_to_theta(const double x[4], hmle_theta *theta);
 
 /* a16 (learned start; Sec. 7 suggests precomputing the initial guess of the
- * optimiser).  A 35-64-64-8 perceptron (tanh, FP32) maps field statistics to
- * an initial theta (4 transformed coordinates of Sec. 5) and log initial
+ * optimiser).  A 35-256-256-256-8 perceptron (tanh) maps field statistics
+ * to an initial theta (4 transformed coordinates of Sec. 5) and log initial
  * simplex steps (4), trained on the GPU with hand-written kernels on fields
- * simulated by hmle_simulate.
+ * simulated by hmle_simulate.  Its matrix products (forward, deltas, weight
+ * gradients) run on the tensor cores with BF16 weights and activations and
+ * FP32 accumulation; the master weights, biases, loss and Adam are FP32.
+ * Parameters: W1 (256 x 35, row-major), b1, W2 (256 x 256), b2, W3, b3,
+ * W4 (8 x 256), b4 -- 142856 floats.  The forward, gradient and training
+ * calls also return TIMEOUT if a bounded wait of the tensor cores ran out.
  *
  * hmle_features: the 35 inputs for one field.  locs n x d row-major and Z
  * (n, caller order), host or device.  On m = min(n, 4096) points at caller

@@ -18,15 +18,19 @@ step:
   dimensions in order.  Features (35): log gamma_k for the 32 bins (an
   empty bin takes the value of the nearest non-empty bin above it, else
   below), log n, d, log sqrt(S).
-* ``mlp_forward`` / ``nll`` / ``mlp_grad`` / ``adam_step`` -- a 35-64-64-8
-  perceptron with tanh hidden layers; outputs (mu_1..4, s_1..4) are the
-  predicted transformed coordinates of Sec. 5 and log step scales, trained
-  with the Gaussian negative log-likelihood
+* ``mlp_forward`` / ``nll`` / ``mlp_grad`` / ``adam_step`` -- a
+  35-256-256-256-8 perceptron with tanh hidden layers; outputs
+  (mu_1..4, s_1..4) are the predicted transformed coordinates of Sec. 5 and
+  log step scales, trained with the Gaussian negative log-likelihood
   sum_c [ exp(-2 s_c) (t_c - mu_c)^2 / 2 + s_c ] averaged over the batch,
-  and Adam (beta1 0.9, beta2 0.999, eps 1e-8; Kingma & Ba 2015).
+  and Adam (beta1 0.9, beta2 0.999, eps 1e-8; Kingma & Ba 2015).  With
+  ``bf16=True`` both operands of every matrix product are first rounded to
+  BF16 (FP32 rounding to nearest even, then BF16 rounding to nearest even)
+  and the product is taken in FP64: the arithmetic of products with BF16
+  weights and activations, up to the accumulation.
 
-Parameter layout (flat, 6984 values): W1 (64 x 35, row-major), b1 (64),
-W2 (64 x 64), b2 (64), W3 (8 x 64), b3 (8).
+Parameter layout (flat, 142856 values): W1 (256 x 35, row-major), b1 (256),
+W2 (256 x 256), b2, W3 (256 x 256), b3, W4 (8 x 256), b4 (8).
 """
 from __future__ import annotations
 
@@ -34,7 +38,8 @@ import math
 
 import numpy as np
 
-NF, NH, NO = 35, 64, 8
+NF, NH, NO = 35, 256, 8
+SIZES = (NF, NH, NH, NH, NO)       # layer widths, input to output
 NBINS = 32
 M_MAX = 4096
 
@@ -92,28 +97,43 @@ def features(locs, Z, m_max: int = M_MAX) -> np.ndarray:
 
 
 def unpack(p):
+    """[(W_1, b_1), ..., (W_4, b_4)], W_l of shape (SIZES[l], SIZES[l - 1])."""
     p = np.asarray(p, dtype=np.float64)
-    o = 0
-    W1 = p[o:o + NH * NF].reshape(NH, NF); o += NH * NF
-    b1 = p[o:o + NH]; o += NH
-    W2 = p[o:o + NH * NH].reshape(NH, NH); o += NH * NH
-    b2 = p[o:o + NH]; o += NH
-    W3 = p[o:o + NO * NH].reshape(NO, NH); o += NO * NH
-    b3 = p[o:o + NO]; o += NO
+    out, o = [], 0
+    for a, b in zip(SIZES[:-1], SIZES[1:]):
+        W = p[o:o + a * b].reshape(b, a); o += a * b
+        c = p[o:o + b]; o += b
+        out.append((W, c))
     assert o == p.size
-    return W1, b1, W2, b2, W3, b3
+    return out
 
 
-NPARAMS = NH * NF + NH + NH * NH + NH + NO * NH + NO
+NPARAMS = sum(a * b + b for a, b in zip(SIZES[:-1], SIZES[1:]))
 
 
-def mlp_forward(p, X):
-    """X: B x 35 (already standardised).  Returns (H1, H2, Y)."""
-    W1, b1, W2, b2, W3, b3 = unpack(p)
-    H1 = np.tanh(X @ W1.T + b1)
-    H2 = np.tanh(H1 @ W2.T + b2)
-    Y = H2 @ W3.T + b3
-    return H1, H2, Y
+def bf16(x):
+    """Round to FP32 (nearest even), then to BF16 (nearest even on the upper
+    16 bits of the FP32 pattern); returned as float64."""
+    x32 = np.ascontiguousarray(x, dtype=np.float32)
+    b = x32.view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def _mm(A, B, lowp):
+    return (bf16(A) @ bf16(B)) if lowp else (A @ B)
+
+
+def mlp_forward(p, X, bf16=False):
+    """X: B x 35 (already standardised).  Returns the activations
+    [H_1, H_2, H_3, Y] (tanh hidden layers, linear output)."""
+    layers = unpack(p)
+    H, out = np.asarray(X, dtype=np.float64), []
+    for l, (W, c) in enumerate(layers):
+        A = _mm(H, W.T, bf16) + c
+        H = A if l == len(layers) - 1 else np.tanh(A)
+        out.append(H)
+    return out
 
 
 def nll(Y, T):
@@ -121,18 +141,25 @@ def nll(Y, T):
     return float(np.mean(np.sum(0.5 * np.exp(-2.0 * s) * (T - mu) ** 2 + s, axis=1)))
 
 
-def mlp_grad(p, X, T):
-    """Gradient of nll(mlp_forward(p, X)[2], T) with respect to p (backprop)."""
-    W1, b1, W2, b2, W3, b3 = unpack(p)
-    H1, H2, Y = mlp_forward(p, X)
+def mlp_grad(p, X, T, bf16=False):
+    """Gradient of nll(mlp_forward(p, X)[-1], T) with respect to p (backprop):
+    D_L = dloss/dY, D_l = (D_{l+1} W_{l+1}) (1 - H_l^2), dW_l = D_l^T H_{l-1},
+    db_l = sum over the batch of D_l."""
+    layers = unpack(p)
+    X = np.asarray(X, dtype=np.float64)
+    acts = mlp_forward(p, X, bf16)
     B = X.shape[0]
+    Y = acts[-1]
     mu, s = Y[:, :4], Y[:, 4:]
     e = np.exp(-2.0 * s)
-    D3 = np.concatenate([-e * (T - mu), 1.0 - e * (T - mu) ** 2], axis=1) / B
-    D2 = (D3 @ W3) * (1.0 - H2 * H2)
-    D1 = (D2 @ W2) * (1.0 - H1 * H1)
-    g = [D1.T @ X, D1.sum(0), D2.T @ H1, D2.sum(0), D3.T @ H2, D3.sum(0)]
-    return np.concatenate([a.ravel() for a in g])
+    D = np.concatenate([-e * (T - mu), 1.0 - e * (T - mu) ** 2], axis=1) / B
+    grads = [None] * len(layers)
+    for l in range(len(layers) - 1, -1, -1):
+        Hin = X if l == 0 else acts[l - 1]
+        grads[l] = (_mm(D.T, Hin, bf16), D.sum(0))
+        if l > 0:
+            D = _mm(D, layers[l][0], bf16) * (1.0 - acts[l - 1] ** 2)
+    return np.concatenate([a.ravel() for gw, gb in grads for a in (gw, gb)])
 
 
 def adam_step(p, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):

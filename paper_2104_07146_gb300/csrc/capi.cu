@@ -65,7 +65,8 @@ struct DevPlan {
   int64_t bytes = 0;
 };
 
-struct Work;  // per-tree evaluation buffers (θ-dependent contents)
+struct Work;   // per-tree evaluation buffers (θ-dependent contents)
+struct Group;  // a batch of evaluations of one tree whose buffers share one layout
 
 struct hmle_tree {
   hmle_ctx *ctx = nullptr;   // used by calls on the tree; never by its destructor
@@ -77,7 +78,8 @@ struct hmle_tree {
   DevPlan dp;
   std::vector<int32_t> lr_ids, dense_ids;
   Work *work = nullptr;
-  std::vector<Work *> pool;  // evaluation buffers of hmle_loglik_batch
+  std::vector<Work *> pool;  // evaluation buffers of hmle_loglik_multi
+  std::vector<Group *> groups;  // the batch of hmle_loglik_batch (at most one, of the last size used)
   bool graphs = true;        // replay the sweep as a captured CUDA graph
   SolvePlan sp{};            // device task lists of the persistent sweeps on one vector
   bool coop = false;         // the device supports cooperative launches
@@ -133,6 +135,31 @@ struct Work {
   int graph_kind = -2;             // profiling kind the graph was captured with
   int graph_nev = 0;               // profiling events recorded by one replay
 };
+
+// a15: a batch of nz evaluations of one tree in one launch per kernel.  The
+// buffers of the nz evaluations (the H-matrix of C, the factor, the
+// workspace, flags, results and the Jacobi counter) are carved from one
+// allocation with the same layout at a fixed stride, so evaluation z's
+// buffers are evaluation 0's shifted by z * stride bytes (FactorArgs::at),
+// and every kernel of the sweep serves the whole batch with gridDim.z = nz.
+// The batch's sweep is captured once as a CUDA graph and replayed for every
+// set of theta (theta lives in each evaluation's device buffer).
+struct Group {
+  int nz = 0;                       // evaluations of the batch
+  int sub = 0;                      // evaluations per launch (a sub-batch)
+  char *arena = nullptr;
+  int64_t stride = 0;
+  std::vector<Work *> w;            // per-evaluation views (own streams for the PCG)
+  // per sub-batch: its stream pair, events and captured sweep
+  std::vector<cudaStream_t> st, side;
+  std::vector<cudaEvent_t> ev_fork, ev_join, done;
+  std::vector<cudaGraphExec_t> exec;
+  std::vector<int64_t> launches;    // kernel launches of one sub-batch sweep
+  unsigned *bar = nullptr;          // grid-barrier words of the batch's persistent sweeps
+  double *host = nullptr;           // pinned scalars of the batched PCG (4 + 4 nz)
+  int nsub() const { return (nz + sub - 1) / sub; }
+};
+
 
 namespace {
 
@@ -230,6 +257,32 @@ void free_work(Work *w) {
   delete w;
 }
 
+void free_group(Group *g) {
+  if (!g) return;
+  for (cudaGraphExec_t x : g->exec)
+    if (x) cudaGraphExecDestroy(x);
+  for (Work *w : g->w) {
+    if (!w) continue;
+    // the arena's views are not separate allocations
+    w->H.tab = w->H.uc = w->H.Cd = w->H.cnorm = nullptr;
+    w->H.rank_c = nullptr; w->H.thd = nullptr; w->H.flags = nullptr;
+    w->F.D = w->F.U = w->F.W = w->F.ws = w->F.ldp = w->F.out = nullptr;
+    w->F.rank_l = w->F.kept = nullptr; w->F.flags = nullptr;
+    w->F.pcg = nullptr;
+    w->d_jacobi = nullptr;
+    free_work(w);
+  }
+  if (g->arena) cudaFree(g->arena);
+  if (g->bar) cudaFree(g->bar);
+  if (g->host) cudaFreeHost(g->host);
+  for (cudaEvent_t e : g->ev_fork) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : g->ev_join) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : g->done) if (e) cudaEventDestroy(e);
+  for (cudaStream_t x : g->st) if (x) cudaStreamDestroy(x);
+  for (cudaStream_t x : g->side) if (x) cudaStreamDestroy(x);
+  delete g;
+}
+
 hmle_status alloc_hm(hmle_ctx *ctx, const hmle_tree *t, hmle_hmatrix *h) {
   cudaStream_t st = ctx->st;
   const Plan &P = t->plan;
@@ -321,6 +374,8 @@ FactorArgs make_fargs(const hmle_tree *t, const hmle_hmatrix *h, hmle_hfactor *f
   F.osamp = t->opts.oversample;
   F.mixed = is_mixed(t->opts.precision) ? t->opts.precision : 0;
   F.fixed_k = t->opts.fixed_rank;
+  F.nz = 1;          // one evaluation; a batch sets nz and the stride of its buffers
+  F.zstride = 0;
   // The low-precision products leave noise of about 1e-7 (FP32-class) or
   // 1e-5 (16-bit) of |C_T| in a Schur complement; truncating below that would
   // keep noise as rank.  The mixed factor is truncated at max(eps, floor);
@@ -598,6 +653,7 @@ hmle_status hmle_opts_default(hmle_opts *o) {
   o->seed = 0x5eed;
   o->leaf_lowrank = 0;
   o->fixed_rank = 0;
+  o->batch_size = 4;
   return HMLE_OK;
 }
 
@@ -661,6 +717,8 @@ hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n, int32_
     return fail(ctx, HMLE_ERR_INVALID_ARG, "max_rank must be a multiple of 8 in [8, 64]");
   if (o.fixed_rank < 0 || o.fixed_rank > o.max_rank)
     return fail(ctx, HMLE_ERR_INVALID_ARG, "fixed_rank must be in [0, max_rank]");
+  if (o.batch_size < 1 || o.batch_size > 64)
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "batch_size must be in [1, 64]");
   if (o.oversample < 4 || o.max_rank + o.oversample > 64)
     return fail(ctx, HMLE_ERR_INVALID_ARG, "oversample >= 4 and max_rank + oversample <= 64");
   if (o.precision != HMLE_FP64 && !is_mixed(o.precision))
@@ -772,12 +830,19 @@ void hmle_tree_destroy(hmle_tree *t) {
     delete t->work;
   }
   for (Work *w : t->pool) free_work(w);
+  for (Group *g : t->groups) free_group(g);
   free_devplan(st, t->dp);
   if (t->T.xyz) cudaFreeAsync(t->T.xyz, st);
   if (t->T.perm) cudaFreeAsync(t->T.perm, st);
   if (t->T.box) cudaFreeAsync(t->T.box, st);
   cudaStreamSynchronize(st);
   delete t;
+}
+
+hmle_status hmle_tree_set_batch_size(hmle_tree *t, int32_t batch_size) {
+  if (!t || batch_size < 1 || batch_size > 64) return HMLE_ERR_INVALID_ARG;
+  t->opts.batch_size = batch_size;
+  return HMLE_OK;
 }
 
 hmle_status hmle_tree_get_info(const hmle_tree *t, hmle_tree_info *info) {
@@ -1144,6 +1209,288 @@ hmle_status ensure_pool(hmle_ctx *ctx, hmle_tree *t, int W) {
   return HMLE_OK;
 }
 
+// The batch of nz evaluations of tree t (created on first use, kept with the
+// tree): one allocation for all nz buffer sets, at a stride of the size of
+// one set, and per-evaluation views of it.
+hmle_status ensure_group(hmle_ctx *ctx, hmle_tree *t, int nz, int sub, Group **out) {
+  for (Group *g : t->groups)
+    if (g->nz == nz && g->sub == sub) { *out = g; return HMLE_OK; }
+  // one batch per tree: a batch of another size is released first (its
+  // streams are idle: every call waits for its batch before returning)
+  for (Group *g : t->groups) free_group(g);
+  t->groups.clear();
+  const Plan &P = t->plan;
+  const int64_t nb = std::max<int64_t>((int64_t)P.blocks.size(), 1);
+  int64_t off = 0;
+  auto take = [&](int64_t bytes) { const int64_t o = off; off += (std::max<int64_t>(bytes, 8) + 255) & ~(int64_t)255; return o; };
+  const int64_t o_tab = take(8 * (int64_t)kTableWords), o_uc = take(8 * P.uc_words), o_cd = take(8 * P.dense_words);
+  const int64_t o_rc = take(4 * nb), o_cn = take(8 * nb), o_th = take(sizeof(ThetaDev)), o_hf = take(4);
+  const int64_t o_d = take(8 * P.dense_words), o_u = take(8 * P.u_words), o_w = take(8 * P.w_words);
+  const int64_t o_ws = take(8 * P.ws_max), o_rl = take(4 * nb), o_kp = take(4 * std::max<int64_t>((int64_t)P.lrt.size(), 1));
+  const int64_t o_ld = take(8 * (int64_t)P.nleaf), o_ff = take(4), o_out = take(16), o_jac = take(8);
+  // the mixed forms' PCG workspace (right-hand side + vectors), as mixed_prepare sizes it
+  int64_t o_pcg = -1;
+  if (is_mixed(t->opts.precision)) {
+    int hmax = 1;
+    for (int K = 0; K < P.nleaf; ++K) hmax = std::max(hmax, P.bh0[K + 1] - P.bh0[K]);
+    o_pcg = take(8 * (t->n + pcg_words(t->n, (int)t->lr_ids.size(), P.kc, hmax * P.kcap) + 2));
+  }
+  Group *g = new (std::nothrow) Group();
+  if (!g) return fail(ctx, HMLE_ERR_OOM, "batch");
+  g->nz = nz;
+  g->sub = std::max(1, std::min(sub, nz));
+  g->stride = off;
+  const int ns = g->nsub();
+  g->st.assign(ns, nullptr); g->side.assign(ns, nullptr);
+  g->ev_fork.assign(ns, nullptr); g->ev_join.assign(ns, nullptr); g->done.assign(ns, nullptr);
+  g->exec.assign(ns, nullptr); g->launches.assign(ns, 0);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&g->st[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_fork[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_join[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->done[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&g->arena, (size_t)(off * nz));
+  if (e == cudaSuccess) e = cudaMemset(g->arena, 0, (size_t)(off * nz));
+  if (e == cudaSuccess) e = cudaMalloc(&g->bar, 3 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(g->bar, 0, 3 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMallocHost(&g->host, sizeof(double) * (4 + 4 * (size_t)nz));
+  if (e != cudaSuccess) { free_group(g); return cuda_fail(ctx, e, "batch buffers"); }
+  for (int z = 0; z < nz; ++z) {
+    Work *w = new (std::nothrow) Work();
+    if (!w) { free_group(g); return fail(ctx, HMLE_ERR_OOM, "batch"); }
+    g->w.push_back(w);
+    e = cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) { free_group(g); return cuda_fail(ctx, e, "batch streams"); }
+    char *b = g->arena + (int64_t)z * off;
+    w->H.tree = t;
+    w->H.tab = (double *)(b + o_tab); w->H.uc = (double *)(b + o_uc); w->H.Cd = (double *)(b + o_cd);
+    w->H.rank_c = (int32_t *)(b + o_rc); w->H.cnorm = (double *)(b + o_cn);
+    w->H.thd = (ThetaDev *)(b + o_th); w->H.flags = (int *)(b + o_hf);
+    w->F.D = (double *)(b + o_d); w->F.U = (double *)(b + o_u); w->F.W = (double *)(b + o_w);
+    w->F.ws = (double *)(b + o_ws); w->F.rank_l = (int32_t *)(b + o_rl); w->F.kept = (int32_t *)(b + o_kp);
+    w->F.ldp = (double *)(b + o_ld); w->F.flags = (int *)(b + o_ff); w->F.out = (double *)(b + o_out);
+    w->d_jacobi = (double *)(b + o_jac);
+    if (o_pcg >= 0) w->F.pcg = (double *)(b + o_pcg);
+  }
+  t->groups.push_back(g);
+  *out = g;
+  return HMLE_OK;
+}
+
+// The sweep of the cnt evaluations z0 .. z0 + cnt - 1 of a batch (one
+// sub-batch): per-evaluation state reset (flags, ranks, Jacobi counters, by
+// strided memsets), the steps with gridDim.z = cnt, and the per-evaluation
+// log-det / quadratic-form reductions.  Returns the number of launches.
+int64_t launch_group_sweep(hmle_ctx *gc, const hmle_tree *t, Group *g, int z0, int cnt, Prof *prof) {
+  cudaStream_t st = gc->st;
+  const Plan &P = t->plan;
+  Work *w0 = g->w[z0];
+  FactorArgs F = make_fargs(t, &w0->H, &w0->F);
+  F.jacobi_flops = w0->d_jacobi;
+  F.nz = cnt;
+  F.zstride = g->stride;
+  const size_t nb = std::max<size_t>(P.blocks.size(), 1);
+  cudaMemset2DAsync(F.flags, (size_t)g->stride, 0, sizeof(int), cnt, st);
+  cudaMemset2DAsync(F.rank_l, (size_t)g->stride, 0, sizeof(int32_t) * nb, cnt, st);
+  cudaMemset2DAsync(w0->d_jacobi, (size_t)g->stride, 0, sizeof(double), cnt, st);
+  int64_t nk = 0;
+  for (int K = 0; K < P.nleaf; ++K)
+    nk += launch_step(st, gc->side, gc->ev_fork, gc->ev_join, F, P.steps[K], K, P, prof);
+  const PanelDesc &rp = P.panels[P.rhs_panel];
+  for (int z = z0; z < z0 + cnt; ++z)
+    launch_finalize(st, g->w[z]->F.ldp, P.nleaf, g->w[z]->F.W + rp.off, t->n, g->w[z]->F.out);
+  return nk + cnt;
+}
+
+// m evaluations of tree t at thetas (Z on the device), in waves of up to nz:
+// a wave runs as sub-batches of `sub` evaluations, each with one launch per
+// kernel for the whole sub-batch, side by side on their own streams (the
+// last wave is filled with copies of its last theta, whose results are not
+// reported).  The mixed forms then solve every evaluation of the wave with
+// one PCG in lockstep.
+hmle_status run_group(hmle_ctx *ctx, hmle_tree *t, const hmle_theta *thetas, int m, const double *zd,
+                      int nz, int sub, cudaEvent_t zready, double *ll, int32_t *status, double *ld_out,
+                      double *q_out) {
+  Group *g = nullptr;
+  hmle_status s0 = ensure_group(ctx, t, nz, sub, &g);
+  if (s0 != HMLE_OK) return s0;
+  const Plan &P = t->plan;
+  const PanelDesc &rp = P.panels[P.rhs_panel];
+  const int ns = g->nsub();
+  auto view = [&](int k) {   // a context view on sub-batch k's streams
+    hmle_ctx c;
+    c.st = g->st[k]; c.side = g->side[k]; c.ev_fork = g->ev_fork[k]; c.ev_join = g->ev_join[k];
+    c.d_jacobi = g->w[k * g->sub]->d_jacobi;
+    return c;
+  };
+  Prof *prof = ctx->prof.kind >= 0 ? &ctx->prof : nullptr;
+  hmle_status first = HMLE_OK;
+  for (int k = 0; k < ns; ++k) CK(cudaStreamWaitEvent(g->st[k], zready, 0), "stream wait");
+  for (int i0 = 0; i0 < m; i0 += nz) {
+    const int cnt = std::min(nz, m - i0);
+    std::vector<hmle_status> fs(nz, HMLE_OK);
+    std::vector<std::string> errs(nz);
+    int nev = 0;
+    for (int k = 0; k < ns; ++k) {
+      const int z0 = k * g->sub, zc = std::min(g->sub, nz - z0);
+      hmle_ctx gc = view(k);
+      for (int z = z0; z < z0 + zc; ++z) {
+        Work *w = g->w[z];
+        const hmle_theta *th = &thetas[i0 + std::min(z, cnt - 1)];
+        fs[z] = do_assemble(&gc, t, th, &w->H);
+        launch_permute_in(g->st[k], zd, t->T.perm, t->n, w->F.W + rp.off);
+        w->F.h = &w->H;
+        w->F.has_rhs = true;
+        if (fs[z] != HMLE_OK) errs[z] = gc.err;
+      }
+      if (prof || !t->graphs) {   // direct launches (CUDA events cannot be read inside a graph)
+        if (prof) prof->used = nev;
+        g->launches[k] = launch_group_sweep(&gc, t, g, z0, zc, prof);
+        nev = prof ? prof->used : 0;
+      } else {
+        if (!g->exec[k]) {
+          cudaGraph_t gr = nullptr;
+          CK(cudaStreamBeginCapture(g->st[k], cudaStreamCaptureModeThreadLocal), "begin capture");
+          const int64_t nk = launch_group_sweep(&gc, t, g, z0, zc, nullptr);
+          cudaError_t e = cudaStreamEndCapture(g->st[k], &gr);
+          if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+          e = cudaGraphInstantiate(&g->exec[k], gr, 0);
+          cudaGraphDestroy(gr);
+          if (e != cudaSuccess) { g->exec[k] = nullptr; return cuda_fail(ctx, e, "graph instantiate"); }
+          g->launches[k] = nk;
+        }
+        CK(cudaGraphLaunch(g->exec[k], g->st[k]), "graph launch");
+      }
+      CK(cudaEventRecord(g->done[k], g->st[k]), "event record");
+    }
+    CK(cudaGetLastError(), "batch launch");
+    for (int k = 0; k < ns; ++k) CK(cudaStreamSynchronize(g->st[k]), "batch sync");
+    if (prof) {
+      prof_collect(prof, nev);
+      for (int z = 0; z < cnt; ++z) {
+        Work *w = g->w[z];
+        std::vector<int32_t> rc(P.blocks.size()), rl(P.blocks.size()), kp(std::max<size_t>(P.lrt.size(), 1));
+        double jf = 0.0;
+        CK(cudaMemcpy(rc.data(), w->H.rank_c, sizeof(int32_t) * rc.size(), cudaMemcpyDeviceToHost), "ranks");
+        CK(cudaMemcpy(rl.data(), w->F.rank_l, sizeof(int32_t) * rl.size(), cudaMemcpyDeviceToHost), "ranks");
+        CK(cudaMemcpy(kp.data(), w->F.kept, sizeof(int32_t) * kp.size(), cudaMemcpyDeviceToHost), "kept");
+        CK(cudaMemcpy(&jf, w->d_jacobi, sizeof(double), cudaMemcpyDeviceToHost), "jacobi");
+        prof->flops += tally_flops(P, prof->kind, rc, rl, kp, t->opts.oversample, jf);
+      }
+    }
+    // results; the mixed forms then solve for every evaluation of the wave
+    // at once (one PCG in lockstep), or, without cooperative launches, run
+    // their PCG solves interleaved on their own streams
+    std::vector<PcgRun> runs(cnt);
+    std::vector<int> live;
+    const bool lockstep = is_mixed(t->opts.precision) && t->coop;
+    for (int z = 0; z < cnt; ++z) {
+      Work *w = g->w[z];
+      w->F.launches = g->launches[z / g->sub] + kAssemblyLaunches + 1;
+      hmle_ctx wc;
+      wc.st = g->st[z / g->sub];
+      if (fs[z] == HMLE_OK) fs[z] = finish_factor(&wc, t, &w->H, &w->F);
+      if (fs[z] != HMLE_OK && errs[z].empty()) errs[z] = wc.err;
+    }
+    if (lockstep) {
+      PcgRun R;
+      hmle_ctx gc = view(0);
+      hmle_status sp = mixed_prepare(&gc, t, &g->w[0]->H, &g->w[0]->F, zd, R);
+      if (sp == HMLE_OK) {
+        for (int z = 1; z < nz; ++z) launch_permute_in(g->st[0], zd, t->T.perm, t->n, g->w[z]->F.pcg);
+        R.nz = nz;
+        R.zs = g->stride / (int64_t)sizeof(double);
+        R.Fs.nz = nz;
+        R.Fs.zstride = g->stride;
+        R.A.zstride = g->stride;
+        R.bar = g->bar;
+        R.host = g->host;
+        R.hostz = g->host + 4;
+        R.g_init = R.g_iter = nullptr;
+        cudaError_t e = cudaMemsetAsync(g->bar, 0, 3 * sizeof(unsigned), g->st[0]);
+        if (e == cudaSuccess) e = pcg_batch_start(R);
+        bool fin = false;
+        while (e == cudaSuccess && !fin) {
+          e = cudaStreamSynchronize(g->st[0]);
+          if (e == cudaSuccess) e = pcg_batch_poll(R, &fin);
+        }
+        if (e != cudaSuccess) sp = cuda_fail(&gc, e, "pcg");
+      }
+      for (int z = 0; z < cnt; ++z) {
+        if (fs[z] != HMLE_OK) continue;
+        hmle_hfactor &F = g->w[z]->F;
+        if (sp != HMLE_OK) { fs[z] = sp; errs[z] = gc.err; continue; }
+        if (R.timed_out) {
+          fs[z] = HMLE_ERR_TIMEOUT;
+          errs[z] = "PCG: a barrier wait of the persistent sweep ran out";
+          continue;
+        }
+        F.quad = R.qz[z];
+        F.pcg_iters = R.itz[z];
+        F.pcg_relres = R.relz[z];
+        F.has_rhs = true;
+        if (!(F.pcg_relres <= t->opts.pcg_tol) || !std::isfinite(F.quad)) {
+          fs[z] = HMLE_ERR_NOT_CONVERGED;
+          errs[z] = "PCG: relative residual above pcg_tol after pcg_max_iter";
+        }
+      }
+    }
+    for (int z = 0; z < cnt && !lockstep; ++z) {
+      Work *w = g->w[z];
+      hmle_ctx wc;
+      if (fs[z] == HMLE_OK && is_mixed(t->opts.precision)) {
+        wc.st = w->st;
+        cudaStreamWaitEvent(w->st, g->done[z / g->sub], 0);
+        fs[z] = mixed_prepare(&wc, t, &w->H, &w->F, zd, runs[z]);
+        if (fs[z] == HMLE_OK) {
+          cudaError_t e = pcg_start(runs[z]);
+          if (e != cudaSuccess) fs[z] = cuda_fail(&wc, e, "pcg");
+          else live.push_back(z);
+        }
+      }
+      if (fs[z] != HMLE_OK && errs[z].empty()) errs[z] = wc.err;
+    }
+    while (!live.empty()) {
+      std::vector<int> next;
+      for (int z : live) {
+        bool fin = false;
+        hmle_ctx wc;
+        cudaError_t e = cudaStreamSynchronize(runs[z].st);
+        if (e == cudaSuccess) e = pcg_poll(runs[z], &fin);
+        if (e != cudaSuccess) {
+          fs[z] = cuda_fail(&wc, e, "pcg");
+          errs[z] = wc.err;
+        } else if (fin) {
+          fs[z] = mixed_result(&wc, t, &g->w[z]->F, runs[z]);
+          if (fs[z] != HMLE_OK) errs[z] = wc.err;
+        } else {
+          next.push_back(z);
+        }
+      }
+      live.swap(next);
+    }
+    for (int z = 0; z < cnt; ++z) {
+      const int i = i0 + z;
+      const hmle_hfactor &F = g->w[z]->F;
+      const hmle_status s = fs[z];
+      const double nn = (double)t->n;
+      ll[i] = (s == HMLE_OK) ? -0.5 * nn * std::log(2.0 * M_PI) - 0.5 * F.logdet - 0.5 * F.quad : -INFINITY;
+      if (ld_out) ld_out[i] = (s == HMLE_OK) ? F.logdet : NAN;
+      if (q_out) q_out[i] = (s == HMLE_OK) ? F.quad : NAN;
+      if (status) status[i] = s;
+      if (s != HMLE_OK && s != HMLE_ERR_NOT_SPD && s != HMLE_ERR_RANK_OVERFLOW && first == HMLE_OK) {
+        first = s;
+        ctx->err = errs[z];
+      }
+    }
+  }
+  return first;
+}
+
 // One evaluation request of a batch: tree, theta, and Z already on the device.
 struct TaskRef {
   hmle_tree *t;
@@ -1258,14 +1605,11 @@ hmle_status run_waves(hmle_ctx *ctx, const std::vector<TaskRef> &tasks, int W, c
 hmle_status batch_eval(hmle_ctx *ctx, hmle_tree *t, const hmle_theta *thetas, int m,
                        const double *zd, int W, double *ll, int32_t *status, double *ld,
                        double *q) {
-  hmle_status s0 = ensure_pool(ctx, t, std::min(W, std::max(m, 1)));
-  if (s0 != HMLE_OK) return s0;
   cudaEvent_t zready;
   CK(cudaEventCreateWithFlags(&zready, cudaEventDisableTiming), "event");
   CK(cudaEventRecord(zready, ctx->st), "event record");
-  std::vector<TaskRef> tasks(m);
-  for (int i = 0; i < m; ++i) tasks[i] = {t, &thetas[i], zd};
-  hmle_status first = run_waves(ctx, tasks, std::min(W, std::max(m, 1)), zready, ll, status, ld, q);
+  hmle_status first = run_group(ctx, t, thetas, m, zd, std::min(W, std::max(m, 1)), t->opts.batch_size, zready,
+                                ll, status, ld, q);
   cudaEventDestroy(zready);
   return first;
 }
@@ -1283,19 +1627,15 @@ hmle_status hmle_loglik_batch(hmle_ctx *ctx, const hmle_tree *tc, const hmle_the
   if (m == 0) return HMLE_OK;
   hmle_tree *t = const_cast<hmle_tree *>(tc);
   const int W = std::min<int>(concurrency, std::max(m, 1));
-  hmle_status s0 = ensure_pool(ctx, t, W);
-  if (s0 != HMLE_OK) return s0;
   // stage Z once (shared by every evaluation, read-only)
   double *zd = nullptr;
   bool owned = false;
-  s0 = stage_vec(ctx, Z, t->n, &zd, &owned);
+  hmle_status s0 = stage_vec(ctx, Z, t->n, &zd, &owned);
   if (s0 != HMLE_OK) return s0;
   cudaEvent_t zready;
   CK(cudaEventCreateWithFlags(&zready, cudaEventDisableTiming), "event");
   CK(cudaEventRecord(zready, ctx->st), "event record");
-  std::vector<TaskRef> tasks(m);
-  for (int i = 0; i < m; ++i) tasks[i] = {t, &thetas[i], zd};
-  hmle_status first = run_waves(ctx, tasks, W, zready, ll, status);
+  hmle_status first = run_group(ctx, t, thetas, m, zd, W, t->opts.batch_size, zready, ll, status, nullptr, nullptr);
   cudaEventDestroy(zready);
   if (owned) cudaFreeAsync(zd, ctx->st);
   cudaStreamSynchronize(ctx->st);

@@ -258,7 +258,8 @@ struct Acc {
 // --- P1 -------------------------------------------------------------------
 // One CTA per row chunk of a gram G = W_A[ov]^T W_B[ov] (ranks x ranks).
 template <class Tc>
-__global__ void __launch_bounds__(kThreads) k_gram(FactorArgs F, int c0) {
+__global__ void __launch_bounds__(kThreads) k_gram(FactorArgs Fz, int c0) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
   Acc a(F);
   const GramChunk ch = F.gchunks[c0 + blockIdx.x];
@@ -277,7 +278,8 @@ __global__ void __launch_bounds__(kThreads) k_gram(FactorArgs F, int c0) {
 }
 
 // Sum of the chunks of a gram, in chunk order.
-__global__ void __launch_bounds__(kThreads) k_gram_reduce(FactorArgs F, int r0) {
+__global__ void __launch_bounds__(kThreads) k_gram_reduce(FactorArgs Fz, int r0) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   const GramReduce R = F.greds[r0 + blockIdx.x];
   const GramTask g = F.grams[R.g];
   const int kc = F.kcap, ka = F.rank_l[g.a], kb = F.rank_l[g.b];
@@ -293,7 +295,8 @@ __global__ void __launch_bounds__(kThreads) k_gram_reduce(FactorArgs F, int r0) 
 // trans = 0: B-entries against Omega (rows in sigma), t_C = V_C^T Omega.
 // trans = 1: A-entries against Q (rows in rho), t_C = U_C^T Q.
 template <class Tc>
-__global__ void __launch_bounds__(kThreads) k_side_t(FactorArgs F, int e0, int ne, int t0, int trans) {
+__global__ void __launch_bounds__(kThreads) k_side_t(FactorArgs Fz, int e0, int ne, int t0, int trans) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
   Acc a(F);
   if ((int)blockIdx.x < ne) {
@@ -361,7 +364,8 @@ constexpr int kSidePairs = 256;
 enum { kLG = 0, kLGt = 1, kLWik = 2, kLWki = 3, kLI = 4 };
 
 template <class Tc>
-__global__ void __launch_bounds__(kThreads) k_side_s(FactorArgs F, int e0, int trans) {
+__global__ void __launch_bounds__(kThreads) k_side_s(FactorArgs Fz, int e0, int trans) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
   __shared__ int kb[kSidePairs + 1];
   __shared__ int pcase[kSidePairs], pnr[kSidePairs], pky[kSidePairs], pwld[kSidePairs];
@@ -464,13 +468,17 @@ __global__ void __launch_bounds__(kThreads) k_side_s(FactorArgs F, int e0, int t
 
 // --- P2c / P4c: rows of Y (or Z) of one leaf --------------------------------
 template <class Tc>
-__global__ void __launch_bounds__(kThreads) k_rows(FactorArgs F, int rt0, int trans) {
+__global__ void __launch_bounds__(kThreads) k_rows(FactorArgs Fz, int rt0, int trans) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
+  // per segment q of the concatenated K (q = 0: U_C, q >= 1: the entries):
+  // the first column's left factor on the leaf's first row, its column
+  // stride, the right factor's first row and its column stride
   __shared__ int kbeg[kMaxEntries + 2];
-  __shared__ int eblk[kMaxEntries + 2];
-  __shared__ int64_t esoff[kMaxEntries + 2];
-  __shared__ int ekx[kMaxEntries + 2];
-  __shared__ short kmap[kMaxRowK];          // column k of the concatenation -> entry
+  __shared__ const double *ap[kMaxEntries + 2];
+  __shared__ const double *bp[kMaxEntries + 2];
+  __shared__ int ald[kMaxEntries + 2], bld[kMaxEntries + 2];
+  __shared__ short kmap[kMaxRowK];          // column k of the concatenation -> segment
   Acc a(F);
   const int kc = F.kc;
   const RowTask R = trans ? F.brow[rt0 + blockIdx.x] : F.arow[rt0 + blockIdx.x];
@@ -481,23 +489,38 @@ __global__ void __launch_bounds__(kThreads) k_rows(FactorArgs F, int rt0, int tr
   const int base = trans ? T.cbeg : T.rbeg;
   const int ld = trans ? L.p : L.m;
   double *Y = F.ws + (trans ? L.zoff : L.yoff);
-  const double *UC = F.uc + (trans ? T.off_vc : T.off_uc);
-  const double *tc = F.ws + L.tcoff;
   const int mi = I1 - I0;
   const int32_t *ents = trans ? F.brow_ent : F.arow_ent;
   const int ne = R.e1 - R.e0;
   // K = [rank_c | k_e1 | k_e2 | ...]: Y[I] = [U_C[I], -U_e1[I], ...] [t_C; s_e1; ...]
+  for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+    const SideEntry E = trans ? F.bent[ents[R.e0 + q]] : F.aent[ents[R.e0 + q]];
+    const BlockDesc X = F.blocks[E.blk];
+    if (X.kind == kLowRank) {
+      ap[q + 1] = F.U + X.off_u + (I0 - X.rbeg);
+      ald[q + 1] = X.rend - X.rbeg;
+    } else {
+      ap[q + 1] = F.D + X.off_d + (I0 - X.rbeg);
+      ald[q + 1] = F.b;
+    }
+    bp[q + 1] = F.ws + E.soff;
+    bld[q + 1] = a.kof(X);
+    kbeg[q + 1] = a.keff(E.blk, X);   // segment lengths first, prefix sums below
+  }
+  if (threadIdx.x == 0) {
+    ap[0] = F.uc + (trans ? T.off_vc : T.off_uc) + (I0 - base);
+    ald[0] = ld;
+    bp[0] = F.ws + L.tcoff;
+    bld[0] = kc;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int k = F.rank_c[L.blk];
     kbeg[0] = 0;
-    for (int q = 0; q < ne; ++q) {
-      const SideEntry E = trans ? F.bent[ents[R.e0 + q]] : F.aent[ents[R.e0 + q]];
-      const BlockDesc X = F.blocks[E.blk];
-      kbeg[q + 1] = k;
-      eblk[q] = E.blk;
-      esoff[q] = E.soff;
-      ekx[q] = a.kof(X);
-      k += a.keff(E.blk, X);
+    for (int q = 1; q <= ne; ++q) {
+      const int len = kbeg[q];
+      kbeg[q] = k;
+      k += len;
     }
     kbeg[ne + 1] = k;
   }
@@ -507,19 +530,16 @@ __global__ void __launch_bounds__(kThreads) k_rows(FactorArgs F, int rt0, int tr
   for (int q = 0; q <= ne; ++q)
     for (int k = kbeg[q] + threadIdx.x; k < min(kbeg[q + 1], K); k += blockDim.x) kmap[k] = (short)q;
   __syncthreads();
-  auto seg = [&](int k) { return (int)kmap[k]; };   // entry index of column k (0 = U_C)
   cta_gemm<false, true, Tc>(
       mi, r, K,
       [&](int i, int k) {
-        int q = seg(k);
-        if (q == 0) return UC[(I0 - base + i) + (int64_t)k * ld];
-        const BlockDesc X = F.blocks[eblk[q - 1]];
-        return -a.U(X, I0 + i, k - kbeg[q]);
+        const int q = kmap[k];
+        const double v = ap[q][i + (int64_t)(k - kbeg[q]) * ald[q]];
+        return q == 0 ? v : -v;
       },
       [&](int k, int j) {
-        int q = seg(k);
-        if (q == 0) return tc[k + (int64_t)j * kc];
-        return F.ws[esoff[q - 1] + (k - kbeg[q]) + (int64_t)j * ekx[q - 1]];
+        const int q = kmap[k];
+        return bp[q][(k - kbeg[q]) + (int64_t)j * bld[q]];
       },
       [&](int i, int j, double v) { Y[(I0 - base + i) + (int64_t)j * ld] = v; }, smem, F.flags);
 }
@@ -572,7 +592,8 @@ __device__ void smem_householder(double *A, int h, int r, double *red) {
 // R factor of one row group of a target's Y (which = 0) or Z (which = 1):
 // rows are streamed 64 at a time below the running R, each block
 // re-triangularised by Householder reflections.
-__global__ void __launch_bounds__(kThreads) k_tsqr_part(FactorArgs F, int t0, int which) {
+__global__ void __launch_bounds__(kThreads) k_tsqr_part(FactorArgs Fz, int t0, int which) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
   __shared__ double red[32];
   const LrTarget L = F.lrt[t0 + blockIdx.x];
@@ -715,7 +736,8 @@ __device__ int smem_pivoted_qr(double *B, int lb, int r, int *piv, double *cn, P
 // sum_{i>=k} sigma_i^2 is <= eps^2 max(sum sigma_i^2, |C_T|_F^2), or the
 // leading fixed_k directions in the fixed-rank mode; M = V_k (r x kcap),
 // k to rank_l.
-__global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, int which, int mode) {
+__global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs Fz, int t0, int which, int mode) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
   __shared__ double red[32];
   __shared__ int s_rot;
@@ -935,7 +957,8 @@ __global__ void __launch_bounds__(kThreads) k_tsqr_final(FactorArgs F, int t0, i
 
 // Re-orthonormalisation of Q1 = Y P R_p11^{-1} (nearly orthonormal kept
 // columns): partial Grams Q1_g^T Q1_g of the row groups ...
-__global__ void __launch_bounds__(kThreads) k_cholqr_part(FactorArgs F, int t0) {
+__global__ void __launch_bounds__(kThreads) k_cholqr_part(FactorArgs Fz, int t0) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
   const LrTarget L = F.lrt[t0 + blockIdx.x];
   const int G = L.gm, g = blockIdx.y;
@@ -954,7 +977,8 @@ __global__ void __launch_bounds__(kThreads) k_cholqr_part(FactorArgs F, int t0) 
 
 // ... then G = sum_g, G = R^T R (Cholesky), M = R^{-1} (k1 x k1, zero
 // elsewhere) so that Q = Q1 M.
-__global__ void __launch_bounds__(kThreads) k_cholqr_final(FactorArgs F, int t0) {
+__global__ void __launch_bounds__(kThreads) k_cholqr_final(FactorArgs Fz, int t0) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
   __shared__ double s_inv;
   const LrTarget L = F.lrt[t0 + blockIdx.x];
@@ -1008,7 +1032,8 @@ __global__ void __launch_bounds__(kThreads) k_cholqr_final(FactorArgs F, int t0)
 // mode 0: Y <- Y M in place (r columns) for row chunk blockIdx.y.
 // mode 1: U_T = Q V_k (rows of rho) and W_T = Z V_k (rows of sigma); the
 //         chunk index runs over rho's chunks, then sigma's.
-__global__ void __launch_bounds__(kThreads) k_tall_apply(FactorArgs F, int t0, int mode) {
+__global__ void __launch_bounds__(kThreads) k_tall_apply(FactorArgs Fz, int t0, int mode) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
   Acc a(F);
   const LrTarget L = F.lrt[t0 + blockIdx.x];
@@ -1053,7 +1078,8 @@ __global__ void __launch_bounds__(kThreads) k_tall_apply(FactorArgs F, int t0, i
 // P = U_A G_AB U_B^T restricted to the target (m x p, ld b) into the step's
 // workspace; k_dense_reduce: S = C_IK - sum of the target's P in pair order.
 template <class Tc>
-__global__ void __launch_bounds__(kThreads) k_dense_pair(FactorArgs F, int q0, int64_t dpws) {
+__global__ void __launch_bounds__(kThreads) k_dense_pair(FactorArgs Fz, int q0, int64_t dpws) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
   Acc a(F);
   const int b = F.b, kc = F.kcap;
@@ -1105,7 +1131,8 @@ __global__ void __launch_bounds__(kThreads) k_dense_pair(FactorArgs F, int q0, i
       [&](int k, int j) { return X[k + j * ldx]; }, put, smem, F.flags);
 }
 
-__global__ void __launch_bounds__(kThreads) k_dense_reduce(FactorArgs F, int d0, int64_t dpws) {
+__global__ void __launch_bounds__(kThreads) k_dense_reduce(FactorArgs Fz, int d0, int64_t dpws) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   const int b = F.b;
   const DenseTarget DT = F.dns[d0 + blockIdx.x];
   const BlockDesc T = F.blocks[DT.blk];
@@ -1125,7 +1152,8 @@ __global__ void __launch_bounds__(kThreads) k_dense_reduce(FactorArgs F, int d0,
 }
 
 // --- P7: Cholesky of the diagonal leaf ------------------------------------
-__global__ void __launch_bounds__(kThreads) k_potrf(FactorArgs F, int d0, int K) {
+__global__ void __launch_bounds__(kThreads) k_potrf(FactorArgs Fz, int d0, int K) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
   const int b = F.b;
   const DenseTarget DT = F.dns[d0];
@@ -1172,7 +1200,8 @@ __global__ void __launch_bounds__(kThreads) k_potrf(FactorArgs F, int d0, int K)
 }
 
 // --- P8: off-diagonal dense blocks of column K: X = S L^{-T} ---------------
-__global__ void __launch_bounds__(kThreads) k_trsm(FactorArgs F, int d0, int K) {
+__global__ void __launch_bounds__(kThreads) k_trsm(FactorArgs Fz, int d0, int K) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
   const int b = F.b;
   const BlockDesc Dg = F.blocks[F.dns[d0].blk];
@@ -1196,7 +1225,8 @@ __global__ void __launch_bounds__(kThreads) k_trsm(FactorArgs F, int d0, int K) 
 }
 
 // --- P9: W <- L_KK^{-1} W on the rows of leaf K of each open panel --------
-__global__ void __launch_bounds__(kThreads) k_wsolve(FactorArgs F, int w0, int d0) {
+__global__ void __launch_bounds__(kThreads) k_wsolve(FactorArgs Fz, int w0, int d0) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
   Acc a(F);
   const int b = F.b;
@@ -1225,7 +1255,8 @@ __global__ void __launch_bounds__(kThreads) k_wsolve(FactorArgs F, int w0, int d
 
 // --- P10a: H = W_A^T W_panel[cols A] -----------------------------------------
 template <class Tc>
-__global__ void __launch_bounds__(kThreads) k_htask(FactorArgs F, int h0) {
+__global__ void __launch_bounds__(kThreads) k_htask(FactorArgs Fz, int h0) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
   Acc a(F);
   const HTask H = F.hts[h0 + blockIdx.x];
@@ -1250,7 +1281,8 @@ __global__ void __launch_bounds__(kThreads) k_htask(FactorArgs F, int h0) {
 
 // --- P10b: W_panel[I] -= sum of the leaf row's updates ----------------------
 template <class Tc>
-__global__ void __launch_bounds__(kThreads) k_updrow(FactorArgs F, int u0) {
+__global__ void __launch_bounds__(kThreads) k_updrow(FactorArgs Fz, int u0) {
+  const FactorArgs F = Fz.at(blockIdx.z);   // evaluation blockIdx.z of the batch
   extern __shared__ double smem[];
   Acc a(F);
   const UpdRow R = F.urows[u0 + blockIdx.x];
@@ -1392,8 +1424,8 @@ int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaE
   const int smd = (gemm_words<Td>() + std::max(F.b, F.kcap) * F.b) * (int)sizeof(double);
   const int stn = kTnSmem * (int)sizeof(double);    // a small-output product and nothing else
   const int r = F.r;
-  if (S.gch1 > S.gch0) { LAUNCH(KK_GRAM, st, k_gram<Td><<<S.gch1 - S.gch0, kThreads, tc_smem<Td>(smt), st>>>(F, S.gch0)); }
-  if (S.gred1 > S.gred0) { LAUNCH(KK_GRAM, st, k_gram_reduce<<<S.gred1 - S.gred0, kThreads, 0, st>>>(F, S.gred0)); }
+  if (S.gch1 > S.gch0) { LAUNCH(KK_GRAM, st, k_gram<Td><<<dim3(S.gch1 - S.gch0, 1, F.nz), kThreads, tc_smem<Td>(smt), st>>>(F, S.gch0)); }
+  if (S.gred1 > S.gred0) { LAUNCH(KK_GRAM, st, k_gram_reduce<<<dim3(S.gred1 - S.gred0, 1, F.nz), kThreads, 0, st>>>(F, S.gred0)); }
   // the dense blocks of column K (P6-P8) only need the grams: fork them to
   // the side stream while the low-rank targets are compressed
   cudaStream_t sd = side ? side : st;
@@ -1403,10 +1435,10 @@ int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaE
   }
   const int nd = S.dns1 - S.dns0;
   const int q0 = PL.dns[S.dns0].p0, q1 = PL.dns[S.dns1 - 1].p1;
-  if (q1 > q0) { LAUNCH(KK_DENSE_PAIR, sd, k_dense_pair<Td><<<q1 - q0, kThreads, smd, sd>>>(F, q0, S.dpws)); }
-  LAUNCH(KK_DENSE_REDUCE, sd, k_dense_reduce<<<nd, kThreads, 0, sd>>>(F, S.dns0, S.dpws));
-  LAUNCH(KK_POTRF, sd, k_potrf<<<1, kThreads, sm, sd>>>(F, S.dns0, K));
-  if (nd > 1) { LAUNCH(KK_TRSM, sd, k_trsm<<<nd - 1, kThreads, sm, sd>>>(F, S.dns0, K)); }
+  if (q1 > q0) { LAUNCH(KK_DENSE_PAIR, sd, k_dense_pair<Td><<<dim3(q1 - q0, 1, F.nz), kThreads, smd, sd>>>(F, q0, S.dpws)); }
+  LAUNCH(KK_DENSE_REDUCE, sd, k_dense_reduce<<<dim3(nd, 1, F.nz), kThreads, 0, sd>>>(F, S.dns0, S.dpws));
+  LAUNCH(KK_POTRF, sd, k_potrf<<<dim3(1, 1, F.nz), kThreads, sm, sd>>>(F, S.dns0, K));
+  if (nd > 1) { LAUNCH(KK_TRSM, sd, k_trsm<<<dim3(nd - 1, 1, F.nz), kThreads, sm, sd>>>(F, S.dns0, K)); }
   const int nt = S.lrt1 - S.lrt0;
   if (nt > 0) {
     int maxch = 0, maxgm = 1, maxgp = 1;
@@ -1421,23 +1453,23 @@ int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaE
     const int qrf_smem = ((r + kQrRows) * r + 2 * (r | 1) * r) * (int)sizeof(double);
     const int cq_smem = 2 * r * r * (int)sizeof(double);
     // Y = S Omega
-    LAUNCH(KK_SIDE_T, st, k_side_t<Tl><<<(S.bent1 - S.bent0) + nt, kThreads, tc_smem<Tl>(smt), st>>>(F, S.bent0, S.bent1 - S.bent0, S.lrt0, 0));
-    if (S.aent1 > S.aent0) LAUNCH(KK_SIDE_S, st, k_side_s<Tl><<<S.aent1 - S.aent0, kThreads, tc_smem<Tl>(stn), st>>>(F, S.aent0, 0));
-    LAUNCH(KK_ROWS, st, k_rows<Tl><<<S.arow1 - S.arow0, kThreads, tc_smem<Tl>(sm), st>>>(F, S.arow0, 0));
+    LAUNCH(KK_SIDE_T, st, k_side_t<Tl><<<dim3((S.bent1 - S.bent0) + nt, 1, F.nz), kThreads, tc_smem<Tl>(smt), st>>>(F, S.bent0, S.bent1 - S.bent0, S.lrt0, 0));
+    if (S.aent1 > S.aent0) LAUNCH(KK_SIDE_S, st, k_side_s<Tl><<<dim3(S.aent1 - S.aent0, 1, F.nz), kThreads, tc_smem<Tl>(stn), st>>>(F, S.aent0, 0));
+    LAUNCH(KK_ROWS, st, k_rows<Tl><<<dim3(S.arow1 - S.arow0, 1, F.nz), kThreads, tc_smem<Tl>(sm), st>>>(F, S.arow0, 0));
     // Q = orth(Y): R of Y, pivoted QR, Q1 = Y P R_p11^{-1}, then CholQR
-    LAUNCH(KK_TSQR_PART, st, k_tsqr_part<<<dim3(nt, maxgm), kThreads, qr_smem, st>>>(F, S.lrt0, 0));
-    LAUNCH(KK_TSQR_FINAL, st, k_tsqr_final<<<nt, kThreads, qrf_smem, st>>>(F, S.lrt0, 0, 0));
-    LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch), kThreads, sm, st>>>(F, S.lrt0, 0));
-    LAUNCH(KK_CHOLQR_PART, st, k_cholqr_part<<<dim3(nt, maxgm), kThreads, kTnSmem * (int)sizeof(double), st>>>(F, S.lrt0));
-    LAUNCH(KK_CHOLQR_FINAL, st, k_cholqr_final<<<nt, kThreads, cq_smem, st>>>(F, S.lrt0));
-    LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch), kThreads, sm, st>>>(F, S.lrt0, 0));
+    LAUNCH(KK_TSQR_PART, st, k_tsqr_part<<<dim3(nt, maxgm, F.nz), kThreads, qr_smem, st>>>(F, S.lrt0, 0));
+    LAUNCH(KK_TSQR_FINAL, st, k_tsqr_final<<<dim3(nt, 1, F.nz), kThreads, qrf_smem, st>>>(F, S.lrt0, 0, 0));
+    LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch, F.nz), kThreads, sm, st>>>(F, S.lrt0, 0));
+    LAUNCH(KK_CHOLQR_PART, st, k_cholqr_part<<<dim3(nt, maxgm, F.nz), kThreads, kTnSmem * (int)sizeof(double), st>>>(F, S.lrt0));
+    LAUNCH(KK_CHOLQR_FINAL, st, k_cholqr_final<<<dim3(nt, 1, F.nz), kThreads, cq_smem, st>>>(F, S.lrt0));
+    LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch, F.nz), kThreads, sm, st>>>(F, S.lrt0, 0));
     // Z = S^T Q
-    LAUNCH(KK_SIDE_T, st, k_side_t<Tl><<<(S.aent1 - S.aent0) + nt, kThreads, tc_smem<Tl>(smt), st>>>(F, S.aent0, S.aent1 - S.aent0, S.lrt0, 1));
-    if (S.bent1 > S.bent0) LAUNCH(KK_SIDE_S, st, k_side_s<Tl><<<S.bent1 - S.bent0, kThreads, tc_smem<Tl>(stn), st>>>(F, S.bent0, 1));
-    LAUNCH(KK_ROWS, st, k_rows<Tl><<<S.brow1 - S.brow0, kThreads, tc_smem<Tl>(sm), st>>>(F, S.brow0, 1));
-    LAUNCH(KK_TSQR_PART, st, k_tsqr_part<<<dim3(nt, maxgp), kThreads, qr_smem, st>>>(F, S.lrt0, 1));
-    LAUNCH(KK_TSQR_FINAL, st, k_tsqr_final<<<nt, kThreads, qrf_smem, st>>>(F, S.lrt0, 1, 1));
-    LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch), kThreads, sm, st>>>(F, S.lrt0, 1));
+    LAUNCH(KK_SIDE_T, st, k_side_t<Tl><<<dim3((S.aent1 - S.aent0) + nt, 1, F.nz), kThreads, tc_smem<Tl>(smt), st>>>(F, S.aent0, S.aent1 - S.aent0, S.lrt0, 1));
+    if (S.bent1 > S.bent0) LAUNCH(KK_SIDE_S, st, k_side_s<Tl><<<dim3(S.bent1 - S.bent0, 1, F.nz), kThreads, tc_smem<Tl>(stn), st>>>(F, S.bent0, 1));
+    LAUNCH(KK_ROWS, st, k_rows<Tl><<<dim3(S.brow1 - S.brow0, 1, F.nz), kThreads, tc_smem<Tl>(sm), st>>>(F, S.brow0, 1));
+    LAUNCH(KK_TSQR_PART, st, k_tsqr_part<<<dim3(nt, maxgp, F.nz), kThreads, qr_smem, st>>>(F, S.lrt0, 1));
+    LAUNCH(KK_TSQR_FINAL, st, k_tsqr_final<<<dim3(nt, 1, F.nz), kThreads, qrf_smem, st>>>(F, S.lrt0, 1, 1));
+    LAUNCH(KK_TALL_APPLY, st, k_tall_apply<<<dim3(nt, maxch, F.nz), kThreads, sm, st>>>(F, S.lrt0, 1));
   }
   if (side) {
     cudaEventRecord(ev_join, side);
@@ -1446,16 +1478,16 @@ int launch_step_t(cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaE
   if (S.wpan1 > S.wpan0) {
     int maxw = 0;
     for (int q = S.wpan0; q < S.wpan1; ++q) maxw = std::max(maxw, PL.panels[PL.wpan[q]].width);
-    LAUNCH(KK_WSOLVE, st, k_wsolve<<<dim3(S.wpan1 - S.wpan0, (maxw + kThreads - 1) / kThreads), kThreads, sm, st>>>(
+    LAUNCH(KK_WSOLVE, st, k_wsolve<<<dim3(S.wpan1 - S.wpan0, (maxw + kThreads - 1) / kThreads, F.nz), kThreads, sm, st>>>(
         F, S.wpan0, S.dns0));
   }
   if (S.ht1 > S.ht0) {
     int maxw = 1;
     for (int q = S.ht0; q < S.ht1; ++q) maxw = std::max(maxw, PL.panels[PL.hts[q].panel].width);
     const int ny = (maxw + (kTnMaxMN - kMaxRank) - 1) / (kTnMaxMN - kMaxRank);
-    LAUNCH(KK_HTASK, st, k_htask<Tl><<<dim3(S.ht1 - S.ht0, ny), kThreads, tc_smem<Tl>(smt), st>>>(F, S.ht0));
+    LAUNCH(KK_HTASK, st, k_htask<Tl><<<dim3(S.ht1 - S.ht0, ny, F.nz), kThreads, tc_smem<Tl>(smt), st>>>(F, S.ht0));
   }
-  if (S.ur1 > S.ur0) { LAUNCH(KK_UPDROW, st, k_updrow<Tl><<<S.ur1 - S.ur0, kThreads, tc_smem<Tl>(sm), st>>>(F, S.ur0)); }
+  if (S.ur1 > S.ur0) { LAUNCH(KK_UPDROW, st, k_updrow<Tl><<<dim3(S.ur1 - S.ur0, 1, F.nz), kThreads, tc_smem<Tl>(sm), st>>>(F, S.ur0)); }
   return nk;
 }
 }  // namespace

@@ -31,6 +31,18 @@ struct AsmArgs {
   const ThetaDev *thd;     // the same theta in device memory (read by captured kernels)
   const double *Cd;        // dense near-field blocks (b x b at each dense block's off_d)
   int b;                   // leaf size (leading dimension of the Cd blocks)
+  // a batch: evaluation z's H-matrix buffers are evaluation 0's shifted by
+  // z * zstride bytes (the H-matrix operator of the batched PCG)
+  int64_t zstride;
+  __host__ __device__ AsmArgs at(int z) const {
+    AsmArgs G = *this;
+    if (z == 0) return G;
+    const int64_t o = (int64_t)z * zstride;
+    auto sh = [o](auto *p) { return p ? reinterpret_cast<decltype(p)>(const_cast<char *>(reinterpret_cast<const char *>(p)) + o) : p; };
+    G.tab = sh(tab); G.uc = sh(uc); G.rank_c = sh(rank_c); G.cnorm = sh(cnorm); G.flags = sh(flags);
+    G.thd = sh(thd); G.Cd = sh(Cd);
+    return G;
+  }
 };
 
 // Everything the sweep kernels read; device pointers.
@@ -79,7 +91,28 @@ struct FactorArgs {
   int b, kcap, kc, r;
   int osamp;               // oversampling of the randomised compression
   int fixed_k;             // > 0: fixed-rank mode (truncate at this rank, no overflow)
-  int mixed;               // 1: the Schur-update and panel-update products in FP32
+  int mixed;               // 0 FP64; 1, 2: the mixed forms (products on the tensor cores)
+  // A batch of nz evaluations of one tree (different theta): every buffer of
+  // evaluation z (the H-matrix of C, the factor, the workspace, the flags) is
+  // that of evaluation 0 shifted by z * zstride bytes, and a sweep kernel
+  // launched with gridDim.z = nz serves evaluation blockIdx.z.
+  int nz;
+  int64_t zstride;
+  __host__ __device__ FactorArgs at(int z) const {
+    FactorArgs G = *this;
+    if (z == 0) return G;
+    const int64_t o = (int64_t)z * zstride;
+    G.D = shift(D, o); G.uc = shift(uc, o); G.Cd = shift(Cd, o); G.rank_c = shift(rank_c, o);
+    G.cnorm = shift(cnorm, o); G.U = shift(U, o); G.W = shift(W, o); G.ws = shift(ws, o);
+    G.rank_l = shift(rank_l, o); G.kept = shift(kept, o); G.jacobi_flops = shift(jacobi_flops, o);
+    G.logdet_parts = shift(logdet_parts, o); G.flags = shift(flags, o); G.tab = shift(tab, o);
+    G.th = shift(th, o);
+    return G;
+  }
+  template <class P>
+  __host__ __device__ static P *shift(P *p, int64_t o) {
+    return p ? reinterpret_cast<P *>(const_cast<char *>(reinterpret_cast<const char *>(p)) + o) : p;
+  }
 };
 
 void launch_matern_table(cudaStream_t st, double nu, double *tab);
@@ -159,7 +192,7 @@ struct CmvLists {
 // y = C x in cluster order (FP64; dense entries generated from the table);
 // t: 2 kc doubles per admissible block.
 void launch_cmatvec(cudaStream_t st, const AsmArgs &A, int n_lr, const CmvLists &L,
-                    const double *x, double *t, double *y);
+                    const double *x, double *t, double *y, int nz = 1, int64_t zs = 0);
 // doubles of workspace pcg_quad needs
 int64_t pcg_words(int64_t n, int n_lr, int kc, int hmax);
 // q = b^T x with C x = b solved by PCG: operator launch_cmatvec, preconditioner
@@ -235,7 +268,18 @@ struct PcgRun {
   int it = 0, state = 0;
   double rel = 1.0, q = 0.0;
   bool timed_out = false;   // a barrier wait of the persistent sweeps ran out
+  // a batch of nz solves in lockstep (pcg_batch_*): evaluation z's vectors,
+  // pool, panel and factor are evaluation 0's shifted by z zs doubles; each
+  // stops updating its solution once it has converged (or reached maxit), as
+  // a single solve would stop, and the batch runs until all have
+  int nz = 1;
+  int64_t zs = 0;
+  double *hostz = nullptr;  // pinned: per evaluation 4 doubles (stopped, iterations, rel, q)
+  std::vector<int> itz;     // per evaluation results of a batch
+  std::vector<double> relz, qz;
 };
+cudaError_t pcg_batch_start(PcgRun &R);
+cudaError_t pcg_batch_poll(PcgRun &R, bool *finished);
 cudaError_t pcg_start(PcgRun &R);
 cudaError_t pcg_poll(PcgRun &R, bool *finished);
 cudaError_t pcg_quad(PcgRun &R);   // start, then synchronise and poll until finished

@@ -11,12 +11,17 @@
 //    non-empty bin above it, else below), then log n, d, log sqrt(S).
 //    h^2 is summed over dimensions in order with unfused multiplies and adds,
 //    so every bin decision is reproducible.
-//  * Perceptron 35 -> 64 (tanh) -> 64 (tanh) -> 8, FP32: outputs are the
-//    predicted transformed coordinates of Sec. 5 (mu_1..4) and log step
-//    scales (s_1..4).  Trained with the Gaussian negative log-likelihood
-//    sum_c [exp(-2 s_c) (t_c - mu_c)^2 / 2 + s_c] (batch mean) and Adam
-//    (beta1 0.9, beta2 0.999, eps 1e-8).  Parameters are one flat array:
-//    W1 (64 x 35, row-major), b1, W2 (64 x 64), b2, W3 (8 x 64), b3.
+//  * Perceptron 35 -> 256 (tanh) -> 256 (tanh) -> 256 (tanh) -> 8: outputs
+//    are the predicted transformed coordinates of Sec. 5 (mu_1..4) and log
+//    step scales (s_1..4).  Every matrix product -- the layers of the forward
+//    pass, the back-propagated deltas and the weight gradients -- runs on the
+//    tensor cores (tc_gemm.cuh, tcgen05.mma) with BF16 operands (the FP32
+//    weights and activations rounded to BF16 as they are staged) and FP32
+//    accumulation; biases, tanh, the loss and Adam are FP32.  Trained with the
+//    Gaussian negative log-likelihood sum_c [exp(-2 s_c) (t_c - mu_c)^2 / 2 +
+//    s_c] (batch mean) and Adam (beta1 0.9, beta2 0.999, eps 1e-8) on FP32
+//    master weights.  Parameters are one flat array: W1 (256 x 35,
+//    row-major), b1, W2 (256 x 256), b2, W3 (256 x 256), b3, W4 (8 x 256), b4.
 //
 // Every reduction runs in a fixed order: features, gradients and training
 // are deterministic.
@@ -32,15 +37,21 @@
 
 #include "../../include/hmle.h"
 #include "common.cuh"
+#include "tc_gemm.cuh"
 
 using hmle::block_sum;
 
 namespace {
 
 constexpr int kBins = 32;
-constexpr int kNF = 35, kNH = 64, kNO = 8;
-constexpr int kOffW1 = 0, kOffB1 = kNH * kNF, kOffW2 = kOffB1 + kNH, kOffB2 = kOffW2 + kNH * kNH,
-              kOffW3 = kOffB2 + kNH, kOffB3 = kOffW3 + kNO * kNH, kNParams = kOffB3 + kNO;
+constexpr int kNF = 35, kNH = 256, kNO = 8, kNL = 4;
+// layer l: kIn[l] -> kOut[l]; W_l at kOffW[l] (kOut x kIn, row-major), b_l after it
+constexpr int kIn[kNL] = {kNF, kNH, kNH, kNH}, kOut[kNL] = {kNH, kNH, kNH, kNO};
+constexpr int off_w(int l) { return l == 0 ? 0 : off_w(l - 1) + kIn[l - 1] * kOut[l - 1] + kOut[l - 1]; }
+constexpr int off_b(int l) { return off_w(l) + kIn[l] * kOut[l]; }
+constexpr int kNParams = off_b(kNL - 1) + kOut[kNL - 1];
+static_assert(kNParams == 142856, "35-256-256-256-8");
+constexpr int kTcBytes = hmle::tc::smem_words<1>() * (int)sizeof(double);
 constexpr int kVarioCtas = 304;
 constexpr int kVarioThreads = 128;
 constexpr int kSampleMax = 4096;
@@ -137,96 +148,89 @@ __global__ void k_vario_final(const double *__restrict__ part, int G, double *__
 }
 
 // --- perceptron -------------------------------------------------------------
-// X: B x 35 raw features; standardised with mu / sd on load.
-__global__ void k_mlp_fwd(const float *__restrict__ p, const float *__restrict__ mu,
-                          const float *__restrict__ sd, const float *__restrict__ X, int B,
-                          float *__restrict__ Xn, float *__restrict__ H1, float *__restrict__ H2,
-                          float *__restrict__ Y) {
-  __shared__ float x[kNF], h1[kNH], h2[kNH];
-  const int b = blockIdx.x, u = threadIdx.x;
-  if (b >= B) return;
-  if (u < kNF) {
-    x[u] = (X[(int64_t)b * kNF + u] - mu[u]) / sd[u];
-    Xn[(int64_t)b * kNF + u] = x[u];
-  }
-  __syncthreads();
-  float a = p[kOffB1 + u];
-  for (int k = 0; k < kNF; ++k) a = fmaf(p[kOffW1 + u * kNF + k], x[k], a);
-  h1[u] = tanhf(a);
-  H1[(int64_t)b * kNH + u] = h1[u];
-  __syncthreads();
-  a = p[kOffB2 + u];
-  for (int k = 0; k < kNH; ++k) a = fmaf(p[kOffW2 + u * kNH + k], h1[k], a);
-  h2[u] = tanhf(a);
-  H2[(int64_t)b * kNH + u] = h2[u];
-  __syncthreads();
-  if (u < kNO) {
-    a = p[kOffB3 + u];
-    for (int k = 0; k < kNH; ++k) a = fmaf(p[kOffW3 + u * kNH + k], h2[k], a);
-    Y[(int64_t)b * kNO + u] = a;
-  }
+// X: B x 35 raw features -> Xn, standardised with mu / sd
+__global__ void k_standardize(const float *__restrict__ X, const float *__restrict__ mu,
+                              const float *__restrict__ sd, int B, float *__restrict__ Xn) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < B * kNF) Xn[e] = (X[e] - mu[e % kNF]) / sd[e % kNF];
 }
 
-// deltas of one sample and its loss term; T: B x 4 targets
-__global__ void k_mlp_bwd(const float *__restrict__ p, const float *__restrict__ H1,
-                          const float *__restrict__ H2, const float *__restrict__ Y,
-                          const float *__restrict__ T, int B, float *__restrict__ D1,
-                          float *__restrict__ D2, float *__restrict__ D3,
-                          float *__restrict__ loss) {
-  __shared__ float d3[kNO], d2[kNH];
-  const int b = blockIdx.x, u = threadIdx.x;
-  if (b >= B) return;
-  if (u < 4) {
-    const float mu = Y[(int64_t)b * kNO + u], s = Y[(int64_t)b * kNO + 4 + u];
-    const float r = T[(int64_t)b * 4 + u] - mu, e = expf(-2.0f * s);
-    d3[u] = -e * r / B;
-    d3[4 + u] = (1.0f - e * r * r) / B;
-    D3[(int64_t)b * kNO + u] = d3[u];
-    D3[(int64_t)b * kNO + 4 + u] = d3[4 + u];
-  }
-  __syncthreads();
-  if (u == 0) {
-    float l = 0.0f;
-    for (int c = 0; c < 4; ++c) {
-      const float mu = Y[(int64_t)b * kNO + c], s = Y[(int64_t)b * kNO + 4 + c];
-      const float r = T[(int64_t)b * 4 + c] - mu;
-      l += 0.5f * expf(-2.0f * s) * r * r + s;
-    }
-    loss[b] = l;
-  }
-  float a = 0.0f;
-  for (int o = 0; o < kNO; ++o) a = fmaf(p[kOffW3 + o * kNH + u], d3[o], a);
-  const float h2 = H2[(int64_t)b * kNH + u];
-  d2[u] = a * (1.0f - h2 * h2);
-  D2[(int64_t)b * kNH + u] = d2[u];
-  __syncthreads();
-  a = 0.0f;
-  for (int j = 0; j < kNH; ++j) a = fmaf(p[kOffW2 + j * kNH + u], d2[j], a);
-  const float h1 = H1[(int64_t)b * kNH + u];
-  D1[(int64_t)b * kNH + u] = a * (1.0f - h1 * h1);
+// out = act(in W^T + b): in B x nin, W nout x nin (row-major), out B x nout.
+// CTA (x, y) computes rows 128 x .. + 127 and columns 64 y .. + 63 on the
+// tensor cores (BF16 operands, FP32 accumulation).
+template <bool TANH>
+__global__ void __launch_bounds__(128) k_layer_fwd(const float *__restrict__ in, int nin,
+                                                   const float *__restrict__ W, const float *__restrict__ b,
+                                                   int nout, int B, float *__restrict__ out, int *flags) {
+  extern __shared__ double smem[];
+  const int m0 = blockIdx.x * hmle::tc::kTM, n0 = blockIdx.y * hmle::tc::kTN;
+  hmle::tc::gemm<1, true, true>(
+      min(hmle::tc::kTM, B - m0), min(hmle::tc::kTN, nout - n0), nin,
+      [&](int i, int k) { return (double)in[(int64_t)(m0 + i) * nin + k]; },
+      [&](int k, int j) { return (double)W[(int64_t)(n0 + j) * nin + k]; },
+      [&](int i, int j, double v) {
+        const float a = (float)v + b[n0 + j];
+        out[(int64_t)(m0 + i) * nout + n0 + j] = TANH ? tanhf(a) : a;
+      },
+      smem, flags);
 }
 
-// one thread per parameter: sum over the batch in sample order
-__global__ void k_mlp_grad(const float *__restrict__ Xn, const float *__restrict__ H1,
-                           const float *__restrict__ H2, const float *__restrict__ D1,
-                           const float *__restrict__ D2, const float *__restrict__ D3, int B,
-                           float *__restrict__ g) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= kNParams) return;
-  const float *D, *In;
-  int nd, ni, row, col;   // col < 0: a bias
-  if (q < kOffB1) { D = D1; nd = kNH; In = Xn; ni = kNF; row = q / kNF; col = q % kNF; }
-  else if (q < kOffW2) { D = D1; nd = kNH; In = nullptr; ni = 0; row = q - kOffB1; col = -1; }
-  else if (q < kOffB2) { D = D2; nd = kNH; In = H1; ni = kNH; row = (q - kOffW2) / kNH; col = (q - kOffW2) % kNH; }
-  else if (q < kOffW3) { D = D2; nd = kNH; In = nullptr; ni = 0; row = q - kOffB2; col = -1; }
-  else if (q < kOffB3) { D = D3; nd = kNO; In = H2; ni = kNH; row = (q - kOffW3) / kNH; col = (q - kOffW3) % kNH; }
-  else { D = D3; nd = kNO; In = nullptr; ni = 0; row = q - kOffB3; col = -1; }
+// deltas of the output layer (B x 8) and the loss of each sample; T: B x 4
+__global__ void k_out_delta(const float *__restrict__ Y, const float *__restrict__ T, int B,
+                            float *__restrict__ D, float *__restrict__ loss) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  float l = 0.0f;
+  for (int c = 0; c < 4; ++c) {
+    const float mu = Y[(int64_t)b * kNO + c], s = Y[(int64_t)b * kNO + 4 + c];
+    const float r = T[(int64_t)b * 4 + c] - mu, e = expf(-2.0f * s);
+    D[(int64_t)b * kNO + c] = -e * r / B;
+    D[(int64_t)b * kNO + 4 + c] = (1.0f - e * r * r) / B;
+    l += 0.5f * e * r * r + s;
+  }
+  loss[b] = l;
+}
+
+// D = (Dn W) * (1 - H^2): Dn B x nn, W nn x nout (row-major), H, D B x nout
+__global__ void __launch_bounds__(128) k_layer_bwd(const float *__restrict__ Dn, int nn,
+                                                   const float *__restrict__ W, int nout,
+                                                   const float *__restrict__ H, int B,
+                                                   float *__restrict__ D, int *flags) {
+  extern __shared__ double smem[];
+  const int m0 = blockIdx.x * hmle::tc::kTM, n0 = blockIdx.y * hmle::tc::kTN;
+  hmle::tc::gemm<1, true, false>(
+      min(hmle::tc::kTM, B - m0), min(hmle::tc::kTN, nout - n0), nn,
+      [&](int i, int k) { return (double)Dn[(int64_t)(m0 + i) * nn + k]; },
+      [&](int k, int j) { return (double)W[(int64_t)k * nout + n0 + j]; },
+      [&](int i, int j, double v) {
+        const int64_t e = (int64_t)(m0 + i) * nout + n0 + j;
+        const float h = H[e];
+        D[e] = (float)v * (1.0f - h * h);
+      },
+      smem, flags);
+}
+
+// gW = D^T Hin: D B x nout, Hin B x nin, gW nout x nin (row-major); the sum
+// over the batch runs on the tensor cores
+__global__ void __launch_bounds__(128) k_layer_wgrad(const float *__restrict__ D, int nout,
+                                                     const float *__restrict__ Hin, int nin, int B,
+                                                     float *__restrict__ gW, int *flags) {
+  extern __shared__ double smem[];
+  const int m0 = blockIdx.x * hmle::tc::kTM, n0 = blockIdx.y * hmle::tc::kTN;
+  hmle::tc::gemm<1, false, false>(
+      min(hmle::tc::kTM, nout - m0), min(hmle::tc::kTN, nin - n0), B,
+      [&](int i, int k) { return (double)D[(int64_t)k * nout + m0 + i]; },
+      [&](int k, int j) { return (double)Hin[(int64_t)k * nin + n0 + j]; },
+      [&](int i, int j, double v) { gW[(int64_t)(m0 + i) * nin + n0 + j] = (float)v; }, smem, flags);
+}
+
+// gb[j] = sum over the batch of D[b, j], in sample order
+__global__ void k_bias_grad(const float *__restrict__ D, int nout, int B, float *__restrict__ gb) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nout) return;
   double s = 0.0;
-  for (int b = 0; b < B; ++b) {
-    const double dv = D[(int64_t)b * nd + row];
-    s += col < 0 ? dv : dv * In[(int64_t)b * ni + col];
-  }
-  g[q] = (float)s;
+  for (int b = 0; b < B; ++b) s += D[(int64_t)b * nout + j];
+  gb[j] = (float)s;
 }
 
 __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
@@ -276,33 +280,34 @@ struct hmle_mlp {
 namespace {
 
 struct Scratch {   // per-call device buffers for B samples
-  float *X = nullptr, *Xn, *H1, *H2, *Y, *T, *D1, *D2, *D3, *loss, *g, *mu, *sd, *lsum;
+  float *X = nullptr, *Xn, *H[kNL], *T, *D[kNL], *loss, *g, *mu, *sd, *lsum;
   int32_t *idx = nullptr;
+  int *flags = nullptr;   // error word of the tensor-core products (kFlagTimeout)
 };
 
 cudaError_t scratch_alloc(Scratch &s, int B, cudaStream_t st) {
-  const size_t fl = (size_t)B * (2 * kNF + 2 * kNH + kNO + 4 + 2 * kNH + kNO + 1) + kNParams + 2 * kNF + 1;
+  size_t acts = 0;
+  for (int l = 0; l < kNL; ++l) acts += 2 * (size_t)kOut[l];
+  const size_t fl = (size_t)B * (2 * kNF + acts + 4 + 1) + kNParams + 2 * kNF + 1;
   float *base = nullptr;
   cudaError_t e = cudaMallocAsync(&base, fl * sizeof(float), st);
   if (e != cudaSuccess) return e;
-  e = cudaMallocAsync(&s.idx, sizeof(int32_t) * std::max(B, 1), st);
+  e = cudaMallocAsync(&s.idx, sizeof(int32_t) * std::max(B, 1) + 16, st);
   if (e != cudaSuccess) { cudaFreeAsync(base, st); return e; }
+  s.flags = reinterpret_cast<int *>(s.idx + std::max(B, 1));
+  e = cudaMemsetAsync(s.flags, 0, sizeof(int), st);
   float *q = base;
   s.X = q; q += (size_t)B * kNF;
   s.Xn = q; q += (size_t)B * kNF;
-  s.H1 = q; q += (size_t)B * kNH;
-  s.H2 = q; q += (size_t)B * kNH;
-  s.Y = q; q += (size_t)B * kNO;
+  for (int l = 0; l < kNL; ++l) { s.H[l] = q; q += (size_t)B * kOut[l]; }
+  for (int l = 0; l < kNL; ++l) { s.D[l] = q; q += (size_t)B * kOut[l]; }
   s.T = q; q += (size_t)B * 4;
-  s.D1 = q; q += (size_t)B * kNH;
-  s.D2 = q; q += (size_t)B * kNH;
-  s.D3 = q; q += (size_t)B * kNO;
   s.loss = q; q += B;
   s.g = q; q += kNParams;
   s.mu = q; q += kNF;
   s.sd = q; q += kNF;
   s.lsum = q;
-  return cudaSuccess;
+  return e;
 }
 
 void scratch_free(Scratch &s, cudaStream_t st) {
@@ -311,21 +316,28 @@ void scratch_free(Scratch &s, cudaStream_t st) {
   s = Scratch{};
 }
 
-void launch_fwd(cudaStream_t st, const hmle_mlp *M, const Scratch &s, int B) {
-  k_mlp_fwd<<<B, kNH, 0, st>>>(M->p, s.mu, s.sd, s.X, B, s.Xn, s.H1, s.H2, s.Y);
+dim3 tiles(int rows, int cols) {
+  return dim3((rows + hmle::tc::kTM - 1) / hmle::tc::kTM, (cols + hmle::tc::kTN - 1) / hmle::tc::kTN);
 }
 
-void launch_grad(cudaStream_t st, const hmle_mlp *M, const Scratch &s, int B) {
-  launch_fwd(st, M, s, B);
-  k_mlp_bwd<<<B, kNH, 0, st>>>(M->p, s.H1, s.H2, s.Y, s.T, B, s.D1, s.D2, s.D3, s.loss);
-  k_mlp_grad<<<(kNParams + 127) / 128, 128, 0, st>>>(s.Xn, s.H1, s.H2, s.D1, s.D2, s.D3, B, s.g);
-  k_sum_f<<<1, 256, 0, st>>>(s.loss, B, s.lsum);
-}
+void launch_fwd(cudaStream_t st, const hmle_mlp *M, const Scratch &s, int B);
+
+void launch_grad(cudaStream_t st, const hmle_mlp *M, const Scratch &s, int B);
 
 hmle_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return HMLE_OK;
   cudaGetLastError();
   return e == cudaErrorMemoryAllocation ? HMLE_ERR_OOM : HMLE_ERR_CUDA;
+}
+
+// the products' error word after a synchronisation: TIMEOUT if a bounded wait
+// of the tensor cores ran out
+hmle_status flag_status(const Scratch &s, cudaStream_t st) {
+  int f = 0;
+  cudaError_t e = cudaMemcpyAsync(&f, s.flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  return (f & hmle::kFlagTimeout) ? HMLE_ERR_TIMEOUT : HMLE_OK;
 }
 
 cudaStream_t ctx_stream(hmle_ctx *ctx);
@@ -342,6 +354,57 @@ bool is_dev(const void *p) {
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
+}  // namespace
+
+namespace {
+
+void launch_fwd(cudaStream_t st, const hmle_mlp *M, const Scratch &s, int B) {
+  k_standardize<<<(B * kNF + 255) / 256, 256, 0, st>>>(s.X, s.mu, s.sd, B, s.Xn);
+  const float *in = s.Xn;
+  for (int l = 0; l < kNL; ++l) {
+    const bool last = l == kNL - 1;
+    const float *W = M->p + off_w(l), *b = M->p + off_b(l);
+    if (last)
+      k_layer_fwd<false><<<tiles(B, kOut[l]), 128, kTcBytes, st>>>(in, kIn[l], W, b, kOut[l], B, s.H[l], s.flags);
+    else
+      k_layer_fwd<true><<<tiles(B, kOut[l]), 128, kTcBytes, st>>>(in, kIn[l], W, b, kOut[l], B, s.H[l], s.flags);
+    in = s.H[l];
+  }
+}
+
+// forward, output deltas, then per layer (last to first): weight gradient,
+// bias gradient, and the deltas of the layer below
+void launch_grad(cudaStream_t st, const hmle_mlp *M, const Scratch &s, int B) {
+  launch_fwd(st, M, s, B);
+  k_out_delta<<<(B + 127) / 128, 128, 0, st>>>(s.H[kNL - 1], s.T, B, s.D[kNL - 1], s.loss);
+  for (int l = kNL - 1; l >= 0; --l) {
+    const float *Hin = l == 0 ? s.Xn : s.H[l - 1];
+    k_layer_wgrad<<<tiles(kOut[l], kIn[l]), 128, kTcBytes, st>>>(s.D[l], kOut[l], Hin, kIn[l], B,
+                                                                 s.g + off_w(l), s.flags);
+    k_bias_grad<<<(kOut[l] + 127) / 128, 128, 0, st>>>(s.D[l], kOut[l], B, s.g + off_b(l));
+    if (l > 0)
+      k_layer_bwd<<<tiles(B, kIn[l]), 128, kTcBytes, st>>>(s.D[l], kOut[l], M->p + off_w(l), kIn[l],
+                                                           s.H[l - 1], B, s.D[l - 1], s.flags);
+  }
+  k_sum_f<<<1, 256, 0, st>>>(s.loss, B, s.lsum);
+}
+
+// dynamic shared memory of the tensor-core kernels (above 48 KB): once
+cudaError_t mlp_setup() {
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [] {
+    err = cudaFuncSetAttribute(k_layer_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcBytes);
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(k_layer_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcBytes);
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(k_layer_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcBytes);
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(k_layer_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcBytes);
+  });
+  return err;
+}
+
 }  // namespace
 
 extern "C" {
@@ -363,9 +426,7 @@ hmle_status hmle_mlp_create(hmle_ctx *ctx, uint64_t seed, hmle_mlp **out) {
       p[off + i] = (float)((2.0 * u - 1.0) * a);
     }
   };
-  fill(kOffW1, kNH, kNF);
-  fill(kOffW2, kNH, kNH);
-  fill(kOffW3, kNO, kNH);
+  for (int l = 0; l < kNL; ++l) fill(off_w(l), kOut[l], kIn[l]);
   for (int k = 0; k < kNF; ++k) { M->mu[k] = 0.0f; M->sd[k] = 1.0f; }
   cudaError_t e = cudaMallocAsync(&M->p, 3 * sizeof(float) * kNParams, st);
   if (e == cudaSuccess) {
@@ -428,7 +489,8 @@ hmle_status hmle_mlp_forward(hmle_ctx *ctx, const hmle_mlp *M, const float *feat
   if (!ctx || !M || !feats || !out || m < 1) return HMLE_ERR_INVALID_ARG;
   cudaStream_t st = ctx_stream(ctx);
   Scratch s;
-  cudaError_t e = scratch_alloc(s, m, st);
+  cudaError_t e = mlp_setup();
+  if (e == cudaSuccess) e = scratch_alloc(s, m, st);
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaMemcpyAsync(s.X, feats, sizeof(float) * m * kNF, cudaMemcpyDefault, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s.mu, M->mu, sizeof(M->mu), cudaMemcpyHostToDevice, st);
@@ -437,11 +499,12 @@ hmle_status hmle_mlp_forward(hmle_ctx *ctx, const hmle_mlp *M, const float *feat
     launch_fwd(st, M, s, m);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(out, s.Y, sizeof(float) * m * kNO, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, s.H[kNL - 1], sizeof(float) * m * kNO, cudaMemcpyDefault, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const hmle_status fs = e == cudaSuccess ? flag_status(s, st) : cuda_status(e);
   scratch_free(s, st);
   cudaStreamSynchronize(st);
-  return cuda_status(e);
+  return fs;
 }
 
 hmle_status hmle_mlp_grad(hmle_ctx *ctx, const hmle_mlp *M, const float *feats,
@@ -449,7 +512,8 @@ hmle_status hmle_mlp_grad(hmle_ctx *ctx, const hmle_mlp *M, const float *feats,
   if (!ctx || !M || !feats || !targets || m < 1) return HMLE_ERR_INVALID_ARG;
   cudaStream_t st = ctx_stream(ctx);
   Scratch s;
-  cudaError_t e = scratch_alloc(s, m, st);
+  cudaError_t e = mlp_setup();
+  if (e == cudaSuccess) e = scratch_alloc(s, m, st);
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaMemcpyAsync(s.X, feats, sizeof(float) * m * kNF, cudaMemcpyDefault, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s.T, targets, sizeof(float) * m * 4, cudaMemcpyDefault, st);
@@ -464,9 +528,10 @@ hmle_status hmle_mlp_grad(hmle_ctx *ctx, const hmle_mlp *M, const float *feats,
   if (e == cudaSuccess) e = cudaMemcpyAsync(&l, s.lsum, sizeof(float), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (loss) *loss = l / m;
+  const hmle_status fs = e == cudaSuccess ? flag_status(s, st) : cuda_status(e);
   scratch_free(s, st);
   cudaStreamSynchronize(st);
-  return cuda_status(e);
+  return fs;
 }
 
 hmle_status hmle_mlp_adam_step(hmle_ctx *ctx, hmle_mlp *M, const float *grad, float lr) {
@@ -495,6 +560,10 @@ hmle_status hmle_mlp_train(hmle_ctx *ctx, hmle_mlp *M, const float *feats, const
     return HMLE_ERR_INVALID_ARG;
   cudaStream_t st = ctx_stream(ctx);
   batch = std::min(batch, m);
+  {
+    const cudaError_t e0 = mlp_setup();
+    if (e0 != cudaSuccess) return cuda_status(e0);
+  }
   // standardisation from the training features (host, double)
   std::vector<float> F((size_t)m * kNF), Tg((size_t)m * 4);
   cudaError_t e = cudaMemcpyAsync(F.data(), feats, sizeof(float) * F.size(), cudaMemcpyDefault, st);
@@ -556,11 +625,12 @@ hmle_status hmle_mlp_train(hmle_ctx *ctx, hmle_mlp *M, const float *feats, const
   }
   if (loss_first) *loss_first = lf;
   if (loss_last) *loss_last = ll;
+  const hmle_status fs = (e == cudaSuccess && s.flags) ? flag_status(s, st) : cuda_status(e);
   scratch_free(s, st);
   if (Fd) cudaFreeAsync(Fd, st);
   if (Td) cudaFreeAsync(Td, st);
   cudaError_t e2 = cudaStreamSynchronize(st);
-  return cuda_status(e != cudaSuccess ? e : e2);
+  return fs != HMLE_OK ? fs : cuda_status(e2);
 }
 
 hmle_status hmle_features(hmle_ctx *ctx, const double *locs, int64_t n, int32_t d, const double *Z,

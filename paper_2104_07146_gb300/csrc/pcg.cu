@@ -24,9 +24,15 @@ constexpr int kThreadsMv = 128;
 
 // --- y = C x, deterministic ------------------------------------------------
 // Stage 1: per admissible block of C, t1 = V^T x[cols], t2 = U^T x[rows].
-__global__ void __launch_bounds__(kThreadsMv) k_cmv_t(AsmArgs A, const double *__restrict__ x,
-                                                      double *__restrict__ t) {
+// In every kernel below, blockIdx.y selects the evaluation of a batch (its
+// vectors at z zs doubles, its H-matrix through AsmArgs::at); one
+// evaluation is the batch of one.
+__global__ void __launch_bounds__(kThreadsMv) k_cmv_t(AsmArgs Az, const double *__restrict__ x,
+                                                      double *__restrict__ t, int64_t zs) {
   __shared__ double red[32];
+  const AsmArgs A = Az.at(blockIdx.y);
+  x += blockIdx.y * zs;
+  t += blockIdx.y * zs;
   const int blk = A.lr_ids[blockIdx.x];
   const BlockDesc B = A.blocks[blk];
   const int m = B.rend - B.rbeg, p = B.cend - B.cbeg, kc = A.kc;
@@ -47,7 +53,7 @@ __global__ void __launch_bounds__(kThreadsMv) k_cmv_t(AsmArgs A, const double *_
 // rows cover I (C x[cols], U t1) and then those whose columns cover I
 // (C^T x[rows], V t2).  lr_slot[blk]: the block's index among the admissible
 // blocks (its t1/t2 slot), -1 for a dense block.
-__global__ void __launch_bounds__(kThreadsMv) k_cmv_rows(AsmArgs A, const int32_t *__restrict__ leaf_beg,
+__global__ void __launch_bounds__(kThreadsMv) k_cmv_rows(AsmArgs Az, const int32_t *__restrict__ leaf_beg,
                                                          const int32_t *__restrict__ row0,
                                                          const int32_t *__restrict__ rblocks,
                                                          const int32_t *__restrict__ col0,
@@ -55,7 +61,11 @@ __global__ void __launch_bounds__(kThreadsMv) k_cmv_rows(AsmArgs A, const int32_
                                                          const int32_t *__restrict__ lr_slot,
                                                          const double *__restrict__ x,
                                                          const double *__restrict__ t,
-                                                         double *__restrict__ y) {
+                                                         double *__restrict__ y, int64_t zs) {
+  const AsmArgs A = Az.at(blockIdx.y);
+  x += blockIdx.y * zs;
+  t += blockIdx.y * zs;
+  y += blockIdx.y * zs;
   const int I = blockIdx.x;
   const int I0 = leaf_beg[I], I1 = leaf_beg[I + 1];
   const int kc = A.kc;
@@ -95,8 +105,11 @@ __global__ void __launch_bounds__(kThreadsMv) k_cmv_rows(AsmArgs A, const int32_
 
 // --- dot products: fixed partition, fixed order -----------------------------
 __global__ void k_dot_part(const double *__restrict__ a, const double *__restrict__ b, int64_t n,
-                           double *__restrict__ part) {
+                           double *__restrict__ part, int64_t zs) {
   __shared__ double red[32];
+  a += blockIdx.y * zs;
+  b += blockIdx.y * zs;
+  part += blockIdx.y * zs;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
   double s = 0.0;
@@ -105,8 +118,10 @@ __global__ void k_dot_part(const double *__restrict__ a, const double *__restric
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-__global__ void k_dot_final(const double *__restrict__ part, int np, double *__restrict__ out) {
+__global__ void k_dot_final(const double *__restrict__ part, int np, double *__restrict__ out, int64_t zs) {
   __shared__ double red[32];
+  part += blockIdx.x * zs;
+  out += blockIdx.x * zs;
   double s = 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
   s = block_sum(s, red);
@@ -115,32 +130,65 @@ __global__ void k_dot_final(const double *__restrict__ part, int np, double *__r
 
 // --- the scalar recurrences and vector updates ------------------------------
 // sc: [0] r.z  [1] p.q  [2] alpha  [3] r.z (new)  [4] beta  [5] r.r  [6] b.b  [7] b.x
-__global__ void k_pcg_alpha(double *sc) { sc[2] = sc[0] / sc[1]; }
-__global__ void k_pcg_beta(double *sc) {
+//     [8] stopped (batch)  [9] iterations (batch)  [10] relative residual (batch)
+// One thread per evaluation (grid nz).
+__global__ void k_pcg_alpha(double *sc, int64_t zs) {
+  sc += blockIdx.x * zs;
+  sc[2] = sc[0] / sc[1];
+}
+__global__ void k_pcg_beta(double *sc, int64_t zs) {
+  sc += blockIdx.x * zs;
   sc[4] = sc[3] / sc[0];
   sc[0] = sc[3];
 }
 
+// x += alpha p, r -= alpha q; an evaluation of a batch that has stopped keeps
+// its x (and r) as they were when it stopped.
 __global__ void k_pcg_xr(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-                         const double *__restrict__ q, const double *__restrict__ sc, int64_t n) {
-  const double alpha = sc[2];
+                         const double *__restrict__ q, const double *__restrict__ sc, int64_t n, int64_t zs) {
+  const int64_t o = blockIdx.y * zs;
+  if (sc[o + 8] != 0.0) return;
+  const double alpha = sc[o + 2];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
-    x[i] = fma(alpha, p[i], x[i]);
-    r[i] = fma(-alpha, q[i], r[i]);
+    x[o + i] = fma(alpha, p[o + i], x[o + i]);
+    r[o + i] = fma(-alpha, q[o + i], r[o + i]);
   }
 }
 
 __global__ void k_pcg_p(double *__restrict__ p, const double *__restrict__ z,
-                        const double *__restrict__ sc, int64_t n) {
-  const double beta = sc[4];
+                        const double *__restrict__ sc, int64_t n, int64_t zs) {
+  const int64_t o = blockIdx.y * zs;
+  const double beta = sc[o + 4];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = fma(beta, p[i], z[i]);
+  if (i < n) p[o + i] = fma(beta, p[o + i], z[o + i]);
 }
 
-void dot(cudaStream_t st, const double *a, const double *b, int64_t n, double *part, double *out) {
-  k_dot_part<<<kDotCtas, 256, 0, st>>>(a, b, n, part);
-  k_dot_final<<<1, 256, 0, st>>>(part, kDotCtas, out);
+// batch: after an iteration's r.r, an evaluation that has not stopped counts
+// the iteration and stops where a single solve would (residual at or below
+// tol, or maxit iterations, or not finite)
+__global__ void k_pcg_check(double *sc, double tol, int maxit, int64_t zs) {
+  sc += blockIdx.x * zs;
+  if (sc[8] != 0.0) return;
+  const double it = sc[9] + 1.0;
+  const double bb = sc[6];
+  const double rel = bb > 0.0 ? sqrt(sc[5] / bb) : 0.0;
+  sc[9] = it;
+  sc[10] = rel;
+  if (!(it < (double)maxit && rel > tol)) sc[8] = 1.0;
+}
+
+__global__ void k_pcg_reset(double *sc, int64_t zs) {
+  sc += blockIdx.x * zs;
+  sc[8] = 0.0;
+  sc[9] = 0.0;
+  sc[10] = 1.0;
+}
+
+void dot(cudaStream_t st, const double *a, const double *b, int64_t n, double *part, double *out,
+         int nz = 1, int64_t zs = 0) {
+  k_dot_part<<<dim3(kDotCtas, nz), 256, 0, st>>>(a, b, n, part, zs);
+  k_dot_final<<<nz, 256, 0, st>>>(part, kDotCtas, out, zs);
 }
 
 unsigned grid1(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -152,10 +200,10 @@ int64_t pcg_words(int64_t n, int n_lr, int kc, int hmax) {
 }
 
 void launch_cmatvec(cudaStream_t st, const AsmArgs &A, int n_lr, const CmvLists &L,
-                    const double *x, double *t, double *y) {
-  if (n_lr > 0) k_cmv_t<<<n_lr, kThreadsMv, 0, st>>>(A, x, t);
-  k_cmv_rows<<<L.nleaf, kThreadsMv, 0, st>>>(A, L.leaf_beg, L.row0, L.rblocks, L.col0, L.cblocks,
-                                             L.lr_slot, x, t, y);
+                    const double *x, double *t, double *y, int nz, int64_t zs) {
+  if (n_lr > 0) k_cmv_t<<<dim3(n_lr, nz), kThreadsMv, 0, st>>>(A, x, t, zs);
+  k_cmv_rows<<<dim3(L.nleaf, nz), kThreadsMv, 0, st>>>(A, L.leaf_beg, L.row0, L.rblocks, L.col0, L.cblocks,
+                                                       L.lr_slot, x, t, y, zs);
 }
 
 namespace {
@@ -177,11 +225,18 @@ PcgBufs carve(double *pool, int64_t n, int n_lr, int kc, const Plan &PL) {
 }
 
 // z = M^{-1} r = L~^{-T} L~^{-1} r through the right-hand-side panel
+void copy_z(cudaStream_t st, double *dst, const double *src, int64_t n, int nz, int64_t zs) {
+  cudaMemcpy2DAsync(dst, sizeof(double) * std::max<int64_t>(zs, n), src, sizeof(double) * std::max<int64_t>(zs, n),
+                    sizeof(double) * n, nz, cudaMemcpyDeviceToDevice, st);
+}
+
 void precond(cudaStream_t st, const FactorArgs &Fs, const Plan &PL, const int32_t *wpan_rhs,
              const int32_t *bh_blocks, const UpdRow *bupd, const UpdEntry *bents, double *panel,
              const double *r, double *z, double *hbuf, int64_t n, const SolvePlan *SP,
              unsigned *bar) {
-  cudaMemcpyAsync(panel, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  const int nz = Fs.nz > 0 ? Fs.nz : 1;
+  const int64_t zs = Fs.zstride / (int64_t)sizeof(double);
+  copy_z(st, panel, r, n, nz, zs);
   if (SP) {
     persistent_solve(st, Fs, *SP, panel, Fs.ws, bar, false);
     persistent_solve(st, Fs, *SP, panel, hbuf, bar, true);
@@ -189,7 +244,7 @@ void precond(cudaStream_t st, const FactorArgs &Fs, const Plan &PL, const int32_
     launch_solve(st, Fs, PL, wpan_rhs);
     launch_backward(st, Fs, PL, panel, bh_blocks, bupd, bents, hbuf);
   }
-  cudaMemcpyAsync(z, panel, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  copy_z(st, z, panel, n, nz, zs);
 }
 
 // Run seq() directly, or through a graph captured into *g on first use.
@@ -220,17 +275,20 @@ cudaError_t launch_iteration(PcgRun &R) {
   const int64_t n = R.n;
   // one iteration; the preconditioner of the next one runs even when this
   // one converges (its result is then unused)
+  const int nz = R.nz;
+  const int64_t zs = R.zs;
   cudaError_t e = run_seq(st, R.g_iter, [&] {
-    launch_cmatvec(st, R.A, R.n_lr, R.L, B.p, B.t, B.qv);
-    dot(st, B.p, B.qv, n, B.part, B.sc + 1);
-    k_pcg_alpha<<<1, 1, 0, st>>>(B.sc);
-    k_pcg_xr<<<grid1(n), 256, 0, st>>>(B.x, B.r, B.p, B.qv, B.sc, n);
-    dot(st, B.r, B.r, n, B.part, B.sc + 5);
+    launch_cmatvec(st, R.A, R.n_lr, R.L, B.p, B.t, B.qv, nz, zs);
+    dot(st, B.p, B.qv, n, B.part, B.sc + 1, nz, zs);
+    k_pcg_alpha<<<nz, 1, 0, st>>>(B.sc, zs);
+    k_pcg_xr<<<dim3(grid1(n), nz), 256, 0, st>>>(B.x, B.r, B.p, B.qv, B.sc, n, zs);
+    dot(st, B.r, B.r, n, B.part, B.sc + 5, nz, zs);
+    if (nz > 1 || R.hostz) k_pcg_check<<<nz, 1, 0, st>>>(B.sc, R.tol, R.maxit, zs);
     precond(st, R.Fs, *R.PL, R.wpan_rhs, R.bh_blocks, R.bupd, R.bents, R.panel, B.r, B.z, B.hbuf, n,
             R.SP, R.bar);
-    dot(st, B.r, B.z, n, B.part, B.sc + 3);
-    k_pcg_beta<<<1, 1, 0, st>>>(B.sc);
-    k_pcg_p<<<grid1(n), 256, 0, st>>>(B.p, B.z, B.sc, n);
+    dot(st, B.r, B.z, n, B.part, B.sc + 3, nz, zs);
+    k_pcg_beta<<<nz, 1, 0, st>>>(B.sc, zs);
+    k_pcg_p<<<dim3(grid1(n), nz), 256, 0, st>>>(B.p, B.z, B.sc, n, zs);
   });
   if (e != cudaSuccess) return e;
   if (R.SP) {
@@ -238,6 +296,9 @@ cudaError_t launch_iteration(PcgRun &R) {
                         cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return e;
   }
+  if (R.hostz)   // batch: every evaluation's stop flag, iterations and residual
+    return cudaMemcpy2DAsync(R.hostz, 4 * sizeof(double), B.sc + 8, sizeof(double) * zs, 3 * sizeof(double),
+                             nz, cudaMemcpyDeviceToHost, st);
   return cudaMemcpyAsync(R.host + 1, B.sc + 5, sizeof(double), cudaMemcpyDeviceToHost, st);
 }
 
@@ -318,14 +379,17 @@ cudaError_t pcg_start(PcgRun &R) {
     if (e0 != cudaSuccess) return e0;
   }
   // x = 0, r = b, z = M^{-1} r, p = z, sc[0] = r.z, sc[6] = b.b
+  const int nz = R.nz;
+  const int64_t zs = R.zs;
   cudaError_t e = run_seq(st, R.g_init, [&] {
-    cudaMemsetAsync(B.x, 0, sizeof(double) * n, st);
-    cudaMemcpyAsync(B.r, R.b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    cudaMemset2DAsync(B.x, sizeof(double) * std::max<int64_t>(zs, n), 0, sizeof(double) * n, nz, st);
+    copy_z(st, B.r, R.b, n, nz, zs);
     precond(st, R.Fs, *R.PL, R.wpan_rhs, R.bh_blocks, R.bupd, R.bents, R.panel, B.r, B.z, B.hbuf, n,
             R.SP, R.bar);
-    cudaMemcpyAsync(B.p, B.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-    dot(st, B.r, B.z, n, B.part, B.sc + 0);
-    dot(st, R.b, R.b, n, B.part, B.sc + 6);
+    copy_z(st, B.p, B.z, n, nz, zs);
+    dot(st, B.r, B.z, n, B.part, B.sc + 0, nz, zs);
+    dot(st, R.b, R.b, n, B.part, B.sc + 6, nz, zs);
+    k_pcg_reset<<<nz, 1, 0, st>>>(B.sc, zs);
   });
   if (e == cudaSuccess) e = cudaMemcpyAsync(R.host + 0, B.sc + 6, sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && R.maxit > 0) e = launch_iteration(R);
@@ -358,6 +422,52 @@ cudaError_t pcg_poll(PcgRun &R, bool *finished) {
   dot(R.st, R.b, B.x, R.n, B.part, B.sc + 7);
   R.state = 1;
   return cudaMemcpyAsync(R.host + 2, B.sc + 7, sizeof(double), cudaMemcpyDeviceToHost, R.st);
+}
+
+// A batch of R.nz solves in lockstep: one launch per kernel for all of them
+// (the persistent sweeps included); each evaluation stops updating its
+// solution where its single solve would stop, and the batch iterates until
+// every evaluation has stopped.  The host reads the nz stop flags after each
+// iteration.
+cudaError_t pcg_batch_start(PcgRun &R) {
+  R.it = 0;
+  R.state = 0;
+  R.timed_out = false;
+  R.itz.assign(R.nz, 0);
+  R.relz.assign(R.nz, 1.0);
+  R.qz.assign(R.nz, 0.0);
+  return pcg_start(R);   // the set-up, then the first iteration (nz-aware)
+}
+
+cudaError_t pcg_batch_poll(PcgRun &R, bool *finished) {
+  *finished = false;
+  const PcgBufs B = carve(R.pool, R.n, R.n_lr, R.A.kc, *R.PL);
+  if (R.state == 2) { *finished = true; return cudaSuccess; }
+  if (R.state == 1) {   // the final dots have completed
+    for (int z = 0; z < R.nz; ++z) R.qz[z] = R.hostz[4 * z + 3];
+    R.state = 2;
+    *finished = true;
+    return cudaGetLastError();
+  }
+  if (R.SP && *reinterpret_cast<volatile unsigned *>(R.host + 3) != 0u) {
+    R.timed_out = true;
+    R.state = 2;
+    *finished = true;
+    return cudaSuccess;
+  }
+  bool all = true;
+  for (int z = 0; z < R.nz; ++z) {
+    R.itz[z] = (int)R.hostz[4 * z + 1];
+    R.relz[z] = R.hostz[4 * z + 2];
+    all = all && (R.maxit <= 0 || R.hostz[4 * z] != 0.0);
+  }
+  ++R.it;
+  if (!all && R.it < R.maxit) return launch_iteration(R);
+  // every evaluation has stopped: q = b.x
+  dot(R.st, R.b, B.x, R.n, B.part, B.sc + 7, R.nz, R.zs);
+  R.state = 1;
+  return cudaMemcpy2DAsync(R.hostz + 3, 4 * sizeof(double), B.sc + 7, sizeof(double) * R.zs, sizeof(double),
+                           R.nz, cudaMemcpyDeviceToHost, R.st);
 }
 
 cudaError_t pcg_quad(PcgRun &R) {

@@ -102,36 +102,50 @@ struct SolveArgs {
                             // factor's workspace), backward kcap per task of a leaf
   unsigned *bar;
   int nleaf;
+  // a batch of nz factors (FactorArgs::at): evaluation z's vector and coupling
+  // vectors are w + z zs and h + z zs; every phase runs the tasks of all nz
+  int nz;
+  int64_t zs;
 };
 
 __global__ void __launch_bounds__(kSolveThreads) k_solve_fwd(SolveArgs S) {
-  const FactorArgs &F = S.F;
   const unsigned G = gridDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int K = 0; K < S.nleaf; ++K) {
-    if (blockIdx.x == 0 && warp == 0) {
-      const BlockDesc D = F.blocks[S.diag[K]];
-      leaf_trsv(F.D + D.off_d, F.b, D.rend - D.rbeg, S.w + D.rbeg, false);
-    }
+    if (warp == 0)
+      for (int z = blockIdx.x; z < S.nz; z += G) {
+        const FactorArgs F = S.F.at(z);
+        const BlockDesc D = F.blocks[S.diag[K]];
+        leaf_trsv(F.D + D.off_d, F.b, D.rend - D.rbeg, S.w + z * S.zs + D.rbeg, false);
+      }
     if (!grid_barrier(S.bar, G)) return;
     // B: h_A = W_A^T w[cols A], a warp per component
-    for (int t = S.s0[K] + blockIdx.x; t < S.s0[K + 1]; t += G) {
+    const int nb = S.s0[K + 1] - S.s0[K];
+    for (int g = blockIdx.x; g < nb * S.nz; g += G) {
+      const int z = g / nb, t = S.s0[K] + g % nb;
+      const FactorArgs F = S.F.at(z);
+      const double *wz = S.w + z * S.zs;
       const HTask T = S.hts[t];
       const BlockDesc A = F.blocks[T.a];
       const PanelDesc PA = F.panels[A.panel];
       const int lda = PA.rend - PA.rbeg, ka = F.rank_l[T.a], p = A.cend - A.cbeg;
       const double *Wa = F.W + PA.off + (int64_t)A.slot * lda + (A.cbeg - PA.rbeg);
-      double *h = S.h + T.hoff;   // where the sweep's own task writes it
+      double *h = S.h + z * S.zs + T.hoff;   // where the sweep's own task writes it
       for (int i = warp; i < ka; i += nw) {
         double s = 0.0;
-        for (int k = lane; k < p; k += 32) s = fma(Wa[k + (int64_t)i * lda], __ldcg(S.w + A.cbeg + k), s);
+        for (int k = lane; k < p; k += 32) s = fma(Wa[k + (int64_t)i * lda], __ldcg(wz + A.cbeg + k), s);
         s = warp_sum(s);
         if (lane == 0) h[i] = s;
       }
     }
     if (!grid_barrier(S.bar, G)) return;
     // C: w[I] -= sum over the row's entries, in order
-    for (int t = S.u0[K] + blockIdx.x; t < S.u0[K + 1]; t += G) {
+    const int nu = S.u0[K + 1] - S.u0[K];
+    for (int g = blockIdx.x; g < nu * S.nz; g += G) {
+      const int z = g / nu, t = S.u0[K] + g % nu;
+      const FactorArgs F = S.F.at(z);
+      double *wz = S.w + z * S.zs;
+      const double *hz = S.h + z * S.zs;
       const UpdRow R = S.rows[t];
       const int I0 = F.leaf_beg[R.leaf], I1 = F.leaf_beg[R.leaf + 1];
       for (int i = I0 + threadIdx.x; i < I1; i += blockDim.x) {
@@ -141,15 +155,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_fwd(SolveArgs S) {
           const BlockDesc A = F.blocks[E.a];
           if (E.hoff < 0) {   // dense: D_A w[cols A]
             const double *Dr = F.D + A.off_d + (i - A.rbeg);
-            for (int j = 0; j < A.cend - A.cbeg; ++j) acc = fma(Dr[(int64_t)j * F.b], __ldcg(S.w + A.cbeg + j), acc);
+            for (int j = 0; j < A.cend - A.cbeg; ++j) acc = fma(Dr[(int64_t)j * F.b], __ldcg(wz + A.cbeg + j), acc);
           } else {            // low rank: U_A[i] h_A (h slot from the task list)
             const double *U = F.U + A.off_u + (i - A.rbeg);
             const int m = A.rend - A.rbeg;
-            const double *h = S.h + E.hoff;
+            const double *h = hz + E.hoff;
             for (int k = 0; k < F.rank_l[E.a]; ++k) acc = fma(U[(int64_t)k * m], __ldcg(h + k), acc);
           }
         }
-        S.w[i] = __ldcg(S.w + i) - acc;
+        wz[i] = __ldcg(wz + i) - acc;
       }
     }
     if (!grid_barrier(S.bar, G)) return;
@@ -157,32 +171,42 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_fwd(SolveArgs S) {
 }
 
 __global__ void __launch_bounds__(kSolveThreads) k_solve_bwd(SolveArgs S) {
-  const FactorArgs &F = S.F;
   const unsigned G = gridDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int K = S.nleaf - 1; K >= 0; --K) {
-    if (blockIdx.x == 0 && warp == 0) {
-      const BlockDesc D = F.blocks[S.diag[K]];
-      leaf_trsv(F.D + D.off_d, F.b, D.rend - D.rbeg, S.w + D.rbeg, true);
-    }
+    if (warp == 0)
+      for (int z = blockIdx.x; z < S.nz; z += G) {
+        const FactorArgs F = S.F.at(z);
+        const BlockDesc D = F.blocks[S.diag[K]];
+        leaf_trsv(F.D + D.off_d, F.b, D.rend - D.rbeg, S.w + z * S.zs + D.rbeg, true);
+      }
     if (!grid_barrier(S.bar, G)) return;
     // B: h_A = U_A^T v[rows A] for the low-rank blocks whose rows start at K
-    for (int t = S.s0[K] + blockIdx.x; t < S.s0[K + 1]; t += G) {
+    const int nb = S.s0[K + 1] - S.s0[K];
+    for (int g = blockIdx.x; g < nb * S.nz; g += G) {
+      const int z = g / nb, t = S.s0[K] + g % nb;
+      const FactorArgs F = S.F.at(z);
+      const double *wz = S.w + z * S.zs;
       const int blk = S.bblk[t];
       const BlockDesc A = F.blocks[blk];
       const int m = A.rend - A.rbeg, ka = F.rank_l[blk];
       const double *U = F.U + A.off_u;
-      double *h = S.h + (int64_t)(t - S.s0[K]) * F.kcap;
+      double *h = S.h + z * S.zs + (int64_t)(t - S.s0[K]) * F.kcap;
       for (int i = warp; i < ka; i += nw) {
         double s = 0.0;
-        for (int k = lane; k < m; k += 32) s = fma(U[k + (int64_t)i * m], __ldcg(S.w + A.rbeg + k), s);
+        for (int k = lane; k < m; k += 32) s = fma(U[k + (int64_t)i * m], __ldcg(wz + A.rbeg + k), s);
         s = warp_sum(s);
         if (lane == 0) h[i] = s;
       }
     }
     if (!grid_barrier(S.bar, G)) return;
     // C: v[J] -= sum over the column leaf's entries, in order
-    for (int t = S.u0[K] + blockIdx.x; t < S.u0[K + 1]; t += G) {
+    const int nu = S.u0[K + 1] - S.u0[K];
+    for (int g = blockIdx.x; g < nu * S.nz; g += G) {
+      const int z = g / nu, t = S.u0[K] + g % nu;
+      const FactorArgs F = S.F.at(z);
+      double *wz = S.w + z * S.zs;
+      const double *hz = S.h + z * S.zs;
       const UpdRow R = S.rows[t];
       const int J0 = F.leaf_beg[R.leaf], J1 = F.leaf_beg[R.leaf + 1];
       for (int j = J0 + threadIdx.x; j < J1; j += blockDim.x) {
@@ -192,16 +216,16 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_bwd(SolveArgs S) {
           const BlockDesc A = F.blocks[E.a];
           if (E.hoff < 0) {   // dense: D_A^T v[rows A], column j - cbeg
             const double *Dc = F.D + A.off_d + (int64_t)(j - A.cbeg) * F.b;
-            for (int i = 0; i < A.rend - A.rbeg; ++i) acc = fma(Dc[i], __ldcg(S.w + A.rbeg + i), acc);
+            for (int i = 0; i < A.rend - A.rbeg; ++i) acc = fma(Dc[i], __ldcg(wz + A.rbeg + i), acc);
           } else {            // low rank: W_A[j] h_A
             const PanelDesc PA = F.panels[A.panel];
             const int lda = PA.rend - PA.rbeg;
             const double *Wr = F.W + PA.off + (int64_t)A.slot * lda + (j - PA.rbeg);
-            const double *h = S.h + E.hoff * F.kcap;
+            const double *h = hz + E.hoff * F.kcap;
             for (int k = 0; k < F.rank_l[E.a]; ++k) acc = fma(Wr[(int64_t)k * lda], __ldcg(h + k), acc);
           }
         }
-        S.w[j] = __ldcg(S.w + j) - acc;
+        wz[j] = __ldcg(wz + j) - acc;
       }
     }
     if (!grid_barrier(S.bar, G)) return;
@@ -245,6 +269,8 @@ cudaError_t persistent_solve(cudaStream_t st, const FactorArgs &F, const SolvePl
   S.w = w;
   S.h = h;
   S.bar = bar;
+  S.nz = F.nz > 0 ? F.nz : 1;
+  S.zs = F.zstride / (int64_t)sizeof(double);
   // arrivals and generation start at zero; the error word is kept (set to
   // zero by the caller once), so a later sweep does not hide an earlier one's
   cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);

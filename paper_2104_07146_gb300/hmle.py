@@ -34,7 +34,7 @@ class Opts(C.Structure):
     _fields_ = [("leaf_size", C.c_int32), ("eta", C.c_double), ("aca_eps", C.c_double),
                 ("max_rank", C.c_int32), ("oversample", C.c_int32), ("precision", C.c_int32),
                 ("seed", C.c_uint64), ("leaf_lowrank", C.c_int32), ("pcg_tol", C.c_double),
-                ("pcg_max_iter", C.c_int32), ("fixed_rank", C.c_int32)]
+                ("pcg_max_iter", C.c_int32), ("fixed_rank", C.c_int32), ("batch_size", C.c_int32)]
 
 
 class FitOpts(C.Structure):
@@ -60,7 +60,7 @@ class Task(C.Structure):
 
 class TuneResult(C.Structure):
     _fields_ = [("leaf_size", C.c_int32), ("concurrency", C.c_int32), ("evals_per_s", C.c_double),
-                ("trials", C.c_int32)]
+                ("trials", C.c_int32), ("batch_size", C.c_int32)]
 
 
 class EvalInfo(C.Structure):
@@ -125,6 +125,7 @@ def lib():
             "hmle_mlp_adam_step": ([P, P, P, C.c_float], C.c_int),
             "hmle_mlp_train": ([P, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_uint64,
                                 P, P], C.c_int),
+            "hmle_tree_set_batch_size": ([P, C.c_int32], C.c_int),
             "hmle_autotune": ([P, P, C.c_int64, C.c_int32, P, P, P, C.c_int32, P, P, C.c_int32, P],
                               C.c_int),
             "hmle_matern_eval_noalloc": ([P, P, C.c_int32, P, C.c_int64, P], C.c_int),
@@ -151,7 +152,7 @@ def exported_symbols():
             "hmle_tree_permutation", "hmle_assemble", "hmle_hmatrix_destroy",
             "hmle_hmatrix_matvec", "hmle_factor", "hmle_factor_destroy", "hmle_loglik",
             "hmle_loglik_eval", "hmle_fit", "hmle_matern_eval", "hmle_profile_select",
-            "hmle_profile_read", "hmle_phase_work", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_predict", "hmle_fit_profiled", "hmle_cross_matvec", "hmle_loglik_multi", "hmle_autotune",
+            "hmle_profile_read", "hmle_phase_work", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_predict", "hmle_fit_profiled", "hmle_cross_matvec", "hmle_loglik_multi", "hmle_autotune", "hmle_tree_set_batch_size",
             "hmle_theta_to_x", "hmle_x_to_theta", "hmle_selftest_barrier", "hmle_selftest_tc_gemm", "hmle_features", "hmle_mlp_nparams",
             "hmle_mlp_create", "hmle_mlp_destroy", "hmle_mlp_set", "hmle_mlp_get",
             "hmle_mlp_forward", "hmle_mlp_grad", "hmle_mlp_adam_step", "hmle_mlp_train",
@@ -223,7 +224,7 @@ class Context:
                                        C.byref(_theta(theta)), p, int(max_concurrency),
                                        C.byref(best), trials, 64, C.byref(nt)), "hmle_autotune")
         conv = lambda r: {"leaf_size": r.leaf_size, "concurrency": r.concurrency,
-                          "evals_per_s": r.evals_per_s}
+                          "batch_size": r.batch_size, "evals_per_s": r.evals_per_s}
         return conv(best), [conv(trials[i]) for i in range(min(nt.value, 64))]
 
     def close(self):

@@ -27,8 +27,9 @@ from .hmle import P, lib
 NF = 35
 DEFAULT_THETA0 = (0.2, 1.0, 0.5, 0.05)
 
-# prior box of the simulated training fields (theta order ell, nu, sigma2, tau2)
-PRIOR = {"ell": (0.02, 0.3), "nu": (0.3, 2.0), "sigma2": (0.25, 4.0), "tau2": (1e-3, 0.1)}
+# prior box of the simulated training fields (theta order ell, nu, sigma2,
+# tau2): ell and tau2 log-uniform, nu and sigma2 uniform
+PRIOR = {"ell": (0.02, 0.3), "nu": (0.3, 2.5), "sigma2": (0.5, 2.0), "tau2": (1e-4, 0.1)}
 
 
 def theta_to_x(theta):
@@ -143,31 +144,34 @@ class LearnedStart:
 
 
 def draw_theta(seed: int, i: int):
-    """theta of training field i: log-uniform ell, sigma2, tau2; uniform nu."""
+    """theta of training field i: log-uniform ell and tau2, uniform nu and
+    sigma2, over the prior box."""
     u = synth.uniform(seed * 1_000_003 + i, 4)
     lo, hi = PRIOR["ell"]
     ell = lo * (hi / lo) ** u[0]
     nu = PRIOR["nu"][0] + (PRIOR["nu"][1] - PRIOR["nu"][0]) * u[1]
-    lo, hi = PRIOR["sigma2"]
-    s2 = lo * (hi / lo) ** u[2]
+    s2 = PRIOR["sigma2"][0] + (PRIOR["sigma2"][1] - PRIOR["sigma2"][0]) * u[2]
     lo, hi = PRIOR["tau2"]
     t2 = lo * (hi / lo) ** u[3]
     return (float(ell), float(nu), float(s2), float(t2))
 
 
-def field(ctx, seed: int, i: int, n: int):
-    """Field i of a seeded family: point set (uniform or blob mixture,
-    alternating), theta from the prior, Z = L~ xi simulated by the
-    H-Cholesky factor at eps 1e-8 (1e-6 when the smoothest fields need more
-    rank than the blocks hold at 1e-8)."""
+def field(ctx, seed: int, i: int, n: int, three_d: bool = False):
+    """Field i of a seeded family: point set (2-D uniform or blob mixture,
+    alternating, or uniform in the unit cube with three_d), theta from the
+    prior, Z = L~ xi simulated by the H-Cholesky factor at eps 1e-8 (1e-6
+    when the smoothest fields need more rank than the blocks hold at 1e-8)."""
     th = draw_theta(seed, i)
-    if i % 2 == 0:
+    if three_d:
+        locs = synth.uniform(seed * 7919 + i, 3 * n).reshape(n, 3)
+    elif i % 2 == 0:
         locs = synth.locations_uniform(n, 2, seed=seed * 7919 + i)
     else:
         locs = synth.locations_blobs(n, 2, 0.3, 8, 0.03, seed=seed * 7919 + i)
     xi = synth.normal(seed * 104729 + i, n)
+    leaf = 32 if n <= 3000 else 64
     for eps in (1e-8, 1e-6):
-        tree = hmle.Tree(ctx, locs, leaf_size=32, aca_eps=eps, max_rank=48, oversample=16)
+        tree = hmle.Tree(ctx, locs, leaf_size=leaf, aca_eps=eps, max_rank=64, oversample=16)
         try:
             Z = tree.simulate(th, xi)
             return locs, Z, th
@@ -179,17 +183,32 @@ def field(ctx, seed: int, i: int, n: int):
     raise hmle.HmleError(5, "simulate: rank overflow at eps 1e-6")
 
 
-def training_set(ctx, count: int, seed: int = 11, n_range=(600, 2400)):
-    """count simulated fields -> (features count x 35, targets count x 4)."""
+def training_set(ctx, count: int, seed: int = 11, n_range=(4096, 16384), three_d_every: int = 0,
+                 time_limit_s: float = 0.0):
+    """Up to count simulated fields -> (features k x 35, targets k x 4): n
+    log-uniform in n_range; every three_d_every-th field 3-D (0: none).
+    With time_limit_s > 0 the generation stops after that many seconds and
+    returns the fields made so far (k <= count)."""
     F = np.zeros((count, NF), dtype=np.float32)
     T = np.zeros((count, 4), dtype=np.float32)
+    t0 = time.time()
+    k = 0
     for i in range(count):
+        if time_limit_s > 0 and time.time() - t0 > time_limit_s:
+            break
         u = synth.uniform(seed * 31337 + i, 1)[0]
-        n = int(n_range[0] + (n_range[1] - n_range[0]) * u)
-        locs, Z, th = field(ctx, seed, i, n)
-        F[i] = features(ctx, locs, Z)
-        T[i] = theta_to_x(th)
-    return F, T
+        n = int(n_range[0] * (n_range[1] / n_range[0]) ** u)
+        three = three_d_every > 0 and i % three_d_every == three_d_every - 1
+        try:
+            locs, Z, th = field(ctx, seed, i, n, three)
+        except hmle.HmleError as e:
+            if e.status != 5:
+                raise
+            continue            # a field whose ranks overflow even at 1e-6: skipped
+        F[k] = features(ctx, locs, Z)
+        T[k] = theta_to_x(th)
+        k += 1
+    return F[:k], T[:k]
 
 
 def compare_starts(ctx, model: LearnedStart, fields, **fit_kw):
@@ -220,28 +239,34 @@ def main():
     """Train on simulated fields, then fit held-out fields from the default
     and from the learned start; prints one JSON summary.
 
-        python -m paper_2104_07146_gb300.learned_start [--train 400] [--test 6] [--n 2000]
+        python -m paper_2104_07146_gb300.learned_start [--train 200000] [--time 600]
+                                                       [--test 6] [--n 2000]
+
+    Training fields: n log-uniform in [4096, 16384], every fourth one 3-D,
+    as many of --train as --time seconds of simulation allow.
     """
     import argparse
     import json
     ap = argparse.ArgumentParser()
-    ap.add_argument("--train", type=int, default=400)
+    ap.add_argument("--train", type=int, default=200_000)
+    ap.add_argument("--time", type=float, default=600.0)
     ap.add_argument("--test", type=int, default=6)
     ap.add_argument("--n", type=int, default=2000)
-    ap.add_argument("--epochs", type=int, default=400)
+    ap.add_argument("--epochs", type=int, default=200)
     a = ap.parse_args()
     ctx = hmle.Context()
     t0 = time.time()
-    F, T = training_set(ctx, a.train, seed=11)
+    F, T = training_set(ctx, a.train, seed=11, n_range=(4096, 16384), three_d_every=4,
+                        time_limit_s=a.time)
     t_data = time.time() - t0
     model = LearnedStart(ctx, seed=1)
     t0 = time.time()
-    l0, l1 = model.train(F, T, epochs=a.epochs, batch=32, lr=2e-3, seed=3)
+    l0, l1 = model.train(F, T, epochs=a.epochs, batch=64, lr=1e-3, seed=3)
     t_train = time.time() - t0
     fields = [field(ctx, 977, i, a.n) for i in range(a.test)]
     rows, tot = compare_starts(ctx, model, fields)
     err = lambda th, ref: [abs(u - v) for u, v in zip(theta_to_x(th), theta_to_x(ref))]
-    out = {"train_fields": a.train, "data_s": t_data, "train_s": t_train, "loss_first": l0,
+    out = {"train_fields": int(F.shape[0]), "train_requested": a.train, "data_s": t_data, "train_s": t_train, "loss_first": l0,
            "loss_last": l1, "test_fields": a.test, "n": a.n, "totals": tot,
            "fields": [{"theta_true": r["theta"], "fallback": r["fallback"],
                        "x_err_learned_start": err(r["learned"]["theta0"], r["theta"]),

@@ -112,4 +112,4 @@ def test_opts_default_and_null_arguments():
 def test_mlp_parameter_count_matches_the_oracle():
     # 35-64-64-8 perceptron: weights and biases of three layers
     _, L = _lib()
-    assert L.hmle_mlp_nparams() == oracle_ls.NPARAMS == 35 * 64 + 64 + 64 * 64 + 64 + 64 * 8 + 8
+    assert L.hmle_mlp_nparams() == oracle_ls.NPARAMS == 35 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 8 + 8

@@ -376,6 +376,27 @@ def test_autotune_picks_a_timed_trial(ctx):
     assert all(t["evals_per_s"] > 0 for t in trials)      # no candidate failed
     assert {t["leaf_size"] for t in trials} <= {32, 64, 128}
     assert all(t["concurrency"] in (1, 2, 4) for t in trials)
+    # the batch sizes tried at concurrency c: c, c / 2, c / 4 (at least 1)
+    assert all(t["batch_size"] in {max(1, t["concurrency"] // k) for k in (1, 2, 4)} for t in trials)
+    assert {t["batch_size"] for t in trials if t["concurrency"] == 4} == {4, 2, 1}
+
+
+def test_batch_sizes_give_the_same_bits(ctx):
+    # the evaluations per launch (gridDim.z) and the sub-batches side by side
+    # change nothing in the results: every output element is computed by the
+    # same code in the same order whatever evaluation slot it lands in
+    from paper_2104_07146_gb300 import hmle
+    locs = synth.locations_blobs(3000, 2, 0.3, 8, 0.03, seed=77)
+    Z = synth.normal(78, 3000)
+    thetas = [(0.05 + 0.01 * k, 0.5 + 0.1 * k, 1.0, 1e-3) for k in range(7)]
+    t = _tree(ctx, locs, leaf_size=32, aca_eps=1e-7, max_rank=48, oversample=16)
+    ref = [t.loglik(th, Z)[0] for th in thetas]
+    for bs in (1, 3, 7):
+        assert hmle.lib().hmle_tree_set_batch_size(t._h, bs) == 0
+        ll, st = t.loglik_batch(thetas, Z, concurrency=7)
+        assert [int(x) for x in st] == [0] * 7
+        assert list(ll) == ref, bs
+    assert hmle.lib().hmle_tree_set_batch_size(t._h, 0) == 1
 
 
 @pytest.mark.slow

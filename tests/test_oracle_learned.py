@@ -47,7 +47,7 @@ def test_sample_indices_spread_over_the_input():
 
 def _params(seed):
     rng = np.random.default_rng(seed)
-    return rng.normal(0, 0.3, ls.NPARAMS)
+    return rng.normal(0, 0.1, ls.NPARAMS)
 
 
 def test_gradient_matches_finite_differences():
@@ -59,7 +59,7 @@ def test_gradient_matches_finite_differences():
     for j in rng.choice(ls.NPARAMS, 40, replace=False):
         e = np.zeros_like(p)
         e[j] = 1e-6
-        fd = (ls.nll(ls.mlp_forward(p + e, X)[2], T) - ls.nll(ls.mlp_forward(p - e, X)[2], T)) / 2e-6
+        fd = (ls.nll(ls.mlp_forward(p + e, X)[-1], T) - ls.nll(ls.mlp_forward(p - e, X)[-1], T)) / 2e-6
         assert abs(fd - g[j]) <= 1e-6 * max(1.0, abs(fd)), (j, fd, g[j])
 
 
@@ -77,3 +77,31 @@ def test_adam_first_step_is_lr_times_sign():
     # m_hat = g, v_hat = g^2: the step is lr g / (|g| + eps)
     assert np.allclose(p1, p - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_bf16_rounding_by_hand():
+    # 8 significant bits: 1 + 2^-8 is a tie between 1 and 1 + 2^-7 and goes
+    # to the even one (1); 1 + 3 2^-9 rounds up; the FP32 rounding comes first
+    x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -9, 1.0 + 2.0 ** -7 + 2.0 ** -8, -3.0, 0.0,
+                  1.0 + 2.0 ** -8 + 2.0 ** -30])
+    r = ls.bf16(x)
+    assert list(r) == [1.0, 1.0, 1.0 + 2.0 ** -7, 1.0 + 2.0 ** -6, -3.0, 0.0, 1.0]
+    y = np.random.default_rng(3).normal(size=1000) * 10.0 ** np.random.default_rng(4).uniform(-5, 5, 1000)
+    assert np.all(np.abs(ls.bf16(y) - y) <= (2.0 ** -8 + 2.0 ** -24) * np.abs(y))
+    assert np.array_equal(ls.bf16(ls.bf16(y)), ls.bf16(y))
+
+
+def test_bf16_products_only_round_the_operands():
+    # with bf16=True the forward pass equals the FP64 pass of a network whose
+    # every product operand was rounded: check the first layer by hand
+    rng = np.random.default_rng(6)
+    p = _params(7)
+    X = rng.normal(size=(5, ls.NF))
+    (W1, b1) = ls.unpack(p)[0]
+    H1 = np.tanh(ls.bf16(X) @ ls.bf16(W1).T + b1)
+    assert np.allclose(ls.mlp_forward(p, X, bf16=True)[0], H1, rtol=0, atol=1e-14)
+    # and its gradient is the FP64 gradient up to the operand rounding
+    T = rng.normal(size=(5, 4))
+    g, gb = ls.mlp_grad(p, X, T), ls.mlp_grad(p, X, T, bf16=True)
+    assert np.max(np.abs(g - gb)) <= 0.05 * np.max(np.abs(g))
+    assert not np.array_equal(g, gb)
