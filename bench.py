@@ -189,10 +189,12 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    # kernels of one step: the batch's sweep (each launch serves all B
-    # evaluations, gridDim.z = B) plus, per evaluation, the three assembly
-    # launches, the permutation of Z and the final reduction
-    launches = args.steps * (info.kernel_launches - 5 + 5 * args.batch)
+    # kernels of one step: the sweeps of the ceil(B / batch_size) sub-batches
+    # (each launch serves batch_size evaluations, gridDim.z) plus, per
+    # evaluation, the three assembly launches, the permutation of Z and the
+    # final reduction (a single evaluation's count holds those five)
+    nsub = -(-args.batch // tree.opts.batch_size)
+    launches = args.steps * (nsub * (info.kernel_launches - 5) + 5 * args.batch)
     # roofline kernel: every launch of it in one batched step (B evaluations
     # per launch, the bench's launch configuration), bracketed by CUDA events
     # on its launching stream; the step's sweep is then launched directly,
@@ -201,7 +203,8 @@ def run_gpu(args):
     step(Zd)
     dom = prof.read()
     prof.enable(False)
-    dom["mode"] = "one batched step of %d evaluations, direct launches" % args.batch
+    dom["mode"] = ("one batched step of %d evaluations (%d per launch), direct launches"
+                   % (args.batch, tree.opts.batch_size))
     # e2e: host Z (pinned) through the C ABI; the copy in and the result out
     # are inside the timed region
     e2 = torch.cuda.Event(enable_timing=True)
@@ -481,7 +484,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--cpu-sample-n", type=int, default=8192)
+    ap.add_argument("--cpu-sample-n", type=int, default=16384)
     ap.add_argument("--batch", type=int, default=32,
                     help="concurrent theta evaluations per step (hmle_loglik_batch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -116,7 +116,7 @@ typedef struct {
  *             approximation; the accuracy then varies from block to block and
  *             no rank overflow is reported).
  *  batch_size evaluations of hmle_loglik_batch served by one launch of every
- *             sweep kernel (gridDim.z), in [1, 64]; default 4.  A batch of
+ *             sweep kernel (gridDim.z), in [1, 64]; default 2.  A batch of
  *             concurrency evaluations runs as ceil(concurrency / batch_size)
  *             such launches sequences on their own streams, side by side, and
  *             the mixed forms' PCG solves all of them in one lockstep
@@ -181,7 +181,7 @@ typedef struct hmle_hfactor hmle_hfactor;
 
 /* Fill *opts with defaults: leaf 64, eta 2, aca_eps 1e-8, max_rank 32,
  * oversample 8, FP64, seed 0x5eed, leaf_lowrank 0, pcg_tol 1e-10,
- * pcg_max_iter 50, fixed_rank 0, batch_size 4.  HMLE_OK for non-NULL opts, else
+ * pcg_max_iter 50, fixed_rank 0, batch_size 2.  HMLE_OK for non-NULL opts, else
  * INVALID_ARG. */
 hmle_status hmle_opts_default(hmle_opts *opts);
 

@@ -72,6 +72,8 @@ def _load():
         lib.oracle_matern_cross.restype = i32
         lib.oracle_forward_solve.argtypes = [i64, p, p, p]
         lib.oracle_forward_solve.restype = i32
+        lib.oracle_cholesky.argtypes = [i64, p]
+        lib.oracle_cholesky.restype = i32
         _lib = lib
     return _lib
 
@@ -129,9 +131,26 @@ def forward_solve(L: np.ndarray, z: np.ndarray) -> np.ndarray:
     return w
 
 
+PLAIN_CHOLESKY_MAX_N = 2048
+
+
+def cholesky_plain(C: np.ndarray) -> np.ndarray:
+    """Dense Cholesky factor by the unblocked row-by-row algorithm written
+    out in the oracle's C code; raises numpy.linalg.LinAlgError when C is not
+    positive definite."""
+    A = np.array(C, dtype=np.float64, order="C", copy=True)
+    if _load().oracle_cholesky(A.shape[0], _ptr(A)) != 0:
+        raise np.linalg.LinAlgError("non-positive pivot")
+    return A
+
+
 def cholesky(C: np.ndarray) -> np.ndarray:
-    """Dense Cholesky factor (LAPACK dpotrf through numpy); raises
+    """Dense Cholesky factor: the plain algorithm (cholesky_plain) up to
+    n = 2048, LAPACK dpotrf through numpy above (the same factor to rounding:
+    a pin checks the two against each other); raises
     numpy.linalg.LinAlgError when C is not positive definite."""
+    if C.shape[0] <= PLAIN_CHOLESKY_MAX_N:
+        return cholesky_plain(C)
     return np.linalg.cholesky(C)
 
 

@@ -168,3 +168,27 @@ int oracle_forward_solve(int64_t n, const double *L, const double *z,
   }
   return 0;
 }
+
+/* C = L L^T by the unblocked row-by-row (Cholesky-Banachiewicz) algorithm,
+ * in place on a row-major n x n array: for row i and j <= i,
+ * s = C_ij - sum_{k<j} L_ik L_jk, then L_ij = s / L_jj (j < i) and
+ * L_ii = sqrt(s).  The strict upper triangle is zeroed.  Returns 1 at a
+ * non-positive pivot. */
+int oracle_cholesky(int64_t n, double *A) {
+  for (int64_t i = 0; i < n; ++i) {
+    double *Li = A + i * n;
+    for (int64_t j = 0; j <= i; ++j) {
+      const double *Lj = A + j * n;
+      double s = Li[j];
+      for (int64_t k = 0; k < j; ++k) s -= Li[k] * Lj[k];
+      if (j < i) {
+        Li[j] = s / Lj[j];
+      } else {
+        if (!(s > 0)) return 1;
+        Li[i] = sqrt(s);
+      }
+    }
+    for (int64_t j = i + 1; j < n; ++j) Li[j] = 0.0;
+  }
+  return 0;
+}

@@ -653,7 +653,7 @@ hmle_status hmle_opts_default(hmle_opts *o) {
   o->seed = 0x5eed;
   o->leaf_lowrank = 0;
   o->fixed_rank = 0;
-  o->batch_size = 4;
+  o->batch_size = 2;
   return HMLE_OK;
 }
 

@@ -1,22 +1,31 @@
-"""The large configuration: one H-matrix log-likelihood evaluation at
+"""The large configuration: H-matrix log-likelihood evaluations at
 n = 2,000,000 (80 % uniform + 20 % in 8 Gaussian blobs, Matern ell = 0.02,
-nu = 0.5, sigma2 = 1, tau2 = 1e-3, leaf 128, eta 2, ACA eps 1e-5).
+nu = 0.5 or 1.0, sigma2 = 1, tau2 = 1e-3, leaf 128, eta 2, ACA eps 1e-5).
 
-    python -m paper_2104_07146_gb300.large [--n 2000000] [--nu 0.5] [--precision 0|1]
+    python -m paper_2104_07146_gb300.large [--n 2000000] [--nu 0.5] [--precision 0|1|2]
 
-Prints one JSON line: tree build time, the times of two evaluations (the
+Prints one JSON line: tree build time, the times of the evaluations (the
 first includes buffer allocation and graph capture), log|C~|, Z^T C~^-1 Z,
-ranks, the algorithmic flops of the sweep and the device memory in use.  Z is
+ranks, the algorithmic flops of the sweep and their rate against the FP64
+peak, the device memory in use against the 180 GB budget of this
+configuration, and a check that holds at any size: the evaluation at
+(sigma2, tau2) scaled by 4 must give log|C~| + n log 4 and Z^T C~^-1 Z / 4
+(every decision of the method is relative, and 4 is exact in binary), so
+|dL| / n of the scaled evaluation against that prediction is reported.  Z is
 seeded white noise: the time of an evaluation does not depend on Z, and a
-field simulated at this size would need a second, tighter factorisation.
+field simulated at this size at eps 1e-9 would need a factor far larger
+than the one at 1e-5.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import time
 
 from . import hmle, synth
+
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x FP64 FMA/clk x 2 flops x GHz (max clock)
 
 
 def main():
@@ -30,6 +39,7 @@ def main():
     locs = synth.locations_blobs(a.n, 2, c["frac_blob"], c["nblobs"], c["sd"], c["seed"])
     Z = synth.normal(c["seed"] + 1, a.n)
     th = (c["theta"][0], a.nu, c["theta"][2], c["theta"][3])
+    th4 = (th[0], th[1], 4.0 * th[2], 4.0 * th[3])
     ctx = hmle.Context()
     t0 = time.time()
     tree = hmle.Tree(ctx, locs, leaf_size=c["leaf"], eta=c["eta"], aca_eps=c["aca_eps"],
@@ -42,18 +52,32 @@ def main():
         ll, info = tree.loglik(th, Z)
         times.append(time.time() - t0)
     free, total = torch.cuda.mem_get_info()
+    t0 = time.time()
+    ll4, info4 = tree.loglik(th4, Z)
+    t4 = time.time() - t0
+    n = a.n
+    expect = ll - 0.5 * n * math.log(4.0) - 0.5 * info.quad * (0.25 - 1.0)
+    rate = info.flops / times[1] / 1e9 if times[1] > 0 else None
     print(json.dumps({
         "config": "large: n=%d, 80%% uniform + 20%% in 8 blobs (sd 0.03), Matern ell=%g nu=%g "
                   "sigma2=1 tau2=1e-3, leaf %d, eta %g, ACA eps %g, rank capacity 48, "
                   "oversampling 16, %s; Z white noise"
-                  % (a.n, th[0], a.nu, c["leaf"], c["eta"], c["aca_eps"],
-                     "mixed FP32 + PCG" if a.precision else "FP64"),
+                  % (n, th[0], a.nu, c["leaf"], c["eta"], c["aca_eps"],
+                     {0: "FP64", 1: "mixed FP32-class tensor-core products + PCG",
+                      2: "mixed 16-bit tensor-core products + PCG"}[a.precision]),
         "tree_build_s": t_tree, "leaves": ti.n_leaves, "dense_blocks": ti.n_dense,
-        "lowrank_blocks": ti.n_lowrank, "eval_s": times, "loglik": ll, "logdet": info.logdet,
+        "lowrank_blocks": ti.n_lowrank, "eval_s": times, "evals_per_s": 1.0 / times[1],
+        "loglik": ll, "logdet": info.logdet,
         "quad": info.quad, "max_rank_c": info.max_rank_c, "max_rank_l": info.max_rank_l,
         "mean_rank_l": info.mean_rank_l, "pcg_iters": info.pcg_iters,
-        "sweep_gflop": info.flops / 1e9, "kernel_launches": info.kernel_launches,
-        "device_gb_in_use": (total - free) / 1e9, "device_gb_total": total / 1e9}))
+        "sweep_gflop": info.flops / 1e9, "sweep_gflops_per_s": rate,
+        "fp64_peak_frac": rate / FP64_PEAK_GFLOPS if rate else None,
+        "kernel_launches": info.kernel_launches,
+        "device_gb_in_use": (total - free) / 1e9, "device_gb_total": total / 1e9,
+        "budget_gb": 180.0,
+        "scaling_check": {"theta4_eval_s": t4, "logdet_dev_per_point": (info4.logdet - info.logdet - n * math.log(4.0)) / n,
+                          "quad_rel_dev": (info4.quad - info.quad / 4.0) / (info.quad / 4.0),
+                          "dL_per_point": abs(ll4 - expect) / n}}))
 
 
 if __name__ == "__main__":

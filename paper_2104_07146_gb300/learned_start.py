@@ -171,7 +171,7 @@ def field(ctx, seed: int, i: int, n: int, three_d: bool = False):
     xi = synth.normal(seed * 104729 + i, n)
     leaf = 32 if n <= 3000 else 64
     for eps in (1e-8, 1e-6):
-        tree = hmle.Tree(ctx, locs, leaf_size=leaf, aca_eps=eps, max_rank=64, oversample=16)
+        tree = hmle.Tree(ctx, locs, leaf_size=leaf, aca_eps=eps, max_rank=48, oversample=16)
         try:
             Z = tree.simulate(th, xi)
             return locs, Z, th

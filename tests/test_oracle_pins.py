@@ -418,3 +418,17 @@ def test_profile_likelihood_of_white_noise_in_closed_form():
     ref = -0.5 * n * math.log(2 * math.pi) - 0.5 * n * math.log(s2_ref) \
         - 0.5 * n * math.log(1 + rho) - 0.5 * n
     assert abs(lp - ref) <= 1e-10 * abs(ref)
+
+
+def test_plain_cholesky_is_the_library_factor():
+    # the oracle's written-out row-by-row Cholesky against LAPACK's (the
+    # factor of an SPD matrix is unique), and its refusal of an indefinite one
+    n = 400
+    locs = synth.locations_uniform(n, 2, seed=17)
+    C = oracle.matern_matrix(locs, (0.1, 1.5, 1.0, 1e-4))
+    L = oracle.cholesky_plain(C)
+    assert np.allclose(L, np.tril(L), rtol=0, atol=0)
+    assert np.max(np.abs(L - np.linalg.cholesky(C))) <= 1e-12
+    assert np.max(np.abs(L @ L.T - C)) <= 1e-12
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.cholesky_plain(np.array([[1.0, 2.0], [2.0, 1.0]]))
