@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "hmle_internal.h"
@@ -59,10 +60,20 @@ __device__ bool grid_barrier(unsigned *bar, unsigned nblk, long long limit = kBa
   return *(volatile unsigned *)(bar + 2) == 0u;
 }
 
-// One warp solves L x = w (forward) or L^T x = w (backward) for the m <= 128
-// rows of a diagonal leaf, L = the b x b dense block at off (ld b); lanes own
-// rows lane, lane + 32, ...
-__device__ void leaf_trsv(const double *__restrict__ L, int b, int m, double *w, bool trans) {
+// The diagonal leaf's triangular solve L x = w (forward) or L^T x = w
+// (backward), m <= 128 rows, L the b x b dense block at L (ld b).  Its lower
+// triangle is first staged in shared memory, packed by rows
+// (P[r (r + 1) / 2 + c] = L[r, c], c <= r): the whole CTA loads it with
+// coalesced reads, then one warp runs the substitution (lanes own rows lane,
+// lane + 32, ...) with no global-memory latency in its dependent chain.
+__device__ void stage_leaf(const double *__restrict__ L, int b, int m, double *P) {
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int r = e % m, c = e / m;
+    if (c <= r) P[r * (r + 1) / 2 + c] = L[r + (int64_t)c * b];
+  }
+}
+
+__device__ void leaf_trsv_packed(const double *P, int m, double *w, bool trans) {
   const int lane = threadIdx.x & 31;
   double x[4];
 #pragma unroll
@@ -74,13 +85,13 @@ __device__ void leaf_trsv(const double *__restrict__ L, int b, int m, double *w,
 #pragma unroll
     for (int q = 0; q < 4; ++q)
       if (q == slot) xi = x[q];
-    xi = __shfl_sync(0xffffffffu, xi, owner) / L[i + (int64_t)i * b];
+    xi = __shfl_sync(0xffffffffu, xi, owner) / P[i * (i + 1) / 2 + i];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int r = lane + 32 * q;
       if (r == i) x[q] = xi;
       else if (r < m && (trans ? r < i : r > i))
-        x[q] = fma(-(trans ? L[i + (int64_t)r * b] : L[r + (int64_t)i * b]), xi, x[q]);
+        x[q] = fma(-(trans ? P[i * (i + 1) / 2 + r] : P[r * (r + 1) / 2 + i]), xi, x[q]);
     }
   }
 #pragma unroll
@@ -109,15 +120,18 @@ struct SolveArgs {
 };
 
 __global__ void __launch_bounds__(kSolveThreads) k_solve_fwd(SolveArgs S) {
+  extern __shared__ double leafP[];   // the packed lower triangle of one diagonal leaf
   const unsigned G = gridDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int K = 0; K < S.nleaf; ++K) {
-    if (warp == 0)
-      for (int z = blockIdx.x; z < S.nz; z += G) {
-        const FactorArgs F = S.F.at(z);
-        const BlockDesc D = F.blocks[S.diag[K]];
-        leaf_trsv(F.D + D.off_d, F.b, D.rend - D.rbeg, S.w + z * S.zs + D.rbeg, false);
-      }
+    for (int z = blockIdx.x; z < S.nz; z += G) {
+      const FactorArgs F = S.F.at(z);
+      const BlockDesc D = F.blocks[S.diag[K]];
+      stage_leaf(F.D + D.off_d, F.b, D.rend - D.rbeg, leafP);
+      __syncthreads();
+      if (warp == 0) leaf_trsv_packed(leafP, D.rend - D.rbeg, S.w + z * S.zs + D.rbeg, false);
+      __syncthreads();
+    }
     if (!grid_barrier(S.bar, G)) return;
     // B: h_A = W_A^T w[cols A], a warp per component
     const int nb = S.s0[K + 1] - S.s0[K];
@@ -171,15 +185,18 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_fwd(SolveArgs S) {
 }
 
 __global__ void __launch_bounds__(kSolveThreads) k_solve_bwd(SolveArgs S) {
+  extern __shared__ double leafP[];   // the packed lower triangle of one diagonal leaf
   const unsigned G = gridDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int K = S.nleaf - 1; K >= 0; --K) {
-    if (warp == 0)
-      for (int z = blockIdx.x; z < S.nz; z += G) {
-        const FactorArgs F = S.F.at(z);
-        const BlockDesc D = F.blocks[S.diag[K]];
-        leaf_trsv(F.D + D.off_d, F.b, D.rend - D.rbeg, S.w + z * S.zs + D.rbeg, true);
-      }
+    for (int z = blockIdx.x; z < S.nz; z += G) {
+      const FactorArgs F = S.F.at(z);
+      const BlockDesc D = F.blocks[S.diag[K]];
+      stage_leaf(F.D + D.off_d, F.b, D.rend - D.rbeg, leafP);
+      __syncthreads();
+      if (warp == 0) leaf_trsv_packed(leafP, D.rend - D.rbeg, S.w + z * S.zs + D.rbeg, true);
+      __syncthreads();
+    }
     if (!grid_barrier(S.bar, G)) return;
     // B: h_A = U_A^T v[rows A] for the low-rank blocks whose rows start at K
     const int nb = S.s0[K + 1] - S.s0[K];
@@ -237,25 +254,34 @@ __global__ void k_barrier_selftest(unsigned *bar, unsigned expect, long long lim
   grid_barrier(bar, expect, limit);
 }
 
-int g_solve_grid = 0;
+// shared memory of the packed leaf (b (b + 1) / 2 doubles) for leaf size b
+int leaf_smem(int b) { return b * (b + 1) / 2 * (int)sizeof(double); }
 
-int solve_grid() {
-  if (g_solve_grid == 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_fwd, kSolveThreads, 0);
-    int per2 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_solve_bwd, kSolveThreads, 0);
-    per = std::min(per, per2);
-    g_solve_grid = std::max(1, std::min(per, 2) * sms);
-  }
-  return g_solve_grid;
+// the cooperative grid: at most 2 CTAs per SM, as many as fit with smem bytes
+// of dynamic shared memory (cached per size)
+int solve_grid(int smem = 0) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  static int cached_smem[4] = {-1, -1, -1, -1}, cached_grid[4] = {0, 0, 0, 0};
+  for (int k = 0; k < 4; ++k)
+    if (cached_smem[k] == smem) return cached_grid[k];
+  int dev = 0, sms = 0, per = 0, per2 = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaFuncSetAttribute(k_solve_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_smem(kMaxLeaf));
+  cudaFuncSetAttribute(k_solve_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_smem(kMaxLeaf));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_fwd, kSolveThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_solve_bwd, kSolveThreads, smem);
+  const int g = std::max(1, std::min(std::min(per, per2), 2) * sms);
+  for (int k = 0; k < 4; ++k)
+    if (cached_smem[k] < 0) { cached_smem[k] = smem; cached_grid[k] = g; break; }
+  return g;
 }
 
 cudaError_t launch_coop(const void *fn, SolveArgs &S, cudaStream_t st) {
   void *args[] = {&S};
-  return cudaLaunchCooperativeKernel(fn, dim3(solve_grid()), dim3(kSolveThreads), args, 0, st);
+  const int smem = leaf_smem(S.F.b);
+  return cudaLaunchCooperativeKernel(fn, dim3(solve_grid(smem)), dim3(kSolveThreads), args, smem, st);
 }
 
 }  // namespace
