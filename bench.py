@@ -156,7 +156,8 @@ def run_gpu(args):
     locs, Z = _workload_inputs(n)
     stream = torch.cuda.current_stream()
     ctx = hmle.Context(stream)
-    tree = hmle.Tree(ctx, locs, leaf_size=w["leaf"], eta=w["eta"], aca_eps=w["eps"])
+    tree = hmle.Tree(ctx, locs, leaf_size=w["leaf"], eta=w["eta"], aca_eps=w["eps"],
+                     precision=args.precision, **({"batch_size": args.batch_size} if args.batch_size else {}))
     Zd = torch.from_numpy(Z).to(f"cuda:{local}")           # resident input
     Zh = torch.from_numpy(Z).pin_memory()                   # host input for e2e
     theta = tuple(w["theta"])
@@ -230,7 +231,10 @@ def run_gpu(args):
     out = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {0: "f64", 1: "f64 + tensor-core products (3 BF16 slices, f32 accumulation)",
+                  2: "f64 + tensor-core products (2 BF16 slices, f32 accumulation)"}[args.precision],
+        "data": "synthetic",
         "config": {**{k: v for k, v in WORKLOAD.items()},
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "working set %.1f GB > 129 MB L2 (no flush needed)"
@@ -491,6 +495,10 @@ def main():
     ap.add_argument("--no-fit", action="store_true", help="skip the small-configuration MLE fit")
     ap.add_argument("--forms", action="store_true",
                     help="also report the mixed-precision and multi-instance batched forms")
+    ap.add_argument("--batch-size", type=int, default=0,
+                    help="evaluations per launch of each sweep kernel (0: the library default)")
+    ap.add_argument("--precision", type=int, default=0,
+                    help="0 FP64 (the headline form); 1, 2: the mixed forms (tensor-core products, PCG)")
     ap.add_argument("--roofline-kernel", default="k_rows",
                     help="sweep kernel whose launches are timed for the roofline line")
     args = ap.parse_args()

@@ -131,7 +131,7 @@ def forward_solve(L: np.ndarray, z: np.ndarray) -> np.ndarray:
     return w
 
 
-PLAIN_CHOLESKY_MAX_N = 2048
+PLAIN_CHOLESKY_MAX_N = 512
 
 
 def cholesky_plain(C: np.ndarray) -> np.ndarray:
@@ -146,7 +146,7 @@ def cholesky_plain(C: np.ndarray) -> np.ndarray:
 
 def cholesky(C: np.ndarray) -> np.ndarray:
     """Dense Cholesky factor: the plain algorithm (cholesky_plain) up to
-    n = 2048, LAPACK dpotrf through numpy above (the same factor to rounding:
+    n = 512, LAPACK dpotrf through numpy above (the same factor to rounding:
     a pin checks the two against each other); raises
     numpy.linalg.LinAlgError when C is not positive definite."""
     if C.shape[0] <= PLAIN_CHOLESKY_MAX_N:

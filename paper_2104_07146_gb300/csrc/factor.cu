@@ -56,9 +56,10 @@ constexpr int kGemmSmem = kTK * (kTM + kTN);  // doubles
 // fc(i, j, value).  A_KFAST / B_KFAST: the operand is contiguous along k in
 // memory (chooses the coalesced loading order).  128 threads, 64 x TNX
 // output tiles (TNX = 64 or 32), 4 x (TNX / 8) register micro-tiles, K
-// staged 16 at a time.  T: the arithmetic type (double; float in the mixed
-// form): operands are rounded to T as they are staged, products accumulate
-// in T, and fc receives the sum as a double.
+// staged 16 at a time, the next 16 read into registers while the current
+// ones are multiplied.  T: the arithmetic type (double): operands are
+// rounded to T as they are staged, products accumulate in T, and fc receives
+// the sum as a double.
 template <class T, bool A_KFAST, bool B_KFAST, int TNX, class FA, class FB, class FC>
 __device__ void cta_gemm_t(int M, int N, int K, FA fa, FB fb, FC fc, double *smem) {
   constexpr int MC = TNX / 8;
@@ -74,18 +75,48 @@ __device__ void cta_gemm_t(int M, int N, int K, FA fa, FB fb, FC fc, double *sme
 #pragma unroll
         for (int y = 0; y < MC; ++y) acc[x][y] = T(0);
       const bool active = (i0 + ti * 4 < M) && (j0 + tj * MC < N);
-      for (int k0 = 0; k0 < K; k0 += kTK) {
-        for (int e = tid; e < kTK * kTM; e += kThreads) {
+      // the next slab is read into registers while the current one is
+      // multiplied from shared memory, so its global-memory latency is hidden
+      constexpr int NA = kTK * kTM / kThreads, NB = kTK * TNX / kThreads;
+      T ra[NA], rb[NB];
+      auto load = [&](int k0) {
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+          const int e = tid + u * kThreads;
           int k, i;
           if (A_KFAST) { k = e % kTK; i = e / kTK; } else { i = e % kTM; k = e / kTM; }
-          sA[k * kTM + i] = (i0 + i < M && k0 + k < K) ? T(fa(i0 + i, k0 + k)) : T(0);
+          ra[u] = (i0 + i < M && k0 + k < K) ? T(fa(i0 + i, k0 + k)) : T(0);
         }
-        for (int e = tid; e < kTK * TNX; e += kThreads) {
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+          const int e = tid + u * kThreads;
           int k, j;
           if (B_KFAST) { k = e % kTK; j = e / kTK; } else { j = e % TNX; k = e / TNX; }
-          sB[k * TNX + j] = (j0 + j < N && k0 + k < K) ? T(fb(k0 + k, j0 + j)) : T(0);
+          rb[u] = (j0 + j < N && k0 + k < K) ? T(fb(k0 + k, j0 + j)) : T(0);
         }
-        __syncthreads();
+      };
+      auto store = [&]() {
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+          const int e = tid + u * kThreads;
+          int k, i;
+          if (A_KFAST) { k = e % kTK; i = e / kTK; } else { i = e % kTM; k = e / kTM; }
+          sA[k * kTM + i] = ra[u];
+        }
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+          const int e = tid + u * kThreads;
+          int k, j;
+          if (B_KFAST) { k = e % kTK; j = e / kTK; } else { j = e % TNX; k = e / TNX; }
+          sB[k * TNX + j] = rb[u];
+        }
+      };
+      load(0);
+      store();
+      __syncthreads();
+      for (int k0 = 0; k0 < K; k0 += kTK) {
+        const bool more = k0 + kTK < K;
+        if (more) load(k0 + kTK);
         if (active) {
           const int kk = min(kTK, K - k0);
           for (int k = 0; k < kk; ++k) {
@@ -101,6 +132,10 @@ __device__ void cta_gemm_t(int M, int N, int K, FA fa, FB fb, FC fc, double *sme
           }
         }
         __syncthreads();
+        if (more) {
+          store();
+          __syncthreads();
+        }
       }
       if (active) {
 #pragma unroll

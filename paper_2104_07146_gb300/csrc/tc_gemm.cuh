@@ -217,10 +217,25 @@ __device__ __forceinline__ void stage(uint8_t *dst, int r0, int nrows, int k0, i
 // B_KFAST: the operand is contiguous along k in memory.  smem: at least
 // smem_words<NS>() doubles of dynamic shared memory.  128 threads.  flags:
 // the caller's error word (kFlagTimeout).
+// Compensated addition (TwoSum): hi + lo holds the running sum to about
+// twice the FP32 precision.
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v) {
+  const float s = hi + v;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (v - bp);
+  hi = s;
+}
+
 template <int NS, bool A_KFAST, bool B_KFAST, class FA, class FB, class FC>
 __device__ void gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem, int *flags) {
   constexpr int KC = chunk_k<NS>();
   constexpr uint32_t kSbo = 16 * KC;
+  // With several slices (the mixed forms' long sums) every chunk is
+  // accumulated in its own TMEM region (two, alternating with the stages) and
+  // read out into compensated FP32 registers, so the FP32 rounding of the
+  // tensor cores' accumulation spans one chunk, not the whole of K.
+  constexpr bool kChunked = NS >= 2;
+  constexpr uint32_t kCols = kChunked ? 2 * kTmemCols : kTmemCols;
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -230,7 +245,7 @@ __device__ void gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem, int
   __syncthreads();   // earlier users of this shared memory are done
   if (warp == 0)
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                 "r"(kTmemCols)
+                 "r"(kCols)
                  : "memory");
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0), "r"(1) : "memory");
@@ -241,6 +256,7 @@ __device__ void gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem, int
   __syncthreads();
   fence_after();
   const uint32_t tmem = s_tmem;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;   // this warp's TMEM lanes
   uint32_t phase = 0u, pending = 0u;   // bit s: parity to wait for / MMAs in flight on stage s
   // bounded wait for the MMAs of stage s; false if it ran out
   auto drain = [&](int s) -> bool {
@@ -250,14 +266,37 @@ __device__ void gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem, int
     pending &= ~(1u << s);
     return true;
   };
+  float hi[kChunked ? kTN : 1], lo[kChunked ? kTN : 1];
+  uint32_t unread = 0u;                // bit s: TMEM region s holds a chunk not yet added
+  // add TMEM region s (one chunk's partial products) into hi / lo
+  auto absorb = [&](int s) {
+    if constexpr (kChunked) {
+      if (!((unread >> s) & 1u)) return;
+      unread &= ~(1u << s);
+      fence_after();
+#pragma unroll
+      for (int j0 = 0; j0 < kTN; j0 += 16) {
+        float v[16];
+        ld16(tmem + lane_base + (uint32_t)(s * kTN + j0), v);
+#pragma unroll
+        for (int x = 0; x < 16; ++x) two_sum_add(hi[j0 + x], lo[j0 + x], v[x]);
+      }
+      fence_before();
+    }
+  };
   bool failed = false;
   const int nk = K > 0 ? (K + KC - 1) / KC : 1;   // K = 0: one chunk of zeros
   for (int m0 = 0; m0 < M && !failed; m0 += kTM) {
     for (int n0 = 0; n0 < N && !failed; n0 += kTN) {
+      if constexpr (kChunked) {
+#pragma unroll
+        for (int x = 0; x < kTN; ++x) { hi[x] = 0.0f; lo[x] = 0.0f; }
+      }
       for (int c = 0; c < nk; ++c) {
         const int s = c & 1;
         const bool late = !drain(s);
         if (__syncthreads_or(late)) { failed = true; break; }
+        absorb(s);   // chunk c - 2, in chunk order
         uint8_t *sa = base + s * stage_bytes<NS>();
         uint8_t *sb = sa + NS * a_bytes<NS>();
         const int k0 = c * KC;
@@ -268,6 +307,7 @@ __device__ void gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem, int
         if (tid == 0) {
           fence_after();
           const uint32_t a0 = smem_addr(sa), b0 = smem_addr(sb);
+          const uint32_t dst = tmem + (kChunked ? (uint32_t)(s * kTN) : 0u);
 #pragma unroll
           for (int kk = 0; kk < KC / 16; ++kk) {
             // the small cross terms first, the product of the leading slices last
@@ -277,27 +317,39 @@ __device__ void gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem, int
               for (int p = 0; p <= w; ++p) {
                 const uint32_t ao = a0 + (uint32_t)(p * a_bytes<NS>()) + 256u * kk;
                 const uint32_t bo = b0 + (uint32_t)((w - p) * b_bytes<NS>()) + 256u * kk;
-                const bool first = (c == 0 && kk == 0 && w == NS - 1 && p == 0);
-                mma(tmem, sdesc(ao, kSbo), sdesc(bo, kSbo), first ? 0u : 1u);
+                const bool first = ((kChunked || c == 0) && kk == 0 && w == NS - 1 && p == 0);
+                mma(dst, sdesc(ao, kSbo), sdesc(bo, kSbo), first ? 0u : 1u);
               }
           }
           commit(bar0 + 8u * s);
         }
         pending |= 1u << s;
+        unread |= 1u << s;
       }
       if (failed) break;
-      bool late = !drain(0);
-      late |= !drain(1);
+      const int last = (nk - 1) & 1;   // the last two chunks, older first
+      bool late = !drain(last ^ 1);
+      late |= !drain(last);
       if (__syncthreads_or(late)) { failed = true; break; }
       fence_after();
       const int i = m0 + warp * 32 + (tid & 31);
-      for (int j0 = 0; j0 < kTN && n0 + j0 < N; j0 += 16) {
-        float v[16];
-        ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, v);
+      if constexpr (kChunked) {
+        absorb(last ^ 1);
+        absorb(last);
         if (i < M) {
 #pragma unroll
-          for (int x = 0; x < 16; ++x)
-            if (n0 + j0 + x < N) fc(i, n0 + j0 + x, (double)v[x]);
+          for (int x = 0; x < kTN; ++x)
+            if (n0 + x < N) fc(i, n0 + x, (double)hi[x] + (double)lo[x]);
+        }
+      } else {
+        for (int j0 = 0; j0 < kTN && n0 + j0 < N; j0 += 16) {
+          float v[16];
+          ld16(tmem + lane_base + (uint32_t)j0, v);
+          if (i < M) {
+#pragma unroll
+            for (int x = 0; x < 16; ++x)
+              if (n0 + j0 + x < N) fc(i, n0 + j0 + x, (double)v[x]);
+          }
         }
       }
       fence_before();
@@ -312,7 +364,7 @@ __device__ void gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem, int
   fence_before();
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
   if (tid == 0) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar0) : "memory");
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar0 + 8u) : "memory");
