@@ -315,8 +315,9 @@ hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tree,
  *          shared by all evaluations;  ll  m outputs (-inf for a failed one);
  *  status  m per-evaluation statuses, or NULL.
  * Returns the first hard error (CUDA, OOM, INVALID_ARG), or HMLE_OK; NOT_SPD
- * and RANK_OVERFLOW are reported per evaluation only.  Device memory grows
- * by one evaluation's buffers per concurrent slot (kept with the tree). */
+ * and RANK_OVERFLOW are reported per evaluation only.  Device memory holds
+ * one evaluation's buffers per concurrent slot, carved from one allocation
+ * and kept with the tree while the batch shape stays the same. */
 hmle_status hmle_loglik_batch(hmle_ctx *ctx, const hmle_tree *tree, const hmle_theta *thetas,
                               int32_t m, const double *Z, int32_t concurrency, double *ll,
                               int32_t *status);
@@ -328,7 +329,10 @@ hmle_status hmle_loglik_batch(hmle_ctx *ctx, const hmle_tree *tree, const hmle_t
  * buffer of its own tree, streams and captured graph as in
  * hmle_loglik_batch.  Z of a task: n_tree doubles in caller order, host or
  * device; tasks that pass the same Z pointer share one staged copy.  ntask
- * = 0 returns HMLE_OK at once.
+ * = 0 returns HMLE_OK at once.  A tree's evaluation buffers are released
+ * after the wave of its last task, so the device holds at most the buffers
+ * of the trees of two waves: many trees of uneven n fit in one call when
+ * their tasks are grouped by tree.
  * Outputs and errors as hmle_loglik_batch. */
 typedef struct {
   const hmle_tree *tree;

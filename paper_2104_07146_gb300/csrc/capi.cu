@@ -1506,6 +1506,16 @@ hmle_status run_waves(hmle_ctx *ctx, const std::vector<TaskRef> &tasks, int W, c
                       double *ll, int32_t *status, double *ld_out = nullptr, double *q_out = nullptr) {
   const int m = (int)tasks.size();
   hmle_status first = HMLE_OK;
+  // the last task of every tree: once its wave is collected, the tree's
+  // evaluation buffers are released, so that many trees of uneven n can be
+  // evaluated in one call without holding every tree's buffers at once
+  std::vector<std::pair<hmle_tree *, int>> last;
+  for (int i = 0; i < m; ++i) {
+    bool found = false;
+    for (auto &u : last)
+      if (u.first == tasks[i].t) { u.second = i; found = true; }
+    if (!found) last.push_back({tasks[i].t, i});
+  }
   for (int i0 = 0; i0 < m; i0 += W) {
     const int cnt = std::min(W, m - i0);
     std::vector<Work *> ws(cnt, nullptr);
@@ -1596,6 +1606,11 @@ hmle_status run_waves(hmle_ctx *ctx, const std::vector<TaskRef> &tasks, int W, c
         ctx->err = wc.err;
       }
     }
+    for (auto &u : last)   // trees with no task after this wave: release their buffers
+      if (u.second >= i0 && u.second < i0 + cnt) {
+        for (Work *w : u.first->pool) free_work(w);
+        u.first->pool.clear();
+      }
   }
   return first;
 }
