@@ -43,6 +43,11 @@ WORKLOAD = dict(workload="medium: n=65536 2-D, 70% uniform + 30% in 8 blobs (sd 
                 "ell=0.05 nu=0.5 sigma2=1 tau2=1e-3, leaf 64, eta 2, ACA eps 1e-6, FP64",
                 n=65536, d=2, theta=[0.05, 0.5, 1.0, 1e-3], leaf=64, eta=2.0, eps=1e-6)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07  # SMs x FP64 FMA/clk x 2 flops x GHz (max clock)
+# DRAM bytes per launch of the FP64 k_rows in this bench's batched step:
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of five
+# launches, mean (8,458,496 + 6,790,656 + 5,495,040 + 3,072,512 + 24,783,872
+# read, nothing written)
+K_ROWS_DRAM_BYTES = 9_720_115
 
 
 def _peaks():
@@ -250,7 +255,12 @@ def run_gpu(args):
                      "flops_per_launch": dom["flops"] / max(dom["launches"], 1),
                      "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                      "frac": (achieved / FP64_PEAK_GFLOPS) if achieved else None,
-                     "traffic": None,
+                     "traffic": K_ROWS_DRAM_BYTES if args.precision == 0 else None,
+                     "traffic_source": (
+                         "dram__bytes_read.sum + dram__bytes_write.sum of 5 launches of the FP64 "
+                         "k_rows in this command's first step, mean per launch (3.1-24.8 MB read, "
+                         "0 written; profiles/k_rows_dram_bench_medium_n65536.md)"
+                         if args.precision == 0 else "not captured for this form"),
                      "note": "FP64 ALU peak from 152 SMs x 2 FMA/clk x 2070 MHz "
                              "(measured FMA loop: 1254.6 GFLOP/s); algorithmic FP64 flops of "
                              "the kernel's launches (plan x ranks of every evaluation) over "
@@ -360,11 +370,22 @@ def other_forms(ctx, locs, Z, Zd, thetas, B, fp64_value):
     for k in ok:                                                  # the same tasks one call each
         tasks[k][0].loglik(tasks[k][1], tasks[k][2])
     dt_loop = time.time() - t0
+    # the same call with failed tasks retried on derived trees (larger rank
+    # capacity, then a looser accuracy), reported per task
+    t0 = time.time()
+    ll_r, st_r, retry = ctx.loglik_multi_retry(tasks, concurrency=16, max_retries=3)
+    dt_r = time.time() - t0
     res["multi_instance"] = {"fields": [(n, d) for (_, _, n, d) in fields], "tasks": len(tasks),
                              "evals_per_s": len(tasks) / dt,
                              "looped_evals_per_s": len(ok) / dt_loop if ok else None,
                              "points_evals_per_s": sum(n for (_, _, n, _) in fields) * 4 / dt,
-                             "status": [int(x) for x in st]}
+                             "status": [int(x) for x in st],
+                             "with_retries": {
+                                 "call_s": dt_r, "status": [int(x) for x in st_r],
+                                 "ok": int(sum(1 for x in st_r if x == 0)),
+                                 "first_try_bits_equal": bool(all(
+                                     ll_r[k] == ll[k] for k in ok)),
+                                 "retried": [dict(task=k, **r) for k, r in enumerate(retry) if r["retries"]]}}
     for t, _, _, _ in fields:
         t.close()
     return res

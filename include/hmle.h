@@ -314,8 +314,9 @@ hmle_status hmle_loglik_eval(hmle_ctx *ctx, const hmle_tree *tree,
  *          Z  n doubles (caller order, host or device),
  *          shared by all evaluations;  ll  m outputs (-inf for a failed one);
  *  status  m per-evaluation statuses, or NULL.
- * Returns the first hard error (CUDA, OOM, INVALID_ARG), or HMLE_OK; NOT_SPD
- * and RANK_OVERFLOW are reported per evaluation only.  Device memory holds
+ * Returns the first hard error (CUDA, OOM, INVALID_ARG, TIMEOUT), or
+ * HMLE_OK; NOT_SPD, RANK_OVERFLOW and NOT_CONVERGED (the mixed form's PCG)
+ * are reported per evaluation only.  Device memory holds
  * one evaluation's buffers per concurrent slot, carved from one allocation
  * and kept with the tree while the batch shape stays the same. */
 hmle_status hmle_loglik_batch(hmle_ctx *ctx, const hmle_tree *tree, const hmle_theta *thetas,
@@ -341,6 +342,33 @@ typedef struct {
 } hmle_task;
 hmle_status hmle_loglik_multi(hmle_ctx *ctx, const hmle_task *tasks, int32_t ntask,
                               int32_t concurrency, double *ll, int32_t *status);
+
+/* a15, robust form (project-written; the paper runs each evaluation once):
+ * hmle_loglik_multi, then every task whose evaluation failed is evaluated
+ * again, up to max_retries (0..8) times, on a tree derived from its own (the
+ * same points and cluster tree, a new plan), one rung further on this ladder
+ * per retry:
+ *  RANK_OVERFLOW   first the rank capacity raised to its largest (max_rank
+ *                  56, oversample 8, ACA capacity 64) if it was lower, then
+ *                  aca_eps x 10 per retry up to 1e-3 (a coarser H-matrix, so
+ *                  the result is that of the looser accuracy: see retry);
+ *  NOT_CONVERGED, NOT_SPD of a mixed form   the products in FP64.
+ * Other failures are not retried.  Derived trees are built once per (tree,
+ * options) in the call and destroyed before it returns.
+ *  ll, status  as hmle_loglik_multi, for the last attempt of each task;
+ *  retry       may be NULL; per task: the retries spent and the options of
+ *              the attempt that produced ll (the tree's own when retries =
+ *              0).
+ * Errors: INVALID_ARG (max_retries outside 0..8), and as hmle_loglik_multi. */
+typedef struct {
+  int32_t retries;   /* retries spent on this task */
+  int32_t max_rank;  /* rank capacity of the attempt that produced ll */
+  int32_t precision; /* its hmle_precision */
+  double aca_eps;    /* its accuracy */
+} hmle_retry_info;
+hmle_status hmle_loglik_multi_retry(hmle_ctx *ctx, const hmle_task *tasks, int32_t ntask,
+                                    int32_t concurrency, int32_t max_retries, double *ll,
+                                    int32_t *status, hmle_retry_info *retry);
 
 /* a15: autotuner of the batched form (project-written; the paper has no
  * counterpart).  For this point set (locs n x d, row-major, host or device)
@@ -376,7 +404,8 @@ hmle_status hmle_autotune(hmle_ctx *ctx, const double *locs, int64_t n, int32_t 
 /* a13 (Sec. 2 and Sec. 5): maximise L over theta by Nelder-Mead in the
  * transformed coordinates sigma = 2/1.1^s0, ell = 1/1.5^l0, nu = 1/1.2^n0,
  * tau = 1/2^t0.  Trial points outside the admissible range of theta, or
- * whose evaluation fails with NOT_SPD or RANK_OVERFLOW, score L = -inf.
+ * whose evaluation fails with NOT_SPD, RANK_OVERFLOW or NOT_CONVERGED (the
+ * mixed form's PCG), score L = -inf.
  * The candidates of one iteration (reflection, expansion, contractions) are
  * evaluated together as one batch.
  *  theta0     start point; fopts may be NULL for hmle_fit_opts_default.

@@ -14,10 +14,16 @@ Trees: leaf 64, eta 2, ACA eps 1e-6, rank capacity 48, oversampling 16; the
 products in the requested precision (default: three BF16 slices on the
 tensor cores, PCG for the quadratic form).
 
+The call is hmle_loglik_multi_retry: a task that fails (rank overflow, or
+a mixed-form PCG that does not converge) is evaluated again on a tree derived
+from its own, one rung of the retry ladder further each time.
+
 Prints one JSON line: the tree-build time, the one call's time and tasks/s,
-the per-status counts, and the tasks of the first fields run again in one
-call and one call each (looped, after one warm-up evaluation per tree) for
-comparison.
+the per-status counts after the retries and the rungs the retried tasks
+ended on, and the tasks of the first fields run again in one call and one
+call each (looped, after one warm-up evaluation per tree) for comparison,
+with the number of first-attempt results bit-equal to the single
+evaluation's.
 """
 from __future__ import annotations
 
@@ -62,6 +68,7 @@ def main():
     ap.add_argument("--concurrency", type=int, default=16)
     ap.add_argument("--looped-fields", type=int, default=4)
     ap.add_argument("--seed", type=int, default=31)
+    ap.add_argument("--retries", type=int, default=3)
     a = ap.parse_args()
     ctx = hmle.Context()
     fields = []
@@ -77,11 +84,17 @@ def main():
     t_tree = time.time() - t0
     tasks = [(tree, th, Z) for (tree, Z, n, d, th0) in fields for th in trial_points(th0, a.trials)]
     t0 = time.time()
-    ll, st = ctx.loglik_multi(tasks, concurrency=a.concurrency)
+    ll, st, retry = ctx.loglik_multi_retry(tasks, concurrency=a.concurrency, max_retries=a.retries)
     dt = time.time() - t0
     counts = {}
     for s in st:
         counts[int(s)] = counts.get(int(s), 0) + 1
+    rungs = {}
+    for r in retry:
+        if r["retries"]:
+            key = "max_rank %d, %s, eps %g" % (r["max_rank"], "FP64" if r["precision"] == 0 else
+                                               "mixed %d" % r["precision"], r["aca_eps"])
+            rungs[key] = rungs.get(key, 0) + 1
     # the first fields' tasks once more: in one call, then one call each
     sub = [k for k, t in enumerate(tasks) if any(t[0] is f[0] for f in fields[:a.looped_fields])]
     t0 = time.time()
@@ -92,24 +105,32 @@ def main():
             f[0].loglik(f[4], f[1])
         except hmle.HmleError:
             pass
+    single = {}
     t0 = time.time()
     for k in sub:
         try:
-            tasks[k][0].loglik(tasks[k][1], tasks[k][2])
+            single[k] = tasks[k][0].loglik(tasks[k][1], tasks[k][2])[0]
         except hmle.HmleError:
             pass
     dt_loop = time.time() - t0
+    # a task that succeeded at its first attempt in the one call gives the
+    # same bits as the single evaluation (same kernels, same order of sums)
+    cmp = [k for k in sub if k in single and st[k] == 0 and retry[k]["retries"] == 0]
+    bits_equal = sum(1 for k in cmp if single[k] == ll[k])
     ns = [f[2] for f in fields]
     print(json.dumps({
         "config": "batched: %d fields, n log-uniform in [2048, 32768] (%d..%d), half 2-D / half 3-D, "
-                  "%d theta per field, leaf 64, eps 1e-6, rank capacity 48, precision %d, concurrency %d"
-                  % (a.fields, min(ns), max(ns), a.trials, a.precision, a.concurrency),
+                  "%d theta per field, leaf 64, eps 1e-6, rank capacity 48, precision %d, concurrency %d, "
+                  "up to %d retries" % (a.fields, min(ns), max(ns), a.trials, a.precision, a.concurrency,
+                                        a.retries),
         "tasks": len(tasks), "tree_build_s": t_tree, "call_s": dt, "tasks_per_s": len(tasks) / dt,
         "points_evals_per_s": sum(f[2] for f in fields) * a.trials / dt,
-        "status_counts": counts,
+        "status_counts": counts, "retried": sum(1 for r in retry if r["retries"]),
+        "retry_rungs": rungs,
         "subset": {"fields": a.looped_fields, "tasks": len(sub),
                    "one_call_tasks_per_s": len(sub) / dt_sub if dt_sub > 0 else None,
-                   "looped_tasks_per_s": len(sub) / dt_loop if dt_loop > 0 else None},
+                   "looped_tasks_per_s": len(sub) / dt_loop if dt_loop > 0 else None,
+                   "bits_equal_to_single": "%d of %d" % (bits_equal, len(cmp))},
         "ll_finite": int(sum(1 for v in ll if math.isfinite(v)))}))
     for f in fields:
         f[0].close()

@@ -83,6 +83,9 @@ struct hmle_tree {
   bool graphs = true;        // replay the sweep as a captured CUDA graph
   SolvePlan sp{};            // device task lists of the persistent sweeps on one vector
   bool coop = false;         // the device supports cooperative launches
+  bool owns_T = true;        // false: T belongs to the tree this one was derived from
+  std::vector<int4> blocks0; // block tree (level, i, j, kind) as built, for derived plans
+  std::vector<int32_t> cb, ce;   // heap-indexed cluster ranges
 };
 
 struct hmle_hmatrix {
@@ -209,6 +212,14 @@ void free_devplan(cudaStream_t st, DevPlan &d) {
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, st);
   d = DevPlan{};
+}
+
+// Failures of one evaluation that a batch reports per evaluation (L = -inf)
+// without stopping the others: the matrix is not numerically SPD at this
+// theta, a low-rank block needed more terms than its capacity, or the mixed
+// form's PCG did not reach its tolerance.
+bool per_eval_status(hmle_status s) {
+  return s == HMLE_OK || s == HMLE_ERR_NOT_SPD || s == HMLE_ERR_RANK_OVERFLOW || s == HMLE_ERR_NOT_CONVERGED;
 }
 
 bool theta_ok(const hmle_theta *t) {
@@ -621,6 +632,96 @@ hmle_status stage_vec(hmle_ctx *ctx, const double *src, int64_t n, double **dev,
   return HMLE_OK;
 }
 
+// The H-matrix plan of a tree from its block tree and options: the schedule
+// of the leaf sweep (Sec. 2, H-Cholesky) with the storage of every block at
+// the tree's rank capacities, uploaded to the device.  A tree derived with
+// other capacities (rank-overflow retry) shares the cluster tree and runs
+// this again.
+hmle_status plan_tree(hmle_ctx *ctx, hmle_tree *t) {
+  cudaStream_t st = ctx->st;
+  const hmle_opts &o = t->opts;
+  const int depth = tree_depth(t->n, o.leaf_size);
+  const std::vector<int32_t> &cb = t->cb, &ce = t->ce;
+  std::vector<int4> blocks = t->blocks0;
+  const int64_t n = t->n;
+  const int d = t->d;
+  const int kc = o.max_rank + 16 <= 64 ? o.max_rank + 16 : 64;  // ACA capacity for C
+  if (!o.leaf_lowrank)  // leaf x leaf admissible blocks are kept dense (exact)
+    for (int4 &q : blocks)
+      if (q.w == kLowRank && q.x == depth) q.w = kDense;
+  std::string err = build_plan(t->plan, (int32_t)n, d, o.leaf_size, depth, cb, ce, blocks, o.max_rank, kc,
+                   o.max_rank + o.oversample, 1);
+  if (!err.empty()) return fail(ctx, HMLE_ERR_INVALID_ARG, "planner: " + err);
+  const Plan &P = t->plan;
+  for (size_t x = 0; x < P.blocks.size(); ++x)
+    (P.blocks[x].kind == kLowRank ? t->lr_ids : t->dense_ids).push_back((int32_t)x);
+  std::vector<int2> dtr(P.dpairs.size()), dtc(P.dpairs.size());
+  for (const DenseTarget &dt : P.dns) {
+    const BlockDesc &T = P.blocks[dt.blk];
+    for (int q = dt.p0; q < dt.p1; ++q) {
+      dtr[q] = make_int2(T.rbeg, T.rend);
+      dtc[q] = make_int2(T.cbeg, T.cend);
+    }
+  }
+  std::vector<int32_t> leaf_beg(P.nleaf + 1);
+  for (int K = 0; K < P.nleaf; ++K) leaf_beg[K] = cb[(1 << depth) - 1 + K];
+  leaf_beg[P.nleaf] = (int32_t)n;
+  DevPlan &dp = t->dp;
+  cudaError_t e = cudaSuccess;
+#define UP(f, v) if (e == cudaSuccess) e = upload(st, &dp.f, v, dp.bytes)
+  UP(blocks, P.blocks); UP(panels, P.panels); UP(grams, P.grams); UP(lrt, P.lrt);
+  UP(gchunks, P.gchunks); UP(greds, P.greds);
+  UP(aent, P.aent); UP(bent, P.bent); UP(apair, P.apair); UP(bpair, P.bpair);
+  UP(lrpairs, P.lrpairs); UP(arow, P.arow); UP(brow, P.brow); UP(arow_ent, P.arow_ent);
+  UP(brow_ent, P.brow_ent); UP(dns, P.dns); UP(dpairs, P.dpairs); UP(wpan, P.wpan);
+  UP(dpair_tr, dtr); UP(dpair_tc, dtc);
+  UP(hts, P.hts); UP(urows, P.urows); UP(uents, P.uents); UP(leaf_beg, leaf_beg);
+  UP(lr_ids, t->lr_ids); UP(dense_ids, t->dense_ids);
+  UP(mv_row0, P.mv_row0); UP(mv_blocks, P.mv_blocks);
+  UP(hts_rhs, P.hts_rhs); UP(urows_rhs, P.urows_rhs); UP(uents_rhs, P.uents_rhs);
+  UP(bh_blocks, P.bh_blocks); UP(bupd, P.bupd); UP(bents, P.bents);
+  UP(mvt_row0, P.mvt_row0); UP(mvt_blocks, P.mvt_blocks);
+  UP(diag, P.diag_of_leaf); UP(ht_rhs0, P.ht_rhs0); UP(ur_rhs0, P.ur_rhs0); UP(bh0, P.bh0);
+  UP(bupd0, P.bupd0);
+  {
+    std::vector<int32_t> slot(std::max<size_t>(P.blocks.size(), 1), -1);
+    for (size_t q = 0; q < t->lr_ids.size(); ++q) slot[t->lr_ids[q]] = (int32_t)q;
+    UP(lr_slot, slot);
+  }
+  {
+    std::vector<int32_t> wr(1, P.rhs_panel);
+    UP(wpan_rhs, wr);
+  }
+#undef UP
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "plan upload");
+  {
+    const DevPlan &d = t->dp;
+    t->sp = SolvePlan{P.nleaf, d.diag, d.ht_rhs0, d.ur_rhs0, d.hts_rhs, d.urows_rhs, d.uents_rhs,
+                      d.bh0, d.bupd0, d.bh_blocks, d.bupd, d.bents};
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->dev);
+    t->coop = coop != 0;
+  }
+  return HMLE_OK;
+}
+
+// A tree on the same points and cluster tree as src with other options
+// (rank capacities, precision, accuracy): only the plan is made again.  The
+// derived tree borrows src's cluster tree and must be destroyed first.
+hmle_status derive_tree(hmle_ctx *ctx, const hmle_tree *src, const hmle_opts &o, hmle_tree **out) {
+  hmle_tree *t = new (std::nothrow) hmle_tree();
+  if (!t) return fail(ctx, HMLE_ERR_OOM, "derived tree");
+  t->ctx = ctx; t->n = src->n; t->d = src->d; t->opts = o; t->graphs = src->graphs;
+  t->T = src->T;
+  t->owns_T = false;
+  t->blocks0 = src->blocks0; t->cb = src->cb; t->ce = src->ce;
+  hmle_status s = plan_tree(ctx, t);
+  if (s != HMLE_OK) { hmle_tree_destroy(t); return s; }
+  *out = t;
+  return HMLE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -755,64 +856,11 @@ hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n, int32_
     hmle_tree_destroy(t);
     return fail(ctx, err.find("non-finite") != std::string::npos ? HMLE_ERR_INVALID_ARG : HMLE_ERR_CUDA, err);
   }
-  const int kc = o.max_rank + 16 <= 64 ? o.max_rank + 16 : 64;  // ACA capacity for C
-  if (!o.leaf_lowrank)  // leaf x leaf admissible blocks are kept dense (exact)
-    for (int4 &q : blocks)
-      if (q.w == kLowRank && q.x == depth) q.w = kDense;
-  err = build_plan(t->plan, (int32_t)n, d, o.leaf_size, depth, cb, ce, blocks, o.max_rank, kc,
-                   o.max_rank + o.oversample, 1);
-  if (!err.empty()) { hmle_tree_destroy(t); return fail(ctx, HMLE_ERR_INVALID_ARG, "planner: " + err); }
-  const Plan &P = t->plan;
-  for (size_t x = 0; x < P.blocks.size(); ++x)
-    (P.blocks[x].kind == kLowRank ? t->lr_ids : t->dense_ids).push_back((int32_t)x);
-  std::vector<int2> dtr(P.dpairs.size()), dtc(P.dpairs.size());
-  for (const DenseTarget &dt : P.dns) {
-    const BlockDesc &T = P.blocks[dt.blk];
-    for (int q = dt.p0; q < dt.p1; ++q) {
-      dtr[q] = make_int2(T.rbeg, T.rend);
-      dtc[q] = make_int2(T.cbeg, T.cend);
-    }
-  }
-  std::vector<int32_t> leaf_beg(P.nleaf + 1);
-  for (int K = 0; K < P.nleaf; ++K) leaf_beg[K] = cb[(1 << depth) - 1 + K];
-  leaf_beg[P.nleaf] = (int32_t)n;
-  DevPlan &dp = t->dp;
-  cudaError_t e = cudaSuccess;
-#define UP(f, v) if (e == cudaSuccess) e = upload(st, &dp.f, v, dp.bytes)
-  UP(blocks, P.blocks); UP(panels, P.panels); UP(grams, P.grams); UP(lrt, P.lrt);
-  UP(gchunks, P.gchunks); UP(greds, P.greds);
-  UP(aent, P.aent); UP(bent, P.bent); UP(apair, P.apair); UP(bpair, P.bpair);
-  UP(lrpairs, P.lrpairs); UP(arow, P.arow); UP(brow, P.brow); UP(arow_ent, P.arow_ent);
-  UP(brow_ent, P.brow_ent); UP(dns, P.dns); UP(dpairs, P.dpairs); UP(wpan, P.wpan);
-  UP(dpair_tr, dtr); UP(dpair_tc, dtc);
-  UP(hts, P.hts); UP(urows, P.urows); UP(uents, P.uents); UP(leaf_beg, leaf_beg);
-  UP(lr_ids, t->lr_ids); UP(dense_ids, t->dense_ids);
-  UP(mv_row0, P.mv_row0); UP(mv_blocks, P.mv_blocks);
-  UP(hts_rhs, P.hts_rhs); UP(urows_rhs, P.urows_rhs); UP(uents_rhs, P.uents_rhs);
-  UP(bh_blocks, P.bh_blocks); UP(bupd, P.bupd); UP(bents, P.bents);
-  UP(mvt_row0, P.mvt_row0); UP(mvt_blocks, P.mvt_blocks);
-  UP(diag, P.diag_of_leaf); UP(ht_rhs0, P.ht_rhs0); UP(ur_rhs0, P.ur_rhs0); UP(bh0, P.bh0);
-  UP(bupd0, P.bupd0);
-  {
-    std::vector<int32_t> slot(std::max<size_t>(P.blocks.size(), 1), -1);
-    for (size_t q = 0; q < t->lr_ids.size(); ++q) slot[t->lr_ids[q]] = (int32_t)q;
-    UP(lr_slot, slot);
-  }
-  {
-    std::vector<int32_t> wr(1, P.rhs_panel);
-    UP(wpan_rhs, wr);
-  }
-#undef UP
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) { hmle_tree_destroy(t); return cuda_fail(ctx, e, "plan upload"); }
-  {
-    const DevPlan &d = t->dp;
-    t->sp = SolvePlan{P.nleaf, d.diag, d.ht_rhs0, d.ur_rhs0, d.hts_rhs, d.urows_rhs, d.uents_rhs,
-                      d.bh0, d.bupd0, d.bh_blocks, d.bupd, d.bents};
-    int coop = 0;
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->dev);
-    t->coop = coop != 0;
-  }
+  t->blocks0 = std::move(blocks);
+  t->cb = std::move(cb);
+  t->ce = std::move(ce);
+  s = plan_tree(ctx, t);
+  if (s != HMLE_OK) { hmle_tree_destroy(t); return s; }
   *out = t;
   return HMLE_OK;
 }
@@ -832,9 +880,11 @@ void hmle_tree_destroy(hmle_tree *t) {
   for (Work *w : t->pool) free_work(w);
   for (Group *g : t->groups) free_group(g);
   free_devplan(st, t->dp);
-  if (t->T.xyz) cudaFreeAsync(t->T.xyz, st);
-  if (t->T.perm) cudaFreeAsync(t->T.perm, st);
-  if (t->T.box) cudaFreeAsync(t->T.box, st);
+  if (t->owns_T) {
+    if (t->T.xyz) cudaFreeAsync(t->T.xyz, st);
+    if (t->T.perm) cudaFreeAsync(t->T.perm, st);
+    if (t->T.box) cudaFreeAsync(t->T.box, st);
+  }
   cudaStreamSynchronize(st);
   delete t;
 }
@@ -1482,7 +1532,7 @@ hmle_status run_group(hmle_ctx *ctx, hmle_tree *t, const hmle_theta *thetas, int
       if (ld_out) ld_out[i] = (s == HMLE_OK) ? F.logdet : NAN;
       if (q_out) q_out[i] = (s == HMLE_OK) ? F.quad : NAN;
       if (status) status[i] = s;
-      if (s != HMLE_OK && s != HMLE_ERR_NOT_SPD && s != HMLE_ERR_RANK_OVERFLOW && first == HMLE_OK) {
+      if (!per_eval_status(s) && first == HMLE_OK) {
         first = s;
         ctx->err = errs[z];
       }
@@ -1601,7 +1651,7 @@ hmle_status run_waves(hmle_ctx *ctx, const std::vector<TaskRef> &tasks, int W, c
       if (ld_out) ld_out[i] = (s == HMLE_OK) ? w->F.logdet : NAN;
       if (q_out) q_out[i] = (s == HMLE_OK) ? w->F.quad : NAN;
       if (status && status[i] == HMLE_OK) status[i] = s;
-      if (s != HMLE_OK && s != HMLE_ERR_NOT_SPD && s != HMLE_ERR_RANK_OVERFLOW && first == HMLE_OK) {
+      if (!per_eval_status(s) && first == HMLE_OK) {
         first = s;
         ctx->err = wc.err;
       }
@@ -1657,9 +1707,44 @@ hmle_status hmle_loglik_batch(hmle_ctx *ctx, const hmle_tree *tc, const hmle_the
   return first;
 }
 
-hmle_status hmle_loglik_multi(hmle_ctx *ctx, const hmle_task *tasks, int32_t m, int32_t concurrency,
-                              double *ll, int32_t *status) {
-  if (!ctx || !tasks || !ll || m < 0) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
+}  // extern "C"
+
+namespace {
+
+// The retry ladder of a failed evaluation: the options of the next attempt
+// after status s, or false when there is none.  A rank overflow first raises
+// the rank capacity to its largest (56 columns plus 8 of oversampling; ACA
+// of C then has 64), then loosens the accuracy tenfold per step up to 1e-3;
+// a mixed-form evaluation whose PCG did not converge, or whose factor lost
+// positive definiteness, is done again in FP64.
+constexpr int kRetryRank = 56, kRetryOversample = 8;
+constexpr double kRetryEpsMax = 1e-3;
+
+bool next_attempt(hmle_opts &o, hmle_status s) {
+  if (s == HMLE_ERR_NOT_CONVERGED || s == HMLE_ERR_NOT_SPD) {
+    if (!is_mixed(o.precision)) return false;
+    o.precision = HMLE_FP64;
+    return true;
+  }
+  if (s != HMLE_ERR_RANK_OVERFLOW || o.fixed_rank > 0) return false;
+  if (o.max_rank < kRetryRank) {
+    o.max_rank = kRetryRank;
+    o.oversample = kRetryOversample;
+    return true;
+  }
+  if (o.aca_eps * 10.0 > kRetryEpsMax * (1.0 + 1e-12)) return false;
+  o.aca_eps *= 10.0;
+  return true;
+}
+
+bool same_opts(const hmle_opts &a, const hmle_opts &b) {
+  return a.max_rank == b.max_rank && a.oversample == b.oversample && a.precision == b.precision &&
+         a.aca_eps == b.aca_eps;
+}
+
+hmle_status multi_eval(hmle_ctx *ctx, const hmle_task *tasks, int32_t m, int32_t concurrency,
+                       int32_t max_retries, double *ll, int32_t *status_out, hmle_retry_info *retry) {
+  if (!ctx || !tasks || !ll || m < 0 || max_retries < 0) return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument");
   if (concurrency <= 0) concurrency = 8;
   if (concurrency > 64) concurrency = 64;
   for (int i = 0; i < m; ++i) {
@@ -1668,6 +1753,7 @@ hmle_status hmle_loglik_multi(hmle_ctx *ctx, const hmle_task *tasks, int32_t m, 
   }
   if (m == 0) return HMLE_OK;
   const int W = std::min<int>(concurrency, std::max(m, 1));
+  std::vector<int32_t> status(m, HMLE_OK);
   // stage every distinct Z once
   std::vector<const double *> src;
   std::vector<double *> dev;
@@ -1691,15 +1777,73 @@ hmle_status hmle_loglik_multi(hmle_ctx *ctx, const hmle_task *tasks, int32_t m, 
   hmle_status first = s0;
   cudaEvent_t zready = nullptr;
   if (first == HMLE_OK) {
-    CK(cudaEventCreateWithFlags(&zready, cudaEventDisableTiming), "event");
-    CK(cudaEventRecord(zready, ctx->st), "event record");
-    first = run_waves(ctx, refs, W, zready, ll, status);
-    cudaEventDestroy(zready);
+    if (cudaEventCreateWithFlags(&zready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(zready, ctx->st) != cudaSuccess)
+      first = fail(ctx, HMLE_ERR_CUDA, "event");
   }
+  if (first == HMLE_OK) first = run_waves(ctx, refs, W, zready, ll, status.data());
+  // retries: failed tasks again on trees derived from their own, one rung of
+  // the ladder further per round, until they succeed or the ladder ends
+  std::vector<hmle_opts> cur(m);
+  std::vector<int32_t> tries(m, 0);
+  for (int i = 0; i < m; ++i) cur[i] = tasks[i].tree->opts;
+  struct Derived { const hmle_tree *src; hmle_opts o; hmle_tree *t; };
+  std::vector<Derived> derived;
+  for (int r = 0; r < max_retries && first == HMLE_OK; ++r) {
+    std::vector<int> again;
+    std::vector<TaskRef> rrefs;
+    for (int i = 0; i < m && first == HMLE_OK; ++i) {
+      if (status[i] == HMLE_OK) continue;
+      hmle_opts o = cur[i];
+      if (!next_attempt(o, (hmle_status)status[i])) continue;
+      hmle_tree *dt = nullptr;
+      for (const Derived &D : derived)
+        if (D.src == tasks[i].tree && same_opts(D.o, o)) dt = D.t;
+      if (!dt) {
+        first = derive_tree(ctx, tasks[i].tree, o, &dt);
+        if (first != HMLE_OK) break;
+        derived.push_back({tasks[i].tree, o, dt});
+      }
+      cur[i] = o;
+      ++tries[i];
+      again.push_back(i);
+      rrefs.push_back({dt, &tasks[i].theta, refs[i].zd});
+    }
+    if (again.empty() || first != HMLE_OK) break;
+    std::vector<double> rll(again.size());
+    std::vector<int32_t> rst(again.size(), HMLE_OK);
+    first = run_waves(ctx, rrefs, std::min<int>(W, (int)again.size()), zready, rll.data(), rst.data());
+    for (size_t k = 0; k < again.size(); ++k) {
+      ll[again[k]] = rll[k];
+      status[again[k]] = rst[k];
+    }
+  }
+  if (zready) cudaEventDestroy(zready);
+  for (const Derived &D : derived) hmle_tree_destroy(D.t);
   for (size_t q = 0; q < dev.size(); ++q)
     if (own[q] && dev[q]) cudaFreeAsync(dev[q], ctx->st);
   cudaStreamSynchronize(ctx->st);
+  if (status_out) std::copy(status.begin(), status.end(), status_out);
+  if (retry)
+    for (int i = 0; i < m; ++i)
+      retry[i] = hmle_retry_info{tries[i], cur[i].max_rank, cur[i].precision, cur[i].aca_eps};
   return first;
+}
+
+}  // namespace
+
+extern "C" {
+
+hmle_status hmle_loglik_multi(hmle_ctx *ctx, const hmle_task *tasks, int32_t m, int32_t concurrency,
+                              double *ll, int32_t *status) {
+  return multi_eval(ctx, tasks, m, concurrency, 0, ll, status, nullptr);
+}
+
+hmle_status hmle_loglik_multi_retry(hmle_ctx *ctx, const hmle_task *tasks, int32_t m, int32_t concurrency,
+                                    int32_t max_retries, double *ll, int32_t *status,
+                                    hmle_retry_info *retry) {
+  if (max_retries > 8) return fail(ctx, HMLE_ERR_INVALID_ARG, "max_retries must be in [0, 8]");
+  return multi_eval(ctx, tasks, m, concurrency, max_retries, ll, status, retry);
 }
 
 hmle_status hmle_simulate(hmle_ctx *ctx, const hmle_tree *tc, const hmle_theta *th,

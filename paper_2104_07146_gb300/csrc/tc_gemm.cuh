@@ -230,11 +230,13 @@ template <int NS, bool A_KFAST, bool B_KFAST, class FA, class FB, class FC>
 __device__ void gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem, int *flags) {
   constexpr int KC = chunk_k<NS>();
   constexpr uint32_t kSbo = 16 * KC;
-  // With several slices (the mixed forms' long sums) every chunk is
-  // accumulated in its own TMEM region (two, alternating with the stages) and
-  // read out into compensated FP32 registers, so the FP32 rounding of the
-  // tensor cores' accumulation spans one chunk, not the whole of K.
+  // With several slices (the mixed forms' long sums) every group of kGroup
+  // chunks (128 values of k) is accumulated in its own TMEM region (two,
+  // alternating) and read out into compensated FP32 registers, so the FP32
+  // rounding of the tensor cores' accumulation spans 128 terms, not the whole
+  // of K, while a product with K <= 128 reads its tile out once.
   constexpr bool kChunked = NS >= 2;
+  constexpr int kGroup = kChunked ? 128 / KC : 1;
   constexpr uint32_t kCols = kChunked ? 2 * kTmemCols : kTmemCols;
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_tmem;
@@ -267,8 +269,8 @@ __device__ void gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem, int
     return true;
   };
   float hi[kChunked ? kTN : 1], lo[kChunked ? kTN : 1];
-  uint32_t unread = 0u;                // bit s: TMEM region s holds a chunk not yet added
-  // add TMEM region s (one chunk's partial products) into hi / lo
+  uint32_t unread = 0u;                // bit r: TMEM region r holds a group not yet added
+  // add TMEM region s (one group's partial products) into hi / lo
   auto absorb = [&](int s) {
     if constexpr (kChunked) {
       if (!((unread >> s) & 1u)) return;
@@ -296,7 +298,9 @@ __device__ void gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem, int
         const int s = c & 1;
         const bool late = !drain(s);
         if (__syncthreads_or(late)) { failed = true; break; }
-        absorb(s);   // chunk c - 2, in chunk order
+        // chunks up to c - 2 are complete: if c - 2 ends its group, add the
+        // group's region (chunk c - 1 and this chunk write the other one)
+        if (c >= 2 && (c - 2) % kGroup == kGroup - 1) absorb(((c - 2) / kGroup) & 1);
         uint8_t *sa = base + s * stage_bytes<NS>();
         uint8_t *sb = sa + NS * a_bytes<NS>();
         const int k0 = c * KC;
@@ -307,7 +311,8 @@ __device__ void gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem, int
         if (tid == 0) {
           fence_after();
           const uint32_t a0 = smem_addr(sa), b0 = smem_addr(sb);
-          const uint32_t dst = tmem + (kChunked ? (uint32_t)(s * kTN) : 0u);
+          const int rg = (c / kGroup) & 1;   // this chunk's TMEM region
+          const uint32_t dst = tmem + (kChunked ? (uint32_t)(rg * kTN) : 0u);
 #pragma unroll
           for (int kk = 0; kk < KC / 16; ++kk) {
             // the small cross terms first, the product of the leading slices last
@@ -317,14 +322,14 @@ __device__ void gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem, int
               for (int p = 0; p <= w; ++p) {
                 const uint32_t ao = a0 + (uint32_t)(p * a_bytes<NS>()) + 256u * kk;
                 const uint32_t bo = b0 + (uint32_t)((w - p) * b_bytes<NS>()) + 256u * kk;
-                const bool first = ((kChunked || c == 0) && kk == 0 && w == NS - 1 && p == 0);
+                const bool first = ((kChunked ? c % kGroup == 0 : c == 0) && kk == 0 && w == NS - 1 && p == 0);
                 mma(dst, sdesc(ao, kSbo), sdesc(bo, kSbo), first ? 0u : 1u);
               }
           }
           commit(bar0 + 8u * s);
         }
         pending |= 1u << s;
-        unread |= 1u << s;
+        unread |= 1u << ((c / kGroup) & 1);
       }
       if (failed) break;
       const int last = (nk - 1) & 1;   // the last two chunks, older first
@@ -334,8 +339,9 @@ __device__ void gemm(int M, int N, int K, FA fa, FB fb, FC fc, double *smem, int
       fence_after();
       const int i = m0 + warp * 32 + (tid & 31);
       if constexpr (kChunked) {
-        absorb(last ^ 1);
-        absorb(last);
+        const int g = (nk - 1) / kGroup;   // the last group, and the one before it if not yet added
+        absorb((g + 1) & 1);
+        absorb(g & 1);
         if (i < M) {
 #pragma unroll
           for (int x = 0; x < kTN; ++x)

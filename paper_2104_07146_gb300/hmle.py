@@ -58,6 +58,11 @@ class Task(C.Structure):
     _fields_ = [("tree", C.c_void_p), ("theta", Theta), ("Z", C.c_void_p)]
 
 
+class RetryInfo(C.Structure):
+    _fields_ = [("retries", C.c_int32), ("max_rank", C.c_int32), ("precision", C.c_int32),
+                ("aca_eps", C.c_double)]
+
+
 class TuneResult(C.Structure):
     _fields_ = [("leaf_size", C.c_int32), ("concurrency", C.c_int32), ("evals_per_s", C.c_double),
                 ("trials", C.c_int32), ("batch_size", C.c_int32)]
@@ -109,6 +114,7 @@ def lib():
             "hmle_cross_matvec": ([P, P, P, P, C.c_int64, C.c_int32, P, P], C.c_int),
             "hmle_fit_profiled": ([P, P, P, P, P, P, P, P, P], C.c_int),
             "hmle_loglik_multi": ([P, P, C.c_int32, C.c_int32, P, P], C.c_int),
+            "hmle_loglik_multi_retry": ([P, P, C.c_int32, C.c_int32, C.c_int32, P, P, P], C.c_int),
             "hmle_theta_to_x": ([P, P], C.c_int),
             "hmle_selftest_barrier": ([P, C.c_int32, P], C.c_int),
             "hmle_selftest_tc_gemm": ([P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
@@ -152,7 +158,7 @@ def exported_symbols():
             "hmle_tree_permutation", "hmle_assemble", "hmle_hmatrix_destroy",
             "hmle_hmatrix_matvec", "hmle_factor", "hmle_factor_destroy", "hmle_loglik",
             "hmle_loglik_eval", "hmle_fit", "hmle_matern_eval", "hmle_profile_select",
-            "hmle_profile_read", "hmle_phase_work", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_predict", "hmle_fit_profiled", "hmle_cross_matvec", "hmle_loglik_multi", "hmle_autotune", "hmle_tree_set_batch_size",
+            "hmle_profile_read", "hmle_phase_work", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_predict", "hmle_fit_profiled", "hmle_cross_matvec", "hmle_loglik_multi", "hmle_loglik_multi_retry", "hmle_autotune", "hmle_tree_set_batch_size",
             "hmle_theta_to_x", "hmle_x_to_theta", "hmle_selftest_barrier", "hmle_selftest_tc_gemm", "hmle_features", "hmle_mlp_nparams",
             "hmle_mlp_create", "hmle_mlp_destroy", "hmle_mlp_set", "hmle_mlp_get",
             "hmle_mlp_forward", "hmle_mlp_grad", "hmle_mlp_adam_step", "hmle_mlp_train",
@@ -192,24 +198,43 @@ class Context:
             msg = lib().hmle_last_error(self._h)
             raise HmleError(st, (what + ": " if what else "") + (msg.decode() if msg else ""))
 
-    def loglik_multi(self, tasks, concurrency=8):
-        """Evaluations over several trees at once: tasks = [(tree, theta, Z), ...].
-        Returns (L array, status array)."""
+    @staticmethod
+    def _tasks(tasks):
         tasks = list(tasks)
-        m = len(tasks)
         keep = []
-        arr = (Task * max(m, 1))()
+        arr = (Task * max(len(tasks), 1))()
         for i, (tree, th, Z) in enumerate(tasks):
             p, k = _ptr(Z)
             keep.append(k)
             arr[i].tree = tree._h
             arr[i].theta = _theta(th)
             arr[i].Z = p.value
+        return arr, len(tasks), keep
+
+    def loglik_multi(self, tasks, concurrency=8):
+        """Evaluations over several trees at once: tasks = [(tree, theta, Z), ...].
+        Returns (L array, status array)."""
+        arr, m, keep = self._tasks(tasks)
         ll = np.empty(m, dtype=np.float64)
         stt = np.empty(m, dtype=np.int32)
         self.check(lib().hmle_loglik_multi(self._h, arr, m, int(concurrency), P(ll.ctypes.data),
                                            P(stt.ctypes.data)), "hmle_loglik_multi")
         return ll, stt
+
+    def loglik_multi_retry(self, tasks, concurrency=8, max_retries=3):
+        """loglik_multi with failed tasks retried on derived trees
+        (hmle_loglik_multi_retry).  Returns (L array, status array, list of
+        per-task dicts: retries, max_rank, precision, aca_eps)."""
+        arr, m, keep = self._tasks(tasks)
+        ll = np.empty(m, dtype=np.float64)
+        stt = np.empty(m, dtype=np.int32)
+        info = (RetryInfo * max(m, 1))()
+        self.check(lib().hmle_loglik_multi_retry(self._h, arr, m, int(concurrency), int(max_retries),
+                                                 P(ll.ctypes.data), P(stt.ctypes.data), info),
+                   "hmle_loglik_multi_retry")
+        return ll, stt, [{"retries": int(info[i].retries), "max_rank": int(info[i].max_rank),
+                          "precision": int(info[i].precision), "aca_eps": float(info[i].aca_eps)}
+                         for i in range(m)]
 
     def autotune(self, locs, theta, Z, max_concurrency=16, **opts):
         """hmle_autotune: returns (best dict, list of trial dicts)."""
