@@ -287,6 +287,35 @@ hmle_status hmle_cross_matvec(hmle_ctx *ctx, const hmle_tree *tree, const hmle_t
                               const double *locs2, int64_t m, int32_t trans, const double *x,
                               double *y);
 
+/* next 1 (Eq. 5-6): the prediction errors of the kriging predictor at m
+ * test locations, for a true model theta_t (the factor f_true of C~ at
+ * theta_t, and its H-matrix) and an approximated model theta_a (f_approx at
+ * theta_a), both factors on one tree.  With c_x(j) the column C12 at theta_x
+ * for test location s_j (no nugget), C~_x the training covariance (nugget
+ * included) and v_x = sigma2_x + tau2_x the variance of Z(s_j):
+ *   e_tt(j) = v_t - c_t^T C~_t^{-1} c_t          E_t[(Z_t - Z)^2]
+ *   e_aa(j) = v_a - c_a^T C~_a^{-1} c_a          E_a[(Z_a - Z)^2]
+ *   e_ta(j) = v_t - 2 l_a^T c_t + l_a^T C~_t l_a, l_a = C~_a^{-1} c_a
+ *                                                E_t[(Z_a - Z)^2]
+ *   MLOE = mean_j (e_ta / e_tt - 1) (Eq. 5), MMOM = mean_j (e_aa / e_ta - 1)
+ * (Eq. 6).  All of it runs on the device in rounds of up to 256 locations:
+ * the columns generated from the Matern function, the solves C~^{-1} as one
+ * cooperative forward and one backward sweep over all the round's columns
+ * (multi-vector form of hmle_solve's sweeps), C~_t l_a as H-matvecs of 32
+ * columns per launch, the dot products per column in a fixed order.  The
+ * solves use the factors as they are (a mixed-form factor carries its
+ * FP32-class products into them).
+ *  locs2      m x d row-major (host or device), 1 <= m <= 2^24;
+ *  mloe, mmom the means (either may be NULL);
+ *  per_point  NULL or 3 m doubles (host): e_tt, e_aa, e_ta per location.
+ * Device memory: 5 x 256 x n doubles of columns plus workspaces, freed
+ * before returning.  Errors: INVALID_ARG (factors of two trees, m out of
+ * range, no output), NOT_IMPLEMENTED (no cooperative launch on the
+ * device), OOM, CUDA, TIMEOUT (a barrier wait of a sweep ran out). */
+hmle_status hmle_prediction_errors(hmle_ctx *ctx, const hmle_hfactor *f_true,
+                                   const hmle_hfactor *f_approx, const double *locs2, int64_t m,
+                                   double *mloe, double *mmom, double *per_point);
+
 /* Kriging prediction (Eq. 4): Z2 = C21 C11^{-1} Z1 at m new locations, the
  * conditional mean of the field there given Z1 (Sec. 1).  C11^{-1} Z1 comes
  * from the factor f of C11 (forward and backward sweeps, as hmle_solve); C21

@@ -285,16 +285,16 @@ def predict(locs1: np.ndarray, Z1: np.ndarray, locs2: np.ndarray, theta) -> np.n
     return matern_cross(locs2, locs1, theta) @ x
 
 
-def mloe_mmom(locs1: np.ndarray, locs2: np.ndarray, theta_t, theta_a):
-    """MLOE and MMOM of Eq. 5-6 with dense FP64 matrices.  For each test
-    location s_j the mean square errors of the kriging predictors under the
+def prediction_errors(locs1: np.ndarray, locs2: np.ndarray, theta_t, theta_a):
+    """The per-location mean square errors behind Eq. 5-6, with dense FP64
+    matrices.  For each test location s_j, the kriging predictors under the
     true (t) and approximated (a) models: with c = cross-covariance column,
     C = training covariance, v = sigma2 + tau2 (the variance of Z(s_j)),
     l_a = C_a^{-1} c_a:
       E_t[(Z_t - Z)^2] = v_t - c_t^T C_t^{-1} c_t
       E_a[(Z_a - Z)^2] = v_a - c_a^T l_a
       E_t[(Z_a - Z)^2] = v_t - 2 l_a^T c_t + l_a^T C_t l_a
-    MLOE = mean(E_t[a] / E_t[t] - 1), MMOM = mean(E_a[a] / E_t[a] - 1)."""
+    Returns the three arrays (M each) in that order."""
     Ct, Ca = matern_matrix(locs1, theta_t), matern_matrix(locs1, theta_a)
     ct = matern_cross(locs1, locs2, theta_t)          # n x M columns c_t(j)
     ca = matern_cross(locs1, locs2, theta_a)
@@ -305,6 +305,14 @@ def mloe_mmom(locs1: np.ndarray, locs2: np.ndarray, theta_t, theta_a):
     e_tt = vt - np.sum(ct * lt, axis=0)
     e_aa = va - np.sum(ca * la, axis=0)
     e_ta = vt - 2.0 * np.sum(la * ct, axis=0) + np.sum(la * (Ct @ la), axis=0)
+    return e_tt, e_aa, e_ta
+
+
+def mloe_mmom(locs1: np.ndarray, locs2: np.ndarray, theta_t, theta_a):
+    """MLOE and MMOM of Eq. 5-6: MLOE = mean(E_t[a] / E_t[t] - 1),
+    MMOM = mean(E_a[a] / E_t[a] - 1) over the per-location errors of
+    prediction_errors."""
+    e_tt, e_aa, e_ta = prediction_errors(locs1, locs2, theta_t, theta_a)
     return float(np.mean(e_ta / e_tt - 1.0)), float(np.mean(e_aa / e_ta - 1.0))
 
 

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -62,6 +63,8 @@ struct DevPlan {
   UpdEntry *bents = nullptr;
   int32_t *mvt_row0 = nullptr, *mvt_blocks = nullptr, *lr_slot = nullptr;
   int32_t *diag = nullptr, *ht_rhs0 = nullptr, *ur_rhs0 = nullptr, *bh0 = nullptr, *bupd0 = nullptr;
+  HTask *hts_mrhs = nullptr;       // the forward lists of the multi-vector sweep: coupling
+  UpdEntry *uents_mrhs = nullptr;  // vectors at kcap doubles per task of the leaf
   int64_t bytes = 0;
 };
 
@@ -82,6 +85,8 @@ struct hmle_tree {
   std::vector<Group *> groups;  // the batch of hmle_loglik_batch (at most one, of the last size used)
   bool graphs = true;        // replay the sweep as a captured CUDA graph
   SolvePlan sp{};            // device task lists of the persistent sweeps on one vector
+  SolvePlan spm{};           // the same for many vectors (compact coupling vectors)
+  int64_t mrhs_h = 0;        // coupling-vector doubles per vector of the multi-vector sweeps
   bool coop = false;         // the device supports cooperative launches
   bool owns_T = true;        // false: T belongs to the tree this one was derived from
   std::vector<int4> blocks0; // block tree (level, i, j, kind) as built, for derived plans
@@ -208,7 +213,7 @@ void free_devplan(cudaStream_t st, DevPlan &d) {
                   d.hts, d.urows, d.uents, d.leaf_beg, d.lr_ids, d.dense_ids, d.mv_row0,
                   d.mv_blocks, d.hts_rhs, d.urows_rhs, d.uents_rhs, d.wpan_rhs, d.bh_blocks,
                   d.bupd, d.bents, d.mvt_row0, d.mvt_blocks, d.lr_slot, d.diag, d.ht_rhs0,
-                  d.ur_rhs0, d.bh0, d.bupd0};
+                  d.ur_rhs0, d.bh0, d.bupd0, d.hts_mrhs, d.uents_mrhs};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, st);
   d = DevPlan{};
@@ -692,6 +697,35 @@ hmle_status plan_tree(hmle_ctx *ctx, hmle_tree *t) {
     std::vector<int32_t> wr(1, P.rhs_panel);
     UP(wpan_rhs, wr);
   }
+  {  // forward lists of the multi-vector sweep: a task's coupling vector at
+     // kcap doubles per task of its leaf instead of its place in the factor's
+     // workspace, so that each vector needs only the largest leaf's share
+    std::vector<HTask> hc = P.hts_rhs;
+    std::vector<UpdEntry> uc = P.uents_rhs;
+    int64_t hw = 1;
+    bool ok = true;
+    for (int K = 0; K < P.nleaf && ok; ++K) {
+      std::map<int64_t, int64_t> slot;
+      for (int q = P.ht_rhs0[K]; q < P.ht_rhs0[K + 1]; ++q) {
+        const int64_t c = (int64_t)(q - P.ht_rhs0[K]) * P.kcap;
+        slot[hc[q].hoff] = c;
+        hc[q].hoff = c;
+      }
+      hw = std::max<int64_t>(hw, (int64_t)(P.ht_rhs0[K + 1] - P.ht_rhs0[K]) * P.kcap);
+      hw = std::max<int64_t>(hw, (int64_t)(P.bh0[K + 1] - P.bh0[K]) * P.kcap);
+      for (int r = P.ur_rhs0[K]; r < P.ur_rhs0[K + 1] && ok; ++r)
+        for (int q = P.urows_rhs[r].e0; q < P.urows_rhs[r].e1; ++q) {
+          if (uc[q].hoff < 0) continue;
+          auto it = slot.find(uc[q].hoff);
+          if (it == slot.end()) { ok = false; break; }
+          uc[q].hoff = it->second;
+        }
+    }
+    if (!ok) return fail(ctx, HMLE_ERR_INVALID_ARG, "planner: a forward update without its leaf's task");
+    t->mrhs_h = hw;
+    UP(hts_mrhs, hc);
+    UP(uents_mrhs, uc);
+  }
 #undef UP
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "plan upload");
@@ -699,6 +733,9 @@ hmle_status plan_tree(hmle_ctx *ctx, hmle_tree *t) {
     const DevPlan &d = t->dp;
     t->sp = SolvePlan{P.nleaf, d.diag, d.ht_rhs0, d.ur_rhs0, d.hts_rhs, d.urows_rhs, d.uents_rhs,
                       d.bh0, d.bupd0, d.bh_blocks, d.bupd, d.bents};
+    t->spm = t->sp;
+    t->spm.hts = d.hts_mrhs;
+    t->spm.uents = d.uents_mrhs;
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->dev);
     t->coop = coop != 0;
@@ -1948,6 +1985,113 @@ hmle_status hmle_cross_matvec(hmle_ctx *ctx, const hmle_tree *t, const hmle_thet
   if (lown) cudaFreeAsync(l2, st);
   if (xown) cudaFreeAsync(xd, st);
   CK(cudaStreamSynchronize(st), "sync");
+  return HMLE_OK;
+}
+
+hmle_status hmle_prediction_errors(hmle_ctx *ctx, const hmle_hfactor *ftc, const hmle_hfactor *fac,
+                                   const double *locs2, int64_t m, double *mloe, double *mmom,
+                                   double *per_point) {
+  if (!ctx || !ftc || !fac || !locs2 || m < 1 || m > (1LL << 24) || (!mloe && !mmom && !per_point))
+    return fail(ctx, HMLE_ERR_INVALID_ARG, "null argument or m out of range");
+  hmle_hfactor *ft = const_cast<hmle_hfactor *>(ftc);
+  hmle_hfactor *fa = const_cast<hmle_hfactor *>(fac);
+  const hmle_tree *t = ft->h->tree;
+  if (fa->h->tree != t) return fail(ctx, HMLE_ERR_INVALID_ARG, "both factors must belong to one tree");
+  if (!t->coop) return fail(ctx, HMLE_ERR_NOT_IMPLEMENTED, "the multi-vector sweeps need cooperative launches");
+  const hmle_theta tht = ft->h->th, tha = fa->h->th;
+  const Plan &P = t->plan;
+  cudaStream_t st = ctx->st;
+  const int64_t n = t->n, ld = n;
+  const int nlr = (int)t->lr_ids.size();
+  constexpr int kBlock = 256;    // test locations per round of the sweeps
+  constexpr int kMvBlock = 32;   // vectors per launch of the H-matvec (its workspace)
+  const int mb = (int)std::min<int64_t>(m, kBlock);
+  const int64_t hs = t->mrhs_h, tw = (int64_t)std::max(nlr, 1) * 2 * P.kc;
+  double *l2 = nullptr;
+  bool lown = false;
+  hmle_status s = stage_vec(ctx, locs2, m * t->d, &l2, &lown);
+  if (s != HMLE_OK) return s;
+  double *tab = nullptr, *V = nullptr, *H = nullptr, *Tw = nullptr, *dots = nullptr;
+  unsigned *bar = nullptr;
+  cudaError_t e = cudaMallocAsync(&tab, sizeof(double) * 2 * kTableWords, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&V, sizeof(double) * 5 * (size_t)mb * ld, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&H, sizeof(double) * (size_t)mb * hs, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&Tw, sizeof(double) * (size_t)kMvBlock * tw, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&dots, sizeof(double) * 4 * mb, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&bar, 4 * sizeof(unsigned), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st);
+  // Ct, Ca: columns c_t(j), c_a(j) of C12 at theta_t and theta_a (cluster
+  // order); Lt = C~t^{-1} Ct, La = C~a^{-1} Ca; Y = C~t La (the H-matrix of
+  // theta_t)
+  double *Ct = V, *Ca = V + (size_t)mb * ld, *Lt = Ca + (size_t)mb * ld, *La = Lt + (size_t)mb * ld,
+         *Y = La + (size_t)mb * ld;
+  const FactorArgs Ft = make_fargs(t, ft->h, ft), Fa = make_fargs(t, fa->h, fa);
+  const hmle_hmatrix *h = ft->h;
+  AsmArgs A{};
+  A.blocks = t->dp.blocks; A.lr_ids = t->dp.lr_ids; A.xyz = t->T.xyz; A.n = n; A.d = t->d;
+  A.tab = h->tab; A.inv_ell = 1.0 / h->th.ell; A.sigma2 = h->th.sigma2; A.tau2 = h->th.tau2;
+  A.kc = P.kc; A.uc = h->uc; A.rank_c = h->rank_c; A.cnorm = h->cnorm; A.flags = h->flags;
+  A.thd = h->thd; A.Cd = h->Cd; A.b = P.b;
+  const CmvLists L{P.nleaf, t->dp.leaf_beg, t->dp.mv_row0, t->dp.mv_blocks, t->dp.mvt_row0,
+                   t->dp.mvt_blocks, t->dp.lr_slot};
+  if (e == cudaSuccess) {
+    launch_matern_table(st, tht.nu, tab);
+    launch_matern_table(st, tha.nu, tab + kTableWords);
+    e = cudaGetLastError();
+  }
+  const double vt = tht.sigma2 + tht.tau2, va = tha.sigma2 + tha.tau2;
+  std::vector<double> hd(4 * (size_t)mb);
+  double sum_loe = 0.0, sum_mom = 0.0;
+  unsigned berr = 0;
+  for (int64_t j0 = 0; j0 < m && e == cudaSuccess; j0 += mb) {
+    const int cnt = (int)std::min<int64_t>(mb, m - j0);
+    const size_t bytes = sizeof(double) * (size_t)cnt * ld;
+    launch_cross_cols(st, tab, t->T.xyz, n, t->d, l2, j0, cnt, 1.0 / tht.ell, tht.sigma2, Ct, ld);
+    launch_cross_cols(st, tab + kTableWords, t->T.xyz, n, t->d, l2, j0, cnt, 1.0 / tha.ell, tha.sigma2, Ca, ld);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Lt, Ct, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(La, Ca, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = persistent_solve_multi(st, Ft, t->spm, Lt, ld, H, hs, cnt, bar, false);
+    if (e == cudaSuccess) e = persistent_solve_multi(st, Ft, t->spm, Lt, ld, H, hs, cnt, bar, true);
+    if (e == cudaSuccess) e = persistent_solve_multi(st, Fa, t->spm, La, ld, H, hs, cnt, bar, false);
+    if (e == cudaSuccess) e = persistent_solve_multi(st, Fa, t->spm, La, ld, H, hs, cnt, bar, true);
+    for (int c0 = 0; c0 < cnt && e == cudaSuccess; c0 += kMvBlock) {
+      const int c = std::min(kMvBlock, cnt - c0);
+      launch_cmatvec(st, A, nlr, L, La + (size_t)c0 * ld, Tw, Y + (size_t)c0 * ld, c, ld, tw);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) break;
+    launch_col_dots(st, Ct, Lt, n, ld, cnt, dots);
+    launch_col_dots(st, Ca, La, n, ld, cnt, dots + mb);
+    launch_col_dots(st, La, Ct, n, ld, cnt, dots + 2 * mb);
+    launch_col_dots(st, La, Y, n, ld, cnt, dots + 3 * mb);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hd.data(), dots, sizeof(double) * 4 * mb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&berr, bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || berr) break;
+    for (int jj = 0; jj < cnt; ++jj) {
+      const double e_tt = vt - hd[jj];                              // E_t[(Z_t - Z)^2]
+      const double e_aa = va - hd[mb + jj];                         // E_a[(Z_a - Z)^2]
+      const double e_ta = vt - 2.0 * hd[2 * mb + jj] + hd[3 * mb + jj];   // E_t[(Z_a - Z)^2]
+      sum_loe += e_ta / e_tt - 1.0;
+      sum_mom += e_aa / e_ta - 1.0;
+      if (per_point) {
+        per_point[3 * (j0 + jj)] = e_tt;
+        per_point[3 * (j0 + jj) + 1] = e_aa;
+        per_point[3 * (j0 + jj) + 2] = e_ta;
+      }
+    }
+  }
+  for (void *p : {(void *)tab, (void *)V, (void *)H, (void *)Tw, (void *)dots, (void *)bar})
+    if (p) cudaFreeAsync(p, st);
+  if (lown) cudaFreeAsync(l2, st);
+  cudaError_t e2 = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "prediction errors");
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "prediction errors");
+  if (berr) return fail(ctx, HMLE_ERR_TIMEOUT, "prediction errors: a barrier wait of a sweep ran out");
+  if (mloe) *mloe = sum_loe / (double)m;
+  if (mmom) *mmom = sum_mom / (double)m;
   return HMLE_OK;
 }
 

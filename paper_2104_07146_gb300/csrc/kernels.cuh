@@ -190,9 +190,21 @@ struct CmvLists {
   const int32_t *leaf_beg, *row0, *rblocks, *col0, *cblocks, *lr_slot;
 };
 // y = C x in cluster order (FP64; dense entries generated from the table);
-// t: 2 kc doubles per admissible block.
+// t: 2 kc doubles per admissible block.  A batch of nz: vectors x, y at
+// z zs doubles, t at z tzs (tzs < 0: zs), the H-matrix A.at(z) (one
+// H-matrix for all when A.zstride = 0).
 void launch_cmatvec(cudaStream_t st, const AsmArgs &A, int n_lr, const CmvLists &L,
-                    const double *x, double *t, double *y, int nz = 1, int64_t zs = 0);
+                    const double *x, double *t, double *y, int nz = 1, int64_t zs = 0, int64_t tzs = -1);
+// Eq. 5-6 helpers.  Columns j0 .. j0 + cnt - 1 of C12 (no nugget):
+// out[i + jj ld] = sigma2 M_nu(|s1_i - s2_{j0+jj}| inv_ell), i < n in cluster
+// order (xyz SoA), locs2 m x d row-major.
+void launch_cross_cols(cudaStream_t st, const double *tab, const double *xyz, int64_t n, int d,
+                       const double *locs2, int64_t j0, int cnt, double inv_ell, double sigma2, double *out,
+                       int64_t ld);
+// out[jj] = sum_i a[i + jj ld] b[i + jj ld], i < n, for jj < cnt: one CTA per
+// column, fixed order.
+void launch_col_dots(cudaStream_t st, const double *a, const double *b, int64_t n, int64_t ld, int cnt,
+                     double *out);
 // doubles of workspace pcg_quad needs
 int64_t pcg_words(int64_t n, int n_lr, int kc, int hmax);
 // q = b^T x with C x = b solved by PCG: operator launch_cmatvec, preconditioner
@@ -219,6 +231,13 @@ struct SolvePlan {
 // (bar[2] != 0 afterwards: a barrier wait ran out).
 cudaError_t persistent_solve(cudaStream_t st, const FactorArgs &F, const SolvePlan &P, double *w,
                              double *h, unsigned *bar, bool backward);
+// The same sweep for nrhs vectors of one factor in one cooperative launch:
+// vector z at w + z ws, its coupling vectors at h + z hs.  P's forward task
+// lists must address the coupling vectors compactly (the hmle_tree's
+// multi-vector plan: kcap doubles per task of a leaf, hs >= the largest
+// leaf's tasks x kcap in either direction).
+cudaError_t persistent_solve_multi(cudaStream_t st, const FactorArgs &F, const SolvePlan &P, double *w,
+                                   int64_t ws, double *h, int64_t hs, int nrhs, unsigned *bar, bool backward);
 
 // Eq. 4: out[j] = sum_i sigma2 M_nu(|s2_j - s1_i| inv_ell) x_i for m new
 // locations locs2 (m x d, row-major) against the n training points xyz (SoA,

@@ -28,11 +28,11 @@ constexpr int kThreadsMv = 128;
 // vectors at z zs doubles, its H-matrix through AsmArgs::at); one
 // evaluation is the batch of one.
 __global__ void __launch_bounds__(kThreadsMv) k_cmv_t(AsmArgs Az, const double *__restrict__ x,
-                                                      double *__restrict__ t, int64_t zs) {
+                                                      double *__restrict__ t, int64_t zs, int64_t tzs) {
   __shared__ double red[32];
   const AsmArgs A = Az.at(blockIdx.y);
   x += blockIdx.y * zs;
-  t += blockIdx.y * zs;
+  t += blockIdx.y * tzs;
   const int blk = A.lr_ids[blockIdx.x];
   const BlockDesc B = A.blocks[blk];
   const int m = B.rend - B.rbeg, p = B.cend - B.cbeg, kc = A.kc;
@@ -61,10 +61,10 @@ __global__ void __launch_bounds__(kThreadsMv) k_cmv_rows(AsmArgs Az, const int32
                                                          const int32_t *__restrict__ lr_slot,
                                                          const double *__restrict__ x,
                                                          const double *__restrict__ t,
-                                                         double *__restrict__ y, int64_t zs) {
+                                                         double *__restrict__ y, int64_t zs, int64_t tzs) {
   const AsmArgs A = Az.at(blockIdx.y);
   x += blockIdx.y * zs;
-  t += blockIdx.y * zs;
+  t += blockIdx.y * tzs;
   y += blockIdx.y * zs;
   const int I = blockIdx.x;
   const int I0 = leaf_beg[I], I1 = leaf_beg[I + 1];
@@ -200,10 +200,11 @@ int64_t pcg_words(int64_t n, int n_lr, int kc, int hmax) {
 }
 
 void launch_cmatvec(cudaStream_t st, const AsmArgs &A, int n_lr, const CmvLists &L,
-                    const double *x, double *t, double *y, int nz, int64_t zs) {
-  if (n_lr > 0) k_cmv_t<<<dim3(n_lr, nz), kThreadsMv, 0, st>>>(A, x, t, zs);
+                    const double *x, double *t, double *y, int nz, int64_t zs, int64_t tzs) {
+  if (tzs < 0) tzs = zs;
+  if (n_lr > 0) k_cmv_t<<<dim3(n_lr, nz), kThreadsMv, 0, st>>>(A, x, t, zs, tzs);
   k_cmv_rows<<<dim3(L.nleaf, nz), kThreadsMv, 0, st>>>(A, L.leaf_beg, L.row0, L.rblocks, L.col0, L.cblocks,
-                                                       L.lr_slot, x, t, y, zs);
+                                                       L.lr_slot, x, t, y, zs, tzs);
 }
 
 namespace {
@@ -349,6 +350,47 @@ __global__ void k_cross_matvec_t(const double *__restrict__ tab, const double *_
     acc = fma(sigma2 * matern_unit(tab, sqrt(h2) * inv_ell), y[j], acc);
   }
   out[i] = acc;
+}
+
+// Eq. 5-6: columns of C12 for a block of new locations, one thread per
+// (training point, column); the training points in cluster order.
+__global__ void k_cross_cols(const double *__restrict__ tab, const double *__restrict__ xyz, int64_t n,
+                             int d, const double *__restrict__ locs2, int64_t j0, double inv_ell,
+                             double sigma2, double *__restrict__ out, int64_t ld) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int jj = blockIdx.y;
+  if (i >= n) return;
+  const double *p = locs2 + (j0 + jj) * d;
+  double h2 = 0.0;
+  for (int k = 0; k < d; ++k) {
+    const double dx = xyz[k * n + i] - p[k];
+    h2 = fma(dx, dx, h2);
+  }
+  out[i + jj * ld] = sigma2 * matern_unit(tab, sqrt(h2) * inv_ell);
+}
+
+// Per-column dot products, one CTA per column, a fixed order of the sums.
+__global__ void k_col_dots(const double *__restrict__ a, const double *__restrict__ b, int64_t n,
+                           int64_t ld, double *__restrict__ out) {
+  __shared__ double red[32];
+  const int64_t o = (int64_t)blockIdx.x * ld;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(a[o + i], b[o + i], s);
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+void launch_cross_cols(cudaStream_t st, const double *tab, const double *xyz, int64_t n, int d,
+                       const double *locs2, int64_t j0, int cnt, double inv_ell, double sigma2, double *out,
+                       int64_t ld) {
+  if (n > 0 && cnt > 0)
+    k_cross_cols<<<dim3((unsigned)((n + 255) / 256), (unsigned)cnt), 256, 0, st>>>(tab, xyz, n, d, locs2, j0,
+                                                                                inv_ell, sigma2, out, ld);
+}
+
+void launch_col_dots(cudaStream_t st, const double *a, const double *b, int64_t n, int64_t ld, int cnt,
+                     double *out) {
+  if (cnt > 0) k_col_dots<<<(unsigned)cnt, 256, 0, st>>>(a, b, n, ld, out);
 }
 
 void launch_cross_matvec(cudaStream_t st, const double *tab, const double *xyz, int64_t n, int d,

@@ -113,10 +113,12 @@ struct SolveArgs {
                             // factor's workspace), backward kcap per task of a leaf
   unsigned *bar;
   int nleaf;
-  // a batch of nz factors (FactorArgs::at): evaluation z's vector and coupling
-  // vectors are w + z zs and h + z zs; every phase runs the tasks of all nz
+  // a batch of nz vectors: vector z and its coupling vectors are w + z zs and
+  // h + z hzs, and its factor is F.at(z) (a batch of factors of one tree, or
+  // one factor for every vector when F.zstride = 0); every phase runs the
+  // tasks of all nz
   int nz;
-  int64_t zs;
+  int64_t zs, hzs;
 };
 
 __global__ void __launch_bounds__(kSolveThreads) k_solve_fwd(SolveArgs S) {
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_fwd(SolveArgs S) {
       const PanelDesc PA = F.panels[A.panel];
       const int lda = PA.rend - PA.rbeg, ka = F.rank_l[T.a], p = A.cend - A.cbeg;
       const double *Wa = F.W + PA.off + (int64_t)A.slot * lda + (A.cbeg - PA.rbeg);
-      double *h = S.h + z * S.zs + T.hoff;   // where the sweep's own task writes it
+      double *h = S.h + z * S.hzs + T.hoff;   // where the sweep's own task writes it
       for (int i = warp; i < ka; i += nw) {
         double s = 0.0;
         for (int k = lane; k < p; k += 32) s = fma(Wa[k + (int64_t)i * lda], __ldcg(wz + A.cbeg + k), s);
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_fwd(SolveArgs S) {
       const int z = g / nu, t = S.u0[K] + g % nu;
       const FactorArgs F = S.F.at(z);
       double *wz = S.w + z * S.zs;
-      const double *hz = S.h + z * S.zs;
+      const double *hz = S.h + z * S.hzs;
       const UpdRow R = S.rows[t];
       const int I0 = F.leaf_beg[R.leaf], I1 = F.leaf_beg[R.leaf + 1];
       for (int i = I0 + threadIdx.x; i < I1; i += blockDim.x) {
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_bwd(SolveArgs S) {
       const BlockDesc A = F.blocks[blk];
       const int m = A.rend - A.rbeg, ka = F.rank_l[blk];
       const double *U = F.U + A.off_u;
-      double *h = S.h + z * S.zs + (int64_t)(t - S.s0[K]) * F.kcap;
+      double *h = S.h + z * S.hzs + (int64_t)(t - S.s0[K]) * F.kcap;
       for (int i = warp; i < ka; i += nw) {
         double s = 0.0;
         for (int k = lane; k < m; k += 32) s = fma(U[k + (int64_t)i * m], __ldcg(wz + A.rbeg + k), s);
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_bwd(SolveArgs S) {
       const int z = g / nu, t = S.u0[K] + g % nu;
       const FactorArgs F = S.F.at(z);
       double *wz = S.w + z * S.zs;
-      const double *hz = S.h + z * S.zs;
+      const double *hz = S.h + z * S.hzs;
       const UpdRow R = S.rows[t];
       const int J0 = F.leaf_beg[R.leaf], J1 = F.leaf_beg[R.leaf + 1];
       for (int j = J0 + threadIdx.x; j < J1; j += blockDim.x) {
@@ -297,8 +299,33 @@ cudaError_t persistent_solve(cudaStream_t st, const FactorArgs &F, const SolvePl
   S.bar = bar;
   S.nz = F.nz > 0 ? F.nz : 1;
   S.zs = F.zstride / (int64_t)sizeof(double);
+  S.hzs = S.zs;
   // arrivals and generation start at zero; the error word is kept (set to
   // zero by the caller once), so a later sweep does not hide an earlier one's
+  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  if (!backward) {
+    S.s0 = P.ht0; S.u0 = P.ur0; S.hts = P.hts; S.rows = P.urows; S.ents = P.uents; S.bblk = nullptr;
+    return launch_coop((const void *)k_solve_fwd, S, st);
+  }
+  S.s0 = P.bh0; S.u0 = P.bu0; S.hts = nullptr; S.rows = P.bupd; S.ents = P.bents; S.bblk = P.bblk;
+  return launch_coop((const void *)k_solve_bwd, S, st);
+}
+
+cudaError_t persistent_solve_multi(cudaStream_t st, const FactorArgs &F1, const SolvePlan &P, double *w,
+                                   int64_t ws, double *h, int64_t hs, int nrhs, unsigned *bar, bool backward) {
+  SolveArgs S;
+  S.F = F1;
+  S.F.nz = 1;
+  S.F.zstride = 0;   // F.at(z) is the one factor for every vector
+  S.diag = P.diag;
+  S.nleaf = P.nleaf;
+  S.w = w;
+  S.h = h;
+  S.bar = bar;
+  S.nz = nrhs;
+  S.zs = ws;
+  S.hzs = hs;
   cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   if (!backward) {

@@ -115,6 +115,7 @@ def lib():
             "hmle_fit_profiled": ([P, P, P, P, P, P, P, P, P], C.c_int),
             "hmle_loglik_multi": ([P, P, C.c_int32, C.c_int32, P, P], C.c_int),
             "hmle_loglik_multi_retry": ([P, P, C.c_int32, C.c_int32, C.c_int32, P, P, P], C.c_int),
+            "hmle_prediction_errors": ([P, P, P, P, C.c_int64, P, P, P], C.c_int),
             "hmle_theta_to_x": ([P, P], C.c_int),
             "hmle_selftest_barrier": ([P, C.c_int32, P], C.c_int),
             "hmle_selftest_tc_gemm": ([P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
@@ -158,7 +159,7 @@ def exported_symbols():
             "hmle_tree_permutation", "hmle_assemble", "hmle_hmatrix_destroy",
             "hmle_hmatrix_matvec", "hmle_factor", "hmle_factor_destroy", "hmle_loglik",
             "hmle_loglik_eval", "hmle_fit", "hmle_matern_eval", "hmle_profile_select",
-            "hmle_profile_read", "hmle_phase_work", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_predict", "hmle_fit_profiled", "hmle_cross_matvec", "hmle_loglik_multi", "hmle_loglik_multi_retry", "hmle_autotune", "hmle_tree_set_batch_size",
+            "hmle_profile_read", "hmle_phase_work", "hmle_simulate", "hmle_loglik_batch", "hmle_solve", "hmle_predict", "hmle_fit_profiled", "hmle_cross_matvec", "hmle_loglik_multi", "hmle_loglik_multi_retry", "hmle_prediction_errors", "hmle_autotune", "hmle_tree_set_batch_size",
             "hmle_theta_to_x", "hmle_x_to_theta", "hmle_selftest_barrier", "hmle_selftest_tc_gemm", "hmle_features", "hmle_mlp_nparams",
             "hmle_mlp_create", "hmle_mlp_destroy", "hmle_mlp_set", "hmle_mlp_get",
             "hmle_mlp_forward", "hmle_mlp_grad", "hmle_mlp_adam_step", "hmle_mlp_train",
@@ -592,6 +593,20 @@ class Factor:
         ctx.check(lib().hmle_predict(ctx._h, self._h, P(Z.ctypes.data), P(L2.ctypes.data),
                                      L2.shape[0], P(out.ctypes.data)), "hmle_predict")
         return out
+
+    def prediction_errors(self, approx: "Factor", locs2):
+        """hmle_prediction_errors with this factor as the true model and
+        `approx` as the approximated one: (MLOE, MMOM, per-location array
+        m x 3 of E_t[(Z_t - Z)^2], E_a[(Z_a - Z)^2], E_t[(Z_a - Z)^2])."""
+        L2 = np.ascontiguousarray(locs2, dtype=np.float64)
+        m = L2.shape[0]
+        per = np.empty((m, 3))
+        a, b = C.c_double(), C.c_double()
+        ctx = self.hm.tree.ctx
+        ctx.check(lib().hmle_prediction_errors(ctx._h, self._h, approx._h, P(L2.ctypes.data), m,
+                                               C.byref(a), C.byref(b), P(per.ctypes.data)),
+                  "hmle_prediction_errors")
+        return a.value, b.value, per
 
     def close(self):
         if self._h:

@@ -1,9 +1,10 @@
 """Prediction errors of the kriging predictor (Eq. 5-7).
 
-Thin driver over the C ABI: the solves (hmle_solve: forward and backward
-sweeps), the cross-covariance products (hmle_cross_matvec) and the H-matvec
-(hmle_hmatrix_matvec) all run in the library's kernels; this module only
-combines their outputs.
+Thin driver over the C ABI.  MLOE and MMOM come from hmle_prediction_errors.
+The per-location columns of the cross-covariance, the solves (cooperative
+sweeps over up to 256 columns at once), the H-matvecs and the dot products
+all run on the device; this module passes the factors and reads back the
+means and the per-location errors.
 
 For test locations s_1..s_M, a true model theta_t and an approximated
 (estimated) model theta_a, with c_x(j) = C_x(train, s_j), C_x the covariance
@@ -14,8 +15,18 @@ of the training points and v_x = sigma2_x + tau2_x the variance of Z(s_j):
   MLOE = mean_j (E_t[(Z_a - Z)^2] / E_t[(Z_t - Z)^2] - 1)   (Eq. 5)
   MMOM = mean_j (E_a[(Z_a - Z)^2] / E_t[(Z_a - Z)^2] - 1)   (Eq. 6)
   RMSE = sqrt(mean((Z_hat - Z)^2))                           (Eq. 7)
+
+    python -m paper_2104_07146_gb300.prediction [--n 65536] [--m 1000]
+
+times MLOE / MMOM at m test locations on the medium workload's point set
+(true model: the workload's theta; approximated: ell and nu 10% off) and
+prints one JSON line.
 """
 from __future__ import annotations
+
+import argparse
+import json
+import time
 
 import numpy as np
 
@@ -25,28 +36,45 @@ def rmse(pred, truth) -> float:
     return float(np.sqrt(np.mean(d * d)))
 
 
-def mloe_mmom(tree, locs2, theta_t, theta_a):
-    """(MLOE, MMOM) of Eq. 5-6 at the M x d test locations locs2: 2 solves,
-    2 cross-covariance products and one H-matvec per test location."""
-    locs2 = np.ascontiguousarray(locs2, dtype=np.float64)
-    M = locs2.shape[0]
+def mloe_mmom(tree, locs2, theta_t, theta_a, per_point=False):
+    """(MLOE, MMOM) of Eq. 5-6 at the M x d test locations locs2 (and the
+    M x 3 per-location errors with per_point=True)."""
     ht, ha = tree.assemble(theta_t), tree.assemble(theta_a)
     ft, fa = ht.factor(None), ha.factor(None)
-    vt = theta_t[2] + theta_t[3]
-    va = theta_a[2] + theta_a[3]
-    loe, mom = [], []
-    for j in range(M):
-        e = np.zeros(M)
-        e[j] = 1.0
-        ct = tree.cross_matvec(theta_t, locs2, e, trans=True)
-        ca = tree.cross_matvec(theta_a, locs2, e, trans=True)
-        lt = ft.solve(ct)
-        la = fa.solve(ca)
-        e_tt = vt - ct @ lt
-        e_aa = va - ca @ la
-        e_ta = vt - 2.0 * (la @ ct) + la @ ht.matvec(la)
-        loe.append(e_ta / e_tt - 1.0)
-        mom.append(e_aa / e_ta - 1.0)
-    for x in (ft, fa, ht, ha):
+    try:
+        loe, mom, per = ft.prediction_errors(fa, locs2)
+    finally:
+        for x in (ft, fa, ht, ha):
+            x.close()
+    return (loe, mom, per) if per_point else (loe, mom)
+
+
+def main():
+    from . import hmle, synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=65536)
+    ap.add_argument("--m", type=int, default=1000)
+    a = ap.parse_args()
+    w = synth.MEDIUM
+    locs = synth.locations_blobs(a.n, 2, w["frac_blob"], w["nblobs"], w["sd"], w["seed"])
+    locs2 = synth.uniform(w["seed"] + 17, 2 * a.m).reshape(a.m, 2)
+    th_t = tuple(w["theta"])
+    th_a = (th_t[0] * 1.1, th_t[1] * 0.9, th_t[2], th_t[3])
+    ctx = hmle.Context()
+    tree = hmle.Tree(ctx, locs, leaf_size=w["leaf"], eta=w["eta"], aca_eps=w["aca_eps"])
+    ht, ha = tree.assemble(th_t), tree.assemble(th_a)
+    ft, fa = ht.factor(None), ha.factor(None)
+    ft.prediction_errors(fa, locs2[:8])          # first use: tables, sweeps' grid size
+    t0 = time.time()
+    loe, mom, per = ft.prediction_errors(fa, locs2)
+    dt = time.time() - t0
+    print(json.dumps({"config": "medium point set n=%d, m=%d uniform test locations, theta_t=%s, "
+                                "theta_a=%s, leaf %d, eps %g" % (a.n, a.m, th_t, th_a, w["leaf"], w["aca_eps"]),
+                      "mloe": loe, "mmom": mom, "seconds": dt, "locations_per_s": a.m / dt,
+                      "min_kriging_variance": float(per[:, 0].min())}))
+    for x in (ft, fa, ht, ha, tree):
         x.close()
-    return float(np.mean(loe)), float(np.mean(mom))
+
+
+if __name__ == "__main__":
+    main()

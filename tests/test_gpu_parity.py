@@ -229,6 +229,33 @@ def test_mloe_mmom_match_dense(ctx):
     assert abs(lo0) <= 1e-6 and abs(mo0) <= 1e-6
 
 
+def test_prediction_errors_per_location_match_dense(ctx):
+    # Eq. 5-6 per test location, all on the device: 300 locations span two
+    # rounds of the multi-vector sweeps (256 + a ragged 44) and ten H-matvec
+    # launches (32 columns each, a ragged 12); every location's three mean
+    # square errors against the dense oracle
+    n, m = 2000, 300
+    allp = synth.locations_uniform(n + m, 2, seed=205)
+    locs1, locs2 = allp[:n], allp[n:]
+    tht, tha = (0.1, 0.5, 1.0, 0.01), (0.13, 0.8, 0.9, 0.02)
+    t = _tree(ctx, locs1, leaf_size=32, aca_eps=1e-10, max_rank=48, oversample=16)
+    ht, ha = t.assemble(tht), t.assemble(tha)
+    ft, fa = ht.factor(None), ha.factor(None)
+    lo, mo, per = ft.prediction_errors(fa, locs2)
+    ref = np.stack(oracle.prediction_errors(locs1, locs2, tht, tha), axis=1)
+    v = np.array([tht[2] + tht[3], tha[2] + tha[3], tht[2] + tht[3]])
+    err = np.abs(per - ref)
+    assert np.all(err <= 2e-6 * v + 1e-4 * np.abs(ref)), np.max(err / (2e-6 * v + 1e-4 * np.abs(ref)))
+    assert np.all(per > 0)
+    lo_r, mo_r = oracle.mloe_mmom(locs1, locs2, tht, tha)
+    assert abs(lo - lo_r) <= 1e-6 + 1e-4 * abs(lo_r), (lo, lo_r)
+    assert abs(mo - mo_r) <= 1e-6 + 1e-4 * abs(mo_r), (mo, mo_r)
+    # the means are those of the per-location errors
+    assert abs(lo - np.mean(per[:, 2] / per[:, 0] - 1.0)) <= 1e-12 * max(1.0, abs(lo))
+    for x in (ft, fa, ht, ha, t):
+        x.close()
+
+
 def test_fixed_rank_mode(ctx):
     # Sec. 2's rank-fixed approximation: every block of C~ and L~ at most k,
     # no rank overflow; at k = 16 on the small configuration L stays close to
