@@ -52,7 +52,7 @@ def test_rank_overflow_is_retried_at_the_largest_capacity(ctx, field):
     ref, st_ref = ctx.loglik_multi([(big, THETA, Z)])
     assert st_ref[0] == 0
     assert ll[0] == ref[0] and ll[1] == ref[0]
-    L = oracle.loglik_dense(locs, Z, THETA)
+    L = oracle.loglik_dense(locs, Z, THETA)[0]
     assert abs(ll[0] - L) / N <= 1e-6
     # no retries: the plain call
     ll_n, st_n, info_n = ctx.loglik_multi_retry([(small, THETA, Z)], max_retries=0)

@@ -346,6 +346,25 @@ def test_deferred_updates_reach_every_panel_row_once_before_its_solve(case):
             assert [tuple(x) for x in uents[r[2]:r[3]]] == [tuple(x) for x in L["uents_rhs"][q[2]:q[3]]]
 
 
+def test_forward_rhs_updates_use_their_own_steps_products(case):
+    # the multi-vector sweeps (hmle_prediction_errors) give each vector kcap
+    # doubles per right-hand-side product of a step instead of the factor's
+    # workspace: every low-rank entry of a step's right-hand-side rows must
+    # use one of that same step's products, and each product's offset is
+    # distinct within the step
+    L = case["L"]
+    hts, uents, urows = L["hts_rhs"], L["uents_rhs"], L["urows_rhs"]
+    N = 1 << case["depth"]
+    for K in range(N):
+        h0, h1 = L["ht_rhs0"][K][0], L["ht_rhs0"][K + 1][0]
+        offs = [int(hts[q][2]) for q in range(h0, h1)]
+        assert len(set(offs)) == len(offs)
+        for q in range(L["ur_rhs0"][K][0], L["ur_rhs0"][K + 1][0]):
+            for e in range(int(urows[q][2]), int(urows[q][3])):
+                h = int(uents[e][1])
+                assert h == -1 or h in offs
+
+
 def test_backward_sweep_lists(case):
     L = case["L"]
     B, owner, N = _blocks(case)
