@@ -18,7 +18,8 @@ The call is hmle_loglik_multi_retry: a task that fails (rank overflow, or
 a mixed-form PCG that does not converge) is evaluated again on a tree derived
 from its own, one rung of the retry ladder further each time.
 
-Prints one JSON line: the tree-build time, the one call's time and tasks/s,
+Prints a JSON line after the trees are built and one after the call, then
+the summary line: the tree-build time, the one call's time and tasks/s,
 the per-status counts after the retries and the rungs the retried tasks
 ended on, and the tasks of the first fields run again in one call and one
 call each (looped, after one warm-up evaluation per tree) for comparison,
@@ -83,6 +84,8 @@ def main():
         fields.append((tree, synth.normal(a.seed * 15485863 + i, n), n, d, field_theta(a.seed, i)))
     t_tree = time.time() - t0
     tasks = [(tree, th, Z) for (tree, Z, n, d, th0) in fields for th in trial_points(th0, a.trials)]
+    print(json.dumps({"phase": "trees", "fields": a.fields, "tasks": len(tasks), "tree_build_s": t_tree}),
+          flush=True)
     t0 = time.time()
     ll, st, retry = ctx.loglik_multi_retry(tasks, concurrency=a.concurrency, max_retries=a.retries)
     dt = time.time() - t0
@@ -95,6 +98,8 @@ def main():
             key = "max_rank %d, %s, eps %g" % (r["max_rank"], "FP64" if r["precision"] == 0 else
                                                "mixed %d" % r["precision"], r["aca_eps"])
             rungs[key] = rungs.get(key, 0) + 1
+    print(json.dumps({"phase": "call", "call_s": dt, "tasks_per_s": len(tasks) / dt, "status_counts": counts,
+                      "retry_rungs": rungs}), flush=True)
     # the first fields' tasks once more: in one call, then one call each
     sub = [k for k, t in enumerate(tasks) if any(t[0] is f[0] for f in fields[:a.looped_fields])]
     t0 = time.time()
