@@ -456,45 +456,66 @@ def batch_thetas(theta, B):
     return out
 
 
-def cpu_baseline(n_sub):
-    """The oracle as it stands (dense FP64) on a subset of the workload,
-    extrapolated to n = 65,536 by its n^3 cost."""
+def _oracle_seconds(n_sub):
+    """Seconds of one dense oracle evaluation (Eq. 1) on the first n_sub points
+    of the workload, and on the first n_sub / 2."""
     import oracle
     locs, Z = _workload_inputs(WORKLOAD["n"])
-    locs, Z = locs[:n_sub], Z[:n_sub]
     theta = tuple(WORKLOAD["theta"])
-    t0 = time.time()
-    oracle.loglik_dense(locs, Z, theta)
-    dt = time.time() - t0
-    scale = (WORKLOAD["n"] / n_sub) ** 3
-    return {"value": 1.0 / (dt * scale), "unit": "evals/s", "cores": os.cpu_count(),
+    out = []
+    for m in (n_sub // 2, n_sub):
+        t0 = time.time()
+        oracle.loglik_dense(locs[:m], Z[:m], theta)
+        out.append(time.time() - t0)
+    return out
+
+
+def extrapolate_seconds(t_half, t_full, n_sub, n):
+    """The dense oracle's time at n from its times at n_sub / 2 and n_sub:
+    t(m) = a m^2 + b m^3 (the matrix generation and the forward substitution
+    grow with m^2, the Cholesky with m^3) through the two points.  When the
+    two times do not fit that form (b <= 0 or a < 0, timing noise), the
+    n_sub time alone scaled by (n / n_sub)^3.  Returns (seconds, how)."""
+    b3 = (t_full - 4.0 * t_half) / 4.0      # b (n_sub / 2)^3
+    a2 = t_half - b3                        # a (n_sub / 2)^2
+    r = n / (n_sub / 2.0)
+    if b3 > 0.0 and a2 >= 0.0:
+        return a2 * r ** 2 + b3 * r ** 3, "a m^2 + b m^3 through both sizes"
+    return t_full * (n / n_sub) ** 3, "m^3 from the larger size"
+
+
+def cpu_baseline(n_sub):
+    """The oracle as it stands (dense FP64) on two subsets of the workload,
+    extrapolated to n = 65,536 (extrapolate_seconds)."""
+    t_half, t_full = _oracle_seconds(n_sub)
+    est, how = extrapolate_seconds(t_half, t_full, n_sub, WORKLOAD["n"])
+    return {"value": 1.0 / est, "unit": "evals/s", "cores": os.cpu_count(),
             "kind": "oracle",
-            "sample": "one dense evaluation on the first %d points of the workload (%.1f s), "
-                      "extrapolated to n=%d by n^3" % (n_sub, dt, WORKLOAD["n"])}
+            "sample": "one dense evaluation on the first %d and %d points of the workload (%.1f s, %.1f s), "
+                      "extrapolated to n=%d by %s (%.0f s)" % (n_sub // 2, n_sub, t_half, t_full,
+                                                              WORKLOAD["n"], how, est)}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import oracle
     n_sub = args.cpu_sample_n
-    locs, Z = _workload_inputs(WORKLOAD["n"])
-    locs, Z = locs[:n_sub], Z[:n_sub]
-    theta = tuple(WORKLOAD["theta"])
     for _ in range(args.warmup):
-        oracle.loglik_dense(locs, Z, theta)
-    t0 = time.time()
-    for _ in range(args.steps):
-        oracle.loglik_dense(locs, Z, theta)
-    dt = (time.time() - t0) / max(args.steps, 1)
-    scale = (WORKLOAD["n"] / n_sub) ** 3
-    v = 1.0 / (dt * scale)
-    sample = ("dense FP64 oracle on the first %d points per step (%.2f s), extrapolated to "
-              "n=%d by n^3" % (n_sub, dt, WORKLOAD["n"]))
+        _oracle_seconds(n_sub)
+    halves, fulls = [], []
+    for _ in range(max(args.steps, 1)):
+        th, tf = _oracle_seconds(n_sub)
+        halves.append(th)
+        fulls.append(tf)
+    t_half, t_full = sum(halves) / len(halves), sum(fulls) / len(fulls)
+    est, how = extrapolate_seconds(t_half, t_full, n_sub, WORKLOAD["n"])
+    v = 1.0 / est
+    sample = ("dense FP64 oracle on the first %d and %d points per step (%.2f s, %.2f s), extrapolated "
+              "to n=%d by %s" % (n_sub // 2, n_sub, t_half, t_full, WORKLOAD["n"], how))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": 0,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * scale * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": WORKLOAD,
         "cpu_baseline": {"value": v, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",

@@ -28,3 +28,18 @@ def test_batch_thetas_are_single_coordinate_neighbours():
 def test_job_rate_uses_the_slowest_rank():
     import bench
     assert bench.job_rate(4, 96, 2000.0) == 4 * 96 / 2.0
+
+
+def test_oracle_extrapolation_is_exact_for_its_model_and_falls_back_to_cubic():
+    import bench
+    a, b = 3e-8, 2e-12
+    t = lambda m: a * m ** 2 + b * m ** 3
+    est, how = bench.extrapolate_seconds(t(8192), t(16384), 16384, 65536)
+    assert abs(est - t(65536)) <= 1e-9 * t(65536) and "both sizes" in how
+    # pure cubic growth is the model with a = 0
+    est, _ = bench.extrapolate_seconds(1.0, 8.0, 16384, 65536)
+    assert abs(est - 512.0) < 1e-9
+    # times that no a m^2 + b m^3 with a, b >= 0 fits: the larger size, cubed
+    for t_half, t_full in ((1.0, 3.0), (1.0, 9.0)):
+        est, how = bench.extrapolate_seconds(t_half, t_full, 16384, 65536)
+        assert est == t_full * 64.0 and "larger size" in how
