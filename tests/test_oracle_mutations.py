@@ -86,3 +86,27 @@ def test_ldlt_mistakes_fail_nugget_and_cholesky_pins():
     good = oracle.loglik_from_matrix(C, Z)[0]
     assert abs(_ll_ldlt(C, Z) - good) < 1e-9 * abs(good)
     assert abs(_ll_ldlt(C, Z, sqrt_d=True) - good) > 1.0
+
+
+def test_prediction_error_mistakes_fail_the_joint_covariance_pin():
+    # Eq. 5-6: a flipped sign of the cross term, or the approximated model's
+    # covariance in the quadratic term, changes E_t[(Z_a - Z)^2] away from
+    # the variance w^T J_t w of the predictor's error
+    rng = np.random.default_rng(22)
+    locs1 = rng.uniform(size=(60, 2))
+    s = rng.uniform(size=(1, 2))
+    tht, tha = (0.15, 0.8, 1.0, 0.02), (0.25, 1.4, 1.5, 0.05)
+    n = len(locs1)
+    Jt = oracle.matern_matrix(np.vstack([locs1, s]), tht)
+    Ja = oracle.matern_matrix(np.vstack([locs1, s]), tha)
+    ct, ca = Jt[:n, n], Ja[:n, n]
+    la = np.linalg.solve(Ja[:n, :n], ca)
+    vt = tht[2] + tht[3]
+    w = np.append(la, -1.0)
+    ref = w @ Jt @ w
+    good = vt - 2.0 * la @ ct + la @ Jt[:n, :n] @ la
+    flipped = vt + 2.0 * la @ ct + la @ Jt[:n, :n] @ la
+    wrong_c = vt - 2.0 * la @ ct + la @ Ja[:n, :n] @ la
+    assert abs(good - ref) <= 1e-10 * vt
+    assert abs(flipped - ref) > 1e-3 * vt
+    assert abs(wrong_c - ref) > 1e-3 * vt

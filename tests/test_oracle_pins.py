@@ -327,6 +327,29 @@ def test_mloe_mmom_vanish_for_the_true_model_and_mloe_is_nonnegative():
         assert lo >= -1e-12
 
 
+def test_prediction_errors_per_location_from_the_joint_covariance():
+    # Per location, by another route than the oracle's solves: the kriging
+    # variance is the conditional variance of Z(s_j) given Z_1, the inverse
+    # of the last diagonal entry of the inverse joint covariance of
+    # (Z_1, Z(s_j)); the error of predictor a under the true model is the
+    # variance w^T J_t w of w = (l_a, -1), the coefficients of Z_a - Z; and
+    # no predictor beats the true model's under the true model
+    rng = np.random.default_rng(21)
+    locs1 = rng.uniform(size=(80, 2))
+    locs2 = rng.uniform(size=(9, 2))
+    tht, tha = (0.15, 0.8, 1.0, 0.02), (0.25, 1.4, 1.5, 0.05)
+    e_tt, e_aa, e_ta = oracle.prediction_errors(locs1, locs2, tht, tha)
+    n = len(locs1)
+    for j in range(len(locs2)):
+        pts = np.vstack([locs1, locs2[j:j + 1]])
+        Jt, Ja = oracle.matern_matrix(pts, tht), oracle.matern_matrix(pts, tha)
+        assert abs(e_tt[j] - 1.0 / np.linalg.inv(Jt)[n, n]) <= 1e-10 * Jt[n, n]
+        assert abs(e_aa[j] - 1.0 / np.linalg.inv(Ja)[n, n]) <= 1e-10 * Ja[n, n]
+        w = np.append(np.linalg.solve(Ja[:n, :n], Ja[:n, n]), -1.0)
+        assert abs(e_ta[j] - w @ Jt @ w) <= 1e-10 * Jt[n, n]
+        assert e_ta[j] >= e_tt[j] - 1e-12
+
+
 # --- LDL^T (Sec. 2: the factorisation without square roots) -------------------
 
 def test_ldlt_hand_examples():
