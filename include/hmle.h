@@ -493,11 +493,12 @@ hmle_status hmle_matern_eval(hmle_ctx *ctx, double nu, const double *x,
  *       memory, out[j*m + i] = M_{nus[j]}(x[i]).  Host pointers are
  *       INVALID_ARG: nothing is staged or copied.
  * The work is enqueued on the context's stream and the call returns without
- * waiting: synchronise that stream before reading out.  The first call on a
- * device looks up the static array's device address (cudaGetSymbolAddress),
- * so make that first call before any stream capture begins.  The address
- * is kept per device for the life of the process (a device reset inside the
- * process invalidates it).  The context's device must be the current device,
+ * waiting: synchronise that stream before reading out.  Every call made
+ * outside a stream capture looks up the static array's device address
+ * (cudaGetSymbolAddress), so a reset of the device inside the process is
+ * followed; a call made while the context's stream is being captured uses
+ * the address of the last call outside a capture, so make the first call on
+ * a device before any capture begins.  The context's device must be the current device,
  * else INVALID_ARG.  Every call shares the one array and overwrites it: calls
  * whose work overlaps on the GPU (other streams, other contexts) race, and
  * must be serialised.  Errors go to hmle_last_error like every entry point. */

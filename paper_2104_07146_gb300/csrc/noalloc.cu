@@ -7,9 +7,12 @@
 // The scratch that the allocating entry point (hmle_matern_eval) obtains
 // with cudaMallocAsync -- one Chebyshev table per value of nu -- lives here
 // in a file-scope static device array instead.  Host code must not use that
-// array's name as a device address: it is resolved once per device with
-// cudaGetSymbolAddress (the first call on a device does this set-up, so that
-// first call should be made before any stream capture begins).
+// array's name as a device address: it is resolved with cudaGetSymbolAddress
+// on every call made outside a stream capture (so a reset of the device's
+// context, which can move the array, is followed), and a call made while the
+// context's stream is being captured uses the address of the last call
+// outside a capture (so the first call on a device must come before any
+// capture begins).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -66,11 +69,18 @@ extern "C" hmle_status hmle_matern_eval_noalloc(hmle_ctx *ctx, const double *nus
   if ((ax.type != cudaMemoryTypeDevice && ax.type != cudaMemoryTypeManaged) ||
       (ao.type != cudaMemoryTypeDevice && ao.type != cudaMemoryTypeManaged))
     return hmle_internal_ctx_fail(ctx, HMLE_ERR_INVALID_ARG, "x and out must be device pointers");
+  cudaStream_t st = hmle_internal_ctx_stream(ctx);
+  bool capturing = true;   // unknown: keep the address already resolved
+  {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) == cudaSuccess) capturing = (cap != cudaStreamCaptureStatusNone);
+    else cudaGetLastError();
+  }
   double *scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
-      // set-up, once per device, with that device current
+    if (!g_scratch_ptr[dev] || !capturing) {
+      // with this device current; again on every call outside a capture
       double *p = nullptr;
       if (cudaGetSymbolAddress((void **)&p, g_matern_scratch) != cudaSuccess || !p) {
         cudaGetLastError();
@@ -80,7 +90,6 @@ extern "C" hmle_status hmle_matern_eval_noalloc(hmle_ctx *ctx, const double *nus
     }
     scratch = g_scratch_ptr[dev];
   }
-  cudaStream_t st = hmle_internal_ctx_stream(ctx);
   cudaGetLastError();   // report only the launches below, not an earlier caller's error
   // every word of each table is written by its table kernel before the
   // evaluation kernel reads it, so nothing left by a previous call is used
