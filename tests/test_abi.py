@@ -113,3 +113,34 @@ def test_mlp_parameter_count_matches_the_oracle():
     # 35-64-64-8 perceptron: weights and biases of three layers
     _, L = _lib()
     assert L.hmle_mlp_nparams() == oracle_ls.NPARAMS == 35 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 8 + 8
+
+
+def test_ctypes_structures_match_the_header_layout(tmp_path):
+    # the binding's ctypes mirrors of the header's structs: same size and the
+    # same offset for every field, as a C compiler lays them out from
+    # include/hmle.h (gcc on this host; the layout rules are the platform ABI's)
+    import ctypes as C
+    import subprocess
+    from paper_2104_07146_gb300 import hmle
+    pairs = {"hmle_opts": hmle.Opts, "hmle_fit_opts": hmle.FitOpts, "hmle_theta": hmle.Theta,
+             "hmle_tree_info": hmle.TreeInfo, "hmle_task": hmle.Task, "hmle_retry_info": hmle.RetryInfo,
+             "hmle_tune_result": hmle.TuneResult, "hmle_eval_info": hmle.EvalInfo}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "hmle.h"', "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f[0], cname, f[0]))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for cname, cls in pairs.items():
+        assert got[(cname, "size")] == C.sizeof(cls), cname
+        for f in cls._fields_:
+            assert got[(cname, f[0])] == getattr(cls, f[0]).offset, (cname, f[0])
