@@ -144,3 +144,45 @@ def test_ctypes_structures_match_the_header_layout(tmp_path):
         assert got[(cname, "size")] == C.sizeof(cls), cname
         for f in cls._fields_:
             assert got[(cname, f[0])] == getattr(cls, f[0]).offset, (cname, f[0])
+
+
+def _prototypes():
+    """name -> list of parameter declarations of every function the header
+    declares."""
+    src = open(os.path.join(ROOT, "include", "hmle.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    out = {}
+    for m in re.finditer(r"\b(hmle_[a-z_]+)\s*\(([^;{]*?)\)\s*;", src):
+        params = [p.strip() for p in m.group(2).split(",") if p.strip() and p.strip() != "void"]
+        out[m.group(1)] = params
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    # every ctypes signature the binding sets has the header's arity, and each
+    # argument's kind (pointer, 64- or 32-bit integer, double, float) matches
+    from paper_2104_07146_gb300 import hmle
+    L = hmle.lib()
+    protos = _prototypes()
+    checked = 0
+    for name, params in protos.items():
+        fn = getattr(L, name)
+        if fn.argtypes is None:
+            continue
+        assert len(fn.argtypes) == len(params), (name, params, fn.argtypes)
+        for decl, at in zip(params, fn.argtypes):
+            if "*" in decl or "[" in decl or "hmle_objective" in decl:
+                assert at not in (C.c_int32, C.c_int64, C.c_double, C.c_float, C.c_uint64), (name, decl)
+            elif re.search(r"\bu?int64_t\b", decl):
+                assert at in (C.c_int64, C.c_uint64), (name, decl)
+            elif re.search(r"\bu?int32_t\b", decl):
+                assert at in (C.c_int32, C.c_uint32), (name, decl)
+            elif re.search(r"\bdouble\b", decl):
+                assert at is C.c_double, (name, decl)
+            elif re.search(r"\bfloat\b", decl):
+                assert at is C.c_float, (name, decl)
+            else:
+                raise AssertionError("unclassified parameter %r of %s" % (decl, name))
+        checked += 1
+    assert checked >= 40
