@@ -179,7 +179,9 @@ typedef struct hmle_tree hmle_tree;
 typedef struct hmle_hmatrix hmle_hmatrix;
 typedef struct hmle_hfactor hmle_hfactor;
 
-/* Fill *opts with defaults: leaf 64, eta 2, aca_eps 1e-8, max_rank 32,
+/* The H-matrix options of Sec. 2's construction (the knobs of this
+ * implementation; the paper leaves them to its library).
+ * Fill *opts with defaults: leaf 64, eta 2, aca_eps 1e-8, max_rank 32,
  * oversample 8, FP64, seed 0x5eed, leaf_lowrank 0, pcg_tol 1e-10,
  * pcg_max_iter 50, fixed_rank 0, batch_size 2.  HMLE_OK for non-NULL opts, else
  * INVALID_ARG. */
@@ -189,7 +191,8 @@ hmle_status hmle_opts_default(hmle_opts *opts);
  * max_iter = 400, unit steps. */
 hmle_status hmle_fit_opts_default(hmle_fit_opts *opts);
 
-/* Create a context on the current CUDA device.  stream: a cudaStream_t to
+/* Plumbing, no counterpart in the paper.
+ * Create a context on the current CUDA device.  stream: a cudaStream_t to
  * launch on, or NULL for a stream owned by the context.  One context per
  * stream; a context must not be shared between host threads. */
 hmle_status hmle_ctx_create(hmle_ctx **ctx, void *stream);
@@ -210,10 +213,12 @@ const char *hmle_last_error(const hmle_ctx *ctx);
 hmle_status hmle_build_tree(hmle_ctx *ctx, const double *locs, int64_t n,
                             int32_t d, const hmle_opts *opts, hmle_tree **out);
 void hmle_tree_destroy(hmle_tree *tree);
-/* Sizes of the trees and the schedule (host struct).  Errors: INVALID_ARG. */
+/* a1-a2 (Sec. 2): sizes of the cluster and block trees and of the schedule
+ * (host struct).  Errors: INVALID_ARG. */
 hmle_status hmle_tree_get_info(const hmle_tree *tree, hmle_tree_info *info);
-/* perm[k] = caller index of the point at cluster position k (host array of
- * n int32).  Errors: INVALID_ARG, CUDA. */
+/* a1 (Sec. 2): the cluster order of the tree's points: perm[k] = caller
+ * index of the point at cluster position k (host array of n int32).
+ * Errors: INVALID_ARG, CUDA. */
 hmle_status hmle_tree_permutation(const hmle_tree *tree, int32_t *perm);
 
 /* a3-a4 (Eq. 2; Sec. 2, low-rank approximation on the fly): assemble
@@ -225,8 +230,10 @@ hmle_status hmle_assemble(hmle_ctx *ctx, const hmle_tree *tree,
                           const hmle_theta *theta, hmle_hmatrix **out);
 void hmle_hmatrix_destroy(hmle_hmatrix *h);
 
-/* y = C~ x for one vector (caller order, host or device, n doubles each);
- * a check of the assembled H-matrix. */
+/* Sec. 2 (the H-matrix approximation of Eq. 2's covariance): y = C~ x for
+ * one vector (caller order, host or device, n doubles each); a check of the
+ * assembled H-matrix, and the operator of the mixed forms' PCG (a14).
+ * Errors: INVALID_ARG, OOM, CUDA. */
 hmle_status hmle_hmatrix_matvec(hmle_ctx *ctx, const hmle_hmatrix *h,
                                 const double *x, double *y);
 
@@ -608,8 +615,9 @@ hmle_status hmle_selftest_tc_gemm(hmle_ctx *ctx, int32_t nslices, int32_t a_kfas
  * ranks the evaluation produced.  Selecting resets the counters.
  * Errors: INVALID_ARG for an unknown name. */
 hmle_status hmle_profile_select(hmle_ctx *ctx, const char *kernel);
-/* Totals since the last hmle_profile_select: summed launch durations (ms),
- * number of launches, algorithmic FP64 flops.  Any pointer may be NULL. */
+/* Measurement support (no counterpart in the paper): totals since the last
+ * hmle_profile_select: summed launch durations (ms), number of launches,
+ * algorithmic FP64 flops.  Any pointer may be NULL.  Errors: INVALID_ARG. */
 hmle_status hmle_profile_read(hmle_ctx *ctx, double *ms, int64_t *launches, double *flops);
 
 /* Measurement support (no counterpart in the paper): the algorithmic work of
